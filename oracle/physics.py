@@ -1,0 +1,243 @@
+"""Forward model, data term and gradient (FP64 oracle; test infrastructure only).
+
+Section 6 of the paper: the sample is probed by plane waves
+u_in^l(r) = exp(j <k_l, r>) and the data term of Eq. (1.1) is
+f_l(x) = 1/2 ||H_l(x) - y_l||^2.  Evaluating H_l once needs one
+Lippmann-Schwinger (LS) solve and the gradient of f_l needs two; both are
+solved with BiCGSTAB.  The discretisation is not printed in the paper (it is in
+a supplement that is not available), so the following reading is fixed here
+and in the CUDA library alike:
+
+* voxel h, background wavenumber k_b; coordinates r = (idx - n/2) h;
+* contrast x real, one value per voxel (x = (eta/eta_b)^2 - 1);
+* (G v)_i = k_b^2 sum_j w_{i-j} v_j over offsets in (-n, n)^3 with
+  w_D = h^3 exp(j k_b |D| h) / (4 pi |D| h) for D != 0 and the self term
+  w_0 = [exp(j k_b a)(1 - j k_b a) - 1] / k_b^2, a = (3/(4 pi))^(1/3) h, the
+  exact integral of the Green's function over the sphere of volume h^3;
+* LS: u = u_in + G (x * u); Born: u_sc = G (x * u_in);
+* detector: the scattered field u - u_in on the last z-slice (M = n^2);
+* gradient: grad f = Re(conj(u) * z), z = (I - G^H X)^{-1} G^H S^T r.
+
+Arrays are indexed [z, y, x] (x fastest in memory).
+"""
+from __future__ import annotations
+
+import math
+from typing import Callable, Sequence, Tuple
+
+import numpy as np
+
+
+def kb_default(h: float = 1.0) -> float:
+    """Background wavenumber for a wavelength of four voxels."""
+    return 2.0 * math.pi / (4.0 * h)
+
+
+def self_term(kb: float, h: float = 1.0) -> complex:
+    """w_0: integral of exp(j kb r)/(4 pi r) over the sphere of volume h^3."""
+    a = (3.0 / (4.0 * math.pi)) ** (1.0 / 3.0) * h
+    return (np.exp(1j * kb * a) * (1.0 - 1j * kb * a) - 1.0) / kb ** 2
+
+
+def green_kernel(n: int, kb: float, h: float = 1.0) -> np.ndarray:
+    """k_b^2 w_D laid out on the periodic grid of edge P = 2n.
+
+    Index i along an axis carries the offset i (i < n) or i - P (i > n); the
+    index i = n (offset -n, never reached by two voxels of the domain) is 0.
+    """
+    P = 2 * n
+    idx = np.arange(P)
+    off = np.where(idx < n, idx, idx - P).astype(np.float64)
+    dz, dy, dx = np.meshgrid(off, off, off, indexing="ij")
+    r = h * np.sqrt(dx ** 2 + dy ** 2 + dz ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        w = h ** 3 * np.exp(1j * kb * r) / (4.0 * math.pi * r)
+    w[0, 0, 0] = self_term(kb, h)
+    unused = idx == n
+    w[unused, :, :] = 0.0
+    w[:, unused, :] = 0.0
+    w[:, :, unused] = 0.0
+    return kb ** 2 * w
+
+
+def green_hat(n: int, kb: float, h: float = 1.0) -> np.ndarray:
+    """K_hat = DFT_P of the periodic kernel (P^3 complex128)."""
+    return np.fft.fftn(green_kernel(n, kb, h))
+
+
+def green_apply(v: np.ndarray, khat: np.ndarray, adjoint: bool = False) -> np.ndarray:
+    """G v (or G^H v) by zero padding to P = 2n and circular convolution.
+
+    Because the periodic kernel holds every offset in (-n, n)^3 exactly once,
+    the circular convolution restricted to the domain equals the aperiodic sum.
+    G is complex symmetric, so G^H uses conj(K_hat).
+    """
+    n = v.shape[0]
+    P = 2 * n
+    pad = np.zeros((P, P, P), dtype=np.complex128)
+    pad[:n, :n, :n] = v
+    k = np.conj(khat) if adjoint else khat
+    out = np.fft.ifftn(k * np.fft.fftn(pad))
+    return out[:n, :n, :n]
+
+
+def incident_field(n: int, kdir: Sequence[float], kb: float, h: float = 1.0) -> np.ndarray:
+    """u_in(r) = exp(j kb <kdir, r>), r = (idx - n/2) h, shape (n, n, n) [z, y, x]."""
+    c = (np.arange(n) - n / 2.0) * h
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    return np.exp(1j * kb * (kdir[0] * X + kdir[1] * Y + kdir[2] * Z))
+
+
+def bicgstab(apply_a: Callable[[np.ndarray], np.ndarray], b: np.ndarray,
+             x0: np.ndarray, tol: float, maxit: int) -> Tuple[np.ndarray, int, float]:
+    """Unpreconditioned BiCGSTAB of van der Vorst (1992), <a, b> = sum conj(a) b.
+
+    Stops when ||r|| <= tol ||b||.  Returns (solution, iterations, relres).
+    """
+    x = x0.astype(np.complex128).copy()
+    r = b - apply_a(x)
+    rhat = r.copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(x), 0, 0.0
+    rho_old = alpha = omega = 1.0 + 0.0j
+    v = np.zeros_like(x)
+    p = np.zeros_like(x)
+    it = 0
+    while it < maxit:
+        if np.linalg.norm(r) <= tol * bnorm:
+            break
+        rho = np.vdot(rhat, r)
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = apply_a(p)
+        alpha = rho / np.vdot(rhat, v)
+        s = r - alpha * v
+        it += 1
+        if np.linalg.norm(s) <= tol * bnorm:
+            x = x + alpha * p
+            r = s
+            break
+        t = apply_a(s)
+        omega = np.vdot(t, s) / np.vdot(t, t)
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho_old = rho
+    return x, it, float(np.linalg.norm(r) / bnorm)
+
+
+class Model:
+    """One configuration of the forward model (grid, wavenumber, directions)."""
+
+    def __init__(self, n: int, kdirs: np.ndarray, model: str = "ls",
+                 kb: float | None = None, h: float = 1.0,
+                 tol: float = 1e-12, maxit: int = 2000):
+        self.n = n
+        self.h = h
+        self.kb = kb_default(h) if kb is None else kb
+        self.kdirs = np.asarray(kdirs, dtype=np.float64)
+        self.model = model
+        self.tol = tol
+        self.maxit = maxit
+        self.khat = green_hat(n, self.kb, h)
+
+    # -- operators ---------------------------------------------------------
+    def G(self, v: np.ndarray) -> np.ndarray:
+        return green_apply(v, self.khat)
+
+    def GH(self, v: np.ndarray) -> np.ndarray:
+        return green_apply(v, self.khat, adjoint=True)
+
+    def u_in(self, l: int) -> np.ndarray:
+        return incident_field(self.n, self.kdirs[l], self.kb, self.h)
+
+    def total_field(self, x: np.ndarray, l: int) -> Tuple[np.ndarray, int]:
+        """u solving u = u_in + G(x u) (LS) or u = u_in (Born)."""
+        uin = self.u_in(l)
+        if self.model == "born":
+            return uin, 0
+        u, it, _ = bicgstab(lambda p: p - self.G(x * p), uin, uin, self.tol, self.maxit)
+        return u, it
+
+    def detect(self, usc: np.ndarray) -> np.ndarray:
+        """S: last z-slice of the scattered field, flattened [y, x] (M = n^2)."""
+        return usc[-1].reshape(-1).copy()
+
+    def lift(self, r: np.ndarray) -> np.ndarray:
+        """S^T: embed a detector vector into the last z-slice of a zero volume."""
+        out = np.zeros((self.n,) * 3, dtype=np.complex128)
+        out[-1] = r.reshape(self.n, self.n)
+        return out
+
+    def forward(self, x: np.ndarray, l: int) -> np.ndarray:
+        """H_l(x): detector samples of the scattered field."""
+        uin = self.u_in(l)
+        if self.model == "born":
+            return self.detect(self.G(x * uin))
+        u, _ = self.total_field(x, l)
+        return self.detect(u - uin)
+
+    def loss_grad(self, x: np.ndarray, l: int, y: np.ndarray) -> Tuple[float, np.ndarray, Tuple[int, int]]:
+        """(f_l(x), grad f_l(x), (forward its, adjoint its))."""
+        uin = self.u_in(l)
+        if self.model == "born":
+            r = self.detect(self.G(x * uin)) - y
+            z = self.GH(self.lift(r))
+            return 0.5 * float(np.vdot(r, r).real), np.real(np.conj(uin) * z), (0, 0)
+        u, it_f = self.total_field(x, l)
+        r = self.detect(u - uin) - y
+        b = self.GH(self.lift(r))
+        z, it_a, _ = bicgstab(lambda q: q - self.GH(x * q), b, b, self.tol, self.maxit)
+        return 0.5 * float(np.vdot(r, r).real), np.real(np.conj(u) * z), (it_f, it_a)
+
+    def batch_loss_grad(self, x: np.ndarray, illum: Sequence[int], ys: np.ndarray,
+                        scale: float) -> Tuple[float, np.ndarray]:
+        """scale * sum_l f_l and scale * sum_l grad f_l; scale = S/L gives F_s (Eq. 4.1)."""
+        loss = 0.0
+        g = np.zeros_like(x, dtype=np.float64)
+        for l in illum:
+            f, gl, _ = self.loss_grad(x, int(l), ys[int(l)])
+            loss += f
+            g += gl
+        return scale * loss, scale * g
+
+    def born_normal(self, dx: np.ndarray, illum: Sequence[int], scale: float) -> np.ndarray:
+        """scale * sum_l Re(J_l^H J_l dx) for the Born Jacobian J_l at x = 0."""
+        out = np.zeros_like(dx, dtype=np.float64)
+        for l in illum:
+            uin = self.u_in(int(l))
+            y = self.detect(self.G(dx * uin))
+            out += np.real(np.conj(uin) * self.GH(self.lift(y)))
+        return scale * out
+
+    def lipschitz(self, illum: Sequence[int], scale: float, start: np.ndarray,
+                  iters: int = 20) -> float:
+        """alpha_s: power iteration on the Born Gauss-Newton operator of F_s.
+
+        The paper leaves alpha_s as 'the Lipschitz constant of F_s' (Algorithm 4.1
+        input); our reading estimates it by ``iters`` power steps from ``start``
+        and returns the final Rayleigh quotient.
+        """
+        q = start / np.linalg.norm(start)
+        lam = 0.0
+        for _ in range(iters):
+            a = self.born_normal(q, illum, scale)
+            lam = float(np.vdot(q, a).real)
+            q = a / np.linalg.norm(a)
+        return lam
+
+
+def simulate(model: Model, x_true: np.ndarray, noise: np.ndarray, snr_db: float) -> np.ndarray:
+    """Measurements y_l = H_l(x_true) + sigma_l * noise_l with per-view SNR.
+
+    sigma_l = ||H_l(x_true)|| / sqrt(M) * 10^(-snr/20) (our reading of the
+    paper's noisy complex measurements).
+    """
+    L = model.kdirs.shape[0]
+    M = model.n * model.n
+    ys = np.zeros((L, M), dtype=np.complex128)
+    for l in range(L):
+        clean = model.forward(x_true, l)
+        sigma = np.linalg.norm(clean) / math.sqrt(M) * 10.0 ** (-snr_db / 20.0)
+        ys[l] = clean + sigma * noise[l]
+    return ys

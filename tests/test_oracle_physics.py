@@ -1,0 +1,189 @@
+"""Pins of the oracle's forward model against definitions it does not use itself.
+
+Each test checks the FFT/BiCGSTAB oracle against an independent statement:
+the O(N^2) direct Green's sum, numerical quadrature of the self term, a dense
+LU solve of the discretised Lippmann-Schwinger system, the first-Born limit,
+the adjoint identity and central finite differences of the data term.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import physics as ph
+
+KB = math.pi / 2.0
+
+
+def direct_green_matrix(n, kb, h=1.0):
+    """Dense (N x N) matrix of G from the pairwise definition (no FFT)."""
+    idx = np.array([(z, y, x) for z in range(n) for y in range(n) for x in range(n)], dtype=float)
+    d = idx[:, None, :] - idx[None, :, :]
+    r = h * np.sqrt(np.sum(d * d, axis=-1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        w = h ** 3 * np.exp(1j * kb * r) / (4 * math.pi * r)
+    a = (3 / (4 * math.pi)) ** (1 / 3) * h
+    # self term by quadrature of r exp(j kb r) over [0, a] (independent of the closed form)
+    re = integrate.quad(lambda t: t * math.cos(kb * t), 0, a, epsabs=1e-14)[0]
+    im = integrate.quad(lambda t: t * math.sin(kb * t), 0, a, epsabs=1e-14)[0]
+    np.fill_diagonal(w, re + 1j * im)
+    return kb ** 2 * w
+
+
+def rand_c(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def test_self_term_matches_quadrature():
+    for kb in (0.3, KB, 2.0):
+        a = (3 / (4 * math.pi)) ** (1 / 3)
+        re = integrate.quad(lambda t: t * math.cos(kb * t), 0, a, epsabs=1e-15)[0]
+        im = integrate.quad(lambda t: t * math.sin(kb * t), 0, a, epsabs=1e-15)[0]
+        assert abs(ph.self_term(kb) - (re + 1j * im)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_green_fft_equals_direct_sum(n):
+    rng = np.random.default_rng(n)
+    v = rand_c(rng, (n, n, n))
+    Gd = direct_green_matrix(n, KB)
+    ref = (Gd @ v.reshape(-1)).reshape(n, n, n)
+    out = ph.green_apply(v, ph.green_hat(n, KB))
+    assert np.max(np.abs(out - ref)) / np.max(np.abs(ref)) < 1e-12
+    refH = (Gd.conj().T @ v.reshape(-1)).reshape(n, n, n)
+    outH = ph.green_apply(v, ph.green_hat(n, KB), adjoint=True)
+    assert np.max(np.abs(outH - refH)) / np.max(np.abs(refH)) < 1e-12
+
+
+def test_green_is_complex_symmetric_and_khat_even():
+    n = 6
+    rng = np.random.default_rng(1)
+    a, b = rand_c(rng, (n,) * 3), rand_c(rng, (n,) * 3)
+    kh = ph.green_hat(n, KB)
+    # <G a, b> = <a, G^H b>
+    lhs = np.vdot(ph.green_apply(a, kh), b)
+    rhs = np.vdot(a, ph.green_apply(b, kh, adjoint=True))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-12
+    # G^T = G: sum (G a) b = sum a (G b)
+    assert abs(np.sum(ph.green_apply(a, kh) * b) - np.sum(a * ph.green_apply(b, kh))) < 1e-10 * abs(lhs)
+    P = 2 * n
+    k = np.arange(P)
+    for ax in range(3):
+        flipped = np.take(kh, (-k) % P, axis=ax)
+        assert np.max(np.abs(flipped - kh)) < 1e-10 * np.max(np.abs(kh))
+    assert np.max(np.abs(kh - np.transpose(kh, (1, 0, 2)))) < 1e-10 * np.max(np.abs(kh))
+
+
+def test_incident_field_is_plane_wave():
+    n = 8
+    k = np.array([0.3, -0.4, math.sqrt(1 - 0.25)])
+    u = ph.incident_field(n, k, KB)
+    assert np.allclose(np.abs(u), 1.0)
+    # phase advance of one voxel along x is kb*kx
+    assert np.allclose(u[:, :, 1:] / u[:, :, :-1], np.exp(1j * KB * k[0]))
+    assert np.allclose(u[1:] / u[:-1], np.exp(1j * KB * k[2]))
+    # centred coordinates: phase zero at idx = n/2
+    assert abs(u[n // 2, n // 2, n // 2] - 1.0) < 1e-15
+
+
+def small_problem(n=5, L=3, contrast=0.3, model="ls", seed=0):
+    rng = np.random.default_rng(seed)
+    x = contrast * rng.uniform(0, 1, (n, n, n))
+    t = math.radians(30)
+    kd = np.array([[math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)]
+                   for p in 2 * math.pi * np.arange(L) / L])
+    return x, ph.Model(n, kd, model=model)
+
+
+def test_ls_bicgstab_equals_dense_lu():
+    n = 5
+    x, m = small_problem(n, contrast=0.5)
+    Gd = direct_green_matrix(n, KB)
+    A = np.eye(n ** 3) - Gd * x.reshape(-1)[None, :]
+    for l in range(3):
+        uin = m.u_in(l)
+        ref = np.linalg.solve(A, uin.reshape(-1)).reshape(n, n, n)
+        u, it = m.total_field(x, l)
+        assert it > 1
+        assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) < 1e-10
+
+
+def test_born_limit_first_order():
+    n = 6
+    x, m = small_problem(n, contrast=1.0)
+    mb = ph.Model(n, m.kdirs, model="born")
+    errs = []
+    eps = [1e-1, 1e-2, 1e-3]
+    for e in eps:
+        hls = m.forward(e * x, 0)
+        hb = mb.forward(e * x, 0)
+        errs.append(np.linalg.norm(hls - hb) / np.linalg.norm(hb))
+    slopes = np.diff(np.log10(errs)) / np.diff(np.log10(eps))
+    assert np.all(np.abs(slopes - 1.0) < 0.1), slopes
+
+
+def _jvp(m, x, l, dx, h=1e-6):
+    return (m.forward(x + h * dx, l) - m.forward(x - h * dx, l)) / (2 * h)
+
+
+@pytest.mark.parametrize("model", ["ls", "born"])
+def test_gradient_central_differences(model):
+    n = 5
+    x, m = small_problem(n, contrast=0.4, model=model)
+    rng = np.random.default_rng(7)
+    y = rand_c(rng, n * n) * 0.05
+    f0, g, _ = m.loss_grad(x, 1, y)
+    for trial in range(4):
+        if trial < 2:
+            dx = np.zeros_like(x)
+            dx[tuple(rng.integers(0, n, 3))] = 1.0      # single-voxel direction
+        else:
+            dx = rng.standard_normal(x.shape)
+        h = 1e-5
+        fp, _, _ = m.loss_grad(x + h * dx, 1, y)
+        fm, _, _ = m.loss_grad(x - h * dx, 1, y)
+        fd = (fp - fm) / (2 * h)
+        an = float(np.sum(g * dx))
+        assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-12) + 1e-12, (fd, an)
+
+
+def test_adjoint_identity():
+    n = 5
+    x, m = small_problem(n, contrast=0.4)
+    rng = np.random.default_rng(3)
+    r = rand_c(rng, n * n)
+    dx = rng.standard_normal(x.shape)
+    # J dx by central differences of H (second order, exact up to O(h^2))
+    jdx = _jvp(m, x, 0, dx, 1e-5)
+    # J^H r from the gradient at y = H(x) - r: grad f = Re(J^H (H - y)) = Re(J^H r)
+    y = m.forward(x, 0) - r
+    _, g, _ = m.loss_grad(x, 0, y)
+    lhs = float(np.real(np.vdot(r, jdx)))
+    rhs = float(np.sum(dx * g))
+    assert abs(lhs - rhs) <= 1e-7 * abs(lhs)
+
+
+def test_lipschitz_power_iteration_matches_eigenvalue():
+    n = 4
+    _, m = small_problem(n, L=2, model="born")
+    N = n ** 3
+    A = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        A[:, j] = m.born_normal(e.reshape(n, n, n), [0, 1], 0.5).reshape(-1)
+    assert np.allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    lam_max = np.linalg.eigvalsh(A)[-1]
+    rng = np.random.default_rng(0)
+    est = m.lipschitz([0, 1], 0.5, rng.standard_normal((n, n, n)), iters=200)
+    assert abs(est - lam_max) <= 1e-6 * lam_max
+
+
+def test_detector_and_lift_are_adjoint():
+    n = 6
+    _, m = small_problem(n)
+    rng = np.random.default_rng(2)
+    v = rand_c(rng, (n, n, n))
+    r = rand_c(rng, n * n)
+    assert abs(np.vdot(r, m.detect(v)) - np.vdot(m.lift(r), v)) < 1e-12
