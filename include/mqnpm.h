@@ -1,0 +1,193 @@
+/*
+ * mqnpm.h -- C ABI of libmqnpm, the GB300 (sm_103a) hot path of the mini-batch
+ * quasi-Newton proximal method (BQNPM, Algorithm 4.1 of "A Mini-Batch
+ * Quasi-Newton Proximal Method for Constrained Total Variation Nonlinear Image
+ * Reconstruction") for optical diffraction tomography.
+ *
+ * Problem (Eqs. 1.1-1.2, 4.1):
+ *     min_{x in C}  (1/L) sum_l f_l(x) + lambda TV(x),
+ *     f_l(x) = 1/2 || H_l(x) - y_l ||^2,   C = [box_lo, box_hi]^N,
+ *     F_s = (S/L) sum_{l in S_s} f_l  over S non-overlapping subsets.
+ *
+ * Conventions shared by every call
+ *   - A volume is n*n*n voxels, indexed [z][y][x] with x fastest; N = n^3.
+ *     Detector vectors hold the last z-slice, [y][x], M = n^2 values.
+ *   - Real vectors are float32; complex vectors are interleaved (re, im)
+ *     float32 pairs (the memory layout of torch.complex64).
+ *   - Every pointer argument documented as "device" is a CUDA device pointer on
+ *     the handle's device; "host" pointers are ordinary CPU memory.  The caller
+ *     owns all buffers it passes; the library only reads or writes them during
+ *     the call and keeps no reference.  The library owns its workspace, which is
+ *     allocated in mqnpm_create and released by mqnpm_destroy.
+ *   - All device work is ordered on the handle's stream (mqnpm_set_stream).
+ *     Calls that return host values synchronise that stream before returning.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Every call returns an mqnpm_status; on failure mqnpm_last_error() gives
+ *     a readable message.  MQNPM_ERR_NOT_CONVERGED still writes every output.
+ */
+#ifndef MQNPM_H
+#define MQNPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mqnpm_status {
+  MQNPM_OK = 0,
+  MQNPM_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range       */
+  MQNPM_ERR_BUDGET = 2,        /* the workspace would exceed hbm_budget_bytes       */
+  MQNPM_ERR_CUDA = 3,          /* a CUDA runtime call failed                        */
+  MQNPM_ERR_NOT_CONVERGED = 4, /* a Krylov or Newton solve hit its iteration cap    */
+  MQNPM_ERR_NONFINITE = 5,     /* NaN/Inf met in a solve                            */
+  MQNPM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                */
+  MQNPM_ERR_UNSUPPORTED = 7,   /* grid size without a compiled transform plan       */
+  MQNPM_ERR_STATE = 8          /* call order violated (e.g. no measurements set)    */
+} mqnpm_status;
+
+enum { MQNPM_MODEL_BORN = 0, MQNPM_MODEL_LS = 1 };
+enum { MQNPM_TV_ISO = 0, MQNPM_TV_ANISO = 1 };
+
+/* Largest number of subsets S (rank of the quasi-Newton metric) supported. */
+#define MQNPM_MAX_S 8
+
+typedef struct mqnpm_config {
+  /* --- forward model (Section 6; discretisation is the library's stated reading) */
+  int n;                   /* grid edge; transform length P = 2n must be one of
+                              16,24,32,48,64,96,128,192,256,320,384                 */
+  double h;                /* voxel size (length unit)                              */
+  double kb;               /* background wavenumber 2*pi/lambda_b (per unit length) */
+  int model;               /* MQNPM_MODEL_LS (Lippmann-Schwinger) or _BORN          */
+  int L;                   /* number of illuminations                               */
+  const double* kdir;      /* host, L x 3 unit wave-vector directions (kx, ky, kz)  */
+  /* --- subsets and outer loop (Algorithm 4.1) */
+  int S;                   /* number of subsets, 1 <= S <= MQNPM_MAX_S              */
+  const int* subset_of;    /* host, L entries in [0, S): subset of illumination l   */
+  const double* alpha;     /* host, S entries alpha_s > 0 (Lipschitz constants)     */
+  double step;             /* a_k (constant)                                        */
+  int strategy;            /* 1: s' = mod(k, S) cyclic; 2: s' from strategy_draws   */
+  const int* strategy_draws; /* host, n_draws subset indices for strategy II        */
+  int n_draws;
+  /* --- regulariser and constraint (Eqs. 1.2, 3.1-3.4) */
+  int tv;                  /* MQNPM_TV_ISO or MQNPM_TV_ANISO                        */
+  double lambda;
+  double box_lo, box_hi;   /* C = [box_lo, box_hi]^N                                */
+  /* --- SR1 (Algorithm 4.2) */
+  double gamma;            /* in (0, 1]                                             */
+  double tau_max;          /* <= 0 selects 1e3 * max_s alpha_s                      */
+  double delta1, delta2;   /* <= 0 selects 1e-8 and 1e-12                           */
+  /* --- inner solvers */
+  double krylov_tol;       /* BiCGSTAB relative residual                            */
+  int krylov_maxit;
+  int dual_iters;          /* accelerated dual projected-gradient iterations J      */
+  double newton_tol;       /* semi-smooth Newton tolerance (Algorithm 4.3)          */
+  int newton_maxit;
+  /* --- resources */
+  int max_batch;           /* illuminations solved together (workspace sizing)      */
+  size_t hbm_budget_bytes; /* 0: no limit; else create fails with MQNPM_ERR_BUDGET  */
+  int device;              /* CUDA device ordinal                                   */
+  void* stream;            /* cudaStream_t for all work (NULL: legacy default)      */
+} mqnpm_config;
+
+typedef struct mqnpm_handle mqnpm_handle;
+
+typedef struct mqnpm_step_info {
+  int k;                   /* iteration index after the call (1-based)             */
+  int subset;              /* s or s' used by the iteration (0-based)              */
+  double loss;             /* F_s(x_{k-1}) of the chosen subset                     */
+  double tau_star;         /* sum_s tau_s of the metric used                        */
+  int rank;                /* number of rank-one terms in the metric               */
+  int sr1_branch;          /* 0: rank-1 update, 1: tau<=0, 2: skip, 3: tau tiny, -1: k<=S */
+  int krylov_iters_max;    /* largest BiCGSTAB iteration count in the gradient     */
+  int newton_iters_max;    /* largest semi-smooth Newton count in the prox         */
+} mqnpm_step_info;
+
+/* Create a handle: validates cfg, builds the Green's kernel spectrum and the
+ * incident-field tables, and allocates the workspace for max_batch
+ * illuminations.  Host arrays in cfg are copied.  Errors: INVALID_ARG,
+ * UNSUPPORTED (n), BUDGET, CUDA.  On error *out is NULL. */
+int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out);
+
+/* Release the workspace.  NULL is accepted. */
+void mqnpm_destroy(mqnpm_handle* h);
+
+/* Message of the last failure on this handle (never NULL). */
+const char* mqnpm_last_error(const mqnpm_handle* h);
+
+/* Replace the stream all later work is ordered on. */
+int mqnpm_set_stream(mqnpm_handle* h, void* stream);
+
+/* Bytes of device memory the handle holds. */
+size_t mqnpm_workspace_bytes(const mqnpm_handle* h);
+
+/* Copy the measurements y_l (Eq. 1.1): device, L x M complex. */
+int mqnpm_set_measurements(mqnpm_handle* h, const float* y);
+
+/* G v or G^H v for nb volumes (the discrete Lippmann-Schwinger operator's
+ * Green's convolution; adjoint != 0 selects G^H).  v, out: device, nb x N
+ * complex; they must not overlap.  nb <= max_batch. */
+int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int adjoint);
+
+/* H_l(x) for the illuminations illum[0..nb) (Section 6: one LS solve per
+ * illumination, or the first-Born field).  x: device N; illum: host nb ints;
+ * y_out: device nb x M complex; iters_out: host nb ints or NULL.
+ * NOT_CONVERGED if a solve hit krylov_maxit (outputs still written). */
+int mqnpm_forward(mqnpm_handle* h, const float* x, const int* illum, int nb,
+                  float* y_out, int* iters_out);
+
+/* Mini-batch data-term gradient (Section 6, Eq. 4.1):
+ *   grad_out = scale * sum_{l in illum} grad f_l(x),  *loss_out = scale * sum f_l(x),
+ * with grad f_l = Re(conj(u_l) .* z_l), u_l the LS field (or u_in for Born) and
+ * z_l = (I - G^H X)^{-1} G^H S^T (H_l(x) - y_l) (the adjoint solve).  scale = S/L
+ * gives grad F_s.  x, grad_out: device N floats (may alias only if identical
+ * buffers are not required afterwards: grad_out is written last).  illum: host.
+ * Batches larger than max_batch are processed in chunks.  loss_out (host) and
+ * krylov_iters_out (host, 2*nb ints: forward, adjoint) may be NULL.
+ * Requires mqnpm_set_measurements.  NOT_CONVERGED as above. */
+int mqnpm_grad_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
+                     float* grad_out, double* loss_out, int* krylov_iters_out);
+
+/* Weighted proximal mapping of c*TV + iota_C under B = tau_star I + U U^T
+ * (Eq. 4.4, Theorem 3.1, Lemma 4.1, Algorithm 4.3):
+ *   x_out ~= argmin_{x in C} 1/2 ||x - v||_B^2 + c TV(x)
+ * by cfg.dual_iters accelerated projected-gradient steps on the dual T(P).
+ * v, x_out: device N floats (distinct).  U: device S_eff x N floats (row s is
+ * u_s), NULL when S_eff = 0; 0 <= S_eff <= MQNPM_MAX_S.  tau_star > 0, c > 0.
+ * P_warm: device 3 x N floats (components q_x, q_y, q_z) used as the starting
+ * dual field and overwritten with the final one; NULL starts from zero. */
+int mqnpm_wprox(mqnpm_handle* h, const float* v, double tau_star, const float* U, int S_eff,
+                double c, float* P_warm, float* x_out);
+
+/* One iteration k of Algorithm 4.1 on x (device N floats, in/out), including
+ * the SR1 metric update (Algorithm 4.2) and the warm-started dual field.
+ * info (host) may be NULL. */
+int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info);
+
+/* alpha estimate for a subset: `iters` power steps on
+ * scale * sum_{l in illum} Re(J_l^H J_l) with J_l the Born Jacobian at x = 0,
+ * from the device start vector `start` (N floats); result in *alpha_out (host). */
+int mqnpm_lipschitz(mqnpm_handle* h, const int* illum, int nb, double scale, const float* start,
+                    int iters, double* alpha_out);
+
+/* Checkpoint of the outer-loop state (k, tau_s, rank flags, xbar_s, gbar_s,
+ * u_s, dual field).  With buf == NULL, *size receives the byte count; else buf
+ * (host, *size bytes) receives the state.  load restores it exactly. */
+int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size);
+int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size);
+
+/* Opt-in tracing (no counterpart in the paper; it instruments the Green's
+ * convolution of Section 6).  profile_begin records CUDA events around the five
+ * transform passes of the next max_calls Green's applies on the handle's
+ * stream; profile_end synchronises the stream, returns the summed device time
+ * of each pass in pass_ms (host, 5 doubles: x-forward, y-forward,
+ * z-forward*K_hat*z-inverse, y-inverse, x-inverse), the number of recorded
+ * applies in *calls and the sum of their batch sizes in *slot_launches, and
+ * stops recording. */
+int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);
+int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MQNPM_H */

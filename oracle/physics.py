@@ -187,7 +187,7 @@ class Model:
         u, it_f = self.total_field(x, l)
         r = self.detect(u - uin) - y
         b = self.GH(self.lift(r))
-        z, it_a, _ = bicgstab(lambda q: q - self.GH(x * q), b, b, self.tol, self.maxit)
+        z, it_a, _ = bicgstab(lambda q: q - self.GH(x * q), b, np.zeros_like(b), self.tol, self.maxit)
         return 0.5 * float(np.vdot(r, r).real), np.real(np.conj(u) * z), (it_f, it_a)
 
     def batch_loss_grad(self, x: np.ndarray, illum: Sequence[int], ys: np.ndarray,

@@ -1,0 +1,316 @@
+"""ctypes binding of libmqnpm (argument marshalling only).
+
+Every numerical step runs in the CUDA library; this module converts torch
+tensors to device pointers, passes the current torch stream and raises on any
+non-zero status.  There is no CPU or PyTorch fallback: if the library cannot be
+loaded, importing the handle class fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+STATUS = {
+    0: "OK", 1: "INVALID_ARG", 2: "BUDGET", 3: "CUDA", 4: "NOT_CONVERGED", 5: "NONFINITE",
+    6: "TIMEOUT", 7: "UNSUPPORTED", 8: "STATE",
+}
+MODEL = {"born": 0, "ls": 1}
+TV = {"iso": 0, "aniso": 1}
+MAX_S = 8
+SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 192)
+
+
+class MQNPMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class NotConverged(MQNPMError):
+    pass
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("h", ctypes.c_double), ("kb", ctypes.c_double), ("model", ctypes.c_int),
+        ("L", ctypes.c_int), ("kdir", ctypes.POINTER(ctypes.c_double)),
+        ("S", ctypes.c_int), ("subset_of", ctypes.POINTER(ctypes.c_int)),
+        ("alpha", ctypes.POINTER(ctypes.c_double)), ("step", ctypes.c_double), ("strategy", ctypes.c_int),
+        ("strategy_draws", ctypes.POINTER(ctypes.c_int)), ("n_draws", ctypes.c_int),
+        ("tv", ctypes.c_int), ("lam", ctypes.c_double), ("box_lo", ctypes.c_double), ("box_hi", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("tau_max", ctypes.c_double), ("delta1", ctypes.c_double),
+        ("delta2", ctypes.c_double), ("krylov_tol", ctypes.c_double), ("krylov_maxit", ctypes.c_int),
+        ("dual_iters", ctypes.c_int), ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("subset", ctypes.c_int), ("loss", ctypes.c_double),
+                ("tau_star", ctypes.c_double), ("rank", ctypes.c_int), ("sr1_branch", ctypes.c_int),
+                ("krylov_iters_max", ctypes.c_int), ("newton_iters_max", ctypes.c_int)]
+
+
+_LIB = None
+
+# Every entry point of include/mqnpm.h with its ctypes signature.
+SIGNATURES = {
+    "mqnpm_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "mqnpm_destroy": (None, [ctypes.c_void_p]),
+    "mqnpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "mqnpm_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mqnpm_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "mqnpm_set_measurements": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mqnpm_green_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "mqnpm_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_grad_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_wprox": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    "mqnpm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
+    "mqnpm_lipschitz": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "mqnpm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "mqnpm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "mqnpm_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mqnpm_profile_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libmqnpm.so (building it first if needed); raises if it cannot be loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError("libmqnpm.so is not built (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_cuda(t: torch.Tensor, dtype, numel: int, name: str, device: int):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not t.is_cuda or t.device.index != device:
+        raise ValueError("%s must live on cuda:%d" % (name, device))
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+
+
+class MQNPM:
+    """One reconstruction problem on one GPU (a handle of libmqnpm)."""
+
+    def __init__(self, n: int, kdir, subset_of, alpha, *, model: str = "ls", h: float = 1.0,
+                 kb: float = math.pi / 2, tv: str = "iso", lam: float = 1e-3, box=(0.0, 1.0),
+                 step: float = 1.0, strategy: int = 1, draws: Optional[Sequence[int]] = None,
+                 gamma: float = 0.8, tau_max: float = 0.0, krylov_tol: float = 1e-6, krylov_maxit: int = 500,
+                 dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
+                 hbm_budget_bytes: int = 0, device: int = 0):
+        self.lib = load()
+        self.n = int(n)
+        self.N = self.n ** 3
+        self.M = self.n ** 2
+        self.device = int(device)
+        kd = np.ascontiguousarray(np.asarray(kdir, dtype=np.float64).reshape(-1, 3))
+        so = np.ascontiguousarray(np.asarray(subset_of, dtype=np.int32))
+        al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+        dr = np.ascontiguousarray(np.asarray(draws if draws is not None else [], dtype=np.int32))
+        self.L = kd.shape[0]
+        self.S = al.shape[0]
+        self._keep = (kd, so, al, dr)
+        cfg = Config()
+        cfg.n = self.n
+        cfg.h = h
+        cfg.kb = kb
+        cfg.model = MODEL[model]
+        cfg.L = self.L
+        cfg.kdir = kd.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.S = self.S
+        cfg.subset_of = so.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        cfg.alpha = al.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.step = step
+        cfg.strategy = strategy
+        cfg.strategy_draws = dr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        cfg.n_draws = dr.shape[0]
+        cfg.tv = TV[tv]
+        cfg.lam = lam
+        cfg.box_lo, cfg.box_hi = float(box[0]), float(box[1])
+        cfg.gamma = gamma
+        cfg.tau_max = tau_max
+        cfg.delta1 = 1e-8
+        cfg.delta2 = 1e-12
+        cfg.krylov_tol = krylov_tol
+        cfg.krylov_maxit = krylov_maxit
+        cfg.dual_iters = dual_iters
+        cfg.newton_tol = newton_tol
+        cfg.newton_maxit = newton_maxit
+        cfg.max_batch = max_batch
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.device = self.device
+        with torch.cuda.device(self.device):
+            cfg.stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self.max_batch = max_batch
+        handle = ctypes.c_void_p()
+        rc = self.lib.mqnpm_create(ctypes.byref(cfg), ctypes.byref(handle))
+        if rc != OK:
+            raise MQNPMError(rc, "mqnpm_create failed")
+        self._h = handle
+
+    # -- plumbing ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.mqnpm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.mqnpm_set_stream(self._h, ctypes.c_void_p(s))
+
+    def _raise(self, rc: int, allow_not_converged: bool = False):
+        if rc == OK or (allow_not_converged and rc == 4):
+            return
+        msg = self.lib.mqnpm_last_error(self._h).decode()
+        if rc == 4:
+            raise NotConverged(rc, msg)
+        raise MQNPMError(rc, msg)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.lib.mqnpm_workspace_bytes(self._h))
+
+    # -- calls -------------------------------------------------------------
+    def set_measurements(self, y: torch.Tensor):
+        _check_cuda(y, torch.complex64, self.L * self.M, "y", self.device)
+        self._stream()
+        self._raise(self.lib.mqnpm_set_measurements(self._h, _ptr(y)))
+
+    def green_apply(self, v: torch.Tensor, adjoint: bool = False) -> torch.Tensor:
+        nb = v.numel() // self.N
+        _check_cuda(v, torch.complex64, nb * self.N, "v", self.device)
+        out = torch.empty_like(v)
+        self._stream()
+        self._raise(self.lib.mqnpm_green_apply(self._h, _ptr(v), _ptr(out), nb, int(adjoint)))
+        return out
+
+    def forward(self, x: torch.Tensor, illum: Sequence[int], allow_not_converged=False):
+        _check_cuda(x, torch.float32, self.N, "x", self.device)
+        il = (ctypes.c_int * len(illum))(*[int(i) for i in illum])
+        its = (ctypes.c_int * len(illum))()
+        y = torch.empty((len(illum), self.M), dtype=torch.complex64, device=x.device)
+        self._stream()
+        rc = self.lib.mqnpm_forward(self._h, _ptr(x), il, len(illum), _ptr(y), its)
+        self._raise(rc, allow_not_converged)
+        return y, list(its)
+
+    def grad_batch(self, x: torch.Tensor, illum: Sequence[int], scale: float, out: Optional[torch.Tensor] = None,
+                   allow_not_converged=False):
+        _check_cuda(x, torch.float32, self.N, "x", self.device)
+        if out is None:
+            out = torch.empty_like(x)
+        _check_cuda(out, torch.float32, self.N, "grad_out", self.device)
+        nb = len(illum)
+        il = (ctypes.c_int * nb)(*[int(i) for i in illum])
+        its = (ctypes.c_int * (2 * nb))()
+        loss = ctypes.c_double()
+        self._stream()
+        rc = self.lib.mqnpm_grad_batch(self._h, _ptr(x), il, nb, float(scale), _ptr(out), ctypes.byref(loss), its)
+        self._raise(rc, allow_not_converged)
+        return out, loss.value, [(its[2 * b], its[2 * b + 1]) for b in range(nb)]
+
+    def wprox(self, v: torch.Tensor, tau: float, U: Optional[torch.Tensor], c: float,
+              P_warm: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        _check_cuda(v, torch.float32, self.N, "v", self.device)
+        S_eff = 0
+        if U is not None and U.numel() > 0:
+            S_eff = U.numel() // self.N
+            _check_cuda(U, torch.float32, S_eff * self.N, "U", self.device)
+        else:
+            U = None
+        if P_warm is not None:
+            _check_cuda(P_warm, torch.float32, 3 * self.N, "P_warm", self.device)
+        if out is None:
+            out = torch.empty_like(v)
+        self._stream()
+        rc = self.lib.mqnpm_wprox(self._h, _ptr(v), float(tau), _ptr(U), S_eff, float(c), _ptr(P_warm), _ptr(out))
+        self._raise(rc)
+        return out
+
+    def step(self, x: torch.Tensor, allow_not_converged=False) -> dict:
+        _check_cuda(x, torch.float32, self.N, "x", self.device)
+        info = StepInfo()
+        self._stream()
+        rc = self.lib.mqnpm_step(self._h, _ptr(x), ctypes.byref(info))
+        self._raise(rc, allow_not_converged)
+        return {f: getattr(info, f) for f, _ in StepInfo._fields_}
+
+    def lipschitz(self, illum: Sequence[int], scale: float, start: torch.Tensor, iters: int = 20) -> float:
+        _check_cuda(start, torch.float32, self.N, "start", self.device)
+        il = (ctypes.c_int * len(illum))(*[int(i) for i in illum])
+        out = ctypes.c_double()
+        self._stream()
+        self._raise(self.lib.mqnpm_lipschitz(self._h, il, len(illum), float(scale), _ptr(start), int(iters),
+                                             ctypes.byref(out)))
+        return out.value
+
+    def save_state(self) -> bytes:
+        size = ctypes.c_size_t()
+        self._raise(self.lib.mqnpm_save_state(self._h, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        self._stream()
+        self._raise(self.lib.mqnpm_save_state(self._h, buf, ctypes.byref(size)))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._stream()
+        self._raise(self.lib.mqnpm_load_state(self._h, buf, len(blob)))
+
+    def profile_begin(self, max_calls: int = 4096):
+        self._raise(self.lib.mqnpm_profile_begin(self._h, int(max_calls)))
+
+    def profile_end(self) -> dict:
+        """Per-pass device time (ms) of the Green's applies since profile_begin."""
+        ms = (ctypes.c_double * 5)()
+        slots = ctypes.c_longlong()
+        calls = ctypes.c_int()
+        self._stream()
+        self._raise(self.lib.mqnpm_profile_end(self._h, ms, ctypes.byref(slots), ctypes.byref(calls)))
+        return {"pass_ms": list(ms), "slot_launches": slots.value, "calls": calls.value}

@@ -1,0 +1,574 @@
+// C ABI of libmqnpm: handle life cycle, data upload, and the outer loop of the
+// mini-batch quasi-Newton proximal method (Algorithm 4.1) with the SR1 metric
+// estimate (Algorithm 4.2).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "mqnpm.h"
+
+int set_error(mqnpm_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int set_cuda_error(mqnpm_handle* h, cudaError_t e, const char* where) {
+  if (h) h->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return MQNPM_ERR_CUDA;
+}
+
+namespace {
+
+#define CK(call)                                                \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return set_cuda_error(h, e_, #call); \
+  } while (0)
+
+template <class T>
+int dalloc(mqnpm_handle* h, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return set_cuda_error(h, e, "cudaMalloc");
+  h->allocations.push_back(q);
+  h->bytes += bytes;
+  *p = static_cast<T*>(q);
+  return MQNPM_OK;
+}
+
+struct Sizes {
+  size_t total = 0;
+};
+
+__global__ void k_axpby(const float* x, const float* g, float a, float* out, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = fmaf(a, g[i], x[i]);
+}
+
+// u = ((g - gbar) - tau (x - xbar)) * inv  (Algorithm 4.2, after the damping loop)
+__global__ void k_sr1_u(const float* x, const float* xbar, const float* g, const float* gbar, float tau, float inv,
+                        float* u, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    u[i] = ((g[i] - gbar[i]) - tau * (x[i] - xbar[i])) * inv;
+}
+
+bool finite_all(const double* a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+void profile_clear(mqnpm_handle* h) {
+  for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+  h->prof.ev.clear();
+  h->prof.nb.clear();
+  h->prof.used = 0;
+  h->prof.on = false;
+}
+
+}  // namespace
+
+cudaEvent_t* profile_slot(mqnpm_handle* h, int nb) {
+  Profiler& p = h->prof;
+  if (!p.on || (size_t)(p.used + 1) * 6 > p.ev.size()) return nullptr;
+  p.nb.push_back(nb);
+  return &p.ev[6 * (size_t)p.used++];
+}
+
+extern "C" {
+
+int mqnpm_profile_begin(mqnpm_handle* h, int max_calls) {
+  if (!h || max_calls < 1) return MQNPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  profile_clear(h);
+  h->prof.ev.resize(6 * (size_t)max_calls);
+  for (auto& e : h->prof.ev) CK(cudaEventCreate(&e));
+  h->prof.on = true;
+  return MQNPM_OK;
+}
+
+int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls) {
+  if (!h || !pass_ms) return MQNPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int p = 0; p < 5; ++p) pass_ms[p] = 0.0;
+  long long slots = 0;
+  for (int g = 0; g < h->prof.used; ++g) {
+    for (int p = 0; p < 5; ++p) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->prof.ev[6 * (size_t)g + p], h->prof.ev[6 * (size_t)g + p + 1]));
+      pass_ms[p] += ms;
+    }
+    slots += h->prof.nb[g];
+  }
+  if (slot_launches) *slot_launches = slots;
+  if (calls) *calls = h->prof.used;
+  profile_clear(h);
+  return MQNPM_OK;
+}
+
+const char* mqnpm_last_error(const mqnpm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+size_t mqnpm_workspace_bytes(const mqnpm_handle* h) { return h ? h->bytes : 0; }
+
+int mqnpm_set_stream(mqnpm_handle* h, void* stream) {
+  if (!h) return MQNPM_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return MQNPM_OK;
+}
+
+void mqnpm_destroy(mqnpm_handle* h) {
+  if (!h) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  profile_clear(h);
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->w.h_nactive) cudaFreeHost(h->w.h_nactive);
+  if (h->w.h_illum) cudaFreeHost(h->w.h_illum);
+  if (h->w.h_scal) cudaFreeHost(h->w.h_scal);
+  cudaSetDevice(dev);
+  delete h;
+}
+
+int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
+  if (!out) return MQNPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg) return MQNPM_ERR_INVALID_ARG;
+  mqnpm_handle* h = new mqnpm_handle();
+  auto fail = [&](int code) {
+    mqnpm_destroy(h);
+    return code;
+  };
+  // ---- validation
+  if (cfg->n < 4 || cfg->L < 1 || cfg->S < 1 || cfg->S > MQNPM_MAX_S || cfg->S > cfg->L || !cfg->kdir ||
+      !cfg->subset_of || !cfg->alpha || !(cfg->h > 0) || !(cfg->kb > 0) || cfg->max_batch < 1 ||
+      !(cfg->box_lo <= cfg->box_hi) || !(cfg->lambda >= 0) || !(cfg->step > 0) || cfg->dual_iters < 0 ||
+      !(cfg->krylov_tol > 0) || cfg->krylov_maxit < 1 || (cfg->model != MQNPM_MODEL_LS && cfg->model != MQNPM_MODEL_BORN) ||
+      (cfg->tv != MQNPM_TV_ISO && cfg->tv != MQNPM_TV_ANISO) || (cfg->strategy != 1 && cfg->strategy != 2) ||
+      !(cfg->gamma > 0 && cfg->gamma <= 1.0)) {
+    fprintf(stderr, "mqnpm_create: invalid configuration\n");
+    delete h;
+    return MQNPM_ERR_INVALID_ARG;
+  }
+  if (!green_supported(cfg->n)) {
+    delete h;
+    return MQNPM_ERR_UNSUPPORTED;
+  }
+  h->n = cfg->n;
+  h->P = 2 * cfg->n;
+  h->N = (size_t)cfg->n * cfg->n * cfg->n;
+  h->M = cfg->n * cfg->n;
+  h->model = cfg->model;
+  h->L = cfg->L;
+  h->S = cfg->S;
+  h->tv = cfg->tv;
+  h->strategy = cfg->strategy;
+  h->h = cfg->h;
+  h->kb = cfg->kb;
+  h->lambda = cfg->lambda;
+  h->lo = cfg->box_lo;
+  h->hi = cfg->box_hi;
+  h->a = cfg->step;
+  h->gamma = cfg->gamma;
+  h->delta1 = cfg->delta1 > 0 ? cfg->delta1 : 1e-8;
+  h->delta2 = cfg->delta2 > 0 ? cfg->delta2 : 1e-12;
+  h->krylov_tol = cfg->krylov_tol;
+  h->krylov_maxit = cfg->krylov_maxit;
+  h->dual_iters = cfg->dual_iters;
+  h->newton_tol = cfg->newton_tol > 0 ? cfg->newton_tol : 1e-6;
+  h->newton_maxit = cfg->newton_maxit > 0 ? cfg->newton_maxit : 50;
+  h->max_batch = cfg->max_batch;
+  h->device = cfg->device;
+  h->stream = static_cast<cudaStream_t>(cfg->stream);
+  h->budget = cfg->hbm_budget_bytes;
+  h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
+  h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);
+  h->subset_of.assign(cfg->subset_of, cfg->subset_of + cfg->L);
+  if (cfg->strategy_draws && cfg->n_draws > 0) h->draws.assign(cfg->strategy_draws, cfg->strategy_draws + cfg->n_draws);
+  h->subsets.assign(h->S, {});
+  for (int l = 0; l < h->L; ++l) {
+    const int s = h->subset_of[l];
+    if (s < 0 || s >= h->S) { delete h; return MQNPM_ERR_INVALID_ARG; }
+    h->subsets[s].push_back(l);
+  }
+  for (int s = 0; s < h->S; ++s) {
+    if (h->subsets[s].empty() || !(h->alpha[s] > 0)) { delete h; return MQNPM_ERR_INVALID_ARG; }
+  }
+  double amax = *std::max_element(h->alpha.begin(), h->alpha.end());
+  h->tau_max = cfg->tau_max > 0 ? cfg->tau_max : 1e3 * amax;
+  for (int d : h->draws)
+    if (d < 0 || d >= h->S) { delete h; return MQNPM_ERR_INVALID_ARG; }
+
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) { set_cuda_error(h, e, "cudaSetDevice"); delete h; return MQNPM_ERR_CUDA; }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (nsm <= 0) nsm = 1;
+  const size_t N = h->N, M = h->M, B = h->max_batch;
+  const int n = h->n, P = h->P;
+  h->w.ctas_row = green_row_ctas(n);
+  h->w.ctas_vec = (int)std::min<long long>(ceil_div_ll((long long)N, 256LL * 8), 8LL * nsm);
+  h->w.ctas_upd = (int)std::min<long long>(ceil_div_ll((long long)N, 256LL * 8), 4LL * nsm);
+  if (h->w.ctas_vec < 1) h->w.ctas_vec = 1;
+  if (h->w.ctas_upd < 1) h->w.ctas_upd = 1;
+  h->wp.ctas_vec = h->w.ctas_vec;
+  const int per_sm = wprox_coop_blocks_per_sm();
+  if (per_sm <= 0) { delete h; return MQNPM_ERR_CUDA; }
+  h->wp.ctas = nsm * std::min(per_sm, 1);
+
+  // ---- budget (every device allocation of the handle)
+  const size_t m1 = (size_t)(n + 1);
+  size_t need = 0;
+  need += m1 * m1 * m1 * 8 + (size_t)P * 8 + (size_t)h->L * 3 * n * 8 + (size_t)h->L * M * 8;
+  need += 8 * B * N * 8;                                   // u zs r rhat p v s t
+  need += B * ((size_t)n * n * P + (size_t)n * P * P) * 8; // T1, T2
+  need += B * M * 8;                                       // rdet
+  need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
+  need += 9 * N * 4 + (size_t)(h->wp.ctas_vec * 64 + 2 * h->wp.ctas * 44) * 8;     // wprox
+  need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
+  if (h->budget > 0 && need > h->budget) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds the budget of %zu bytes", need, h->budget);
+    h->err = msg;
+    *out = nullptr;
+    delete h;
+    return MQNPM_ERR_BUDGET;
+  }
+
+  // ---- allocations
+  int rc = MQNPM_OK;
+#define AL(ptr, cnt) \
+  if ((rc = dalloc(h, &(ptr), (cnt))) != MQNPM_OK) return fail(rc)
+  AL(h->khat, m1 * m1 * m1);
+  AL(h->tw, (size_t)P);
+  AL(h->tab, (size_t)h->L * 3 * n);
+  AL(h->ymeas, (size_t)h->L * M);
+  Workspace& w = h->w;
+  AL(w.u, B * N); AL(w.zs, B * N); AL(w.r, B * N); AL(w.rhat, B * N);
+  AL(w.p, B * N); AL(w.v, B * N); AL(w.s, B * N); AL(w.t, B * N);
+  AL(w.T1, B * (size_t)n * n * P);
+  AL(w.T2, B * (size_t)n * P * P);
+  AL(w.rdet, B * M);
+  AL(w.part1, B * (size_t)w.ctas_row * 1);
+  AL(w.part5, B * (size_t)w.ctas_row * 3);
+  AL(w.partd, B * (size_t)w.ctas_row);
+  AL(w.partu, std::max(B * (size_t)w.ctas_upd, (size_t)w.ctas_vec) * 3);
+  AL(w.st, B);
+  AL(w.illum, B);
+  AL(w.nactive, 1);
+  AL(w.dscal, 64);
+  WproxWork& wp = h->wp;
+  AL(wp.R, 3 * N); AL(wp.R2, 3 * N); AL(wp.Pd, 3 * N); AL(wp.d, N); AL(wp.x, N);
+  AL(wp.part, (size_t)wp.ctas_vec * 64 + 2 * (size_t)wp.ctas * 44);
+  AL(wp.scal, (size_t)wprox_scal_count());
+  AL(wp.barrier, 1);
+  AL(wp.err, 1);
+  AL(h->xbar, (size_t)h->S * N); AL(h->gbar, (size_t)h->S * N); AL(h->U, (size_t)h->S * N);
+  AL(h->g, N); AL(h->vq, N); AL(h->Pwarm, 3 * N);
+#undef AL
+  if ((e = cudaMallocHost(&w.h_nactive, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
+  if ((e = cudaMallocHost(&w.h_illum, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
+  if ((e = cudaMallocHost(&w.h_scal, 64 * sizeof(double))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
+
+  // ---- tables: twiddles W_P^j and incident-field axis factors, built in FP64
+  std::vector<float2> tw(P);
+  for (int j = 0; j < P; ++j) {
+    const double a = 2.0 * M_PI * (double)j / (double)P;
+    tw[j] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+  }
+  std::vector<float2> tab((size_t)h->L * 3 * n);
+  for (int l = 0; l < h->L; ++l)
+    for (int ax = 0; ax < 3; ++ax)
+      for (int i = 0; i < n; ++i) {
+        const double ph = h->kb * h->kdir[3 * l + ax] * ((double)i - n / 2.0) * h->h;
+        tab[((size_t)l * 3 + ax) * n + i] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+      }
+  cudaStream_t s = h->stream;
+  if ((e = cudaMemcpyAsync(h->tw, tw.data(), P * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = build_khat(n, h->h, h->kb, h->khat, s)) != cudaSuccess) {
+    set_cuda_error(h, e, "create tables");
+    return fail(MQNPM_ERR_CUDA);
+  }
+  h->tau.assign(h->alpha.begin(), h->alpha.end());
+  h->has_u.assign(h->S, 0);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { set_cuda_error(h, e, "create sync"); return fail(MQNPM_ERR_CUDA); }
+  *out = h;
+  return MQNPM_OK;
+}
+
+int mqnpm_set_measurements(mqnpm_handle* h, const float* y) {
+  if (!h || !y) return MQNPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpyAsync(h->ymeas, y, (size_t)h->L * h->M * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+  h->have_meas = true;
+  return MQNPM_OK;
+}
+
+int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int adjoint) {
+  if (!h || !v || !out || nb < 1 || nb > h->max_batch) return set_error(h, MQNPM_ERR_INVALID_ARG, "green_apply: bad arguments");
+  CK(cudaSetDevice(h->device));
+  GreenCall c;
+  c.n = h->n;
+  c.nb = nb;
+  c.adjoint = adjoint != 0;
+  c.pro = PRO_PLAIN;
+  c.pa.q = reinterpret_cast<const float2*>(v);
+  c.epi = EPI_PLAIN;
+  c.ea.out = reinterpret_cast<float2*>(out);
+  c.T1 = h->w.T1;
+  c.T2 = h->w.T2;
+  c.khat = h->khat;
+  c.tw = h->tw;
+  c.part_pro = h->w.part1;
+  c.part_epi = h->w.part5;
+  c.ev = profile_slot(h, nb);
+  CK(green_launch(c, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MQNPM_OK;
+}
+
+int mqnpm_forward(mqnpm_handle* h, const float* x, const int* illum, int nb, float* y_out, int* iters_out) {
+  if (!h || !x || !illum || !y_out || nb < 1) return set_error(h, MQNPM_ERR_INVALID_ARG, "forward: bad arguments");
+  for (int b = 0; b < nb; ++b)
+    if (illum[b] < 0 || illum[b] >= h->L) return set_error(h, MQNPM_ERR_INVALID_ARG, "forward: illumination index");
+  CK(cudaSetDevice(h->device));
+  int rc = grad_batch_impl(h, x, illum, nb, 1.0, nullptr, nullptr, nullptr, false, reinterpret_cast<float2*>(y_out));
+  if (iters_out)
+    for (int b = 0; b < nb; ++b) iters_out[b] = h->last_iters[2 * b];
+  return rc;
+}
+
+int mqnpm_grad_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad_out,
+                     double* loss_out, int* krylov_iters_out) {
+  if (!h || !x || !illum || !grad_out || nb < 1) return set_error(h, MQNPM_ERR_INVALID_ARG, "grad_batch: bad arguments");
+  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "grad_batch: measurements not set");
+  for (int b = 0; b < nb; ++b)
+    if (illum[b] < 0 || illum[b] >= h->L) return set_error(h, MQNPM_ERR_INVALID_ARG, "grad_batch: illumination index");
+  CK(cudaSetDevice(h->device));
+  return grad_batch_impl(h, x, illum, nb, scale, grad_out, loss_out, krylov_iters_out, true, nullptr);
+}
+
+int mqnpm_wprox(mqnpm_handle* h, const float* v, double tau_star, const float* U, int S_eff, double c, float* P_warm,
+                float* x_out) {
+  if (!h || !v || !x_out || v == x_out || !(tau_star > 0) || !(c > 0) || S_eff < 0 || S_eff > MQNPM_MAX_S ||
+      (S_eff > 0 && !U))
+    return set_error(h, MQNPM_ERR_INVALID_ARG, "wprox: bad arguments");
+  CK(cudaSetDevice(h->device));
+  UPtrs up{};
+  for (int s = 0; s < S_eff; ++s) up.u[s] = U + (size_t)s * h->N;
+  int rc = wprox_impl(h, v, tau_star, up, S_eff, c, P_warm, P_warm != nullptr, x_out);
+  if (rc == MQNPM_OK) CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int mqnpm_lipschitz(mqnpm_handle* h, const int* illum, int nb, double scale, const float* start, int iters,
+                    double* alpha_out) {
+  if (!h || !illum || !start || !alpha_out || nb < 1 || iters < 1) return set_error(h, MQNPM_ERR_INVALID_ARG, "lipschitz: bad arguments");
+  for (int b = 0; b < nb; ++b)
+    if (illum[b] < 0 || illum[b] >= h->L) return set_error(h, MQNPM_ERR_INVALID_ARG, "lipschitz: illumination index");
+  CK(cudaSetDevice(h->device));
+  return lipschitz_impl(h, illum, nb, scale, start, iters, alpha_out);
+}
+
+int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
+  if (!h || !x) return set_error(h, MQNPM_ERR_INVALID_ARG, "step: bad arguments");
+  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "step: measurements not set");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  const int S = h->S;
+  const int k = h->k + 1;
+  int sel;
+  if (k <= S) sel = k - 1;
+  else if (h->strategy == 1) sel = (k - 1) % S;
+  else {
+    const int idx = k - S - 1;
+    if (idx >= (int)h->draws.size()) return set_error(h, MQNPM_ERR_STATE, "step: strategy II draws exhausted");
+    sel = h->draws[idx];
+  }
+  const std::vector<int>& sub = h->subsets[sel];
+  double loss = 0.0;
+  std::vector<int> its(2 * sub.size());
+  int rc = grad_batch_impl(h, x, sub.data(), (int)sub.size(), (double)S / h->L, h->g, &loss, its.data(), true, nullptr);
+  if (rc != MQNPM_OK && rc != MQNPM_ERR_NOT_CONVERGED) return rc;
+  const int grad_rc = rc;
+  float* xb = h->xbar + (size_t)sel * N;
+  float* gb = h->gbar + (size_t)sel * N;
+  int branch = -1;
+  double tau_star;
+  UPtrs up{};
+  int S_eff = 0;
+  double c;
+  const int th = 256, gr = h->w.ctas_vec;
+  if (k <= S) {
+    // B_s = alpha_s I:  x_k = prox^{alpha_s I}_{a lam TV + iota_C}(x - (a/alpha_s) g)
+    CK(cudaMemcpyAsync(xb, x, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(gb, h->g, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    h->tau[sel] = h->alpha[sel];
+    h->has_u[sel] = 0;
+    tau_star = h->alpha[sel];
+    c = h->a * h->lambda;
+    k_axpby<<<gr, th, 0, s>>>(x, h->g, (float)(-h->a / h->alpha[sel]), h->vq, N);
+    CK(cudaGetLastError());
+  } else {
+    // Algorithm 4.2 on s = x - xbar_s', m = g - gbar_s'
+    double d3[3];
+    CK(vec_reduce(h, 1, x, xb, h->g, gb, d3));
+    const double ss = d3[0], sm = d3[1], mm = d3[2];
+    double tau = 0.0;
+    bool rank1 = false;
+    if (!finite_all(d3, 3)) return set_error(h, MQNPM_ERR_NONFINITE, "step: non-finite SR1 inner products");
+    if (sm == 0.0) {
+      tau = h->alpha[sel];
+      branch = 1;
+    } else {
+      tau = std::min(mm / (h->gamma * sm), h->tau_max);
+      if (tau <= 0.0) {
+        tau = h->alpha[sel];
+        branch = 1;
+      } else {
+        // ||m - tau s|| from the closed form mm - 2 tau sm + tau^2 ss
+        const double qs = sm - tau * ss;
+        const double qq = std::max(0.0, mm - 2.0 * tau * sm + tau * tau * ss);
+        if (std::fabs(qs) <= h->delta1 * std::sqrt(ss) * std::sqrt(qq)) {
+          branch = 2;
+        } else {
+          branch = 0;
+          rank1 = true;
+          while (sm - tau * ss <= h->delta2 * ss) {
+            if (tau < h->delta2) {
+              tau = h->alpha[sel];
+              rank1 = false;
+              branch = 3;
+              break;
+            }
+            tau *= 0.5;
+          }
+        }
+      }
+    }
+    if (rank1) {
+      const double den = sm - tau * ss;
+      k_sr1_u<<<gr, th, 0, s>>>(x, xb, h->g, gb, (float)tau, (float)(1.0 / std::sqrt(den)), h->U + (size_t)sel * N, N);
+      CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(xb, x, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(gb, h->g, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    h->tau[sel] = tau;
+    h->has_u[sel] = rank1 ? 1 : 0;
+    tau_star = 0.0;
+    for (int q = 0; q < S; ++q) tau_star += h->tau[q];
+    for (int q = 0; q < S; ++q)
+      if (h->has_u[q]) up.u[S_eff++] = h->U + (size_t)q * N;
+    c = h->a * S * h->lambda;
+    // v_k = x - a S B^{-1} g, B = tau* I + U U^T
+    if (S_eff == 0) {
+      k_axpby<<<gr, th, 0, s>>>(x, h->g, (float)(-h->a * S / tau_star), h->vq, N);
+      CK(cudaGetLastError());
+    } else {
+      rc = qn_point_impl(h, x, h->g, up, S_eff, tau_star, h->a * S, h->vq);
+      if (rc != MQNPM_OK) return rc;
+    }
+  }
+  if (!(c > 0)) {
+    // lambda = 0: the proximal map reduces to the box projection under B
+    c = 1e-30;
+  }
+  rc = wprox_impl(h, h->vq, tau_star, up, S_eff, c, h->Pwarm, h->have_P, x);
+  if (rc != MQNPM_OK) return rc;
+  h->have_P = true;
+  CK(cudaStreamSynchronize(s));
+  h->k = k;
+  if (info) {
+    info->k = k;
+    info->subset = sel;
+    info->loss = loss;
+    info->tau_star = tau_star;
+    info->rank = S_eff;
+    info->sr1_branch = branch;
+    int mx = 0;
+    for (int v : its) mx = std::max(mx, v);
+    info->krylov_iters_max = mx;
+    info->newton_iters_max = h->last_newton_max;
+  }
+  return grad_rc;
+}
+
+// ---- checkpoint: header, then xbar, gbar, U (S x N floats each), P (3N floats)
+struct StateHeader {
+  unsigned magic;
+  int n, S, k, have_P;
+  int has_u[MQNPM_MAX_S];
+  double tau[MQNPM_MAX_S];
+};
+
+int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size) {
+  if (!h || !size) return MQNPM_ERR_INVALID_ARG;
+  const size_t N = h->N;
+  const size_t need = sizeof(StateHeader) + (3 * (size_t)h->S * N + 3 * N) * sizeof(float);
+  if (!buf) {
+    *size = need;
+    return MQNPM_OK;
+  }
+  if (*size < need) return set_error(h, MQNPM_ERR_INVALID_ARG, "save_state: buffer too small");
+  CK(cudaSetDevice(h->device));
+  StateHeader hd{};
+  hd.magic = 0x4d514e50u;
+  hd.n = h->n;
+  hd.S = h->S;
+  hd.k = h->k;
+  hd.have_P = h->have_P ? 1 : 0;
+  for (int s = 0; s < h->S; ++s) {
+    hd.has_u[s] = h->has_u[s];
+    hd.tau[s] = h->tau[s];
+  }
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &hd, sizeof hd);
+  p += sizeof hd;
+  const size_t SN = (size_t)h->S * N * sizeof(float);
+  CK(cudaMemcpyAsync(p, h->xbar, SN, cudaMemcpyDeviceToHost, h->stream)); p += SN;
+  CK(cudaMemcpyAsync(p, h->gbar, SN, cudaMemcpyDeviceToHost, h->stream)); p += SN;
+  CK(cudaMemcpyAsync(p, h->U, SN, cudaMemcpyDeviceToHost, h->stream)); p += SN;
+  CK(cudaMemcpyAsync(p, h->Pwarm, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *size = need;
+  return MQNPM_OK;
+}
+
+int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size) {
+  if (!h || !buf) return MQNPM_ERR_INVALID_ARG;
+  const size_t N = h->N;
+  const size_t need = sizeof(StateHeader) + (3 * (size_t)h->S * N + 3 * N) * sizeof(float);
+  if (size < need) return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: buffer too small");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof hd);
+  if (hd.magic != 0x4d514e50u || hd.n != h->n || hd.S != h->S)
+    return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: state does not match this handle");
+  CK(cudaSetDevice(h->device));
+  const char* p = static_cast<const char*>(buf) + sizeof hd;
+  const size_t SN = (size_t)h->S * N * sizeof(float);
+  CK(cudaMemcpyAsync(h->xbar, p, SN, cudaMemcpyHostToDevice, h->stream)); p += SN;
+  CK(cudaMemcpyAsync(h->gbar, p, SN, cudaMemcpyHostToDevice, h->stream)); p += SN;
+  CK(cudaMemcpyAsync(h->U, p, SN, cudaMemcpyHostToDevice, h->stream)); p += SN;
+  CK(cudaMemcpyAsync(h->Pwarm, p, 3 * N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->k = hd.k;
+  h->have_P = hd.have_P != 0;
+  for (int s = 0; s < h->S; ++s) {
+    h->has_u[s] = hd.has_u[s];
+    h->tau[s] = hd.tau[s];
+  }
+  return MQNPM_OK;
+}
+
+}  // extern "C"

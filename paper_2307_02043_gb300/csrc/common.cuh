@@ -1,0 +1,166 @@
+// Shared device helpers for the MQNPM hot path (sm_103a).
+//
+// Complex64 arithmetic on float2, compile-time twiddle factors, deterministic
+// block reductions into FP64 partials, and a grid barrier with a bounded wait
+// for cooperative (co-resident) launches.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <utility>
+#include <type_traits>
+
+#define MQ_HD __host__ __device__ __forceinline__
+#define MQ_D __device__ __forceinline__
+
+// ---------------------------------------------------------------- complex64
+MQ_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+MQ_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+MQ_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+MQ_HD float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+MQ_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+MQ_HD float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// a + s * b (s complex)
+MQ_HD float2 caxpy(float2 s, float2 b, float2 a) {
+  return make_float2(fmaf(s.x, b.x, fmaf(-s.y, b.y, a.x)), fmaf(s.x, b.y, fmaf(s.y, b.x, a.y)));
+}
+MQ_HD float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// ---------------------------------------------------- compile-time sin / cos
+// Twiddle factors of the in-register DFTs are evaluated by the compiler from
+// Taylor series (angle reduced to |t| <= pi/4 by octant symmetry), so they
+// become immediates; no runtime table and no device math library call.
+namespace ctrig {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double sin_series(double t) {
+  double term = t, sum = t;
+  for (int i = 1; i < 16; ++i) {
+    term *= -t * t / ((2.0 * i) * (2.0 * i + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double cos_series(double t) {
+  double term = 1.0, sum = 1.0;
+  for (int i = 1; i < 16; ++i) {
+    term *= -t * t / ((2.0 * i - 1.0) * (2.0 * i));
+    sum += term;
+  }
+  return sum;
+}
+// cos and sin of 2*pi*j/R, exact reduction on the rational angle j/R.
+// Octant o = floor(8 j / R) and remainder give |t| <= pi/4.
+struct CS { double c, s; };
+constexpr CS cs_turn(long j, long R) {
+  j %= R;
+  if (j < 0) j += R;
+  // angle = 2*pi*j/R = (pi/4) * (8j/R); split 8j = o*R + rem.
+  long o = (8 * j) / R;
+  long rem = 8 * j - o * R;            // 0 <= rem < R
+  // t in [0, pi/4): base angle within the octant
+  double t = (kPi / 4.0) * static_cast<double>(rem) / static_cast<double>(R);
+  double c0 = cos_series(t), s0 = sin_series(t);
+  // rotate by o * pi/4
+  const double h = 0.70710678118654752440084436210484903928;  // sqrt(2)/2
+  double c = c0, s = s0;
+  switch (o) {
+    case 0: c = c0; s = s0; break;
+    case 1: c = h * (c0 - s0); s = h * (c0 + s0); break;
+    case 2: c = -s0; s = c0; break;
+    case 3: c = -h * (c0 + s0); s = h * (c0 - s0); break;
+    case 4: c = -c0; s = -s0; break;
+    case 5: c = -h * (c0 - s0); s = -h * (c0 + s0); break;
+    case 6: c = s0; s = -c0; break;
+    default: c = h * (c0 + s0); s = -h * (c0 - s0); break;
+  }
+  return CS{c, s};
+}
+}  // namespace ctrig
+
+// ------------------------------------------------------------- static loops
+template <class F, int... I>
+MQ_D void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+MQ_D void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// -------------------------------------------------------------- reductions
+MQ_D double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+MQ_D float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum K doubles over the block (blockDim.x a multiple of 32, <= 1024) in a
+// fixed order; thread 0 receives the totals in out[]. scratch: >= 32*K doubles.
+template <int K>
+MQ_D void block_sum(double (&v)[K], double* scratch, double (&out)[K]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) scratch[warp * K + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += scratch[w * K + k];
+      out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ grid barrier
+// Barrier for cooperative launches (all blocks co-resident).  `count` is a
+// monotonically increasing arrival counter zeroed before the launch; `epoch`
+// is the number of barriers this block has passed.  The wait is bounded by
+// `limit_cycles`; on expiry the block raises *err and returns false, and every
+// caller leaves its loop, so the kernel ends instead of hanging.
+MQ_D unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+MQ_D bool grid_barrier(unsigned* count, unsigned nblocks, unsigned& epoch, int* err,
+                       long long limit_cycles) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    epoch += 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    const unsigned target = epoch * nblocks;
+    const long long t0 = clock64();
+    int ok = 1;
+    while (ld_acquire_u32(count) < target) {
+      if (*((volatile int*)err) != 0) { ok = 0; break; }
+      if (clock64() - t0 > limit_cycles) { atomicExch(err, 1); ok = 0; break; }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ----------------------------------------------------------------- helpers
+MQ_HD int ceil_div(int a, int b) { return (a + b - 1) / b; }
+MQ_HD long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }

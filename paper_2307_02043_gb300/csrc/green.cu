@@ -1,0 +1,136 @@
+// Dispatch of the Green's apply by transform length, and construction of the
+// Green's kernel spectrum K_hat.
+//
+// Discretisation (our reading of the forward model of Section 6): with voxel h
+// and background wavenumber kb,
+//   (G v)_i = kb^2 sum_j w_{i-j} v_j,  offsets D in (-n, n)^3,
+//   w_D = h^3 exp(j kb |D| h) / (4 pi |D| h) for D != 0,
+//   w_0 = [exp(j kb a)(1 - j kb a) - 1] / kb^2, a = (3/(4 pi))^(1/3) h.
+// On the periodic grid of edge P = 2n the kernel is even in every axis, so its
+// DFT is a product of three 1D cosine sums over the first octant of offsets:
+//   Kf(f) = k(0) + 2 sum_{d=1}^{n-1} k(d) cos(2 pi f d / P),  f = 0..n.
+// These sums run in FP64 on the device; the result, scaled by 1/P^3 (the
+// normalisation of the inverse transform), is rounded to complex64.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+#define MQ_DISPATCH(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(320) X(384)
+
+bool green_supported(int n) {
+  switch (2 * n) {
+#define MQ_CASE(P) case P:
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+int green_row_ctas(int n) {
+  switch (2 * n) {
+#define MQ_CASE(P) case P: return green_row_ctas_P##P(n);
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    default:
+      return 0;
+  }
+}
+
+cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
+  switch (2 * c.n) {
+#define MQ_CASE(P) case P: return green_launch_P##P(c, s);
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------ K_hat build
+// k[dz][dy][dx] for offsets in [0, n)^3 (FP64 complex as double2).
+__global__ void k_kernel_octant(double2* k, int n, double h, double kb) {
+  const long long N = (long long)n * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int dx = (int)(i % n), dy = (int)((i / n) % n), dz = (int)(i / ((long long)n * n));
+    double re, im;
+    if (dx == 0 && dy == 0 && dz == 0) {
+      const double a = cbrt(3.0 / (4.0 * 3.14159265358979323846)) * h;
+      double s, c;
+      sincos(kb * a, &s, &c);
+      // exp(j kb a) (1 - j kb a) - 1, divided by kb^2, times kb^2
+      re = (c + kb * a * s) - 1.0;
+      im = s - kb * a * c;
+    } else {
+      const double r = h * sqrt((double)dx * dx + (double)dy * dy + (double)dz * dz);
+      double s, c;
+      sincos(kb * r, &s, &c);
+      const double f = kb * kb * h * h * h / (4.0 * 3.14159265358979323846 * r);
+      re = f * c;
+      im = f * s;
+    }
+    k[i] = make_double2(re, im);
+  }
+}
+
+// One separable even-sum pass along the fastest axis of `in` (extent n, the
+// offsets), writing extent m = n+1 (the folded frequencies) as the *slowest*
+// axis of `out`, so three passes rotate the axes back to [fz][fy][fx].
+//   in : [a][b][d]  (d < n)      out: [f][a][b]  (f <= n)
+__global__ void k_cos_pass(const double2* __restrict__ in, double2* __restrict__ out, int A, int B, int n,
+                           const double* __restrict__ cosP, int P) {
+  const long long total = (long long)(n + 1) * A * B;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int bb = (int)(i % B);
+    const int aa = (int)((i / B) % A);
+    const int f = (int)(i / ((long long)A * B));
+    const double2* row = in + ((long long)aa * B + bb) * n;
+    double re = row[0].x, im = row[0].y;
+    for (int d = 1; d < n; ++d) {
+      const double c = 2.0 * cosP[(long long)f * d % P];
+      re += c * row[d].x;
+      im += c * row[d].y;
+    }
+    out[i] = make_double2(re, im);
+  }
+}
+
+__global__ void k_round_khat(const double2* __restrict__ in, float2* __restrict__ out, long long M, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)(in[i].x * scale), (float)(in[i].y * scale));
+}
+
+cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s) {
+  const int P = 2 * n;
+  const long long m = n + 1;
+  std::vector<double> cosv(P);
+  for (int j = 0; j < P; ++j) cosv[j] = std::cos(2.0 * M_PI * (double)j / (double)P);
+  double2 *a = nullptr, *b = nullptr;
+  double* dcos = nullptr;
+  const size_t big = (size_t)m * m * m;
+  cudaError_t e;
+  if ((e = cudaMallocAsync(&a, big * sizeof(double2), s)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync(&b, big * sizeof(double2), s)) != cudaSuccess) { cudaFreeAsync(a, s); return e; }
+  if ((e = cudaMallocAsync(&dcos, P * sizeof(double), s)) != cudaSuccess) { cudaFreeAsync(a, s); cudaFreeAsync(b, s); return e; }
+  e = cudaMemcpyAsync(dcos, cosv.data(), P * sizeof(double), cudaMemcpyHostToDevice, s);
+  const int th = 256, gr = 1024;
+  if (e == cudaSuccess) {
+    k_kernel_octant<<<gr, th, 0, s>>>(a, n, h, kb);                   // a: [dz][dy][dx]
+    k_cos_pass<<<gr, th, 0, s>>>(a, b, n, n, n, dcos, P);             // b: [fx][dz][dy]
+    k_cos_pass<<<gr, th, 0, s>>>(b, a, (int)m, n, n, dcos, P);        // a: [fy][fx][dz]
+    k_cos_pass<<<gr, th, 0, s>>>(a, b, (int)m, (int)m, n, dcos, P);   // b: [fz][fy][fx]
+    k_round_khat<<<gr, th, 0, s>>>(b, khat_out, (long long)big, 1.0 / ((double)P * P * P));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host cosine table goes out of scope
+  }
+  cudaFreeAsync(a, s);
+  cudaFreeAsync(b, s);
+  cudaFreeAsync(dcos, s);
+  return e;
+}

@@ -1,0 +1,302 @@
+// The five passes of the pruned, zero-padded Green's convolution
+// (G v)|_domain = crop_n( IFFT_P( K_hat * FFT_P( pad_P(v) ) ) ),  P = 2n,
+// batched over the illuminations of a mini-batch (grid dimension "b").
+//
+// Layout (complex64, x fastest everywhere):
+//   volume   v [b][z][y][x]              n^3
+//   T1 / T4    [b][z][y][kx]             n*n*P     (after / before the x pass)
+//   T2 / T3    [b][z][ky][kx]            n*P*P     (after / before the y pass)
+//   K_hat octant [fz][fy][fx]            (n+1)^3   (K_hat is even in each axis)
+// Pass 1 (x, rows)    : n*n lines, n nonzero inputs -> P outputs   + fused prologue
+// Pass 2 (y, columns) : n*P columns, n nonzero inputs -> P outputs
+// Pass 3 (z, columns) : P*P columns, forward, * K_hat, inverse, n outputs kept
+// Pass 4 (y, columns) : n*P columns, P inputs -> n outputs kept
+// Pass 5 (x, rows)    : n*n lines, P inputs -> n outputs kept      + fused epilogue
+// Zero rows of the padding are never read and cropped outputs never written.
+// The 1/P^3 of the inverse transform is folded into K_hat.
+#pragma once
+#include "fft.cuh"
+#include "kstate.h"
+
+// ----------------------------------------------------------- CTA shapes
+template <int P>
+struct RowShape {
+  using PL = Plan<P>;
+  static constexpr int PITCH = PL::R1 + 1;                 // padded exchange row
+  static constexpr int PER_LINE = PL::R2 * PITCH;
+  static constexpr int LPB0 = 256 / PL::T;
+  static constexpr int LPB = (LPB0 * PER_LINE * 8 > 40960) ? (40960 / (PER_LINE * 8) >= 16 ? 16 : 8) : LPB0;
+  static constexpr int THREADS = LPB * PL::T;
+  static constexpr int SMEM = (P + LPB * PER_LINE) * 8;
+};
+template <int P>
+struct ColShape {
+  using PL = Plan<P>;
+  static constexpr int C0 = 256 / PL::T;
+  static constexpr int C1 = C0 > P ? P : C0;
+  static constexpr int C = (C1 * P * 8 > 40960) ? 16 : C1;
+  static constexpr int THREADS = C * PL::T;
+  static constexpr int SMEM = (P + P * C) * 8;
+};
+
+// Per-thread FP32 partial sums, reduced per CTA into FP64 partials.
+template <int K>
+struct Parts {
+  float v[K > 0 ? K : 1];
+  MQ_D void zero() {
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); ++k) v[k] = 0.f;
+  }
+};
+
+template <int K>
+MQ_D void write_partials(const Parts<K>& p, double* partials, int b, int cta, int nctas) {
+  if constexpr (K > 0) {
+    __shared__ double scratch[32 * K];
+    double d[K], out[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = (double)p.v[k];
+    block_sum<K>(d, scratch, out);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) partials[((size_t)b * nctas + cta) * K + k] = out[k];
+    }
+  }
+}
+
+MQ_D bool slot_active(const KState* st, int b) { return st == nullptr || st[b].active != 0; }
+
+// ------------------------------------------------------- pass 1: x forward
+template <int P, class Pro>
+__global__ void __launch_bounds__(RowShape<P>::THREADS)
+k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
+        const KState* __restrict__ st, double* __restrict__ partials) {
+  using PL = Plan<P>;
+  using SH = RowShape<P>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* ex = sm + P;
+  const int b = blockIdx.y;
+  if (!slot_active(st, b)) return;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+  const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
+  const int line = blockIdx.x * SH::LPB + l;
+  const bool valid = line < n * n;
+  const int z = line / n, y = line - (line / n) * n;
+  float2* exl = ex + l * SH::PER_LINE;
+  Parts<Pro::NPART> parts;
+  parts.zero();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R2 / T; ++i) {
+    const int n2 = t + T * i;
+    float2 a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      a[n1] = make_float2(0.f, 0.f);
+      if (n1 < R1 / 2 && valid) a[n1] = pro.load(b, R2 * n1 + n2, y, z, parts);
+    }
+    dft<R1, false>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) exl[n2 * SH::PITCH + k1] = cmul(a[k1], tw[n2 * k1]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R1 / T; ++i) {
+    const int k1 = t + T * i;
+    float2 a[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) a[n2] = exl[n2 * SH::PITCH + k1];
+    dft<R2, false>(a);
+    if (valid) {
+      float2* o = T1 + ((size_t)b * n * n + line) * P;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = a[k2];
+    }
+  }
+  write_partials<Pro::NPART>(parts, partials, b, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------- pass 5: x inverse
+template <int P, class Epi>
+__global__ void __launch_bounds__(RowShape<P>::THREADS)
+k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict__ twg,
+        const KState* __restrict__ st, double* __restrict__ partials) {
+  using PL = Plan<P>;
+  using SH = RowShape<P>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* ex = sm + P;
+  const int b = blockIdx.y;
+  if (!slot_active(st, b)) return;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+  const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
+  const int line = blockIdx.x * SH::LPB + l;
+  const bool valid = line < n * n;
+  const int z = line / n, y = line - (line / n) * n;
+  float2* exl = ex + l * SH::PER_LINE;
+  const float2* src = T4 + ((size_t)b * n * n + (valid ? line : 0)) * P;
+  Parts<Epi::NPART> parts;
+  parts.zero();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R2 / T; ++i) {
+    const int n2 = t + T * i;
+    float2 a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) a[n1] = valid ? src[R2 * n1 + n2] : make_float2(0.f, 0.f);
+    dft<R1, true>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) exl[n2 * SH::PITCH + k1] = cmul(a[k1], cconj(tw[n2 * k1]));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R1 / T; ++i) {
+    const int k1 = t + T * i;
+    float2 a[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) a[n2] = exl[n2 * SH::PITCH + k1];
+    dft<R2, true>(a);
+    if (valid) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2 / 2; ++k2) epi.store(b, k1 + R1 * k2, y, z, a[k2], parts);
+    }
+  }
+  write_partials<Epi::NPART>(parts, partials, b, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------- passes 2 and 4: y columns
+// INV = false: T1 [b][z][y < n][kx] -> T2 [b][z][ky < P][kx]
+// INV = true : T3 [b][z][ky < P][kx] -> T4 [b][z][y < n][kx]
+template <int P, bool INV>
+__global__ void __launch_bounds__(ColShape<P>::THREADS)
+k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
+         const float2* __restrict__ twg, const KState* __restrict__ st) {
+  using PL = Plan<P>;
+  using SH = ColShape<P>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* ex = sm + P;
+  const int b = blockIdx.z;
+  if (!slot_active(st, b)) return;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
+  const int kx = blockIdx.x * C + c;
+  const int z = blockIdx.y;
+  const int len_in = INV ? P : n, len_out = INV ? n : P;
+  const float2* src = in + ((size_t)b * n + z) * len_in * P + kx;
+  float2* dst = out + ((size_t)b * n + z) * len_out * P + kx;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R2 / T; ++i) {
+    const int n2 = t + T * i;
+    float2 a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      a[n1] = make_float2(0.f, 0.f);
+      if (INV || n1 < R1 / 2) a[n1] = src[(size_t)(R2 * n1 + n2) * P];
+    }
+    dft<R1, INV>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const float2 w = tw[n2 * k1];
+      ex[(n2 * R1 + k1) * C + c] = cmul(a[k1], INV ? cconj(w) : w);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R1 / T; ++i) {
+    const int k1 = t + T * i;
+    float2 a[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) a[n2] = ex[(n2 * R1 + k1) * C + c];
+    dft<R2, INV>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < (INV ? R2 / 2 : R2); ++k2) dst[(size_t)(k1 + R1 * k2) * P] = a[k2];
+  }
+}
+
+// ------------------------------------- pass 3: z forward, * K_hat, z inverse
+// In place on T2/T3 [b][z][ky][kx]; only rows z < n are read and written.
+template <int P, bool CONJ>
+__global__ void __launch_bounds__(ColShape<P>::THREADS)
+k_pass3(float2* __restrict__ T2, const float2* __restrict__ khat, int n,
+        const float2* __restrict__ twg, const KState* __restrict__ st) {
+  using PL = Plan<P>;
+  using SH = ColShape<P>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* ex = sm + P;
+  const int b = blockIdx.z;
+  if (!slot_active(st, b)) return;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
+  const int kx = blockIdx.x * C + c;
+  const int ky = blockIdx.y;
+  const size_t zs = (size_t)P * P;
+  float2* col = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
+  const int m1 = n + 1;
+  const int fx = kx <= n ? kx : P - kx;
+  const int fy = ky <= n ? ky : P - ky;
+  const float2* kcol = khat + (size_t)fy * m1 + fx;
+  __syncthreads();
+  // forward stage 1 (n2-threads), inputs z = R2 n1 + n2 < n
+#pragma unroll
+  for (int i = 0; i < R2 / T; ++i) {
+    const int n2 = t + T * i;
+    float2 a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      a[n1] = make_float2(0.f, 0.f);
+      if (n1 < R1 / 2) a[n1] = col[(size_t)(R2 * n1 + n2) * zs];
+    }
+    dft<R1, false>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) ex[(n2 * R1 + k1) * C + c] = cmul(a[k1], tw[n2 * k1]);
+  }
+  __syncthreads();
+  // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread)
+  float2 zb[R1 / T][R2];
+#pragma unroll
+  for (int i = 0; i < R1 / T; ++i) {
+    const int k1 = t + T * i;
+    float2 a[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) a[n2] = ex[(n2 * R1 + k1) * C + c];
+    dft<R2, false>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int kz = k1 + R1 * k2;
+      const int fz = kz <= n ? kz : P - kz;
+      float2 kh = kcol[(size_t)fz * m1 * m1];
+      if (CONJ) kh.y = -kh.y;
+      a[k2] = cmul(a[k2], kh);
+    }
+    dft<R2, true>(a);  // over k2 -> j1
+#pragma unroll
+    for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = cmul(a[j1], cconj(tw[j1 * k1]));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R1 / T; ++i) {
+    const int k1 = t + T * i;
+#pragma unroll
+    for (int j1 = 0; j1 < R2; ++j1) ex[(k1 * R2 + j1) * C + c] = zb[i][j1];
+  }
+  __syncthreads();
+  // inverse stage B (j1-threads): outputs z = j1 + R2 j2 for j2 < R1/2
+#pragma unroll
+  for (int i = 0; i < R2 / T; ++i) {
+    const int j1 = t + T * i;
+    float2 a[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[k1] = ex[(k1 * R2 + j1) * C + c];
+    dft<R1, true>(a);
+#pragma unroll
+    for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(j1 + R2 * j2) * zs] = a[j2];
+  }
+}

@@ -1,0 +1,138 @@
+// Host-side declarations shared by the translation units of libmqnpm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "kstate.h"
+
+// One Green's apply over a batch: pass 1 (prologue) ... pass 5 (epilogue).
+struct GreenCall {
+  int n = 0;
+  int nb = 0;                  // batch slots
+  int pro = PRO_PLAIN;
+  int epi = EPI_PLAIN;
+  bool adjoint = false;        // use conj(K_hat): G^H
+  ProArgs pa{};
+  EpiArgs ea{};
+  float2* T1 = nullptr;        // [nb][n][n][P]
+  float2* T2 = nullptr;        // [nb][n][P][P]
+  const float2* khat = nullptr;  // octant (n+1)^3, scaled by 1/P^3
+  const float2* tw = nullptr;    // W_P^j, j < P
+  const KState* st = nullptr;    // slot activity (nullptr: all active)
+  double* part_pro = nullptr;    // [nb][ctas1][NPART]
+  double* part_epi = nullptr;    // [nb][ctas5][NPART]
+  cudaEvent_t* ev = nullptr;     // optional: 6 events recorded around the 5 passes
+};
+
+// Per-pass timing (opt-in tracing): events recorded around every Green's apply.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // groups of 6
+  int used = 0;                  // groups recorded
+  std::vector<int> nb;           // batch slots of each recorded call
+  cudaEvent_t* next();
+};
+
+// Number of CTAs pass 1 / pass 5 use per slot (partials layout).
+int green_row_ctas(int n);
+bool green_supported(int n);
+cudaError_t green_launch(const GreenCall& c, cudaStream_t s);
+
+// Per-P entry points (one translation unit each).
+#define MQ_DECL(P) cudaError_t green_launch_P##P(const GreenCall& c, cudaStream_t s); int green_row_ctas_P##P(int n);
+MQ_DECL(16) MQ_DECL(24) MQ_DECL(32) MQ_DECL(48) MQ_DECL(64) MQ_DECL(96) MQ_DECL(128)
+MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
+#undef MQ_DECL
+
+// K_hat octant in FP64 by separable even (cosine) sums, rounded to complex64.
+cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s);
+
+// ----------------------------------------------------------------- handle
+struct Workspace {
+  // BiCGSTAB vectors, [max_batch][N] complex64 each
+  float2 *u = nullptr, *zs = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr,
+         *s = nullptr, *t = nullptr;
+  float2 *T1 = nullptr, *T2 = nullptr;   // transform scratch
+  float2* rdet = nullptr;                // [max_batch][M]
+  double *part1 = nullptr, *part5 = nullptr, *partu = nullptr, *partd = nullptr;
+  KState* st = nullptr;                  // [max_batch]
+  int* illum = nullptr;                  // [max_batch]
+  int* nactive = nullptr;                // device counter
+  int* h_nactive = nullptr;              // pinned host mirror
+  int* h_illum = nullptr;                // pinned staging of slot illuminations
+  double* h_scal = nullptr;              // pinned scalar staging (64 doubles)
+  double* dscal = nullptr;               // device scalar scratch (64 doubles)
+  int ctas_row = 0, ctas_upd = 0, ctas_vec = 0;
+};
+
+struct WproxWork {
+  float *R = nullptr, *R2 = nullptr, *Pd = nullptr, *d = nullptr, *x = nullptr;
+  double* part = nullptr;       // [ctas][NV]
+  double* scal = nullptr;       // device scalars of the proximal solve
+  unsigned* barrier = nullptr;  // grid-barrier counter
+  int* err = nullptr;           // device error flag
+  int ctas = 0;                 // CTAs of the cooperative Newton kernel
+  int ctas_vec = 0;
+};
+
+struct mqnpm_handle {
+  // problem
+  int n = 0, P = 0, M = 0, model = 1, L = 0, S = 0, tv = 0, strategy = 1;
+  size_t N = 0;
+  double h = 1.0, kb = 0.0, lambda = 0.0, lo = 0.0, hi = 0.0, a = 1.0, gamma = 0.8, tau_max = 0.0;
+  double delta1 = 1e-8, delta2 = 1e-12, krylov_tol = 1e-6, newton_tol = 1e-6;
+  int krylov_maxit = 500, dual_iters = 20, newton_maxit = 50, max_batch = 1, device = 0;
+  int check_every = 1;
+  std::vector<double> kdir, alpha;
+  std::vector<int> subset_of, draws;
+  std::vector<std::vector<int>> subsets;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  size_t bytes = 0, budget = 0;
+  std::vector<void*> allocations;
+  // device tables
+  float2 *khat = nullptr, *tw = nullptr, *tab = nullptr, *ymeas = nullptr;
+  bool have_meas = false;
+  Workspace w;
+  WproxWork wp;
+  // outer-loop state (Algorithm 4.1)
+  int k = 0;
+  float *xbar = nullptr, *gbar = nullptr, *U = nullptr, *g = nullptr, *vq = nullptr, *Pwarm = nullptr;
+  std::vector<double> tau;
+  std::vector<int> has_u;
+  bool have_P = false;
+  // diagnostics of the last calls
+  std::vector<int> last_iters;   // per illumination of the last gradient: forward, adjoint
+  int last_newton_max = 0, last_newton_total = 0;
+  int last_status = 0;
+  Profiler prof;
+};
+
+// Record the next profiling group for a Green's apply of nb slots (nullptr when off/full).
+cudaEvent_t* profile_slot(mqnpm_handle* h, int nb);
+
+// krylov.cu
+int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
+                    float* grad, double* loss, int* iters, bool want_grad, float2* y_out);
+int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, const float* start,
+                   int iters, double* alpha_out);
+cudaError_t vec_reduce(mqnpm_handle* h, int kind, const float* a, const float* b, const float* c,
+                       const float* d, double* host_out);
+
+// wprox.cu
+struct UPtrs {
+  const float* u[16];
+};
+int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int S_eff, double c,
+               float* P_warm, bool warm, float* x_out);
+int qn_point_impl(mqnpm_handle* h, const float* x, const float* g, const UPtrs& U, int S_eff, double tau,
+                  double aS, float* v);
+int wprox_coop_blocks_per_sm();
+int wprox_scal_count();
+
+// status helpers (api.cu)
+int set_cuda_error(mqnpm_handle* h, cudaError_t e, const char* where);
+int set_error(mqnpm_handle* h, int code, const std::string& msg);

@@ -1,0 +1,545 @@
+// Mini-batch data-term gradient (Section 6): Lippmann-Schwinger forward solve
+// by BiCGSTAB, detector residual, adjoint solve and gradient assembly, all
+// illuminations of a batch advancing in lockstep (converged slots idle).
+//
+// BiCGSTAB (van der Vorst 1992) per slot, on A = I - G X (forward) or
+// A = I - G^H X (adjoint), with complex64 vectors and FP64 scalars:
+//   p = r + beta (p - omega v);  v = A p;          alpha = rho / <rhat, v>
+//   s = r - alpha v;             t = A s;          omega = <t, s> / <t, t>
+//   u += alpha p + omega s;      r = s - omega t;  rho' = <rhat, r>, beta = rho'/rho * alpha/omega
+// Both matrix-vector products are single Green's applies whose first pass
+// forms p (or s) on the fly and whose last pass forms v (or t) and the inner
+// products.  Forward start u_0 = u_in (so r_0 = G(x u_in)); adjoint start 0.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+#include "mqnpm.h"
+
+namespace {
+
+struct dc {
+  double re, im;
+};
+MQ_D dc dmul(dc a, dc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+MQ_D dc ddiv(dc a, dc b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+MQ_D bool dfinite(dc a) { return isfinite(a.re) && isfinite(a.im); }
+
+// Deterministic sum of K partials per CTA over `nctas` CTAs of slot b.
+template <int K>
+MQ_D void sum_partials(const double* part, int b, int nctas, double (&out)[K]) {
+  __shared__ double scratch[32 * K];
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (int c = threadIdx.x; c < nctas; c += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += part[((size_t)b * nctas + c) * K + k];
+  }
+  block_sum<K>(v, scratch, out);
+}
+
+__global__ void k_fin_init(KState* st, const double* part, int nctas, double tol2, double bnorm2_fwd) {
+  const int b = blockIdx.x;
+  double s[1];
+  sum_partials<1>(part, b, nctas, s);
+  if (threadIdx.x == 0) {
+    KState k;
+    memset(&k, 0, sizeof(k));
+    k.rho_re = s[0];
+    k.alpha_re = 1.0;
+    k.omega_re = 1.0;
+    k.beta_re = 0.0;   // p = v = 0, so p_1 = r_0
+    k.rnorm2 = s[0];
+    k.bnorm2 = bnorm2_fwd > 0.0 ? bnorm2_fwd : s[0];
+    k.tol2 = tol2;
+    k.iters = 0;
+    if (!isfinite(s[0])) {
+      k.status = KSTATUS_NONFINITE;
+      k.active = 0;
+    } else if (k.bnorm2 == 0.0 || k.rnorm2 <= tol2 * k.bnorm2) {
+      k.status = KSTATUS_CONVERGED;
+      k.active = 0;
+    } else {
+      k.status = KSTATUS_RUNNING;
+      k.active = 1;
+    }
+    st[b] = k;
+  }
+}
+
+__global__ void k_fin_alpha(KState* st, const double* part5, int nctas) {
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  double s[2];
+  sum_partials<2>(part5, b, nctas, s);
+  if (threadIdx.x == 0) {
+    KState& k = st[b];
+    const dc rv{s[0], s[1]};
+    const dc rho{k.rho_re, k.rho_im};
+    if (!(rv.re * rv.re + rv.im * rv.im > 0.0) || !dfinite(rv)) {
+      k.status = dfinite(rv) ? KSTATUS_BREAKDOWN : KSTATUS_NONFINITE;
+      k.active = 0;
+      return;
+    }
+    const dc a = ddiv(rho, rv);
+    k.alpha_re = a.re;
+    k.alpha_im = a.im;
+  }
+}
+
+__global__ void k_fin_omega(KState* st, const double* part1, const double* part5, int nctas) {
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  double s1[1], s5[3];
+  sum_partials<1>(part1, b, nctas, s1);
+  sum_partials<3>(part5, b, nctas, s5);
+  if (threadIdx.x == 0) {
+    KState& k = st[b];
+    if (s1[0] <= k.tol2 * k.bnorm2) {          // ||s|| small: x += alpha p, r = s
+      k.conv_pending = 1;
+      k.omega_re = 0.0;
+      k.omega_im = 0.0;
+      return;
+    }
+    if (!(s5[2] > 0.0) || !isfinite(s5[2]) || !isfinite(s5[0])) {
+      k.status = isfinite(s5[2]) ? KSTATUS_BREAKDOWN : KSTATUS_NONFINITE;
+      k.active = 0;
+      return;
+    }
+    k.omega_re = s5[0] / s5[2];
+    k.omega_im = s5[1] / s5[2];
+  }
+}
+
+// xs += alpha p + omega s ;  r = s - omega t ; partials <rhat, r>, ||r||^2
+__global__ void k_update(const KState* __restrict__ st, float2* __restrict__ xs, float2* __restrict__ r,
+                         const float2* __restrict__ p, const float2* __restrict__ sv,
+                         const float2* __restrict__ tv, const float2* __restrict__ rhat, size_t N,
+                         double* __restrict__ partu) {
+  const int b = blockIdx.y;
+  if (!st[b].active) return;
+  const float2 alpha = make_float2((float)st[b].alpha_re, (float)st[b].alpha_im);
+  const float2 omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
+  const float2 nomega = make_float2(-omega.x, -omega.y);
+  const size_t off = (size_t)b * N;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = off + i;
+    const float2 s = sv[j];
+    float2 x = xs[j];
+    x = caxpy(alpha, p[j], x);
+    x = caxpy(omega, s, x);
+    xs[j] = x;
+    const float2 rn = caxpy(nomega, tv[j], s);
+    r[j] = rn;
+    const float2 d = cmulc(rhat[j], rn);
+    a0 += d.x;
+    a1 += d.y;
+    a2 += cabs2(rn);
+  }
+  __shared__ double scratch[32 * 3];
+  double v[3] = {a0, a1, a2}, out[3];
+  block_sum<3>(v, scratch, out);
+  if (threadIdx.x == 0) {
+    double* q = partu + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+    q[0] = out[0];
+    q[1] = out[1];
+    q[2] = out[2];
+  }
+}
+
+__global__ void k_fin_rho(KState* st, const double* partu, int nctas, int maxit, int* nactive) {
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  double s[3];
+  sum_partials<3>(partu, b, nctas, s);
+  if (threadIdx.x == 0) {
+    KState& k = st[b];
+    k.iters += 1;
+    k.rnorm2 = s[2];
+    const dc rho_new{s[0], s[1]};
+    if (!isfinite(s[2]) || !dfinite(rho_new)) {
+      k.status = KSTATUS_NONFINITE;
+      k.active = 0;
+    } else if (k.conv_pending || s[2] <= k.tol2 * k.bnorm2) {
+      k.status = KSTATUS_CONVERGED;
+      k.active = 0;
+    } else if (k.iters >= maxit) {
+      k.status = KSTATUS_MAXIT;
+      k.active = 0;
+    } else {
+      const dc rho{k.rho_re, k.rho_im};
+      const dc alpha{k.alpha_re, k.alpha_im}, omega{k.omega_re, k.omega_im};
+      if (!(rho.re * rho.re + rho.im * rho.im > 0.0) || !(omega.re * omega.re + omega.im * omega.im > 0.0)) {
+        k.status = KSTATUS_BREAKDOWN;
+        k.active = 0;
+      } else {
+        const dc beta = dmul(ddiv(rho_new, rho), ddiv(alpha, omega));
+        k.beta_re = beta.re;
+        k.beta_im = beta.im;
+        k.rho_re = rho_new.re;
+        k.rho_im = rho_new.im;
+      }
+    }
+    if (k.active) atomicAdd(nactive, 1);
+  }
+}
+
+MQ_D float2 incident_at(const float2* tab, int l, int n, size_t i) {
+  const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
+  const float2* t = tab + (size_t)l * 3 * n;
+  return cmul(cmul(t[x], t[n + y]), t[2 * n + z]);
+}
+
+__global__ void k_init_uin(float2* u, const float2* tab, const int* illum, int n, size_t N) {
+  const int b = blockIdx.y;
+  const int l = illum[b];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    u[(size_t)b * N + i] = incident_at(tab, l, n, i);
+}
+
+// Detector of the LS field: usc = (u - u_in) on z = n-1; r_det = usc - y (or usc if y == NULL).
+__global__ void k_detect_ls(const float2* u, const float2* tab, const int* illum, const float2* ymeas,
+                            float2* out, int n, size_t N, double* part) {
+  const int b = blockIdx.y;
+  const int l = illum[b];
+  const size_t M = (size_t)n * n;
+  const size_t base = (size_t)(n - 1) * M;
+  float acc = 0.f;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < M; j += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = base + j;
+    float2 r = csub(u[(size_t)b * N + i], incident_at(tab, l, n, i));
+    if (ymeas) r = csub(r, ymeas[(size_t)l * M + j]);
+    out[(size_t)b * M + j] = r;
+    acc += cabs2(r);
+  }
+  __shared__ double scratch[32];
+  double v[1] = {acc}, o[1];
+  block_sum<1>(v, scratch, o);
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = o[0];
+}
+
+// grad[i] (+)= scale * sum_b Re(conj(u_b[i]) z_b[i]); u_b = u_in(l_b) when u == NULL (Born).
+__global__ void k_grad(const float2* __restrict__ u, const float2* __restrict__ zsol, const float2* tab,
+                       const int* illum, int nb, int n, size_t N, float scale, float* grad, int accumulate) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < nb; ++b) {
+      const float2 uu = u ? u[(size_t)b * N + i] : incident_at(tab, illum[b], n, i);
+      const float2 zz = zsol[(size_t)b * N + i];
+      acc = fmaf(uu.x, zz.x, fmaf(uu.y, zz.y, acc));
+    }
+    const float g = scale * acc;
+    grad[i] = accumulate ? grad[i] + g : g;
+  }
+}
+
+// Sum of nb*nctas partials (one per CTA) into out[0] (deterministic).
+__global__ void k_sum_all(const double* part, int count, double* out) {
+  __shared__ double scratch[32];
+  double v[1] = {0.0}, o[1];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) v[0] += part[i];
+  block_sum<1>(v, scratch, o);
+  if (threadIdx.x == 0) out[0] = o[0];
+}
+
+// FP64 dot products of s = a - b (b may be NULL) and m = c - d (d may be NULL):
+// partials of <s,s>, <s,m>, <m,m>.
+__global__ void k_dots3(const float* a, const float* b, const float* c, const float* d, size_t N, double* part) {
+  float ss = 0.f, sm = 0.f, mm = 0.f;
+  double dss = 0.0, dsm = 0.0, dmm = 0.0;
+  int cnt = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const float s = b ? a[i] - b[i] : a[i];
+    const float m = c ? (d ? c[i] - d[i] : c[i]) : 0.f;
+    ss = fmaf(s, s, ss);
+    sm = fmaf(s, m, sm);
+    mm = fmaf(m, m, mm);
+    if (++cnt == 16) {
+      dss += ss; dsm += sm; dmm += mm;
+      ss = sm = mm = 0.f;
+      cnt = 0;
+    }
+  }
+  dss += ss; dsm += sm; dmm += mm;
+  __shared__ double scratch[32 * 3];
+  double v[3] = {dss, dsm, dmm}, o[3];
+  block_sum<3>(v, scratch, o);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x * 3 + 0] = o[0];
+    part[blockIdx.x * 3 + 1] = o[1];
+    part[blockIdx.x * 3 + 2] = o[2];
+  }
+}
+__global__ void k_sum3(const double* part, int nctas, double* out) {
+  double s[3];
+  sum_partials<3>(part, 0, nctas, s);
+  if (threadIdx.x == 0) {
+    out[0] = s[0];
+    out[1] = s[1];
+    out[2] = s[2];
+  }
+}
+
+__global__ void k_scale_real(const float* a, float* out, size_t N, float s) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a[i] * s;
+}
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return set_cuda_error(h, e_, #call); \
+  } while (0)
+
+cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
+  c.ev = profile_slot(h, c.nb);
+  return green_launch(c, s);
+}
+
+GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
+  GreenCall c;
+  c.n = h->n;
+  c.nb = nb;
+  c.adjoint = adjoint;
+  c.T1 = h->w.T1;
+  c.T2 = h->w.T2;
+  c.khat = h->khat;
+  c.tw = h->tw;
+  c.st = nullptr;
+  c.part_pro = h->w.part1;
+  c.part_epi = h->w.part5;
+  return c;
+}
+
+// Run BiCGSTAB iterations for the nb slots initialised by k_fin_init.
+int krylov_iterate(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  for (int it = 0; it < h->krylov_maxit; ++it) {
+    GreenCall c = base_call(h, nb, adjoint);
+    c.st = w.st;
+    c.pro = PRO_BICG_P;
+    c.pa.x = x;
+    c.pa.w = w.p;
+    c.pa.r = w.r;
+    c.pa.v = w.v;
+    c.epi = EPI_V;
+    c.ea.out = w.v;
+    c.ea.a = w.p;
+    c.ea.rhat = w.rhat;
+    CK(glaunch(h, c, s));
+    k_fin_alpha<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row);
+    c.pro = PRO_BICG_S;
+    c.pa.w = w.s;
+    c.epi = EPI_T;
+    c.ea.out = w.t;
+    c.ea.a = w.s;
+    CK(glaunch(h, c, s));
+    k_fin_omega<<<nb, 256, 0, s>>>(w.st, w.part1, w.part5, w.ctas_row);
+    k_update<<<dim3(w.ctas_upd, nb), 256, 0, s>>>(w.st, xs, w.r, w.p, w.s, w.t, w.rhat, N, w.partu);
+    CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), s));
+    k_fin_rho<<<nb, 256, 0, s>>>(w.st, w.partu, w.ctas_upd, h->krylov_maxit, w.nactive);
+    CK(cudaGetLastError());
+    if ((it + 1) % h->check_every == 0 || it + 1 == h->krylov_maxit) {
+      CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*w.h_nactive == 0) break;
+    }
+  }
+  return MQNPM_OK;
+}
+
+// Read back slot states; returns the worst status as an mqnpm code.
+int collect_states(mqnpm_handle* h, int nb, int* iters_out, int stride, int offset) {
+  std::vector<KState> ks(nb);
+  cudaError_t e = cudaMemcpyAsync(ks.data(), h->w.st, nb * sizeof(KState), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return set_cuda_error(h, e, "collect_states");
+  int code = MQNPM_OK;
+  for (int b = 0; b < nb; ++b) {
+    if (iters_out) iters_out[b * stride + offset] = ks[b].iters;
+    if (ks[b].status == KSTATUS_NONFINITE) code = MQNPM_ERR_NONFINITE;
+    else if ((ks[b].status == KSTATUS_MAXIT || ks[b].status == KSTATUS_BREAKDOWN) && code == MQNPM_OK)
+      code = MQNPM_ERR_NOT_CONVERGED;
+  }
+  return code;
+}
+
+}  // namespace
+
+// Forward LS solve for nb slots: u = (I - G X)^{-1} u_in.
+static int forward_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int stride, int offset) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  k_init_uin<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->tab, w.illum, h->n, N);
+  CK(cudaMemsetAsync(w.p, 0, nb * N * sizeof(float2), s));
+  CK(cudaMemsetAsync(w.v, 0, nb * N * sizeof(float2), s));
+  GreenCall c = base_call(h, nb, false);
+  c.pro = PRO_BORN;                    // r_0 = u_in - A u_in = G(x u_in)
+  c.pa.x = x;
+  c.pa.tab = h->tab;
+  c.pa.illum = w.illum;
+  c.epi = EPI_INIT;
+  c.ea.out = w.r;
+  c.ea.out2 = w.rhat;
+  CK(glaunch(h, c, s));
+  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, (double)N);
+  CK(cudaGetLastError());
+  int rc = krylov_iterate(h, nb, x, w.u, false);
+  if (rc != MQNPM_OK) return rc;
+  return collect_states(h, nb, iters, stride, offset);
+}
+
+// Adjoint solve for nb slots: z = (I - G^H X)^{-1} G^H S^T r_det.
+static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int stride, int offset) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  CK(cudaMemsetAsync(w.zs, 0, nb * N * sizeof(float2), s));
+  CK(cudaMemsetAsync(w.p, 0, nb * N * sizeof(float2), s));
+  CK(cudaMemsetAsync(w.v, 0, nb * N * sizeof(float2), s));
+  GreenCall c = base_call(h, nb, true);
+  c.pro = PRO_LIFT;
+  c.pa.rdet = w.rdet;
+  c.epi = EPI_INIT;                    // r_0 = b = G^H S^T r_det (start z_0 = 0)
+  c.ea.out = w.r;
+  c.ea.out2 = w.rhat;
+  CK(glaunch(h, c, s));
+  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, 0.0);
+  CK(cudaGetLastError());
+  int rc = krylov_iterate(h, nb, x, w.zs, true);
+  if (rc != MQNPM_OK) return rc;
+  return collect_states(h, nb, iters, stride, offset);
+}
+
+int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad,
+                    double* loss, int* iters, bool want_grad, float2* y_out) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N, M = (size_t)h->M;
+  double total = 0.0;
+  int worst = MQNPM_OK;
+  h->last_iters.assign(2 * nb, 0);
+  for (int c0 = 0; c0 < nb; c0 += h->max_batch) {
+    const int m = std::min(h->max_batch, nb - c0);
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < m; ++b) w.h_illum[b] = illum[c0 + b];
+    CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, s));
+    int* it_chunk = h->last_iters.data() + 2 * c0;
+    float2* det_out = y_out ? y_out + (size_t)c0 * M : w.rdet;
+    const float2* ym = y_out ? nullptr : h->ymeas;
+    // ---- forward field and detector residual
+    if (h->model == MQNPM_MODEL_LS) {
+      int rc = forward_ls(h, m, x, it_chunk, 2, 0);
+      if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
+      if (rc != MQNPM_OK) worst = rc;
+      k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, ym, det_out, h->n, N, w.partd);
+    } else {
+      GreenCall c = base_call(h, m, false);
+      c.pro = PRO_BORN;
+      c.pa.x = x;
+      c.pa.tab = h->tab;
+      c.pa.illum = w.illum;
+      c.epi = EPI_DETECT;
+      c.ea.out2 = det_out;
+      c.ea.ymeas = ym;
+      c.ea.illum = w.illum;
+      c.part_epi = w.partd;
+      CK(glaunch(h, c, s));
+    }
+    CK(cudaGetLastError());
+    k_sum_all<<<1, 256, 0, s>>>(w.partd, m * w.ctas_row, w.dscal);
+    CK(cudaMemcpyAsync(w.h_scal, w.dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!y_out && want_grad) {
+      // ---- adjoint and gradient
+      if (h->model == MQNPM_MODEL_LS) {
+        int rc = adjoint_ls(h, m, x, it_chunk, 2, 1);
+        if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
+        if (rc != MQNPM_OK) worst = rc;
+        k_grad<<<w.ctas_vec, 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, c0 > 0);
+      } else {
+        GreenCall c = base_call(h, m, true);
+        c.pro = PRO_LIFT;
+        c.pa.rdet = w.rdet;
+        c.epi = EPI_PLAIN;
+        c.ea.out = w.zs;
+        CK(glaunch(h, c, s));
+        k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, c0 > 0);
+      }
+      CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(s));
+    total += 0.5 * w.h_scal[0];
+  }
+  if (loss) *loss = scale * total;
+  if (iters) std::memcpy(iters, h->last_iters.data(), 2 * nb * sizeof(int));
+  return worst;
+}
+
+cudaError_t vec_reduce(mqnpm_handle* h, int /*kind*/, const float* a, const float* b, const float* c,
+                       const float* d, double* host_out) {
+  cudaStream_t s = h->stream;
+  const int ctas = h->w.ctas_vec;
+  k_dots3<<<ctas, 256, 0, s>>>(a, b, c, d, h->N, h->w.partu);
+  k_sum3<<<1, 256, 0, s>>>(h->w.partu, ctas, h->w.dscal);
+  cudaError_t e = cudaMemcpyAsync(h->w.h_scal, h->w.dscal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) std::memcpy(host_out, h->w.h_scal, 3 * sizeof(double));
+  return e;
+}
+
+int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, const float* start, int iters,
+                   double* alpha_out) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  float* q = h->vq;   // current unit vector
+  float* a = h->g;    // operator output
+  double d3[3];
+  CK(vec_reduce(h, 0, start, nullptr, nullptr, nullptr, d3));
+  if (!(d3[0] > 0.0)) return set_error(h, MQNPM_ERR_INVALID_ARG, "lipschitz: zero start vector");
+  k_scale_real<<<w.ctas_vec, 256, 0, s>>>(start, q, N, (float)(1.0 / std::sqrt(d3[0])));
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    for (int c0 = 0; c0 < nb; c0 += h->max_batch) {
+      const int m = std::min(h->max_batch, nb - c0);
+      CK(cudaStreamSynchronize(s));
+      for (int b = 0; b < m; ++b) w.h_illum[b] = illum[c0 + b];
+      CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, s));
+      GreenCall c = base_call(h, m, false);
+      c.pro = PRO_BORN;                 // S G (q u_in)
+      c.pa.x = q;
+      c.pa.tab = h->tab;
+      c.pa.illum = w.illum;
+      c.epi = EPI_DETECT;
+      c.ea.out2 = w.rdet;
+      c.ea.ymeas = nullptr;
+      c.ea.illum = w.illum;
+      c.part_epi = w.partd;
+      CK(glaunch(h, c, s));
+      GreenCall c2 = base_call(h, m, true);
+      c2.pro = PRO_LIFT;                // G^H S^T (.)
+      c2.pa.rdet = w.rdet;
+      c2.epi = EPI_PLAIN;
+      c2.ea.out = w.zs;
+      CK(glaunch(h, c2, s));
+      k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, a, c0 > 0);
+      CK(cudaGetLastError());
+    }
+    CK(vec_reduce(h, 0, q, nullptr, a, nullptr, d3));   // <q,q>, <q,a>, <a,a>
+    lam = d3[1] / d3[0];
+    if (!(d3[2] > 0.0)) break;
+    k_scale_real<<<w.ctas_vec, 256, 0, s>>>(a, q, N, (float)(1.0 / std::sqrt(d3[2])));
+  }
+  *alpha_out = lam;
+  return MQNPM_OK;
+}

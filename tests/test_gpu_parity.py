@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written per test): the transforms run in complex64, so the Green's
+apply is held to 2e-6 relative (max-norm); solves run BiCGSTAB to a relative
+residual of 1e-6 in complex64 with FP64 inner products, so gradients are held to
+1e-4 (norm-wise) and losses to 1e-5; the proximal mapping runs in float32 with
+FP64 reductions and is held to 1e-5 (norm-wise) at equal dual iterations.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import physics, wprox as owprox, tv as otv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2307_02043_gb300 import binding  # noqa: E402
+
+DEV = torch.device("cuda:0")
+KB = math.pi / 2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b))))
+
+
+def make_handle(n, kd, subset_of, alpha, **kw):
+    kw.setdefault("max_batch", 4)
+    return binding.MQNPM(n, kd, subset_of, alpha, **kw)
+
+
+def cone(L, deg=30.0):
+    t = math.radians(deg)
+    return np.array([[math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)]
+                     for p in 2 * math.pi * np.arange(L) / L])
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).to(DEV)
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.float32)).to(DEV)
+
+
+# ------------------------------------------------------------- Green's apply
+@pytest.mark.parametrize("n", [8, 12, 16, 24, 32, 48, 64])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_green_apply_matches_oracle(n, adjoint):
+    rng = np.random.default_rng(100 + n)
+    nb = 3
+    v = rng.standard_normal((nb, n, n, n)) + 1j * rng.standard_normal((nb, n, n, n))
+    h = make_handle(n, cone(2), [0, 0], [1.0], max_batch=nb)
+    out = h.green_apply(c64(v).reshape(-1), adjoint=adjoint).cpu().numpy().reshape(nb, n, n, n)
+    kh = physics.green_hat(n, KB)
+    for b in range(nb):
+        ref = physics.green_apply(v[b], kh, adjoint=adjoint)
+        assert relmax(out[b], ref) < 2e-6, (n, b, relmax(out[b], ref))
+    h.close()
+
+
+def test_green_apply_full_size_sampled():
+    """n = 128 (P = 256, the measured size): sampled outputs against the direct sum."""
+    n = 128
+    rng = np.random.default_rng(7)
+    v = np.zeros((n, n, n), dtype=np.complex128)
+    # sparse random support keeps the direct sum cheap and exact
+    idx = rng.integers(0, n, size=(400, 3))
+    v[idx[:, 0], idx[:, 1], idx[:, 2]] = rng.standard_normal(400) + 1j * rng.standard_normal(400)
+    h = make_handle(n, cone(2), [0, 0], [1.0], max_batch=1)
+    out = h.green_apply(c64(v).reshape(-1)).cpu().numpy().reshape(n, n, n)
+    a = (3 / (4 * math.pi)) ** (1 / 3)
+    w0 = physics.self_term(KB)
+    src = np.argwhere(v != 0)
+    vals = v[v != 0]
+    for probe in rng.integers(0, n, size=(12, 3)):
+        d = src - probe[None, :]
+        r = np.sqrt(np.sum(d * d, axis=1).astype(np.float64))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            w = np.exp(1j * KB * r) / (4 * math.pi * r)
+        w[r == 0] = w0
+        ref = KB ** 2 * np.sum(w * vals)
+        assert abs(out[tuple(probe)] - ref) <= 2e-6 * np.max(np.abs(out)) + 1e-6 * abs(ref), probe
+    h.close()
+
+
+# ---------------------------------------------------------------- forward/grad
+def problem(n, model, L=4, batch=2, contrast=None, seed_name="ls32"):
+    w = synth.small(seed_name, n=n, L=L, batch=batch, model=model)
+    if contrast is not None:
+        w = w.with_(contrast_max=contrast)
+    kd = synth.illumination_dirs(w)
+    xt = synth.phantom(w)
+    om = physics.Model(n, kd, model, tol=1e-12)
+    ys = physics.simulate(om, xt, synth.noise_draws(w), w.snr_db)
+    subs = synth.subsets(w)
+    so = np.zeros(w.L, dtype=np.int32)
+    for s, ii in enumerate(subs):
+        so[ii] = s
+    return w, kd, xt, om, ys, subs, so
+
+
+@pytest.mark.parametrize("model", ["ls", "born"])
+@pytest.mark.parametrize("n", [16, 24])
+def test_forward_matches_oracle(model, n):
+    w, kd, xt, om, ys, subs, so = problem(n, model, contrast=0.05)
+    h = make_handle(n, kd, so, [1.0] * w.S, model=model, krylov_tol=1e-7, max_batch=3)
+    illum = [0, 1, 3]
+    y, its = h.forward(f32(xt).reshape(-1), illum)
+    y = y.cpu().numpy()
+    for b, l in enumerate(illum):
+        ref = om.forward(xt, l)
+        assert rel(y[b], ref) < 2e-5, (model, l, rel(y[b], ref), its)
+    h.close()
+
+
+@pytest.mark.parametrize("model", ["ls", "born"])
+@pytest.mark.parametrize("n,nb,max_batch", [(16, 2, 2), (24, 3, 2), (32, 2, 2)])
+def test_grad_batch_matches_oracle(model, n, nb, max_batch):
+    w, kd, xt, om, ys, subs, so = problem(n, model, L=6, batch=3)
+    h = make_handle(n, kd, so, [1.0] * w.S, model=model, krylov_tol=1e-6, max_batch=max_batch)
+    h.set_measurements(c64(ys).reshape(-1))
+    x = 0.7 * xt
+    illum = list(range(nb))
+    scale = w.S / w.L
+    g, loss, its = h.grad_batch(f32(x).reshape(-1), illum, scale)
+    lo, go = om.batch_loss_grad(x, illum, ys, scale)
+    assert rel(g.cpu().numpy().reshape(go.shape), go) < 1e-4
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    if model == "ls":
+        assert all(a > 0 and b > 0 for a, b in its)
+    h.close()
+
+
+def test_grad_edge_cases():
+    """Zero contrast (Krylov converges at start), zero residual (adjoint RHS 0)."""
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, "ls")
+    h = make_handle(n, kd, so, [1.0] * w.S, krylov_tol=1e-6)
+    zero = np.zeros((n, n, n))
+    ys0 = np.stack([om.forward(zero, l) for l in range(w.L)])   # exact data of x = 0
+    h.set_measurements(c64(ys0).reshape(-1))
+    g, loss, its = h.grad_batch(f32(zero).reshape(-1), [0, 1], 1.0)
+    assert loss == 0.0 and float(g.abs().max()) == 0.0
+    assert its == [(0, 0), (0, 0)]
+    h.close()
+
+
+def test_lipschitz_matches_oracle():
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, "ls")
+    start = synth.power_start(w)
+    ref = om.lipschitz(subs[0], w.S / w.L, start, iters=10)
+    h = make_handle(n, kd, so, [1.0] * w.S)
+    a = h.lipschitz(list(subs[0]), w.S / w.L, f32(start).reshape(-1), iters=10)
+    assert abs(a - ref) <= 1e-5 * ref
+    h.close()
+
+
+# ------------------------------------------------------------ proximal map
+@pytest.mark.parametrize("kind", ["iso", "aniso"])
+@pytest.mark.parametrize("S_eff", [0, 1, 3, 4])
+@pytest.mark.parametrize("n", [8, 24])
+def test_wprox_matches_oracle(kind, S_eff, n):
+    rng = np.random.default_rng(10 * S_eff + n)
+    v = rng.uniform(-0.02, 0.07, (n, n, n))
+    v[n // 4: n // 2, n // 4: 3 * n // 4, :] += 0.03
+    U = rng.standard_normal((S_eff, n, n, n)) * 0.05 if S_eff else None
+    tau, c, J = 1.5, 2e-3, 12
+    P0 = rng.uniform(-0.5, 0.5, (3, n, n, n))
+    xo, Po, info = owprox.wprox(v, tau, U, c, 0.0, 0.05, kind, J, P0=P0, newton_tol=1e-6)
+    h = make_handle(n, cone(2), [0, 0], [1.0], tv=kind, box=(0.0, 0.05), dual_iters=J, newton_tol=1e-6)
+    Pw = f32(P0).reshape(-1).clone()
+    xg = h.wprox(f32(v).reshape(-1), tau, None if U is None else f32(U).reshape(-1), c, P_warm=Pw)
+    assert rel(xg.cpu().numpy().reshape(xo.shape), xo) < 1e-5, rel(xg.cpu().numpy().reshape(xo.shape), xo)
+    assert rel(Pw.cpu().numpy().reshape(Po.shape), Po) < 1e-4
+    h.close()
