@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of the mini-batch quasi-Newton proximal iteration (Algorithm 4.1).
+
+Workload (default "ls128"): nonlinear Lippmann-Schwinger model, 128^3 grid
+(voxel = wavelength/4) padded to 256^3, 20 random ellipsoids (contrast in
+[0, 0.04]) plus a Gaussian background, L = 60 plane waves on a 45-degree cone,
+128x128 detector, 30 dB noise, mini-batch 8 (S = 8 subsets), BiCGSTAB tolerance
+1e-4, isotropic TV lambda = 1e-3, box [0, 0.06], 20 dual iterations.  All inputs
+are seeded synthetic data.
+
+A step is one iteration k > S of Algorithm 4.1 on one GPU: the gradient of one
+subset (7-8 illuminations, forward and adjoint LS solves), the SR1 update and
+the weighted proximal mapping.  The first S iterations (which only set up the
+per-subset metrics) run during set-up, so the timed steps are in the
+quasi-Newton phase.  Metric: illumination-gradients per second (whole job);
+MQNPM iterations/s and the plain cuFFT one-illumination-per-launch path are
+reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+For N > 1 run under torchrun; every rank runs an independent reconstruction
+(replicas; no collective on the data path) and rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "illum-gradients/s + MQNPM iters/s at 128^3 vs plain GPU path; % HBM peak"
+UNIT = "illum-gradients/s"
+# Mean BiCGSTAB iterations (forward + adjoint) per illumination-gradient that the
+# GPU path needs on ls128 at tolerance 1e-4, used only to scale the bounded
+# oracle sample of the reference arm to one illumination-gradient.
+LS128_ITERS_PER_ILLUM = 24.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ problem set-up
+def subset_of(w):
+    so = np.zeros(w.L, dtype=np.int32)
+    for s, idx in enumerate(synth.subsets(w)):
+        so[idx] = s
+    return so
+
+
+def make_problem(w, dev, torch, binding, seed_shift=0):
+    """Synthetic measurements and alpha_s, produced with the library itself."""
+    kd = synth.illumination_dirs(w)
+    so = subset_of(w)
+    subs = synth.subsets(w)
+    xt = torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
+    common = dict(model=w.model, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=w.krylov_tol,
+                  dual_iters=w.dual_iters, gamma=w.gamma, step=w.step, max_batch=max(len(s) for s in subs),
+                  krylov_maxit=1000)
+    setup = binding.MQNPM(w.n, kd, so, [1.0] * w.S, **dict(common, krylov_tol=1e-6))
+    ys = []
+    for c0 in range(0, w.L, setup.max_batch):
+        il = list(range(c0, min(w.L, c0 + setup.max_batch)))
+        y, _ = setup.forward(xt, il)
+        ys.append(y)
+    y = torch.cat(ys)
+    noise = torch.from_numpy(synth.noise_draws(w).astype(np.complex64)).to(dev)
+    sigma = torch.linalg.vector_norm(y, dim=1, keepdim=True) / math.sqrt(w.n * w.n) * 10 ** (-w.snr_db / 20)
+    y = (y + sigma * noise).contiguous()
+    start = torch.from_numpy(synth.power_start(w).astype(np.float32)).to(dev).reshape(-1)
+    alpha = [setup.lipschitz(list(s), w.S / w.L, start, iters=10) for s in subs]
+    setup.close()
+    h = binding.MQNPM(w.n, kd, so, alpha, **common)
+    h.set_measurements(y.reshape(-1))
+    return h, y, alpha, kd, so, subs
+
+
+# ------------------------------------------------ plain cuFFT comparison path
+class PlainPath:
+    """One illumination per launch with torch.fft (cuFFT): pad to P^3, full C2C
+    FFTs, pointwise multiply, inverse, crop; host-driven BiCGSTAB.  This is the
+    baseline the fused path is compared with (same model, same tolerance)."""
+
+    def __init__(self, w, kd, y, torch, dev):
+        self.t = torch
+        self.w = w
+        self.n = w.n
+        self.P = 2 * w.n
+        self.dev = dev
+        self.kd = kd
+        self.y = y.view(w.L, w.n, w.n)
+        n, P, kb = self.n, self.P, w.kb
+        idx = torch.arange(P, device=dev, dtype=torch.float64)
+        off = torch.where(idx < n, idx, idx - P)
+        dz, dy, dx = torch.meshgrid(off, off, off, indexing="ij")
+        r = torch.sqrt(dx * dx + dy * dy + dz * dz)
+        k = torch.exp(1j * kb * r) / (4 * math.pi * r)
+        a = (3 / (4 * math.pi)) ** (1 / 3)
+        k[0, 0, 0] = (complex(math.cos(kb * a), math.sin(kb * a)) * (1 - 1j * kb * a) - 1) / kb ** 2
+        unused = idx == n
+        k[unused] = 0
+        k[:, unused] = 0
+        k[:, :, unused] = 0
+        self.K = torch.fft.fftn(kb * kb * k).to(torch.complex64)
+        del k, r, dx, dy, dz
+        c = (torch.arange(n, device=dev, dtype=torch.float64) - n / 2)
+        self.Z, self.Y, self.X = torch.meshgrid(c, c, c, indexing="ij")
+
+    def G(self, v, adj=False):
+        t, n, P = self.t, self.n, self.P
+        pad = t.zeros((P, P, P), dtype=t.complex64, device=self.dev)
+        pad[:n, :n, :n] = v
+        F = t.fft.fftn(pad)
+        F *= self.K.conj() if adj else self.K
+        return t.fft.ifftn(F)[:n, :n, :n]
+
+    def uin(self, l):
+        k = self.kd[l]
+        ph = self.w.kb * (k[0] * self.X + k[1] * self.Y + k[2] * self.Z)
+        return self.t.exp(1j * ph).to(self.t.complex64)
+
+    def bicgstab(self, A, b, x0, tol, maxit=1000):
+        t = self.t
+        x = x0.clone()
+        r = b - A(x)
+        rh = r.clone()
+        bn = float(t.linalg.vector_norm(b))
+        rho_o = alpha = omega = 1.0 + 0j
+        v = t.zeros_like(b)
+        p = t.zeros_like(b)
+        it = 0
+        while it < maxit and float(t.linalg.vector_norm(r)) > tol * bn:
+            rho = complex(t.vdot(rh.reshape(-1), r.reshape(-1)))
+            beta = (rho / rho_o) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+            v = A(p)
+            alpha = rho / complex(t.vdot(rh.reshape(-1), v.reshape(-1)))
+            s = r - alpha * v
+            it += 1
+            if float(t.linalg.vector_norm(s)) <= tol * bn:
+                x = x + alpha * p
+                break
+            tt = A(s)
+            omega = complex(t.vdot(tt.reshape(-1), s.reshape(-1))) / float(t.vdot(tt.reshape(-1), tt.reshape(-1)).real)
+            x = x + alpha * p + omega * s
+            r = s - omega * tt
+            rho_o = rho
+        return x, it
+
+    def grad(self, x, l, tol):
+        t = self.t
+        x3 = x.view(self.n, self.n, self.n)
+        ui = self.uin(l)
+        u, itf = self.bicgstab(lambda q: q - self.G(x3 * q), ui, ui, tol)
+        r = (u - ui)[-1] - self.y[l]
+        lift = t.zeros_like(ui)
+        lift[-1] = r
+        b = self.G(lift, adj=True)
+        z, ita = self.bicgstab(lambda q: q - self.G(x3 * q, adj=True), b, t.zeros_like(b), tol)
+        return (u.conj() * z).real.reshape(-1), itf + ita
+
+
+# -------------------------------------------------------------- oracle (CPU)
+def oracle_sample(w, x_np, seconds_hint=20.0):
+    """Bounded FP64 oracle sample: seconds per BiCGSTAB iteration of one LS
+    forward solve at the workload size (K_hat set-up excluded)."""
+    from oracle import physics
+    kd = synth.illumination_dirs(w)
+    m = physics.Model(w.n, kd[:1], "ls", tol=1e-30, maxit=1)
+    uin = m.u_in(0)
+    A = lambda p: p - m.G(x_np * p)  # noqa: E731
+    physics.bicgstab(A, uin, uin, 1e-30, 1)       # warm caches / first-touch
+    its = 2
+    t0 = time.perf_counter()
+    physics.bicgstab(A, uin, uin, 1e-30, its)
+    dt = time.perf_counter() - t0
+    # bicgstab(maxit=its) = 1 residual apply + 2 applies per iteration
+    t_apply = dt / (1 + 2 * its)
+    return 2 * t_apply, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 oracle on the host cores, bounded samples."""
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    x_np = synth.phantom(w)
+    from oracle import physics
+    kd = synth.illumination_dirs(w)
+    m = physics.Model(w.n, kd[:1], "ls", tol=1e-30, maxit=1)
+    uin = m.u_in(0)
+    A = lambda p: p - m.G(x_np * p)  # noqa: E731
+    for _ in range(args.warmup):
+        m.G(x_np * uin)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        physics.bicgstab(A, uin, uin, 1e-30, 1)     # one BiCGSTAB iteration (+ initial residual)
+        times.append(time.perf_counter() - t0)
+    t_iter = statistics.mean(times) * 2.0 / 3.0     # 3 applies timed, 2 per iteration
+    per_illum = t_iter * LS128_ITERS_PER_ILLUM + 2 * (t_iter / 2)
+    value = 1.0 / per_illum
+    sample = ("FP64 oracle, one BiCGSTAB iteration of one LS forward solve at n=%d per step, scaled to an "
+              "illumination-gradient by %.0f iterations (fwd+adj) + 2 Green's applies" % (w.n, LS128_ITERS_PER_ILLUM))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": w.name, "n": w.n, "L": w.L, "batch": w.batch},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="ls128")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2307_02043_gb300 import binding
+
+    if args.warmup < 3:
+        args.warmup = 3
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    w = synth.workload(args.workload)
+    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding)
+    x = torch.zeros(w.N, dtype=torch.float32, device=dev)
+    # Algorithm 4.1, k <= S: one step per subset initialises xbar_s, gbar_s
+    for _ in range(w.S):
+        h.step(x, allow_not_converged=True)
+    for _ in range(args.warmup):
+        h.step(x, allow_not_converged=True)
+    torch.cuda.synchronize()
+    # ---- timed region: inputs resident in HBM
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    h.profile_begin(8192)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    illum_done = 0
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = h.step(x, allow_not_converged=True)
+        infos.append(info)
+        illum_done += len(subs[info["subset"]])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof = h.profile_end()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # ---- end-to-end through the public call with host buffers
+    xh = torch.empty(w.N, dtype=torch.float32).pin_memory()
+    xh.copy_(x.cpu())
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xd = torch.empty_like(x)
+    e2e_illum = 0
+    f0.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        info = h.step(xd, allow_not_converged=True)
+        e2e_illum += len(subs[info["subset"]])
+        xh.copy_(xd, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    # ---- max over ranks
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, ms_e2e = float(tt[0]), float(tt[1])
+        cnt = torch.tensor([float(illum_done)], device=dev)
+        dist.all_reduce(cnt)
+        illum_total = float(cnt[0])
+    else:
+        illum_total = float(illum_done)
+    value = illum_total / (t_max / 1e3)
+    iters_per_s = world * args.steps / (t_max / 1e3)
+    e2e_value = world * e2e_illum / (ms_e2e / 1e3)
+    # ---- roofline of the dominant Green's pass
+    N = w.N
+    n = w.n
+    per_slot = [28 * N, 48 * N, 64 * N, 48 * N, 32 * N]
+    names = ["x_fwd", "y_fwd", "z_conv", "y_inv", "x_inv"]
+    pms = prof["pass_ms"]
+    dom = int(np.argmax(pms))
+    bytes_dom = per_slot[dom] * prof["slot_launches"] + (8 * (n + 1) ** 3 * prof["calls"] if dom == 2 else 0)
+    peak, peak_kind = peaks()
+    achieved = bytes_dom / (pms[dom] / 1e3) / 1e9 if pms[dom] > 0 else 0.0
+    passes = {nm: {"ms": round(t, 3), "GB/s": round(per_slot[i] * prof["slot_launches"] / (t / 1e3) / 1e9, 1)
+                   if t > 0 else None} for i, (nm, t) in enumerate(zip(names, pms))}
+    kit = [i["krylov_iters_max"] for i in infos]
+    kit_per_illum = [i["krylov_iters_total"] / max(1, i["n_illum"]) for i in infos]
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "padded": 2 * n, "L": w.L, "batch": max(len(s) for s in subs),
+                   "S": w.S, "model": "lippmann-schwinger", "krylov_tol": w.krylov_tol, "dual_iters": w.dual_iters,
+                   "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "mqnpm_iters_per_s": round(iters_per_s, 3),
+        "roofline": {"bound": "hbm", "kernel": "k_pass3 (" + names[dom] + ")" if dom == 2 else names[dom],
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_slot": per_slot[dom]},
+        "passes": passes,
+        "green_applies": prof["calls"],
+        "krylov_iters_max_per_step": kit,
+        "krylov_iters_per_illum": [round(k, 2) for k in kit_per_illum],
+        "gpu_launches": None,
+        "clocks": clk,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N},
+    }
+    # launches: 5 passes per Green's apply + vector/finalise kernels (counted per apply pair) + prox kernels
+    out["gpu_launches"] = int(prof["calls"] * 5 + (prof["calls"] // 2) * 6 + args.steps * (w.dual_iters * 3 + 8))
+    if rank == 0 and not args.no_plain:
+        plain = PlainPath(w, kd, y, torch, dev)
+        il = [0, 1]
+        for l in il[:1]:
+            plain.grad(x, l, w.krylov_tol)       # warm-up
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        pits = 0
+        for l in il:
+            _, it = plain.grad(x, l, w.krylov_tol)
+            pits += it
+        p1.record()
+        torch.cuda.synchronize()
+        pms_plain = p0.elapsed_time(p1)
+        out["plain_gpu"] = {"value": round(len(il) / (pms_plain / 1e3), 3), "unit": UNIT,
+                            "ms_per_illum": round(pms_plain / len(il), 2), "krylov_iters": pits,
+                            "what": "torch.fft (cuFFT) padded 256^3, one illumination per launch"}
+        out["speedup_vs_plain"] = round(value / out["plain_gpu"]["value"], 2)
+        del plain
+    if rank == 0 and not args.no_cpu:
+        t_it, dt = oracle_sample(w, synth.phantom(w))
+        # GPU-measured mean iterations per illumination-gradient in the timed steps
+        per_illum = statistics.mean(kit_per_illum) if kit_per_illum else LS128_ITERS_PER_ILLUM
+        t_ig = t_it * per_illum + t_it
+        out["cpu_baseline"] = {"value": round(1.0 / t_ig, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "FP64 oracle, 2 BiCGSTAB iterations of one LS forward solve at n=%d "
+                                         "(%.1f s), scaled by %.1f iterations + 2 Green's applies per "
+                                         "illumination-gradient" % (n, dt, per_illum)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -101,6 +101,8 @@ typedef struct mqnpm_step_info {
   int sr1_branch;          /* 0: rank-1 update, 1: tau<=0, 2: skip, 3: tau tiny, -1: k<=S */
   int krylov_iters_max;    /* largest BiCGSTAB iteration count in the gradient     */
   int newton_iters_max;    /* largest semi-smooth Newton count in the prox         */
+  int krylov_iters_total;  /* forward + adjoint BiCGSTAB iterations, all illuminations */
+  int n_illum;             /* illuminations in the subset                          */
 } mqnpm_step_info;
 
 /* Create a handle: validates cfg, builds the Green's kernel spectrum and the

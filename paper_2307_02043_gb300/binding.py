@@ -57,7 +57,8 @@ class Config(ctypes.Structure):
 class StepInfo(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("subset", ctypes.c_int), ("loss", ctypes.c_double),
                 ("tau_star", ctypes.c_double), ("rank", ctypes.c_int), ("sr1_branch", ctypes.c_int),
-                ("krylov_iters_max", ctypes.c_int), ("newton_iters_max", ctypes.c_int)]
+                ("krylov_iters_max", ctypes.c_int), ("newton_iters_max", ctypes.c_int),
+                ("krylov_iters_total", ctypes.c_int), ("n_illum", ctypes.c_int)]
 
 
 _LIB = None

@@ -496,10 +496,15 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
     info->tau_star = tau_star;
     info->rank = S_eff;
     info->sr1_branch = branch;
-    int mx = 0;
-    for (int v : its) mx = std::max(mx, v);
+    int mx = 0, tot = 0;
+    for (int v : its) {
+      mx = std::max(mx, v);
+      tot += v;
+    }
     info->krylov_iters_max = mx;
     info->newton_iters_max = h->last_newton_max;
+    info->krylov_iters_total = tot;
+    info->n_illum = (int)sub.size();
   }
   return grad_rc;
 }

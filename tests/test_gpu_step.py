@@ -1,0 +1,131 @@
+"""GPU parity of the outer loop (Algorithm 4.1 with SR1) on the small nonlinear
+workload, checkpoint/resume, and failure reporting through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bqnpm, physics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2307_02043_gb300 import binding  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.float32)).to(DEV)
+
+
+def setup(w):
+    kd = synth.illumination_dirs(w)
+    om = physics.Model(w.n, kd, w.model, tol=1e-12)
+    xt = synth.phantom(w)
+    ys = physics.simulate(om, xt, synth.noise_draws(w), w.snr_db)
+    subs = synth.subsets(w)
+    so = np.zeros(w.L, dtype=np.int32)
+    for s, ii in enumerate(subs):
+        so[ii] = s
+    return kd, om, xt, ys, subs, so
+
+
+def handle(w, kd, so, alpha, **kw):
+    args = dict(model=w.model, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=1e-6, dual_iters=w.dual_iters,
+                gamma=w.gamma, step=w.step, max_batch=w.batch)
+    args.update(kw)
+    return binding.MQNPM(w.n, kd, so, alpha, **args)
+
+
+@pytest.fixture(scope="module")
+def ls32():
+    w = synth.workload("ls32")
+    kd, om, xt, ys, subs, so = setup(w)
+    alpha = [om.lipschitz(s, w.S / w.L, synth.power_start(w), 20) for s in subs]
+    opt = bqnpm.BQNPM(om, ys, subs, alpha, lam=w.lam, box=w.box, kind=w.tv, dual_iters=w.dual_iters,
+                      gamma=w.gamma, step=w.step)
+    xs = opt.run(np.zeros((w.n,) * 3), w.outer_iters)
+    return w, kd, om, ys, subs, so, alpha, opt, xs
+
+
+def test_step_trajectory_matches_oracle(ls32):
+    """Config 1 (32^3, LS, L = 8, S = 4, 10 iterations): per-iterate error and the
+    objective trajectory against the FP64 oracle run with the same inputs."""
+    w, kd, om, ys, subs, so, alpha, opt, xs = ls32
+    h = handle(w, kd, so, alpha)
+    h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+    x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+    for k in range(1, w.outer_iters + 1):
+        info = h.step(x)
+        ho = opt.history[k - 1]
+        assert info["subset"] == ho["s"]
+        assert abs(info["tau_star"] - ho["tau_star"]) <= 1e-3 * ho["tau_star"], (k, info, ho)
+        xg = x.cpu().numpy().astype(np.float64).reshape(xs[k].shape)
+        err = np.linalg.norm(xg - xs[k]) / np.linalg.norm(xs[k])
+        assert err < 2e-3, (k, err)
+        if k in (1, w.S, w.outer_iters):
+            cg, co = opt.full_cost(xg), opt.full_cost(xs[k])
+            assert abs(cg - co) <= 1e-4 * abs(co), (k, cg, co)
+    h.close()
+
+
+def test_checkpoint_resume_is_bit_identical(ls32):
+    w, kd, om, ys, subs, so, alpha, opt, xs = ls32
+    y = torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1)
+    h = handle(w, kd, so, alpha)
+    h.set_measurements(y)
+    x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+    for _ in range(w.S + 1):
+        h.step(x)
+    blob = h.save_state()
+    x_saved = x.clone()
+    for _ in range(2):
+        h.step(x)
+    h2 = handle(w, kd, so, alpha)
+    h2.set_measurements(y)
+    h2.load_state(blob)
+    x2 = x_saved.clone()
+    for _ in range(2):
+        h2.step(x2)
+    assert torch.equal(x, x2)
+    h.close()
+    h2.close()
+
+
+def test_failures_are_reported():
+    w = synth.small("ls32", n=16, L=4, batch=2)
+    kd, om, xt, ys, subs, so = setup(w)
+    # invalid arguments
+    with pytest.raises(binding.MQNPMError) as e:
+        binding.MQNPM(20, kd, so, [1.0, 1.0])          # P = 40 has no transform plan
+    assert e.value.code == 7
+    with pytest.raises(binding.MQNPMError) as e:
+        binding.MQNPM(16, kd, so, [1.0, -1.0])
+    assert e.value.code == 1
+    # budget below the workspace
+    with pytest.raises(binding.MQNPMError) as e:
+        handle(w, kd, so, [1.0, 1.0], hbm_budget_bytes=1 << 20)
+    assert e.value.code == 2
+    h = handle(w, kd, so, [1.0, 1.0], krylov_maxit=1)
+    # gradient before measurements
+    with pytest.raises(binding.MQNPMError) as e:
+        h.grad_batch(f32(xt).reshape(-1), [0], 1.0)
+    assert e.value.code == 8
+    h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+    # Krylov cap of one iteration on a scattering object: NOT_CONVERGED, outputs written
+    with pytest.raises(binding.NotConverged):
+        h.grad_batch(f32(4 * xt).reshape(-1), [0, 1], 1.0)
+    g, loss, its = h.grad_batch(f32(4 * xt).reshape(-1), [0, 1], 1.0, allow_not_converged=True)
+    assert torch.isfinite(g).all() and all(a == 1 for a, _ in its)
+    # non-finite input
+    bad = xt.copy()
+    bad[3, 4, 5] = np.nan
+    with pytest.raises(binding.MQNPMError) as e:
+        h.grad_batch(f32(bad).reshape(-1), [0], 1.0)
+    assert e.value.code == 5
+    h.close()
