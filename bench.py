@@ -46,6 +46,8 @@ UNIT = "illum-gradients/s"
 # GPU path needs on ls128 at tolerance 1e-4, used only to scale the bounded
 # oracle sample of the reference arm to one illumination-gradient.
 LS128_ITERS_PER_ILLUM = 24.0
+# Iterations of Algorithm 4.1 from x0 = 0 completed when the timed steps end.
+SETUP_ITERS = 38
 
 
 def peaks():
@@ -277,6 +279,30 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def green_only(args, torch, binding):
+    """Batched Green's applies on the workload grid (a small case for profiler
+    captures): prints per-pass times and achieved GB/s as one JSON line."""
+    w = synth.workload(args.workload)
+    dev = torch.device("cuda", 0)
+    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, max_batch=args.batch)
+    g = torch.Generator(device=dev).manual_seed(0)
+    v = torch.randn(args.batch * w.N, dtype=torch.complex64, device=dev, generator=g)
+    for _ in range(args.warmup):
+        h.green_apply(v)
+    h.profile_begin(args.steps)
+    for _ in range(args.steps):
+        h.green_apply(v)
+    prof = h.profile_end()
+    N = w.N
+    per_slot = [24 * N, 48 * N, 64 * N, 48 * N, 24 * N]   # plain prologue/epilogue
+    slots = prof["slot_launches"]
+    res = {"workload": w.name, "batch": args.batch, "applies": prof["calls"],
+           "pass_ms": [round(t / prof["calls"], 4) for t in prof["pass_ms"]],
+           "pass_GBps": [round(b * slots / (t / 1e3) / 1e9, 1) for b, t in zip(per_slot, prof["pass_ms"])]}
+    print(json.dumps(res), flush=True)
+    h.close()
+
+
 # ---------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -287,6 +313,9 @@ def main():
     ap.add_argument("--workload", default="ls128")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--green-only", action="store_true",
+                    help="small case for profiler captures: batched Green's applies of the workload grid")
+    ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -298,6 +327,10 @@ def main():
     import torch.distributed as dist
     from paper_2307_02043_gb300 import binding
 
+    if args.green_only:
+        green_only(args, torch, binding)
+        return
+
     if args.warmup < 3:
         args.warmup = 3
     torch.cuda.set_device(local)
@@ -307,8 +340,10 @@ def main():
     w = synth.workload(args.workload)
     h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding)
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
-    # Algorithm 4.1, k <= S: one step per subset initialises xbar_s, gbar_s
-    for _ in range(w.S):
+    # Set-up iterations from x0 = 0: the S initial steps of Algorithm 4.1 and the
+    # reconstruction up to iteration SETUP_ITERS, so that the warm-up and timed
+    # steps sit where the paper's BQNPM-I reached ASPM's best SNR (38 iterations).
+    for _ in range(max(w.S, SETUP_ITERS - args.warmup - args.steps)):
         h.step(x, allow_not_converged=True)
     for _ in range(args.warmup):
         h.step(x, allow_not_converged=True)
@@ -324,6 +359,12 @@ def main():
     torch.cuda.synchronize()
     illum_done = 0
     infos = []
+    launches0 = h.launch_count
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    try:
+        nvtx.range_push("timed")
+    except Exception:
+        nvtx = None
     e0.record(stream)
     for _ in range(args.steps):
         info = h.step(x, allow_not_converged=True)
@@ -331,6 +372,10 @@ def main():
         illum_done += len(subs[info["subset"]])
     e1.record(stream)
     torch.cuda.synchronize()
+    if nvtx is not None:
+        nvtx.range_pop()
+    launches = h.launch_count - launches0
+    prox_trace = h.prox_trace()
     if world > 1:
         dist.barrier()
     prof = h.profile_end()
@@ -395,14 +440,17 @@ def main():
                      "algorithmic_bytes_per_slot": per_slot[dom]},
         "passes": passes,
         "green_applies": prof["calls"],
+        "phase_ms": {k: round(statistics.mean(i["ms_" + k] for i in infos), 3) for k in ("gradient", "metric", "prox")},
+        "newton_iters_max": [i["newton_iters_max"] for i in infos],
+        "prox_trace_us": prox_trace,
         "krylov_iters_max_per_step": kit,
         "krylov_iters_per_illum": [round(k, 2) for k in kit_per_illum],
         "gpu_launches": None,
         "clocks": clk,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N},
     }
-    # launches: 5 passes per Green's apply + vector/finalise kernels (counted per apply pair) + prox kernels
-    out["gpu_launches"] = int(prof["calls"] * 5 + (prof["calls"] // 2) * 6 + args.steps * (w.dual_iters * 3 + 8))
+    out["gpu_launches"] = int(launches)
+    out["config"]["iterations"] = "k = %d..%d from x0 = 0" % (infos[0]["k"], infos[-1]["k"])
     if rank == 0 and not args.no_plain:
         plain = PlainPath(w, kd, y, torch, dev)
         il = [0, 1]

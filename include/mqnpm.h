@@ -103,6 +103,9 @@ typedef struct mqnpm_step_info {
   int newton_iters_max;    /* largest semi-smooth Newton count in the prox         */
   int krylov_iters_total;  /* forward + adjoint BiCGSTAB iterations, all illuminations */
   int n_illum;             /* illuminations in the subset                          */
+  double ms_gradient;      /* device time of the subset gradient                   */
+  double ms_metric;        /* device time of the SR1 update and quasi-Newton point */
+  double ms_prox;          /* device time of the weighted proximal mapping         */
 } mqnpm_step_info;
 
 /* Create a handle: validates cfg, builds the Green's kernel spectrum and the
@@ -186,6 +189,16 @@ int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size);
  * z-forward*K_hat*z-inverse, y-inverse, x-inverse), the number of recorded
  * applies in *calls and the sum of their batch sizes in *slot_launches, and
  * stops recording. */
+/* Phase trace of the last weighted proximal mapping: out (host, 2*cap
+ * long longs) receives out[1] = start time (ns, GPU global timer) and, for
+ * e = 1..*count, the pair (tag, time) stamped when the e-th grid barrier was
+ * passed (tags: 1 Gram set-up, 2 unweighted x, 3 divergence and U^T d,
+ * 4 Newton evaluation, 5 x after a rejected trial, 6 dual update, 99 end). */
+int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count);
+
+/* Number of CUDA kernels this handle has launched since creation. */
+long long mqnpm_launch_count(const mqnpm_handle* h);
+
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);
 int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls);
 

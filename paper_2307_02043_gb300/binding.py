@@ -58,7 +58,8 @@ class StepInfo(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("subset", ctypes.c_int), ("loss", ctypes.c_double),
                 ("tau_star", ctypes.c_double), ("rank", ctypes.c_int), ("sr1_branch", ctypes.c_int),
                 ("krylov_iters_max", ctypes.c_int), ("newton_iters_max", ctypes.c_int),
-                ("krylov_iters_total", ctypes.c_int), ("n_illum", ctypes.c_int)]
+                ("krylov_iters_total", ctypes.c_int), ("n_illum", ctypes.c_int),
+                ("ms_gradient", ctypes.c_double), ("ms_metric", ctypes.c_double), ("ms_prox", ctypes.c_double)]
 
 
 _LIB = None
@@ -84,6 +85,9 @@ SIGNATURES = {
                                        ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "mqnpm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "mqnpm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "mqnpm_prox_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int)]),
     "mqnpm_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mqnpm_profile_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]),
@@ -217,6 +221,11 @@ class MQNPM:
     def workspace_bytes(self) -> int:
         return int(self.lib.mqnpm_workspace_bytes(self._h))
 
+    @property
+    def launch_count(self) -> int:
+        """Kernels launched by this handle since creation."""
+        return int(self.lib.mqnpm_launch_count(self._h))
+
     # -- calls -------------------------------------------------------------
     def set_measurements(self, y: torch.Tensor):
         _check_cuda(y, torch.complex64, self.L * self.M, "y", self.device)
@@ -303,6 +312,24 @@ class MQNPM:
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._stream()
         self._raise(self.lib.mqnpm_load_state(self._h, buf, len(blob)))
+
+    def prox_trace(self) -> dict:
+        """Time (us) spent per phase tag in the last weighted proximal mapping."""
+        cap = 1024
+        buf = (ctypes.c_longlong * (2 * cap))()
+        cnt = ctypes.c_int()
+        self._stream()
+        self._raise(self.lib.mqnpm_prox_trace(self._h, buf, cap, ctypes.byref(cnt)))
+        names = {1: "gram", 2: "x_plain", 3: "div_UTd", 4: "newton_eval", 5: "x_fixup", 6: "dual_update", 99: "tail"}
+        out = {"barriers": cnt.value - 1, "total_us": 0.0}
+        prev = buf[1]
+        for e in range(1, cnt.value + 1):
+            tag, t = buf[2 * e], buf[2 * e + 1]
+            key = names.get(int(tag), str(tag))
+            out[key] = out.get(key, 0.0) + (t - prev) / 1e3
+            out["total_us"] += (t - prev) / 1e3
+            prev = t
+        return {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
 
     def profile_begin(self, max_calls: int = 4096):
         self._raise(self.lib.mqnpm_profile_begin(self._h, int(max_calls)))

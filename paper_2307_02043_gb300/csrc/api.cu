@@ -83,6 +83,16 @@ cudaEvent_t* profile_slot(mqnpm_handle* h, int nb) {
 
 extern "C" {
 
+int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count) {
+  if (!h || !out || cap < 1 || !count) return MQNPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  const int m = std::min(cap, h->wp.trace_cap);
+  CK(cudaMemcpyAsync(out, h->wp.trace, 2 * (size_t)m * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *count = (int)std::min<long long>(out[0] + 1, m - 1);
+  return MQNPM_OK;
+}
+
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls) {
   if (!h || max_calls < 1) return MQNPM_ERR_INVALID_ARG;
   CK(cudaSetDevice(h->device));
@@ -115,6 +125,8 @@ int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches
 
 const char* mqnpm_last_error(const mqnpm_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
+long long mqnpm_launch_count(const mqnpm_handle* h) { return h ? h->launches : 0; }
+
 size_t mqnpm_workspace_bytes(const mqnpm_handle* h) { return h ? h->bytes : 0; }
 
 int mqnpm_set_stream(mqnpm_handle* h, void* stream) {
@@ -131,6 +143,8 @@ void mqnpm_destroy(mqnpm_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   profile_clear(h);
+  for (cudaEvent_t ev : h->step_ev)
+    if (ev) cudaEventDestroy(ev);
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_nactive) cudaFreeHost(h->w.h_nactive);
   if (h->w.h_illum) cudaFreeHost(h->w.h_illum);
@@ -221,9 +235,8 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   if (h->w.ctas_vec < 1) h->w.ctas_vec = 1;
   if (h->w.ctas_upd < 1) h->w.ctas_upd = 1;
   h->wp.ctas_vec = h->w.ctas_vec;
-  const int per_sm = wprox_coop_blocks_per_sm();
-  if (per_sm <= 0) { delete h; return MQNPM_ERR_CUDA; }
-  h->wp.ctas = nsm * std::min(per_sm, 1);
+  h->wp.nsm = nsm;
+  const int wp_blocks = 2 * nsm;   // the cooperative prox kernel runs at most 2 blocks per SM
 
   // ---- budget (every device allocation of the handle)
   const size_t m1 = (size_t)(n + 1);
@@ -233,7 +246,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   need += B * ((size_t)n * n * P + (size_t)n * P * P) * 8; // T1, T2
   need += B * M * 8;                                       // rdet
   need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
-  need += 9 * N * 4 + (size_t)(h->wp.ctas_vec * 64 + 2 * h->wp.ctas * 44) * 8;     // wprox
+  need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * 44 + wp_blocks * 44 + 200) * 8;   // wprox
   need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
   if (h->budget > 0 && need > h->budget) {
     char msg[160];
@@ -267,11 +280,25 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(w.nactive, 1);
   AL(w.dscal, 64);
   WproxWork& wp = h->wp;
-  AL(wp.R, 3 * N); AL(wp.R2, 3 * N); AL(wp.Pd, 3 * N); AL(wp.d, N); AL(wp.x, N);
-  AL(wp.part, (size_t)wp.ctas_vec * 64 + 2 * (size_t)wp.ctas * 44);
-  AL(wp.scal, (size_t)wprox_scal_count());
-  AL(wp.barrier, 1);
+  AL(wp.R, 3 * N); AL(wp.Pd, 3 * N); AL(wp.d, N); AL(wp.x, N);
+  AL(wp.part, (size_t)wp_blocks * wprox_part_len());
+  AL(wp.tot, (size_t)wprox_part_len());
+  AL(wp.stat, 4);
+  AL(wp.gram, (size_t)wp.ctas_vec * 44);
+  AL(wp.scal, (size_t)woodbury_scal_count());
+  AL(wp.barrier, 2);
   AL(wp.err, 1);
+  wp.trace_cap = 1024;
+  AL(wp.trace, 2 * (size_t)wp.trace_cap);
+  {
+    std::vector<float> mom = wprox_momentum(h->dual_iters);
+    AL(wp.mom, mom.size());
+    wp.mom_len = h->dual_iters;
+    if ((e = cudaMemcpy(wp.mom, mom.data(), mom.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      set_cuda_error(h, e, "momentum table");
+      return fail(MQNPM_ERR_CUDA);
+    }
+  }
   AL(h->xbar, (size_t)h->S * N); AL(h->gbar, (size_t)h->S * N); AL(h->U, (size_t)h->S * N);
   AL(h->g, N); AL(h->vq, N); AL(h->Pwarm, 3 * N);
 #undef AL
@@ -332,6 +359,7 @@ int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int a
   c.part_pro = h->w.part1;
   c.part_epi = h->w.part5;
   c.ev = profile_slot(h, nb);
+  c.launches = &h->launches;
   CK(green_launch(c, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return MQNPM_OK;
@@ -399,7 +427,12 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
   const std::vector<int>& sub = h->subsets[sel];
   double loss = 0.0;
   std::vector<int> its(2 * sub.size());
+  if (!h->step_ev[0]) {
+    for (auto& ev : h->step_ev) CK(cudaEventCreate(&ev));
+  }
+  CK(cudaEventRecord(h->step_ev[0], s));
   int rc = grad_batch_impl(h, x, sub.data(), (int)sub.size(), (double)S / h->L, h->g, &loss, its.data(), true, nullptr);
+  CK(cudaEventRecord(h->step_ev[1], s));
   if (rc != MQNPM_OK && rc != MQNPM_ERR_NOT_CONVERGED) return rc;
   const int grad_rc = rc;
   float* xb = h->xbar + (size_t)sel * N;
@@ -420,6 +453,7 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
     c = h->a * h->lambda;
     k_axpby<<<gr, th, 0, s>>>(x, h->g, (float)(-h->a / h->alpha[sel]), h->vq, N);
     CK(cudaGetLastError());
+    h->launches += 1;
   } else {
     // Algorithm 4.2 on s = x - xbar_s', m = g - gbar_s'
     double d3[3];
@@ -461,6 +495,7 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
       const double den = sm - tau * ss;
       k_sr1_u<<<gr, th, 0, s>>>(x, xb, h->g, gb, (float)tau, (float)(1.0 / std::sqrt(den)), h->U + (size_t)sel * N, N);
       CK(cudaGetLastError());
+      h->launches += 1;
     }
     CK(cudaMemcpyAsync(xb, x, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(gb, h->g, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -475,6 +510,7 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
     if (S_eff == 0) {
       k_axpby<<<gr, th, 0, s>>>(x, h->g, (float)(-h->a * S / tau_star), h->vq, N);
       CK(cudaGetLastError());
+      h->launches += 1;
     } else {
       rc = qn_point_impl(h, x, h->g, up, S_eff, tau_star, h->a * S, h->vq);
       if (rc != MQNPM_OK) return rc;
@@ -484,7 +520,9 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
     // lambda = 0: the proximal map reduces to the box projection under B
     c = 1e-30;
   }
+  CK(cudaEventRecord(h->step_ev[2], s));
   rc = wprox_impl(h, h->vq, tau_star, up, S_eff, c, h->Pwarm, h->have_P, x);
+  CK(cudaEventRecord(h->step_ev[3], s));
   if (rc != MQNPM_OK) return rc;
   h->have_P = true;
   CK(cudaStreamSynchronize(s));
@@ -505,6 +543,14 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
     info->newton_iters_max = h->last_newton_max;
     info->krylov_iters_total = tot;
     info->n_illum = (int)sub.size();
+    float t01 = 0.f, t12 = 0.f, t23 = 0.f;
+    CK(cudaEventSynchronize(h->step_ev[3]));
+    CK(cudaEventElapsedTime(&t01, h->step_ev[0], h->step_ev[1]));
+    CK(cudaEventElapsedTime(&t12, h->step_ev[1], h->step_ev[2]));
+    CK(cudaEventElapsedTime(&t23, h->step_ev[2], h->step_ev[3]));
+    info->ms_gradient = t01;
+    info->ms_metric = t12;
+    info->ms_prox = t23;
   }
   return grad_rc;
 }

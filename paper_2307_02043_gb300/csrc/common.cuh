@@ -127,6 +127,32 @@ MQ_D void block_sum(double (&v)[K], double* scratch, double (&out)[K]) {
   __syncthreads();
 }
 
+// Sum K per-thread float partials over the block: the warp tree runs in FP32
+// (GB300's FP64 rate is a small fraction of its FP32 rate), the per-warp
+// results are combined in FP64 in warp order.  Thread 0 receives out[].
+// scratch: >= 32*K doubles.
+template <int K>
+MQ_D void block_sum_f(const float (&v)[K], double* scratch, double (&out)[K]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float w = warp_sumf(v[k]);
+    if (lane == 0) scratch[warp * K + k] = (double)w;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += scratch[w * K + k];
+    scratch[32 * K + k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = scratch[32 * K + k];
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------ grid barrier
 // Barrier for cooperative launches (all blocks co-resident).  `count` is a
 // monotonically increasing arrival counter zeroed before the launch; `epoch`

@@ -104,5 +104,6 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
   if (c.ev && e == cudaSuccess) cudaEventRecord(c.ev[5], s);
+  if (c.launches) *c.launches += 5;
   return e;
 }

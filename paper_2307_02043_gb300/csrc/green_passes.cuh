@@ -52,11 +52,9 @@ struct Parts {
 template <int K>
 MQ_D void write_partials(const Parts<K>& p, double* partials, int b, int cta, int nctas) {
   if constexpr (K > 0) {
-    __shared__ double scratch[32 * K];
-    double d[K], out[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) d[k] = (double)p.v[k];
-    block_sum<K>(d, scratch, out);
+    __shared__ double scratch[33 * K];
+    double out[K];
+    block_sum_f<K>(p.v, scratch, out);
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < K; ++k) partials[((size_t)b * nctas + cta) * K + k] = out[k];

@@ -25,6 +25,7 @@ struct GreenCall {
   double* part_pro = nullptr;    // [nb][ctas1][NPART]
   double* part_epi = nullptr;    // [nb][ctas5][NPART]
   cudaEvent_t* ev = nullptr;     // optional: 6 events recorded around the 5 passes
+  long long* launches = nullptr; // optional kernel-launch counter (+5 per apply)
 };
 
 // Per-pass timing (opt-in tracing): events recorded around every Green's apply.
@@ -69,12 +70,19 @@ struct Workspace {
 };
 
 struct WproxWork {
-  float *R = nullptr, *R2 = nullptr, *Pd = nullptr, *d = nullptr, *x = nullptr;
-  double* part = nullptr;       // [ctas][NV]
-  double* scal = nullptr;       // device scalars of the proximal solve
-  unsigned* barrier = nullptr;  // grid-barrier counter
+  float *R = nullptr, *Pd = nullptr, *d = nullptr, *x = nullptr;
+  float* mom = nullptr;         // momentum table of the dual iterations (dual_iters)
+  int mom_len = 0;
+  double* part = nullptr;       // [2 * nsm][44] per-block partials of the cooperative kernel
+  double* tot = nullptr;        // [44] reduced totals
+  double* stat = nullptr;       // [4] Newton statistics of the last call
+  double* gram = nullptr;       // partials of the Woodbury Gram pass [ctas_vec][44]
+  double* scal = nullptr;       // Woodbury scalars (G, M, U^T g)
+  unsigned* barrier = nullptr;  // [2]: arrival counter, released generation
   int* err = nullptr;           // device error flag
-  int ctas = 0;                 // CTAs of the cooperative Newton kernel
+  long long* trace = nullptr;   // phase trace of the last call: (tag, ns) per barrier
+  int trace_cap = 0;
+  int nsm = 0;
   int ctas_vec = 0;
 };
 
@@ -109,6 +117,8 @@ struct mqnpm_handle {
   int last_newton_max = 0, last_newton_total = 0;
   int last_status = 0;
   Profiler prof;
+  long long launches = 0;        // kernels launched by this handle since creation
+  cudaEvent_t step_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // phase timing of mqnpm_step
 };
 
 // Record the next profiling group for a Green's apply of nb slots (nullptr when off/full).
@@ -130,8 +140,9 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
                float* P_warm, bool warm, float* x_out);
 int qn_point_impl(mqnpm_handle* h, const float* x, const float* g, const UPtrs& U, int S_eff, double tau,
                   double aS, float* v);
-int wprox_coop_blocks_per_sm();
-int wprox_scal_count();
+std::vector<float> wprox_momentum(int J);
+int wprox_part_len();
+int woodbury_scal_count();
 
 // status helpers (api.cu)
 int set_cuda_error(mqnpm_handle* h, cudaError_t e, const char* where);

@@ -143,9 +143,10 @@ __global__ void k_update(const KState* __restrict__ st, float2* __restrict__ xs,
     a1 += d.y;
     a2 += cabs2(rn);
   }
-  __shared__ double scratch[32 * 3];
-  double v[3] = {a0, a1, a2}, out[3];
-  block_sum<3>(v, scratch, out);
+  __shared__ double scratch[33 * 3];
+  const float v[3] = {a0, a1, a2};
+  double out[3];
+  block_sum_f<3>(v, scratch, out);
   if (threadIdx.x == 0) {
     double* q = partu + ((size_t)b * gridDim.x + blockIdx.x) * 3;
     q[0] = out[0];
@@ -219,9 +220,10 @@ __global__ void k_detect_ls(const float2* u, const float2* tab, const int* illum
     out[(size_t)b * M + j] = r;
     acc += cabs2(r);
   }
-  __shared__ double scratch[32];
-  double v[1] = {acc}, o[1];
-  block_sum<1>(v, scratch, o);
+  __shared__ double scratch[33];
+  const float v[1] = {acc};
+  double o[1];
+  block_sum_f<1>(v, scratch, o);
   if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = o[0];
 }
 
@@ -300,6 +302,7 @@ __global__ void k_scale_real(const float* a, float* out, size_t N, float s) {
 
 cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
   c.ev = profile_slot(h, c.nb);
+  c.launches = &h->launches;
   return green_launch(c, s);
 }
 
@@ -348,6 +351,7 @@ int krylov_iterate(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adj
     CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), s));
     k_fin_rho<<<nb, 256, 0, s>>>(w.st, w.partu, w.ctas_upd, h->krylov_maxit, w.nactive);
     CK(cudaGetLastError());
+    h->launches += 4;   // fin_alpha, fin_omega, update, fin_rho
     if ((it + 1) % h->check_every == 0 || it + 1 == h->krylov_maxit) {
       CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -394,6 +398,7 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   CK(glaunch(h, c, s));
   k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, (double)N);
   CK(cudaGetLastError());
+  h->launches += 2;   // init_uin, fin_init
   int rc = krylov_iterate(h, nb, x, w.u, false);
   if (rc != MQNPM_OK) return rc;
   return collect_states(h, nb, iters, stride, offset);
@@ -416,6 +421,7 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   CK(glaunch(h, c, s));
   k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, 0.0);
   CK(cudaGetLastError());
+  h->launches += 1;
   int rc = krylov_iterate(h, nb, x, w.zs, true);
   if (rc != MQNPM_OK) return rc;
   return collect_states(h, nb, iters, stride, offset);
@@ -479,6 +485,8 @@ int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, d
     }
     CK(cudaStreamSynchronize(s));
     total += 0.5 * w.h_scal[0];
+    // detector (LS) + loss sum + gradient assembly (when requested)
+    h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + 1 + ((!y_out && want_grad) ? 1 : 0);
   }
   if (loss) *loss = scale * total;
   if (iters) std::memcpy(iters, h->last_iters.data(), 2 * nb * sizeof(int));
@@ -491,6 +499,7 @@ cudaError_t vec_reduce(mqnpm_handle* h, int /*kind*/, const float* a, const floa
   const int ctas = h->w.ctas_vec;
   k_dots3<<<ctas, 256, 0, s>>>(a, b, c, d, h->N, h->w.partu);
   k_sum3<<<1, 256, 0, s>>>(h->w.partu, ctas, h->w.dscal);
+  h->launches += 2;
   cudaError_t e = cudaMemcpyAsync(h->w.h_scal, h->w.dscal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) std::memcpy(host_out, h->w.h_scal, 3 * sizeof(double));

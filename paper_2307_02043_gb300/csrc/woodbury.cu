@@ -1,0 +1,165 @@
+// Quasi-Newton point of Algorithm 4.1 for k > S:
+//   v_k = x - a S B^{-1} g,  B = tau* I + U U^T,
+//   B^{-1} = tau*^{-1} I - tau*^{-2} U (I + U^T U / tau*)^{-1} U^T   (Woodbury, Section 4.4).
+// One reduction pass forms U^T U and U^T g; a one-block kernel forms the S x S
+// inverse; a last pass applies the low-rank correction.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+#include "mqnpm.h"
+
+namespace {
+
+constexpr int OFF_G = 0;       // U^T U        (8 x 8)
+constexpr int OFF_M = 64;      // (I + U^T U / tau)^{-1}
+constexpr int OFF_UV = 128;    // U^T g
+
+template <int S>
+MQ_D void block_reduce_store(float (&acc)[S], double* dst) {
+  __shared__ double scratch[33 * S];
+  double o[S];
+  block_sum_f<S>(acc, scratch, o);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) dst[s] = o[s];
+  }
+}
+
+// Partials of U^T U (upper triangle) and U^T g.
+template <int S>
+__global__ void k_gram(UPtrs U, const float* __restrict__ g, int N, double* part) {
+  constexpr int NG = S * (S + 1) / 2;
+  float acc[NG + S];
+#pragma unroll
+  for (int k = 0; k < NG + S; ++k) acc[k] = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    float u[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] = U.u[s][i];
+    int k = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int t = s; t < S; ++t) {
+        acc[k] = fmaf(u[s], u[t], acc[k]);
+        ++k;
+      }
+    const float gi = g[i];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[NG + s] = fmaf(u[s], gi, acc[NG + s]);
+  }
+  block_reduce_store<NG + S>(acc, part + (size_t)blockIdx.x * (NG + S));
+}
+
+template <int S>
+MQ_D bool chol_solve(double (&A)[S * S], double (&b)[S]) {
+  for (int j = 0; j < S; ++j) {
+    double s = A[j * S + j];
+    for (int k = 0; k < j; ++k) s -= A[j * S + k] * A[j * S + k];
+    if (!(s > 0.0)) return false;
+    const double l = sqrt(s);
+    A[j * S + j] = l;
+    for (int i = j + 1; i < S; ++i) {
+      double t = A[i * S + j];
+      for (int k = 0; k < j; ++k) t -= A[i * S + k] * A[j * S + k];
+      A[i * S + j] = t / l;
+    }
+  }
+  for (int i = 0; i < S; ++i) {
+    double t = b[i];
+    for (int k = 0; k < i; ++k) t -= A[i * S + k] * b[k];
+    b[i] = t / A[i * S + i];
+  }
+  for (int i = S - 1; i >= 0; --i) {
+    double t = b[i];
+    for (int k = i + 1; k < S; ++k) t -= A[k * S + i] * b[k];
+    b[i] = t / A[i * S + i];
+  }
+  return true;
+}
+
+// Reduce the partials; G, U^T g and M = (I + G/tau)^{-1} into scal.
+template <int S>
+__global__ void k_gram_setup(const double* part, int nctas, double tau, double* scal) {
+  constexpr int NG = S * (S + 1) / 2, NV = NG + S;
+  __shared__ double scratch[32 * NV];
+  double v[NV], o[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int c = threadIdx.x; c < nctas; c += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += part[(size_t)c * NV + k];
+  block_sum<NV>(v, scratch, o);
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int s = 0; s < S; ++s)
+      for (int t = s; t < S; ++t) {
+        scal[OFF_G + s * S + t] = o[k];
+        scal[OFF_G + t * S + s] = o[k];
+        ++k;
+      }
+    for (int s = 0; s < S; ++s) scal[OFF_UV + s] = o[NG + s];
+    for (int col = 0; col < S; ++col) {
+      double A[S * S], e[S];
+      for (int i = 0; i < S; ++i)
+        for (int j = 0; j < S; ++j) A[i * S + j] = (i == j ? 1.0 : 0.0) + scal[OFF_G + i * S + j] / tau;
+      for (int i = 0; i < S; ++i) e[i] = (i == col) ? 1.0 : 0.0;
+      chol_solve<S>(A, e);
+      for (int i = 0; i < S; ++i) scal[OFF_M + i * S + col] = e[i];
+    }
+  }
+}
+
+// v = x - (aS/tau) g + (aS/tau^2) U M U^T g
+template <int S>
+__global__ void k_qn_point(const float* __restrict__ x, const float* __restrict__ g, UPtrs U, const double* scal,
+                           double aS, double tau, float* __restrict__ v, int N) {
+  __shared__ float coef[S];
+  if (threadIdx.x < S) {
+    double cs = 0.0;
+    for (int t = 0; t < S; ++t) cs += scal[OFF_M + threadIdx.x * S + t] * scal[OFF_UV + t];
+    coef[threadIdx.x] = (float)(aS / (tau * tau) * cs);
+  }
+  __syncthreads();
+  const float a0 = (float)(aS / tau);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    float acc = fmaf(-a0, g[i], x[i]);
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc = fmaf(coef[s], U.u[s][i], acc);
+    v[i] = acc;
+  }
+}
+
+template <int S>
+cudaError_t qn_point(mqnpm_handle* h, const float* x, const float* g, const UPtrs& U, double tau, double aS, float* v) {
+  cudaStream_t s = h->stream;
+  const int ctas = h->wp.ctas_vec;
+  k_gram<S><<<ctas, 256, 0, s>>>(U, g, (int)h->N, h->wp.gram);
+  k_gram_setup<S><<<1, 256, 0, s>>>(h->wp.gram, ctas, tau, h->wp.scal);
+  k_qn_point<S><<<ctas, 256, 0, s>>>(x, g, U, h->wp.scal, aS, tau, v, (int)h->N);
+  h->launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int qn_point_impl(mqnpm_handle* h, const float* x, const float* g, const UPtrs& U, int S_eff, double tau,
+                  double aS, float* v) {
+  cudaError_t e;
+  switch (S_eff) {
+    case 1: e = qn_point<1>(h, x, g, U, tau, aS, v); break;
+    case 2: e = qn_point<2>(h, x, g, U, tau, aS, v); break;
+    case 3: e = qn_point<3>(h, x, g, U, tau, aS, v); break;
+    case 4: e = qn_point<4>(h, x, g, U, tau, aS, v); break;
+    case 5: e = qn_point<5>(h, x, g, U, tau, aS, v); break;
+    case 6: e = qn_point<6>(h, x, g, U, tau, aS, v); break;
+    case 7: e = qn_point<7>(h, x, g, U, tau, aS, v); break;
+    case 8: e = qn_point<8>(h, x, g, U, tau, aS, v); break;
+    default: return set_error(h, MQNPM_ERR_INVALID_ARG, "qn_point: S_eff out of range");
+  }
+  return e == cudaSuccess ? MQNPM_OK : set_cuda_error(h, e, "qn_point");
+}
+
+int woodbury_scal_count() { return 136; }
