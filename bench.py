@@ -279,6 +279,33 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def prox_only(args, torch, binding):
+    """Weighted proximal mappings on the workload grid with S_eff = S rank-one
+    terms (a small case for profiler captures): prints time and phase trace."""
+    w = synth.workload(args.workload)
+    dev = torch.device("cuda", 0)
+    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, tv=w.tv, lam=w.lam,
+                      box=w.box, dual_iters=w.dual_iters, max_batch=1)
+    g = torch.Generator(device=dev).manual_seed(0)
+    x_true = torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
+    v = x_true + 0.01 * torch.randn(w.N, device=dev, generator=g)
+    U = 0.02 * torch.randn(w.S * w.N, device=dev, generator=g)
+    tau, c = 50.0, w.S * w.lam
+    P = torch.zeros(3 * w.N, device=dev)
+    for _ in range(args.warmup):
+        h.wprox(v, tau, U, c, P_warm=P)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        h.wprox(v, tau, U, c, P_warm=P)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": w.name, "S_eff": w.S, "dual_iters": w.dual_iters,
+                      "ms_per_prox": round(e0.elapsed_time(e1) / args.steps, 3), "trace_us": h.prox_trace()}),
+          flush=True)
+    h.close()
+
+
 def green_only(args, torch, binding):
     """Batched Green's applies on the workload grid (a small case for profiler
     captures): prints per-pass times and achieved GB/s as one JSON line."""
@@ -316,6 +343,8 @@ def main():
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
+    ap.add_argument("--prox-only", action="store_true",
+                    help="small case for profiler captures: weighted proximal mappings on the workload grid")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -329,6 +358,9 @@ def main():
 
     if args.green_only:
         green_only(args, torch, binding)
+        return
+    if args.prox_only:
+        prox_only(args, torch, binding)
         return
 
     if args.warmup < 3:

@@ -329,6 +329,8 @@ class MQNPM:
             out[key] = out.get(key, 0.0) + (t - prev) / 1e3
             out["total_us"] += (t - prev) / 1e3
             prev = t
+        out["dual_update_block0"] = buf[2000] / 1e3
+        out["pre_dual_block0"] = buf[2001] / 1e3
         return {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
 
     def profile_begin(self, max_calls: int = 4096):

@@ -290,6 +290,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(wp.err, 1);
   wp.trace_cap = 1024;
   AL(wp.trace, 2 * (size_t)wp.trace_cap);
+  AL(wp.status, N);
   {
     std::vector<float> mom = wprox_momentum(h->dual_iters);
     AL(wp.mom, mom.size());

@@ -80,6 +80,7 @@ struct WproxWork {
   double* scal = nullptr;       // Woodbury scalars (G, M, U^T g)
   unsigned* barrier = nullptr;  // [2]: arrival counter, released generation
   int* err = nullptr;           // device error flag
+  unsigned char* status = nullptr;  // per-voxel inner/clipped status of the Newton evaluations
   long long* trace = nullptr;   // phase trace of the last call: (tag, ns) per barrier
   int trace_cap = 0;
   int nsm = 0;

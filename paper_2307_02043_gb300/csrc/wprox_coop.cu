@@ -1,8 +1,8 @@
 // The whole weighted proximal mapping (Eq. 4.4) as one cooperative kernel.
 //
 // Phases, separated by grid-wide barriers (deterministic reductions: the last
-// block to arrive sums the per-block partials in block order and releases the
-// others; every wait is bounded):
+// block to arrive sums the per-block partials in a fixed order and releases
+// the others; every wait is bounded):
 //   G  (U != 0, once)  G = U^T U, U^T v; every block forms M = (I + G/tau)^{-1}.
 //   per dual iteration j = 1..J, then once more on P_J:
 //   A  d = d(R) and U^T d              -> gamma = (c/tau^2) M U^T d   (Woodbury)
@@ -11,8 +11,9 @@
 //      x = clip(w - U beta/tau) speculatively, so the accepted evaluation leaves x.
 //   X  (U = 0) x = clip(v - (c/tau) d(R))
 //   D  P_j = Proj(R_j + tau/(4 D c) grad x),  R_{j+1} = P_j + mom_j (P_j - P_{j-1})
-// At 128^3 the working set (v, d, x, U, R, P) stays resident in the 129 MB L2
-// across phases, so most of the traffic after the first touch is L2 traffic.
+// Every streaming loop handles four consecutive voxels per thread with 16-byte
+// loads (the grid edge n is a multiple of 4), so each thread keeps its whole
+// working set of loads in flight.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -24,8 +25,8 @@
 namespace {
 
 constexpr int WP_THREADS = 256;
+constexpr int NW = WP_THREADS / 32;
 constexpr int NVMAX = 44;     // S + S(S+1)/2 for S = 8
-constexpr int ILP_FOR(int S) { return S <= 4 ? 4 : 1; }
 
 struct WpArgs {
   const float* v;
@@ -36,19 +37,20 @@ struct WpArgs {
   float* x;
   float* xout;
   const float* mom;
-  double* part;       // [gridDim.x][NVMAX]
-  double* tot;        // [NVMAX]
-  unsigned* count;    // arrivals (monotonic)
-  unsigned* gen;      // released barrier generation
+  double* part;           // [NVMAX][gridDim.x] (value-major)
+  double* tot;            // [NVMAX]
+  unsigned* count;        // arrivals (monotonic)
+  unsigned* gen;          // released barrier generation
   int* err;
-  double* stat;       // [0] last newton count, [1] max, [2] total, [3] evaluations
+  double* stat;           // [0] last newton count, [1] max, [2] total, [3] evaluations
+  unsigned char* status;  // per voxel: 1 if the last evaluated z was strictly inside the box
   int n, N, J;
   double tau, c;
   float lo, hi, step;
   double tol;
   int maxit;
   long long limit;
-  long long* trace;   // optional: (phase tag, ns) after every barrier, recorded by block 0
+  long long* trace;       // optional: (phase tag, ns) after every barrier, recorded by block 0
   int trace_cap;
 };
 
@@ -58,23 +60,42 @@ MQ_D void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier with an optional sum of NV doubles per block (held in blk[]
-// by thread 0).  The totals land in sh_tot (shared) for every thread.
 MQ_D long long globaltimer() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// Partials are stored value-major, part[k * gridDim.x + b], so that the last
-// block reads each value's partials with coalesced, independent loads: warp w
-// reduces the values k = w, w + nwarps, ... (lane sums a fixed stripe of
-// blocks, then a fixed shuffle tree), which keeps the order deterministic.
+// Four consecutive floats as an addressable array.
+struct F4 {
+  float v[4];
+  MQ_D static F4 load(const float* p, int k4) {
+    const float4 q = reinterpret_cast<const float4*>(p)[k4];
+    return F4{{q.x, q.y, q.z, q.w}};
+  }
+  MQ_D void store(float* p, int k4) const {
+    reinterpret_cast<float4*>(p)[k4] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  MQ_D static F4 zero() { return F4{{0.f, 0.f, 0.f, 0.f}}; }
+  // read-only path: only for data no thread of the kernel writes
+  MQ_D static F4 ldg(const float* p, int k4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + k4);
+    return F4{{q.x, q.y, q.z, q.w}};
+  }
+};
+
+// Grid-wide barrier with an optional sum of NV doubles per block (blk[], shared).
+// Partials are stored value-major, part[k * gridDim.x + b]; the last block to
+// arrive reduces value k in warp k % nwarps: lane sums a fixed stripe of blocks,
+// then a fixed shuffle tree, so the order is deterministic.  The totals land in
+// sh_tot (shared) for every thread.
 template <int NV>
 MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, unsigned& epoch, int tag) {
   __shared__ int s_last, s_ok;
   __syncthreads();
-  if (threadIdx.x < NV) a.part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = blk[threadIdx.x];
+  if constexpr (NV > 0) {
+    if (threadIdx.x < NV) a.part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = blk[threadIdx.x];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -86,9 +107,9 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, unsign
   if (s_last) {
     if constexpr (NV > 0) {
       __threadfence();
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
       const int nb = gridDim.x;
-      for (int k = warp; k < NV; k += nw) {
+      for (int k = warp; k < NV; k += NW) {
         const double* p = a.part + (size_t)k * nb;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int b = lane;
@@ -130,26 +151,37 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, unsign
   return true;
 }
 
-MQ_D void coords(int i, int n, int& x, int& y, int& z) {
-  const int r = i / n;
-  x = i - r * n;
+// Coordinates of the first of four voxels i4 = 4 k4 (n is a multiple of 4).
+MQ_D void coords4(int k4, int n, int& x0, int& y, int& z) {
+  const int i4 = 4 * k4;
+  const int r = i4 / n;
+  x0 = i4 - r * n;
   z = r / n;
   y = r - z * n;
 }
 
-// d(R) at voxel i = (x, y, z): sum_d q_d(i - e_d)[i_d >= 1] - q_d(i)[i_d <= n-2]
-MQ_D float div_at(const float* __restrict__ R, int N, int n, int i, int x, int y, int z) {
+// d(R) = sum_d q_d(i - e_d)[i_d >= 1] - q_d(i)[i_d <= n-2] at four voxels.
+MQ_D F4 div4(const float* __restrict__ R, int N, int n, int k4, int x0, int y, int z) {
+  const int n4 = n / 4, nn4 = n * n / 4;
   const float* qx = R;
   const float* qy = R + N;
   const float* qz = R + 2 * (size_t)N;
-  float s = 0.f;
-  if (x > 0) s += qx[i - 1];
-  if (x < n - 1) s -= qx[i];
-  if (y > 0) s += qy[i - n];
-  if (y < n - 1) s -= qy[i];
-  if (z > 0) s += qz[i - n * n];
-  if (z < n - 1) s -= qz[i];
-  return s;
+  const F4 ax = F4::load(qx, k4), ay = F4::load(qy, k4), az = F4::load(qz, k4);
+  const float axm = x0 > 0 ? qx[4 * k4 - 1] : 0.f;
+  const F4 aym = y > 0 ? F4::load(qy, k4 - n4) : F4::zero();
+  const F4 azm = z > 0 ? F4::load(qz, k4 - nn4) : F4::zero();
+  F4 d;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float s = (m == 0) ? axm : ax.v[m - 1];
+    if (x0 + m < n - 1) s -= ax.v[m];
+    s += aym.v[m];
+    if (y < n - 1) s -= ay.v[m];
+    s += azm.v[m];
+    if (z < n - 1) s -= az.v[m];
+    d.v[m] = s;
+  }
+  return d;
 }
 
 template <int TV>
@@ -223,14 +255,14 @@ struct NewtonState {
   int* accepted_last;
 };
 
-// One decision of Algorithm 4.3 after phi and H were evaluated at beta_eval
-// (tot = [phi - beta_eval (S values), upper triangle of U^T diag(inner) U]).
+// One decision of Algorithm 4.3 after phi was evaluated at beta_eval
+// (tot[0..S) = U^T(w - clip(z))) with htri = sum_{inner} u u^T (upper triangle).
 // Accept the trial if it reduces ||phi|| (or halving is exhausted), stop at
-// ||phi|| <= tol_abs, else take the Newton step H^{-1} phi from the accepted
-// point; a rejected trial is halved.  Returns 1 when the solve is finished.
+// ||phi|| <= tol_abs, else take the Newton step -H^{-1} phi from the accepted
+// point, H = I + htri/tau; a rejected trial is halved.  Returns 1 when done.
 template <int S>
-__device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, double tau, double tol_abs, int maxit,
-                                          bool out_of_evals) {
+__device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, const double* htri, double tau,
+                                          double tol_abs, int maxit, bool out_of_evals) {
   double phi[S], nphi = 0.0;
   for (int s = 0; s < S; ++s) {
     phi[s] = tot[s] + ns.beta_eval[s];
@@ -253,10 +285,10 @@ __device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, 
   *ns.nphi_cur = nphi;
   if (nphi <= tol_abs || *ns.accepted >= maxit || out_of_evals || !isfinite(nphi)) return 1;
   double H[S * S];
-  int k = S;
+  int k = 0;
   for (int s = 0; s < S; ++s)
     for (int t = s; t < S; ++t) {
-      const double hst = tot[k++] / tau + (s == t ? 1.0 : 0.0);
+      const double hst = htri[k++] / tau + (s == t ? 1.0 : 0.0);
       H[s * S + t] = hst;
       H[t * S + s] = hst;
     }
@@ -280,68 +312,336 @@ MQ_D void block_partial(const float (&acc)[K], double (&out)[K]) {
   block_sum_f<K>(acc, scratch, out);
 }
 
-template <int S, int TV>
-__global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs a) {
-  constexpr int NG = S * (S + 1) / 2;
-  constexpr int NV = S + NG;
-  constexpr int ILP = ILP_FOR(S);
-  __shared__ double sG[S > 0 ? S * S : 1], sM[S > 0 ? S * S : 1], sUv[S > 0 ? S : 1];
-  __shared__ double sGamma[S > 0 ? S : 1], sUtw[S > 0 ? S : 1], sBeta[S > 0 ? S : 1], sBetaEval[S > 0 ? S : 1];
-  __shared__ double sTot[NVMAX];
-  __shared__ float sTheta[S > 0 ? S : 1], sGam[S > 0 ? S : 1];
-  __shared__ int sDone, sAcceptedLast;
-  __shared__ double sScale;
-  const int n = a.n, N = a.N;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = gridDim.x * blockDim.x;
-  const float cdt = (float)(a.c / a.tau);
-  unsigned epoch = 0;
-  __shared__ double blk[NVMAX];
-  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[1] = globaltimer();
+MQ_D float dot4(const F4& a, const F4& b) {
+  return fmaf(a.v[0], b.v[0], fmaf(a.v[1], b.v[1], fmaf(a.v[2], b.v[2], a.v[3] * b.v[3])));
+}
 
-  // ---------------------------------------------------------------- phase G
-  if constexpr (S > 0) {
-    float acc[NG + S];
+// Shared state of the cooperative kernel (identical in every block).
+template <int S>
+struct Shared {
+  static constexpr int SS = S > 0 ? S : 1;
+  static constexpr int NG = S * (S + 1) / 2;
+  static constexpr int NGG = NG > 0 ? NG : 1;
+  WpArgs a;
+  float trU[NW][SS][33];   // per-warp transpose of u for status flips
+  float trSign[NW][32];
+  float dH[NW][NGG];
+  double Htot[NGG];        // sum_{status inner} u u^T (upper triangle)
+  double G[SS * SS], M[SS * SS], Uv[SS];
+  double gamma[SS], beta[SS], beta_eval[SS], dir[SS], phi_cur[SS];
+  double tot[NVMAX], blk[NVMAX];
+  float theta[SS], gam[SS];
+  int done, accepted_last, halvings, accepted;
+  double scale, nphi_cur, tstep;
+  bool first;
+};
+
+// ---- phase G: block partials of U^T U (upper triangle) and U^T v into blk.
+template <int S>
+__device__ __noinline__ void pass_gram(Shared<S>* sh) {
+  constexpr int NG = S * (S + 1) / 2;
+  const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
+  const int N4 = a.N / 4, tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  float acc[NG + S];
 #pragma unroll
-    for (int k = 0; k < NG + S; ++k) acc[k] = 0.f;
-    for (int i0 = tid; i0 < N; i0 += ILP * stride) {
+  for (int k = 0; k < NG + S; ++k) acc[k] = 0.f;
+  for (int k4 = tid; k4 < N4; k4 += stride) {
+    F4 u[S];
 #pragma unroll
-      for (int q = 0; q < ILP; ++q) {
-        const int i = i0 + q * stride;
-        if (i < N) {
-          float u[S];
+    for (int s = 0; s < S; ++s) u[s] = F4::load(a.U.u[s], k4);
+    const F4 v4 = F4::load(a.v, k4);
+    int k = 0;
 #pragma unroll
-          for (int s = 0; s < S; ++s) u[s] = a.U.u[s][i];
-          const float vi = a.v[i];
-          int k = 0;
+    for (int s = 0; s < S; ++s)
 #pragma unroll
-          for (int s = 0; s < S; ++s)
+      for (int t = s; t < S; ++t) {
+        acc[k] += dot4(u[s], u[t]);
+        ++k;
+      }
 #pragma unroll
-            for (int t = s; t < S; ++t) {
-              acc[k] = fmaf(u[s], u[t], acc[k]);
-              ++k;
-            }
+    for (int s = 0; s < S; ++s) acc[NG + s] += dot4(u[s], v4);
+  }
+  double o[NG + S];
+  block_partial<NG + S>(acc, o);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NG + S; ++k) sh->blk[k] = o[k];
+}
+
+// ---- phase A: d = d(src), block partials of U^T d into blk.
+template <int S>
+__device__ __noinline__ void pass_div(Shared<S>* sh, const float* src) {
+  const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
+  const int n = a.n, N = a.N, N4 = a.N / 4;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const float* __restrict__ rs = src;
+  float* __restrict__ dout = a.d;
+  float acc[S];
 #pragma unroll
-          for (int s = 0; s < S; ++s) acc[NG + s] = fmaf(u[s], vi, acc[NG + s]);
+  for (int s = 0; s < S; ++s) acc[s] = 0.f;
+  for (int k4 = tid; k4 < N4; k4 += stride) {
+    int x0, y, z;
+    coords4(k4, n, x0, y, z);
+    F4 u[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] = F4::ldg(a.U.u[s], k4);   // U is read-only in the kernel
+    const F4 dv = div4(rs, N, n, k4, x0, y, z);
+    dv.store(dout, k4);
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] += dot4(u[s], dv);
+  }
+  double o[S];
+  block_partial<S>(acc, o);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < S; ++k) sh->blk[k] = o[k];
+}
+
+// ---- phase X (U = 0): x = clip(v - (c/tau) d(src)).
+__device__ __noinline__ void pass_x(const WpArgs* pa, const float* src, float* xw) {
+  const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
+  const int n = a.n, N = a.N, N4 = a.N / 4;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const float cdt = (float)(a.c / a.tau);
+  for (int k4 = tid; k4 < N4; k4 += stride) {
+    int x0, y, z;
+    coords4(k4, n, x0, y, z);
+    const F4 dv = div4(src, N, n, k4, x0, y, z);
+    const F4 v4 = F4::load(a.v, k4);
+    F4 xo;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) xo.v[m] = clampf(v4.v[m] - cdt * dv.v[m], a.lo, a.hi);
+    xo.store(xw, k4);
+  }
+}
+
+// ---- phase N: one evaluation at theta = gamma - beta_eval/tau.  Writes
+// x = clip(z) speculatively, block partials of U^T(w - clip(z)) into blk[0..S)
+// and of the status flips of sum_{inner} u u^T into blk[S..S+NG).
+template <int S>
+__device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
+  constexpr int NG = S * (S + 1) / 2;
+  const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
+  const int N4 = a.N / 4;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int gw = tid >> 5, nwt = stride >> 5;
+  const float cdt = (float)(a.c / a.tau);
+  int ps0 = 0, pt0 = 0, ps1 = 0, pt1 = 0;   // this lane's pairs: lane, lane + 32
+  {
+    int k = 0;
+    for (int s = 0; s < S; ++s)
+      for (int t = s; t < S; ++t) {
+        if (k == lane) { ps0 = s; pt0 = t; }
+        if (k == lane + 32) { ps1 = s; pt1 = t; }
+        ++k;
+      }
+  }
+  float th[S], ga[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) { th[s] = sh->theta[s]; ga[s] = sh->gam[s]; }
+  float acc[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) acc[s] = 0.f;
+  float dH0 = 0.f, dH1 = 0.f;
+  const float* __restrict__ din = a.d;
+  float* __restrict__ xout = xw;
+  uchar4* __restrict__ stat = reinterpret_cast<uchar4*>(a.status);
+  for (int wbase = gw * 32; wbase < N4; wbase += nwt * 32) {
+    const int k4 = wbase + lane;
+    const bool valid = k4 < N4;
+    F4 u[S];
+    float sign[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) u[s] = F4::ldg(a.U.u[s], k4);   // U, v are read-only in the kernel
+      const F4 v4 = F4::ldg(a.v, k4), d4 = F4::load(din, k4);
+      const uchar4 st4 = stat[k4];
+      const unsigned char old[4] = {st4.x, st4.y, st4.z, st4.w};
+      unsigned char nw[4];
+      F4 xo;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float base = v4.v[m] - cdt * d4.v[m];
+        float zz = base, ww = base;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          zz = fmaf(u[s].v[m], th[s], zz);
+          ww = fmaf(u[s].v[m], ga[s], ww);
         }
+        const float xc = clampf(zz, a.lo, a.hi);
+        xo.v[m] = xc;
+        const float e = ww - xc;
+#pragma unroll
+        for (int s = 0; s < S; ++s) acc[s] = fmaf(u[s].v[m], e, acc[s]);
+        nw[m] = (zz > a.lo && zz < a.hi) ? 1 : 0;
+        if (nw[m] != old[m]) sign[m] = nw[m] ? 1.f : -1.f;
+      }
+      xo.store(xout, k4);
+      if (sign[0] != 0.f || sign[1] != 0.f || sign[2] != 0.f || sign[3] != 0.f)
+        stat[k4] = make_uchar4(nw[0], nw[1], nw[2], nw[3]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < S; ++s) u[s] = F4::zero();
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      unsigned flips = __ballot_sync(0xffffffffu, sign[m] != 0.f);
+      if (flips) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) sh->trU[wib][s][lane] = u[s].v[m];
+        sh->trSign[wib][lane] = sign[m];
+        __syncwarp();
+        while (flips) {
+          const int jl = __ffs(flips) - 1;
+          flips &= flips - 1;
+          const float sg = sh->trSign[wib][jl];
+          if (lane < NG) dH0 = fmaf(sg * sh->trU[wib][ps0][jl], sh->trU[wib][pt0][jl], dH0);
+          if (lane + 32 < NG) dH1 = fmaf(sg * sh->trU[wib][ps1][jl], sh->trU[wib][pt1][jl], dH1);
+        }
+        __syncwarp();
       }
     }
-    double o[NG + S];
-    block_partial<NG + S>(acc, o);
-    if (threadIdx.x == 0)
-      for (int k = 0; k < NG + S; ++k) blk[k] = o[k];
-    if (!grid_reduce<NG + S>(blk, sTot, a, epoch, 1)) return;
+  }
+  double o[S];
+  block_partial<S>(acc, o);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < S; ++k) sh->blk[k] = o[k];
+  if (lane < NG) sh->dH[wib][lane] = dH0;
+  if (lane + 32 < NG) sh->dH[wib][lane + 32] = dH1;
+  __syncthreads();
+  if (threadIdx.x < NG) {
+    double sacc = 0.0;
+    for (int w = 0; w < NW; ++w) sacc += (double)sh->dH[w][threadIdx.x];
+    sh->blk[S + threadIdx.x] = sacc;
+  }
+}
+
+// ---- x = clip(v - (c/tau) d + U theta) for the accepted beta (after a rejected trial).
+template <int S>
+__device__ __noinline__ void pass_fixup(Shared<S>* sh, float* xw) {
+  const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
+  const int N4 = a.N / 4, tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const float cdt = (float)(a.c / a.tau);
+  float th[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) th[s] = sh->theta[s];
+  for (int k4 = tid; k4 < N4; k4 += stride) {
+    const F4 v4 = F4::load(a.v, k4), d4 = F4::load(a.d, k4);
+    F4 xo;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) xo.v[m] = v4.v[m] - cdt * d4.v[m];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const F4 u4 = F4::load(a.U.u[s], k4);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) xo.v[m] = fmaf(u4.v[m], th[s], xo.v[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) xo.v[m] = clampf(xo.v[m], a.lo, a.hi);
+    xo.store(xw, k4);
+  }
+}
+
+// ---- phase D: P = Proj(R + step grad x), R = P + mom (P - P_prev), in place.
+template <int TV>
+__device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
+  const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
+  const int n = a.n, N = a.N, N4 = a.N / 4;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int n4 = n / 4, nn4 = n * n / 4;
+  const float* __restrict__ xs = a.x;
+  float* __restrict__ Rx = a.R;
+  float* __restrict__ Ry = a.R + N;
+  float* __restrict__ Rz = a.R + 2 * (size_t)N;
+  float* __restrict__ Px = a.Pd;
+  float* __restrict__ Py = a.Pd + N;
+  float* __restrict__ Pz = a.Pd + 2 * (size_t)N;
+  const float step = a.step;
+  // two groups of four voxels per iteration, every load issued before any store
+  constexpr int G = 2;
+  for (int kb = tid; kb < N4; kb += G * stride) {
+    int x0[G], y[G], z[G];
+    bool ok[G];
+    F4 x4[G], xy[G], xz[G], rx[G], ry[G], rz[G], ox[G], oy[G], oz[G];
+    float xnext[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const int k4 = kb + q * stride;
+      ok[q] = k4 < N4;
+      const int kk = ok[q] ? k4 : kb;
+      coords4(kk, n, x0[q], y[q], z[q]);
+      x4[q] = F4::load(xs, kk);
+      xnext[q] = (x0[q] + 4 < n) ? xs[4 * kk + 4] : 0.f;
+      xy[q] = (y[q] < n - 1) ? F4::load(xs, kk + n4) : x4[q];
+      xz[q] = (z[q] < n - 1) ? F4::load(xs, kk + nn4) : x4[q];
+      rx[q] = F4::load(Rx, kk);
+      ry[q] = F4::load(Ry, kk);
+      rz[q] = F4::load(Rz, kk);
+      ox[q] = F4::load(Px, kk);
+      oy[q] = F4::load(Py, kk);
+      oz[q] = F4::load(Pz, kk);
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float xn = (m < 3) ? x4[q].v[m + 1] : xnext[q];
+        const float gx = (x0[q] + m < n - 1) ? xn - x4[q].v[m] : 0.f;
+        float px = rx[q].v[m] + step * gx;
+        float py = ry[q].v[m] + step * (xy[q].v[m] - x4[q].v[m]);
+        float pz = rz[q].v[m] + step * (xz[q].v[m] - x4[q].v[m]);
+        project<TV>(px, py, pz);
+        rx[q].v[m] = px + mom * (px - ox[q].v[m]);
+        ry[q].v[m] = py + mom * (py - oy[q].v[m]);
+        rz[q].v[m] = pz + mom * (pz - oz[q].v[m]);
+        ox[q].v[m] = px;
+        oy[q].v[m] = py;
+        oz[q].v[m] = pz;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      if (!ok[q]) continue;
+      const int k4 = kb + q * stride;
+      ox[q].store(Px, k4);
+      oy[q].store(Py, k4);
+      oz[q].store(Pz, k4);
+      rx[q].store(Rx, k4);
+      ry[q].store(Ry, k4);
+      rz[q].store(Rz, k4);
+    }
+  }
+}
+
+template <int S, int TV>
+__global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
+  constexpr int NG = S * (S + 1) / 2;
+  constexpr int NV = S + NG;
+  __shared__ Shared<S> sh;
+  if (threadIdx.x == 0) sh.a = args;
+  __syncthreads();
+  const WpArgs& a = sh.a;
+  unsigned epoch = 0;
+  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.trace[1] = globaltimer();
+    a.trace[2 * 1000] = 0;
+    a.trace[2 * 1000 + 1] = 0;
+  }
+
+  if constexpr (S > 0) {
+    pass_gram<S>(&sh);
+    if (!grid_reduce<NG + S>(sh.blk, sh.tot, a, epoch, 1)) return;
     if (threadIdx.x == 0) {
       int k = 0;
       for (int s = 0; s < S; ++s)
         for (int t = s; t < S; ++t) {
-          sG[s * S + t] = sTot[k];
-          sG[t * S + s] = sTot[k];
+          sh.G[s * S + t] = sh.tot[k];
+          sh.G[t * S + s] = sh.tot[k];
+          sh.Htot[k] = sh.tot[k];      // every voxel starts with status "inner"
           ++k;
         }
-      for (int s = 0; s < S; ++s) sUv[s] = sTot[NG + s];
-      form_woodbury<S>(sG, a.tau, sM);
-      for (int s = 0; s < S; ++s) sBeta[s] = 0.0;
+      for (int s = 0; s < S; ++s) sh.Uv[s] = sh.tot[NG + s];
+      form_woodbury<S>(sh.G, a.tau, sh.M);
+      for (int s = 0; s < S; ++s) sh.beta[s] = 0.0;
     }
     __syncthreads();
   }
@@ -352,189 +652,83 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs a) {
     const float* src = final_eval ? a.Pd : a.R;
     float* xw = final_eval ? a.xout : a.x;
     if constexpr (S == 0) {
-      // ------------------------------------------------------------ phase X
-      for (int i0 = tid; i0 < N; i0 += ILP * stride) {
-#pragma unroll
-        for (int q = 0; q < ILP; ++q) {
-          const int i = i0 + q * stride;
-          if (i < N) {
-            int x, y, z;
-            coords(i, n, x, y, z);
-            xw[i] = clampf(a.v[i] - cdt * div_at(src, N, n, i, x, y, z), a.lo, a.hi);
-          }
-        }
-      }
+      pass_x(&sh.a, src, xw);
       if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, epoch, 2)) return;
     } else {
-      // ------------------------------------------------------------ phase A
-      {
-        float acc[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) acc[s] = 0.f;
-        for (int i0 = tid; i0 < N; i0 += ILP * stride) {
-#pragma unroll
-          for (int q = 0; q < ILP; ++q) {
-            const int i = i0 + q * stride;
-            if (i < N) {
-              int x, y, z;
-              coords(i, n, x, y, z);
-              const float dd = div_at(src, N, n, i, x, y, z);
-              a.d[i] = dd;
-#pragma unroll
-              for (int s = 0; s < S; ++s) acc[s] = fmaf(a.U.u[s][i], dd, acc[s]);
-            }
-          }
-        }
-        double o[S];
-        block_partial<S>(acc, o);
-        if (threadIdx.x == 0)
-          for (int k = 0; k < S; ++k) blk[k] = o[k];
-        if (!grid_reduce<S>(blk, sTot, a, epoch, 3)) return;
-        if (threadIdx.x == 0) {
-          double nrm = 0.0;
-          for (int s = 0; s < S; ++s) {
-            double g = 0.0;
-            for (int t = 0; t < S; ++t) g += sM[s * S + t] * sTot[t];
-            sGamma[s] = a.c / (a.tau * a.tau) * g;
-          }
-          for (int s = 0; s < S; ++s) {
-            double g = sUv[s] - a.c / a.tau * sTot[s];
-            for (int t = 0; t < S; ++t) g += sG[s * S + t] * sGamma[t];
-            sUtw[s] = g;
-            nrm += g * g;
-          }
-          sScale = fmax(1.0, sqrt(nrm));
-          for (int s = 0; s < S; ++s) sBetaEval[s] = sBeta[s];
-          sDone = 0;
-        }
-        __syncthreads();
-      }
-      // ------------------------------------------------------------ phase N
-      // decision state (meaningful in thread 0 only)
-      __shared__ double dir[S], phi_cur[S];
-      __shared__ double nphi_cur, tstep;
-      __shared__ int halvings, accepted;
-      __shared__ bool first;
+      pass_div<S>(&sh, src);
+      if (!grid_reduce<S>(sh.blk, sh.tot, a, epoch, 3)) return;
       if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) { dir[s] = 0.0; phi_cur[s] = 0.0; }
-        nphi_cur = 0.0;
-        tstep = 1.0;
-        halvings = 0;
-        accepted = 0;
-        first = true;
+        double nrm = 0.0;
+        for (int s = 0; s < S; ++s) {
+          double g = 0.0;
+          for (int t = 0; t < S; ++t) g += sh.M[s * S + t] * sh.tot[t];
+          sh.gamma[s] = a.c / (a.tau * a.tau) * g;
+        }
+        for (int s = 0; s < S; ++s) {
+          double g = sh.Uv[s] - a.c / a.tau * sh.tot[s];
+          for (int t = 0; t < S; ++t) g += sh.G[s * S + t] * sh.gamma[t];
+          nrm += g * g;       // (U^T w)_s
+        }
+        sh.scale = fmax(1.0, sqrt(nrm));
+        for (int s = 0; s < S; ++s) {
+          sh.beta_eval[s] = sh.beta[s];
+          sh.dir[s] = 0.0;
+          sh.phi_cur[s] = 0.0;
+        }
+        sh.nphi_cur = 0.0;
+        sh.tstep = 1.0;
+        sh.halvings = 0;
+        sh.accepted = 0;
+        sh.first = true;
+        sh.done = 0;
       }
       __syncthreads();
       const int max_evals = a.maxit * 8;
       int my_evals = 0;
       while (true) {
         if (threadIdx.x < S) {
-          sTheta[threadIdx.x] = (float)(sGamma[threadIdx.x] - sBetaEval[threadIdx.x] / a.tau);
-          sGam[threadIdx.x] = (float)sGamma[threadIdx.x];
+          sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta_eval[threadIdx.x] / a.tau);
+          sh.gam[threadIdx.x] = (float)sh.gamma[threadIdx.x];
         }
         __syncthreads();
-        float th[S], ga[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) { th[s] = sTheta[s]; ga[s] = sGam[s]; }
-        float acc[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = 0.f;
-        for (int i0 = tid; i0 < N; i0 += ILP * stride) {
-#pragma unroll
-          for (int q = 0; q < ILP; ++q) {
-            const int i = i0 + q * stride;
-            if (i < N) {
-              const float base = a.v[i] - cdt * a.d[i];
-              float u[S];
-              float zz = base, ww = base;
-#pragma unroll
-              for (int s = 0; s < S; ++s) {
-                u[s] = a.U.u[s][i];
-                zz = fmaf(u[s], th[s], zz);
-                ww = fmaf(u[s], ga[s], ww);
-              }
-              const float xc = clampf(zz, a.lo, a.hi);
-              xw[i] = xc;
-              const float e = ww - xc;
-              const float in = (zz > a.lo && zz < a.hi) ? 1.f : 0.f;
-#pragma unroll
-              for (int s = 0; s < S; ++s) acc[s] = fmaf(u[s], e, acc[s]);
-              int k = S;
-#pragma unroll
-              for (int s = 0; s < S; ++s) {
-                const float us = in * u[s];
-#pragma unroll
-                for (int t = s; t < S; ++t) {
-                  acc[k] = fmaf(us, u[t], acc[k]);
-                  ++k;
-                }
-              }
-            }
-          }
-        }
-        double o[NV];
-        block_partial<NV>(acc, o);
-        if (threadIdx.x == 0)
-          for (int k = 0; k < NV; ++k) blk[k] = o[k];
-        if (!grid_reduce<NV>(blk, sTot, a, epoch, 4)) return;
+        pass_newton<S>(&sh, xw);
+        if (!grid_reduce<NV>(sh.blk, sh.tot, a, epoch, 4)) return;
         ++my_evals;
+        if (threadIdx.x < NG) sh.Htot[threadIdx.x] += sh.tot[S + threadIdx.x];
+        __syncthreads();
         if (threadIdx.x == 0) {
-          NewtonState<S> ns{sBeta, sBetaEval, dir, phi_cur, &nphi_cur, &tstep, &halvings, &accepted, &first,
-                            &sAcceptedLast};
-          const int done = newton_decide<S>(ns, sTot, a.tau, a.tol * sScale, a.maxit, my_evals >= max_evals);
-          sDone = done;
-          if (done) last_newton = accepted;
+          NewtonState<S> ns{sh.beta, sh.beta_eval, sh.dir, sh.phi_cur, &sh.nphi_cur, &sh.tstep, &sh.halvings,
+                            &sh.accepted, &sh.first, &sh.accepted_last};
+          const int done = newton_decide<S>(ns, sh.tot, sh.Htot, a.tau, a.tol * sh.scale, a.maxit,
+                                            my_evals >= max_evals);
+          sh.done = done;
+          if (done) last_newton = sh.accepted;
         }
         __syncthreads();
-        if (sDone) break;
+        if (sh.done) break;
       }
       if (threadIdx.x == 0) {
         newton_max = max(newton_max, last_newton);
         newton_total += last_newton;
       }
       evals += my_evals;
-      if (!sAcceptedLast) {
+      if (!sh.accepted_last) {
         // the last evaluation was a rejected trial: write x for the accepted beta
-        if (threadIdx.x < S) sTheta[threadIdx.x] = (float)(sGamma[threadIdx.x] - sBeta[threadIdx.x] / a.tau);
+        if (threadIdx.x < S) sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta[threadIdx.x] / a.tau);
         __syncthreads();
-        float th[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) th[s] = sTheta[s];
-        for (int i = tid; i < N; i += stride) {
-          float zz = a.v[i] - cdt * a.d[i];
-#pragma unroll
-          for (int s = 0; s < S; ++s) zz = fmaf(a.U.u[s][i], th[s], zz);
-          xw[i] = clampf(zz, a.lo, a.hi);
-        }
+        pass_fixup<S>(&sh, xw);
         if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, epoch, 5)) return;
       }
     }
     if (final_eval) break;
-    // -------------------------------------------------------------- phase D
-    const float mom = a.mom[j];
-    for (int i0 = tid; i0 < N; i0 += ILP * stride) {
-#pragma unroll
-      for (int q = 0; q < ILP; ++q) {
-        const int i = i0 + q * stride;
-        if (i < N) {
-          int x, y, z;
-          coords(i, n, x, y, z);
-          const float x0 = a.x[i];
-          const float gx = x < n - 1 ? a.x[i + 1] - x0 : 0.f;
-          const float gy = y < n - 1 ? a.x[i + n] - x0 : 0.f;
-          const float gz = z < n - 1 ? a.x[i + n * n] - x0 : 0.f;
-          float px = a.R[i] + a.step * gx;
-          float py = a.R[(size_t)N + i] + a.step * gy;
-          float pz = a.R[2 * (size_t)N + i] + a.step * gz;
-          project<TV>(px, py, pz);
-          const float ox = a.Pd[i], oy = a.Pd[(size_t)N + i], oz = a.Pd[2 * (size_t)N + i];
-          a.Pd[i] = px;
-          a.Pd[(size_t)N + i] = py;
-          a.Pd[2 * (size_t)N + i] = pz;
-          a.R[i] = px + mom * (px - ox);
-          a.R[(size_t)N + i] = py + mom * (py - oy);
-          a.R[2 * (size_t)N + i] = pz + mom * (pz - oz);
-        }
-      }
+    long long t_pre = 0;
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) t_pre = globaltimer();
+    pass_dual<TV>(&sh.a, a.mom[j]);
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+      // block 0's own time in the dual update and in the work since the last barrier
+      const long long t_post = globaltimer();
+      a.trace[2 * 1000] += t_post - t_pre;
+      a.trace[2 * 1000 + 1] += t_pre - a.trace[2 * epoch + 1];
     }
     if (!grid_reduce<0>(nullptr, nullptr, a, epoch, 6)) return;
   }
@@ -591,10 +785,17 @@ cudaError_t dispatch(mqnpm_handle* h, int S, WpArgs& a) {
 int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int S_eff, double c, float* P_warm,
                bool warm, float* x_out) {
   if (S_eff < 0 || S_eff > MQNPM_MAX_S) return set_error(h, MQNPM_ERR_INVALID_ARG, "wprox: S_eff out of range");
+  if (h->n % 4 != 0) return set_error(h, MQNPM_ERR_UNSUPPORTED, "wprox: grid edge must be a multiple of 4");
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   const int J = h->dual_iters;
   if ((int)h->wp.mom_len != J) return set_error(h, MQNPM_ERR_STATE, "wprox: momentum table not initialised");
+  // 16-byte vector access needs 16-byte aligned vectors
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (!aligned(v) || !aligned(x_out) || (P_warm && !aligned(P_warm)))
+    return set_error(h, MQNPM_ERR_INVALID_ARG, "wprox: vectors must be 16-byte aligned");
+  for (int q = 0; q < S_eff; ++q)
+    if (!aligned(U.u[q])) return set_error(h, MQNPM_ERR_INVALID_ARG, "wprox: U rows must be 16-byte aligned");
   if (warm && P_warm) {
     CK(cudaMemcpyAsync(h->wp.Pd, P_warm, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   } else {
@@ -603,6 +804,7 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   CK(cudaMemcpyAsync(h->wp.R, h->wp.Pd, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(h->wp.err, 0, sizeof(int), s));
   CK(cudaMemsetAsync(h->wp.barrier, 0, 2 * sizeof(unsigned), s));
+  if (S_eff > 0) CK(cudaMemsetAsync(h->wp.status, 1, N, s));
   WpArgs a;
   a.v = v;
   a.U = U;
@@ -618,6 +820,7 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.gen = h->wp.barrier + 1;
   a.err = h->wp.err;
   a.stat = h->wp.stat;
+  a.status = h->wp.status;
   a.n = h->n;
   a.N = (int)N;
   a.J = J;
