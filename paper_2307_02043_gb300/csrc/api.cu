@@ -276,6 +276,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(w.partd, B * (size_t)w.ctas_row);
   AL(w.partu, std::max(B * (size_t)w.ctas_upd, (size_t)w.ctas_vec) * 3);
   AL(w.st, B);
+  AL(w.gerr, 1);
   AL(w.illum, B);
   AL(w.nactive, 1);
   AL(w.dscal, 64);
@@ -321,6 +322,11 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
         tab[((size_t)l * 3 + ax) * n + i] = make_float2((float)std::cos(ph), (float)std::sin(ph));
       }
   cudaStream_t s = h->stream;
+  if ((e = make_t2_tensor_map(w.T2, n, (int)B, w.t2map)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w.gerr, 0, sizeof(int), s)) != cudaSuccess) {
+    set_cuda_error(h, e, "tensor map of the transform buffer");
+    return fail(MQNPM_ERR_CUDA);
+  }
   if ((e = cudaMemcpyAsync(h->tw, tw.data(), P * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = build_khat(n, h->h, h->kb, h->khat, s)) != cudaSuccess) {
@@ -361,8 +367,13 @@ int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int a
   c.part_epi = h->w.part5;
   c.ev = profile_slot(h, nb);
   c.launches = &h->launches;
+  c.tmap = h->w.t2map;
+  c.err = h->w.gerr;
   CK(green_launch(c, h->stream));
+  int gerr = 0;
+  CK(cudaMemcpyAsync(&gerr, h->w.gerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (gerr) return set_error(h, MQNPM_ERR_TIMEOUT, "green_apply: a bounded wait for a tile load gave up");
   return MQNPM_OK;
 }
 

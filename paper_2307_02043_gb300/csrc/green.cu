@@ -14,7 +14,10 @@
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "green_passes.cuh"
 #include "internal.h"
 
 #define MQ_DISPATCH(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(320) X(384)
@@ -48,6 +51,40 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+// ---------------------------------------------------------- T2 tensor map
+// T2 viewed as a 3D tensor of 8-byte elements: x = kx (P), y = ky (P),
+// z = slot * n + z (max_batch * n).  Pass 3 loads boxes of C x 1 x n: one
+// column set of one slot.  The encoder comes from the driver through the
+// runtime's entry-point query, so the library does not link libcuda.
+cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, void* map_out) {
+  const int P = 2 * n;
+  int C = 0;
+  switch (P) {
+#define MQ_CASE(PP) case PP: C = ColShape<PP>::C; break;
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)max_batch * n};
+  const cuuint64_t strides[2] = {(cuuint64_t)P * 8, (cuuint64_t)P * P * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)C, 1u, (cuuint32_t)n};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = encode(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, T2, dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------ K_hat build

@@ -74,15 +74,19 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
   }
   if (c.ev) cudaEventRecord(c.ev[2], s);
   {
-    dim3 grid(P / CS::C, P, c.nb);
+    // one CTA per (kx tile, ky) column set; the batch is looped inside (TMA double buffer)
+    dim3 grid(P / CS::C, P);
+    const int smem = (int)Pass3Smem<P>::bytes(c.n);
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);
+    if (tm == nullptr || c.err == nullptr) return cudaErrorInvalidValue;
     if (c.adjoint) {
       auto kern = k_pass3<P, true>;
-      if ((e = set_smem(kern, CS::SMEM)) != cudaSuccess) return e;
-      kern<<<grid, CS::THREADS, CS::SMEM, s>>>(c.T2, c.khat, c.n, c.tw, c.st);
+      if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+      kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.n, c.nb, c.tw, c.st, c.err);
     } else {
       auto kern = k_pass3<P, false>;
-      if ((e = set_smem(kern, CS::SMEM)) != cudaSuccess) return e;
-      kern<<<grid, CS::THREADS, CS::SMEM, s>>>(c.T2, c.khat, c.n, c.tw, c.st);
+      if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+      kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.n, c.nb, c.tw, c.st, c.err);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -26,7 +26,12 @@ struct GreenCall {
   double* part_epi = nullptr;    // [nb][ctas5][NPART]
   cudaEvent_t* ev = nullptr;     // optional: 6 events recorded around the 5 passes
   long long* launches = nullptr; // optional kernel-launch counter (+5 per apply)
+  const void* tmap = nullptr;    // CUtensorMap of T2 for the pass-3 tile loads
+  int* err = nullptr;            // device flag raised when a bounded wait gives up
 };
+
+// Tensor map of the pass-3 buffer T2 = [max_batch * n][P][P] complex64, box C x 1 x n.
+cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, void* map_out /* CUtensorMap, 64 B aligned */);
 
 // Per-pass timing (opt-in tracing): events recorded around every Green's apply.
 struct Profiler {
@@ -67,6 +72,8 @@ struct Workspace {
   double* h_scal = nullptr;              // pinned scalar staging (64 doubles)
   double* dscal = nullptr;               // device scalar scratch (64 doubles)
   int ctas_row = 0, ctas_upd = 0, ctas_vec = 0;
+  int* gerr = nullptr;                   // raised by a Green's pass whose bounded wait gave up
+  alignas(64) unsigned char t2map[128];  // CUtensorMap of T2
 };
 
 struct WproxWork {

@@ -303,6 +303,8 @@ __global__ void k_scale_real(const float* a, float* out, size_t N, float s) {
 cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
   c.ev = profile_slot(h, c.nb);
   c.launches = &h->launches;
+  c.tmap = h->w.t2map;
+  c.err = h->w.gerr;
   return green_launch(c, s);
 }
 
@@ -490,6 +492,9 @@ int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, d
   }
   if (loss) *loss = scale * total;
   if (iters) std::memcpy(iters, h->last_iters.data(), 2 * nb * sizeof(int));
+  int gerr = 0;
+  CK(cudaMemcpy(&gerr, w.gerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (gerr) return set_error(h, MQNPM_ERR_TIMEOUT, "a bounded wait for a transform tile load gave up");
   return worst;
 }
 
