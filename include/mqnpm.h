@@ -202,6 +202,36 @@ long long mqnpm_launch_count(const mqnpm_handle* h);
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);
 int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls);
 
+/* Allocation-free Green's convolution (no counterpart in the paper: the
+ * operation is the G v / G^H v of Section 6, as mqnpm_green_apply computes it
+ * for one volume, without a handle).  It is for callers that cannot allocate
+ * device memory: code running inside another framework's memory pool or on a
+ * device whose memory is already handed out, and allocator hooks that must not
+ * re-enter the allocator.  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine; its scratch is one file-scope device array of
+ * mqnpm_noalloc_scratch_bytes() bytes (3,012,352 B, 2.9 MiB), present on every GPU
+ * that loads the library, whose address is taken with cudaGetSymbolAddress
+ * once per device.
+ *   n: grid edge, at most 32, with 2n a compiled transform length
+ *      (n in {8, 12, 16, 24, 32}); larger or unsupported n returns
+ *      MQNPM_ERR_INVALID_ARG and prints why on stderr.
+ *   h, kb: voxel size and background wavenumber (> 0).
+ *   v, out: device, n^3 complex64 each ([z][y][x], interleaved re/im), distinct.
+ *   adjoint != 0 selects G^H.  stream: cudaStream_t (NULL: legacy stream).
+ * Works on the current device.  The first call on a device, and the first after
+ * n, h or kb changed, builds the kernel spectrum in the scratch array and
+ * synchronises the stream; make such a call before any stream capture.  Every
+ * call synchronises the stream before it returns (it reads the device error
+ * flag, which must start at zero and is reset when raised).  All calls on one
+ * device share the scratch array: calls from several host threads are
+ * serialised by a lock, but calls on different streams whose work overlaps in
+ * any other way (e.g. a captured graph replayed beside a direct call) race.
+ * Returns MQNPM_OK, MQNPM_ERR_INVALID_ARG, MQNPM_ERR_CUDA or MQNPM_ERR_TIMEOUT
+ * (a bounded wait for a tile load gave up). */
+int mqnpm_green_apply_noalloc(int n, double h, double kb, const float* v, float* out, int adjoint,
+                              void* stream);
+size_t mqnpm_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,9 @@ SIGNATURES = {
     "mqnpm_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mqnpm_profile_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_green_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "mqnpm_noalloc_scratch_bytes": (ctypes.c_size_t, []),
 }
 
 
@@ -132,6 +135,23 @@ def _check_cuda(t: torch.Tensor, dtype, numel: int, name: str, device: int):
         raise ValueError("%s must be contiguous" % name)
     if t.numel() != numel:
         raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+
+
+def green_apply_noalloc(n: int, h: float, kb: float, v: torch.Tensor, out: torch.Tensor,
+                        adjoint: bool = False) -> torch.Tensor:
+    """G v (or G^H v) of one n^3 volume into `out` with the library's static
+    device scratch: the C call allocates nothing (n <= 32)."""
+    lib = load()
+    dev = v.device.index if v.is_cuda else -1
+    _check_cuda(v, torch.complex64, n ** 3, "v", dev)
+    _check_cuda(out, torch.complex64, n ** 3, "out", dev)
+    with torch.cuda.device(dev):
+        s = torch.cuda.current_stream(dev).cuda_stream
+        rc = lib.mqnpm_green_apply_noalloc(int(n), float(h), float(kb), _ptr(v), _ptr(out), int(adjoint),
+                                           ctypes.c_void_p(s))
+    if rc != OK:
+        raise MQNPMError(rc, "green_apply_noalloc failed")
+    return out
 
 
 class MQNPM:

@@ -143,6 +143,27 @@ __global__ void k_round_khat(const double2* __restrict__ in, float2* __restrict_
     out[i] = make_float2((float)(in[i].x * scale), (float)(in[i].y * scale));
 }
 
+// The same construction with caller-provided device scratch: a, b hold
+// (n+1)^3 double2 each, dcos holds P doubles.  No device allocation.
+cudaError_t build_khat_scratch(int n, double h, double kb, float2* khat_out, double2* a, double2* b, double* dcos,
+                               cudaStream_t s) {
+  const int P = 2 * n;
+  const long long m = n + 1;
+  std::vector<double> cosv(P);
+  for (int j = 0; j < P; ++j) cosv[j] = std::cos(2.0 * M_PI * (double)j / (double)P);
+  cudaError_t e = cudaMemcpyAsync(dcos, cosv.data(), P * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int th = 256, gr = 1024;
+  k_kernel_octant<<<gr, th, 0, s>>>(a, n, h, kb);
+  k_cos_pass<<<gr, th, 0, s>>>(a, b, n, n, n, dcos, P);
+  k_cos_pass<<<gr, th, 0, s>>>(b, a, (int)m, n, n, dcos, P);
+  k_cos_pass<<<gr, th, 0, s>>>(a, b, (int)m, (int)m, n, dcos, P);
+  k_round_khat<<<gr, th, 0, s>>>(b, khat_out, m * m * m, 1.0 / ((double)P * P * P));
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host cosine table goes out of scope
+  return e;
+}
+
 cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s) {
   const int P = 2 * n;
   const long long m = n + 1;
