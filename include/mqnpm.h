@@ -154,7 +154,7 @@ int mqnpm_grad_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, 
                      float* grad_out, double* loss_out, int* krylov_iters_out);
 
 /* Weighted proximal mapping of c*TV + iota_C under B = tau_star I + U U^T
- * (Eq. 4.4, Theorem 3.1, Lemma 4.1, Algorithm 4.3):
+ * (Eq. 4.5, Theorem 3.1, Lemma 4.1, Algorithm 4.3):
  *   x_out ~= argmin_{x in C} 1/2 ||x - v||_B^2 + c TV(x)
  * by cfg.dual_iters accelerated projected-gradient steps on the dual T(P).
  * v, x_out: device N floats (distinct).  U: device S_eff x N floats (row s is

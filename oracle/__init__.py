@@ -13,10 +13,10 @@ physics  Lippmann-Schwinger / first-Born forward model, detector, data term
          our stated reading, the paper defers it to a supplement).
 tv       finite differences D^d (Section 3.1), discrete TV (Eqs. 3.1-3.2),
          its dual map d(P) and the projection onto the dual ball (Eqs. 3.3-3.4).
-wprox    structured weighted proximal mapping: Woodbury inverse (Section 4.4),
+wprox    structured weighted proximal mapping: Woodbury inverse (Section 4.3),
          prox of the box under tau*I + U U^T (Theorem 3.1) by semi-smooth Newton
          (Algorithm 4.3), and the dual fast projected gradient on T(P)
-         (Eq. 4.8, Lemma 4.1).
+         (Eq. 4.10, Lemma 4.1).
 sr1      the memory-efficient SR1 estimate of B_s (Algorithm 4.2).
 bqnpm    the outer loop (Algorithm 4.1) with strategies I and II.
 

@@ -9,7 +9,7 @@ Iteration k (1-based):
            s = x_{k-1} - xbar_{s'}, m = g - gbar_{s'}; then xbar_{s'}, gbar_{s'} <- x_{k-1}, g;
            B = sum_s B_s = tau* I + U U^T;  v_k = x_{k-1} - a S B^{-1} g
            (step 10 of Algorithm 4.1 with x_s^k = x_{k-1}, g_s^k = g for all s);
-           x_k = prox^{B}_{a S lam TV + iota_C}(v_k)   (Eq. 4.4).
+           x_k = prox^{B}_{a S lam TV + iota_C}(v_k)   (Eq. 4.5).
 Readings: B_s = alpha_s I until subset s is revisited; tau_max = 1e3 max_s alpha_s;
 the dual field P of the proximal mapping is warm-started from the previous
 outer iteration (P_0 = 0 at k = 1).

@@ -4,7 +4,7 @@ Section 3.1 defines D^d through the entries -delta[i-j] + delta[i-j-R_d]; as
 printed the stride and the boundary rule are garbled.  Our reading: forward
 differences along dimension d with Neumann boundary,
     (D^d x)_i = x_{i+e_d} - x_i  if i_d < R_d - 1,   0 on the last slice,
-which keeps ||d||^2 <= 4D (Section 3.2 and the proof of Lemma 4.1).
+which keeps ||d||^2 <= 4D (Section 3.3 and the proof of Lemma 4.1).
 
 Dimension d = 1 is the fastest array axis (x), d = 2 is y, d = 3 is z.  A dual
 field P in R^{D x N} is stored as an array of shape (D, *x.shape) with
@@ -48,7 +48,7 @@ def forward_diff_T(q: np.ndarray, d: int) -> np.ndarray:
 
 
 def d_of(P: np.ndarray) -> np.ndarray:
-    """d(P) = sum_d (D^d)^T q_d (Section 3.2)."""
+    """d(P) = sum_d (D^d)^T q_d (Section 3.3)."""
     out = np.zeros(P.shape[1:], dtype=np.float64)
     for d in range(P.shape[0]):
         out += forward_diff_T(P[d], d)

@@ -1,15 +1,15 @@
 """Weighted proximal mapping of c*TV + box under B = tau*I + U U^T
 (FP64 oracle; test infrastructure only).
 
-Problem (Eq. 4.4 with B^k = tau* I + U U^T, Section 4.4):
+Problem (Eq. 4.5 with B^k = tau* I + U U^T, Section 4.3):
     x* = argmin_{x in C} 1/2 ||x - v||_B^2 + c TV(x),   C = [lo, hi]^N.
 Steps, in the paper's order:
-  * Woodbury inverse of B (Section 4.4);
-  * w(P) = v - c B^{-1} d(P) (Eq. 4.6);
+  * Woodbury inverse of B (Section 4.3);
+  * w(P) = v - c B^{-1} d(P) (defined with Eq. 4.7);
   * prox^B_{iota_C}(w) = clip(w - U beta*/tau) with beta* the root of
     phi(beta) = U^T(w - clip(w - U beta/tau)) + beta (Theorem 3.1, '+' case,
     h = iota_C), found by semi-smooth Newton (Algorithm 4.3);
-  * accelerated projected gradient on T(P) (Eq. 4.8) with the gradient of
+  * accelerated projected gradient on T(P) (Eq. 4.10) with the gradient of
     Lemma 4.1, step 1/Lip = omega_min/(4 D c) where omega_min(B) = tau
     (U U^T has rank <= S < N), momentum of Beck-Teboulle's FGP;
   * output x = prox^B_{iota_C}(w(P_J)).
@@ -40,7 +40,7 @@ def _flatU(U: Optional[np.ndarray], N: int) -> np.ndarray:
 
 def woodbury_inverse(tau: float, U: np.ndarray):
     """Return y -> B^{-1} y for B = tau I + U U^T (U is N x S):
-    B^{-1} = tau^{-1} I - tau^{-2} U (I + U^T U / tau)^{-1} U^T  (Section 4.4)."""
+    B^{-1} = tau^{-1} I - tau^{-2} U (I + U^T U / tau)^{-1} U^T  (Section 4.3)."""
     S = U.shape[1]
     small = np.eye(S) + (U.T @ U) / tau
 
@@ -123,7 +123,7 @@ class WProx:
                                self.newton_tol, self.newton_maxit)
 
     def T(self, v: np.ndarray, P: np.ndarray) -> float:
-        """T(P) = ||w||_B^2 - ||w - prox^B_C(w)||_B^2 (Eq. 4.8)."""
+        """T(P) = ||w||_B^2 - ||w - prox^B_C(w)||_B^2 (Eq. 4.10)."""
         w = self.w_of(v, P)
         x, _, _ = self.prox_box(w)
         e = w - x

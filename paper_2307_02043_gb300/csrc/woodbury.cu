@@ -1,6 +1,6 @@
 // Quasi-Newton point of Algorithm 4.1 for k > S:
 //   v_k = x - a S B^{-1} g,  B = tau* I + U U^T,
-//   B^{-1} = tau*^{-1} I - tau*^{-2} U (I + U^T U / tau*)^{-1} U^T   (Woodbury, Section 4.4).
+//   B^{-1} = tau*^{-1} I - tau*^{-2} U (I + U^T U / tau*)^{-1} U^T   (Woodbury, Section 4.3).
 // One reduction pass forms U^T U and U^T g; a one-block kernel forms the S x S
 // inverse; a last pass applies the low-rank correction.
 #include <algorithm>

@@ -1,4 +1,4 @@
-// The whole weighted proximal mapping (Eq. 4.4) as one cooperative kernel.
+// The whole weighted proximal mapping (Eq. 4.5) as one cooperative kernel.
 //
 // Phases, separated by grid-wide barriers (deterministic reductions: the last
 // block to arrive sums the per-block partials in a fixed order and releases

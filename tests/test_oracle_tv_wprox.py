@@ -22,7 +22,7 @@ def test_d_and_dT_are_adjoint_and_bounded():
         assert abs(np.sum(x * tvops.d_of(P)) - np.sum(tvops.dT(x) * P)) < 1e-12
         K = ind.grad_matrix(shape)
         assert np.allclose(K @ x.reshape(-1), tvops.dT(x).reshape(-1))
-        # ||d||^2 = ||K||^2 <= 4 D (Section 3.2 / Lemma 4.1)
+        # ||d||^2 = ||K||^2 <= 4 D (Section 3.3 / Lemma 4.1)
         assert np.linalg.norm(K, 2) ** 2 <= 4 * len(shape) + 1e-12
 
 
@@ -191,7 +191,7 @@ def test_duality_gap_decreases():
 
 
 def test_appendix_a_identity():
-    """argmin_{x in C} (1/S) sum_s Fbar_s(x) + lam TV(x) equals the WPM of Eq. (4.4)."""
+    """argmin_{x in C} (1/S) sum_s Fbar_s(x) + lam TV(x) (Eq. 4.4) equals the WPM of Eq. (4.5)."""
     rng = np.random.default_rng(11)
     shape = (3, 3, 3)
     N = 27
