@@ -271,6 +271,18 @@ class PlainPath:
 
 
 # -------------------------------------------------------------- oracle (CPU)
+def aggregate_ranks(torch, dist, device, ms, ms_e2e, illum, illum_e2e):
+    """Whole-job figures of replicated runs: the slowest rank's times (max) and
+    the illumination-gradients of all ranks (sum).  dist = None for one rank."""
+    if dist is None:
+        return float(ms), float(ms_e2e), float(illum), float(illum_e2e)
+    tt = torch.tensor([float(ms), float(ms_e2e)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cnt = torch.tensor([float(illum), float(illum_e2e)], dtype=torch.float64, device=device)
+    dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(tt[1]), float(cnt[0]), float(cnt[1])
+
+
 def oracle_sample(w, x_np, seconds_hint=20.0):
     """Bounded FP64 oracle sample: seconds per BiCGSTAB iteration of one LS
     forward solve at the workload size (K_hat set-up excluded)."""
@@ -472,19 +484,11 @@ def main():
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
     # ---- max over ranks
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, ms_e2e = float(tt[0]), float(tt[1])
-        cnt = torch.tensor([float(illum_done)], device=dev)
-        dist.all_reduce(cnt)
-        illum_total = float(cnt[0])
-    else:
-        illum_total = float(illum_done)
+    t_max, ms_e2e, illum_total, e2e_total = aggregate_ranks(torch, dist if world > 1 else None, dev, ms, ms_e2e,
+                                                            illum_done, e2e_illum)
     value = illum_total / (t_max / 1e3)
     iters_per_s = world * args.steps / (t_max / 1e3)
-    e2e_value = world * e2e_illum / (ms_e2e / 1e3)
+    e2e_value = e2e_total / (ms_e2e / 1e3)
     # ---- roofline of the dominant Green's pass
     N = w.N
     n = w.n
