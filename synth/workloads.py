@@ -148,10 +148,14 @@ def phantom(w: Workload) -> np.ndarray:
         hi_c = (n - 1) - w.margin - rmax
         centre = rng.uniform(lo_c, hi_c, size=3)          # (cx, cy, cz)
         value = rng.uniform(0.0, w.contrast_max)
-        d = np.stack([X - centre[0], Y - centre[1], Z - centre[2]], axis=-1)
+        # only the bounding box of the bounding sphere can be inside
+        lo = np.maximum(np.floor(centre - rmax).astype(int), 0)
+        hi = np.minimum(np.ceil(centre + rmax).astype(int) + 1, n)
+        box = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        d = np.stack([X[box] - centre[0], Y[box] - centre[1], Z[box] - centre[2]], axis=-1)
         local = d @ rot                                   # coordinates in the body frame
         inside = np.sum((local / axes) ** 2, axis=-1) <= 1.0
-        x = np.where(inside, np.maximum(x, value), x)
+        x[box] = np.where(inside, np.maximum(x[box], value), x[box])
     amp, sigma = w.background
     if amp > 0.0:
         mid = (n - 1) / 2.0
