@@ -1,0 +1,210 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration the
+bench times (batch 8 at 128^3, batch 16 at 192^3, the uneven grids 96^3 and
+160^3), through outputs the oracle computes one by one and properties that
+hold at any size.
+
+Tolerances (written per test):
+  * Green's apply: 2e-6 relative (max-norm), the complex64 transform floor, as
+    in the small-size parity tests.
+  * Born gradient: the Born loss is exactly quadratic in x, so its central
+    difference equals <grad, d> for any step; only FP32/complex64 rounding of
+    the fields remains: 1e-4.
+  * LS gradient: central difference with step 0.02 along the phantom; the
+    truncation term is ~(0.02 x phase shift)^2 ~ 1e-4 and the loss noise of a
+    1e-6 Krylov tolerance ~1e-5 / 0.16 relative, so 2e-3.
+  * batching: slots of one batched launch and separate launches differ only in
+    the summation order of the gradient over illuminations: 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import physics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2307_02043_gb300 import binding  # noqa: E402
+
+DEV = torch.device("cuda:0")
+KB = math.pi / 2
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def subset_of(w):
+    so = np.zeros(w.L, dtype=np.int32)
+    for s, ii in enumerate(synth.subsets(w)):
+        so[ii] = s
+    return so
+
+
+def handle(w, model, tol, max_batch, one_subset=False):
+    """A handle for workload w; one_subset puts every illumination in one
+    subset (the gradient calls below name their illuminations explicitly)."""
+    so = np.zeros(w.L, dtype=np.int32) if one_subset else subset_of(w)
+    S = 1 if one_subset else w.S
+    return binding.MQNPM(w.n, synth.illumination_dirs(w), so, [1.0] * S, model=model,
+                         krylov_tol=tol, krylov_maxit=500, max_batch=max_batch, tv=w.tv, lam=w.lam, box=w.box)
+
+
+def phantom(w):
+    return torch.from_numpy(synth.phantom(w).astype(np.float32)).to(DEV).reshape(-1)
+
+
+def measure(h, w, xt, illum):
+    """Noise-free data of the phantom for the illuminations used (others 0)."""
+    y_sub, _ = h.forward(xt, illum)
+    y = torch.zeros((w.L, w.n * w.n), dtype=torch.complex64, device=DEV)
+    y[torch.tensor(illum, device=DEV)] = y_sub
+    h.set_measurements(y.reshape(-1))
+
+
+def dot64(a, b):
+    return float(torch.dot(a.double(), b.double()))
+
+
+def central_difference_check(h, x0, d, illum, eps, tol):
+    g, f0, its = h.grad_batch(x0, illum, 1.0)
+    g = g.clone()
+    _, fp, _ = h.grad_batch(x0 + eps * d, illum, 1.0)
+    _, fm, _ = h.grad_batch(x0 - eps * d, illum, 1.0)
+    fd = (fp - fm) / (2 * eps)
+    an = dot64(g, d)
+    assert np.isfinite(f0) and f0 > 0
+    assert abs(fd - an) <= tol * abs(an), (fd, an, abs(fd - an) / abs(an))
+    return its
+
+
+# --------------------------------------------------------------- Green's apply
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_green_dense_128_matches_oracle(adjoint):
+    """All outputs of G v / G^H v at 128^3 (P = 256) against the FP64 oracle."""
+    n = 128
+    rng = np.random.default_rng(11 + adjoint)
+    v = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    w = synth.workload("ls128")
+    h = handle(w, "ls", 1e-4, 1)
+    out = h.green_apply(torch.from_numpy(v.astype(np.complex64)).to(DEV).reshape(-1), adjoint=adjoint)
+    ref = physics.green_apply(v, physics.green_hat(n, KB), adjoint=adjoint)
+    assert relmax(out.cpu().numpy().reshape(n, n, n), ref) < 2e-6
+    h.close()
+
+
+@pytest.mark.parametrize("n,adjoint", [(96, False), (160, False), (192, False), (192, True)])
+def test_green_sampled_direct_sum(n, adjoint):
+    """Grids of the uneven mix (96, 160) and of the large case (192, the largest
+    transform): sampled outputs against the direct sum over a sparse support."""
+    rng = np.random.default_rng(n)
+    v = np.zeros((n, n, n), dtype=np.complex128)
+    idx = rng.integers(0, n, size=(400, 3))
+    v[idx[:, 0], idx[:, 1], idx[:, 2]] = rng.standard_normal(400) + 1j * rng.standard_normal(400)
+    h = binding.MQNPM(n, [[0.0, 0.0, 1.0]], [0], [1.0], max_batch=1)
+    out = h.green_apply(torch.from_numpy(v.astype(np.complex64)).to(DEV).reshape(-1), adjoint=adjoint)
+    out = out.cpu().numpy().reshape(n, n, n)
+    w0 = physics.self_term(KB)
+    src = np.argwhere(v != 0)
+    vals = v[v != 0]
+    for probe in rng.integers(0, n, size=(16, 3)):
+        dd = src - probe[None, :]
+        r = np.sqrt(np.sum(dd * dd, axis=1).astype(np.float64))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.exp(1j * KB * r) / (4 * math.pi * r)
+        g[r == 0] = w0
+        if adjoint:
+            g = np.conj(g)
+        ref = KB ** 2 * np.sum(g * vals)
+        assert abs(out[tuple(probe)] - ref) <= 2e-6 * np.max(np.abs(out)) + 1e-6 * abs(ref), probe
+    h.close()
+
+
+# ------------------------------------------------------------------ gradients
+def test_born128_gradient_is_the_exact_derivative():
+    """born128, batch 8: the Born loss is quadratic, so the central difference
+    along the phantom equals <grad, d> up to rounding."""
+    w = synth.workload("born128")
+    h = handle(w, "born", 1e-6, w.batch)
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    measure(h, w, xt, illum)
+    central_difference_check(h, 0.5 * xt, xt, illum, 0.25, 1e-4)
+    h.close()
+
+
+def test_ls128_gradient_central_difference():
+    """ls128, batch 8 (the measured launch shape), Krylov tolerance 1e-6."""
+    w = synth.workload("ls128")
+    h = handle(w, "ls", 1e-6, w.batch)
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    assert len(illum) == 8
+    measure(h, w, xt, illum)
+    its = central_difference_check(h, 0.5 * xt, xt, illum, 0.02, 2e-3)
+    assert all(a > 0 and b > 0 for a, b in its)
+    h.close()
+
+
+def test_ls128_batched_equals_single_launches():
+    """The bench configuration (batch 8, tolerance 1e-4): each slot of the
+    batched solve gives the gradient and iteration counts of a solve alone."""
+    w = synth.workload("ls128")
+    hb = handle(w, "ls", w.krylov_tol, w.batch)
+    h1 = handle(w, "ls", w.krylov_tol, 1)
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    measure(hb, w, xt, illum)
+    measure(h1, w, xt, illum)
+    x0 = 0.5 * xt
+    gb, fb, itb = hb.grad_batch(x0, illum, 1.0)
+    gb = gb.clone()
+    acc = torch.zeros_like(gb, dtype=torch.float64)
+    f1 = 0.0
+    its1 = []
+    for l in illum:
+        g, f, it = h1.grad_batch(x0, [l], 1.0)
+        acc += g.double()
+        f1 += f
+        its1 += it
+    assert itb == its1
+    assert abs(fb - f1) <= 1e-6 * abs(f1)
+    assert float((gb.double() - acc).norm() / acc.norm()) < 1e-5
+    hb.close()
+    h1.close()
+
+
+def test_ls192_batch16_gradient():
+    """ls192 (the largest grid, P = 384), batch 16 workspace: the batched
+    gradient of 15 illuminations is finite and a 4-illumination central
+    difference matches it."""
+    w = synth.workload("ls192")
+    h = handle(w, "ls", 1e-6, w.batch)
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    assert len(illum) == 15
+    measure(h, w, xt, illum)
+    g, f, its = h.grad_batch(0.5 * xt, illum, w.S / w.L)
+    assert torch.isfinite(g).all() and f > 0 and all(a > 0 and b > 0 for a, b in its)
+    central_difference_check(h, 0.5 * xt, xt, illum[:4], 0.02, 2e-3)
+    h.close()
+
+
+@pytest.mark.parametrize("n", [96, 160])
+def test_uneven_grid_gradient(n):
+    """The first request of the uneven mix with grid n (its L, cone and batch
+    size b as the workspace): central difference of its first subset's
+    gradient.  The handle holds one subset because the mix has S = ceil(L/b)
+    up to 15 and the gradient does not depend on the partition."""
+    w = next(r for r in synth.uneven_requests() if r.n == n)
+    h = handle(w, "ls", 1e-6, w.batch, one_subset=True)
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    measure(h, w, xt, illum)
+    central_difference_check(h, 0.5 * xt, xt, illum, 0.02, 2e-3)
+    h.close()
