@@ -193,7 +193,11 @@ int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size);
  * long longs) receives out[1] = start time (ns, GPU global timer) and, for
  * e = 1..*count, the pair (tag, time) stamped when the e-th grid barrier was
  * passed (tags: 1 Gram set-up, 2 unweighted x, 3 divergence and U^T d,
- * 4 Newton evaluation, 5 x after a rejected trial, 6 dual update, 99 end). */
+ * 4 Newton evaluation, 5 x after a rejected trial, 6 dual update, 99 end),
+ * for at most 999 barriers.  With cap >= 1003, out[2000..2005] hold block 0's
+ * accumulated times (ns) in the dual update, before the dual update, in the
+ * Newton evaluation pass, in the Newton decision, in the divergence pass and
+ * waiting in grid barriers. */
 int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count);
 
 /* Number of CUDA kernels this handle has launched since creation. */

@@ -349,8 +349,10 @@ class MQNPM:
             out[key] = out.get(key, 0.0) + (t - prev) / 1e3
             out["total_us"] += (t - prev) / 1e3
             prev = t
-        out["dual_update_block0"] = buf[2000] / 1e3
-        out["pre_dual_block0"] = buf[2001] / 1e3
+        acc = ["dual_update_block0", "pre_dual_block0", "newton_pass_block0", "newton_decide_block0",
+               "div_pass_block0", "barrier_wait_block0"]
+        for k, nm in enumerate(acc):
+            out[nm] = buf[2000 + k] / 1e3
         return {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
 
     def profile_begin(self, max_calls: int = 4096):

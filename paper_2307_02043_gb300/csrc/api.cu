@@ -246,7 +246,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   need += B * ((size_t)n * n * P + (size_t)n * P * P) * 8; // T1, T2
   need += B * M * 8;                                       // rdet
   need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
-  need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * 44 + wp_blocks * 44 + 200) * 8;   // wprox
+  need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * 44 + 200) * 8 + wprox_part_count(wp_blocks) * 8;   // wprox
   need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
   if (h->budget > 0 && need > h->budget) {
     char msg[160];
@@ -282,12 +282,12 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(w.dscal, 64);
   WproxWork& wp = h->wp;
   AL(wp.R, 3 * N); AL(wp.Pd, 3 * N); AL(wp.d, N); AL(wp.x, N);
-  AL(wp.part, (size_t)wp_blocks * wprox_part_len());
+  AL(wp.part, wprox_part_count(wp_blocks));
   AL(wp.tot, (size_t)wprox_part_len());
   AL(wp.stat, 4);
   AL(wp.gram, (size_t)wp.ctas_vec * 44);
   AL(wp.scal, (size_t)woodbury_scal_count());
-  AL(wp.barrier, 2);
+  AL(wp.barrier, (size_t)wprox_barrier_words());
   AL(wp.err, 1);
   wp.trace_cap = 1024;
   AL(wp.trace, 2 * (size_t)wp.trace_cap);

@@ -82,12 +82,12 @@ struct WproxWork {
   float *R = nullptr, *Pd = nullptr, *d = nullptr, *x = nullptr;
   float* mom = nullptr;         // momentum table of the dual iterations (dual_iters)
   int mom_len = 0;
-  double* part = nullptr;       // [2 * nsm][44] per-block partials of the cooperative kernel
+  double* part = nullptr;       // per-block and per-group partials of the cooperative kernel
   double* tot = nullptr;        // [44] reduced totals
   double* stat = nullptr;       // [4] Newton statistics of the last call
   double* gram = nullptr;       // partials of the Woodbury Gram pass [ctas_vec][44]
   double* scal = nullptr;       // Woodbury scalars (G, M, U^T g)
-  unsigned* barrier = nullptr;  // [2]: arrival counter, released generation
+  unsigned* barrier = nullptr;  // arrival counters and released generation (wprox_barrier_words())
   int* err = nullptr;           // device error flag
   unsigned char* status = nullptr;  // per-voxel inner/clipped status of the Newton evaluations
   long long* trace = nullptr;   // phase trace of the last call: (tag, ns) per barrier
@@ -152,6 +152,8 @@ int qn_point_impl(mqnpm_handle* h, const float* x, const float* g, const UPtrs& 
                   double aS, float* v);
 std::vector<float> wprox_momentum(int J);
 int wprox_part_len();
+size_t wprox_part_count(int max_blocks);   // doubles of the partials buffer
+int wprox_barrier_words();                // unsigned words of the barrier counters
 int woodbury_scal_count();
 
 // status helpers (api.cu)

@@ -53,62 +53,66 @@ __global__ void k_gram(UPtrs U, const float* __restrict__ g, int N, double* part
   block_reduce_store<NG + S>(acc, part + (size_t)blockIdx.x * (NG + S));
 }
 
-template <int S>
-MQ_D bool chol_solve(double (&A)[S * S], double (&b)[S]) {
-  for (int j = 0; j < S; ++j) {
-    double s = A[j * S + j];
-    for (int k = 0; k < j; ++k) s -= A[j * S + k] * A[j * S + k];
-    if (!(s > 0.0)) return false;
-    const double l = sqrt(s);
-    A[j * S + j] = l;
-    for (int i = j + 1; i < S; ++i) {
-      double t = A[i * S + j];
-      for (int k = 0; k < j; ++k) t -= A[i * S + k] * A[j * S + k];
-      A[i * S + j] = t / l;
-    }
-  }
-  for (int i = 0; i < S; ++i) {
-    double t = b[i];
-    for (int k = 0; k < i; ++k) t -= A[i * S + k] * b[k];
-    b[i] = t / A[i * S + i];
-  }
-  for (int i = S - 1; i >= 0; --i) {
-    double t = b[i];
-    for (int k = i + 1; k < S; ++k) t -= A[k * S + i] * b[k];
-    b[i] = t / A[i * S + i];
-  }
-  return true;
-}
-
-// Reduce the partials; G, U^T g and M = (I + G/tau)^{-1} into scal.
+// Reduce the partials; G, U^T g and M = (I + G/tau)^{-1} into scal.  One warp
+// per reduced value (fixed order: deterministic); one Cholesky factorisation of
+// I + G/tau, then one thread per column of M for the two triangular solves.
 template <int S>
 __global__ void k_gram_setup(const double* part, int nctas, double tau, double* scal) {
   constexpr int NG = S * (S + 1) / 2, NV = NG + S;
-  __shared__ double scratch[32 * NV];
-  double v[NV], o[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  for (int c = threadIdx.x; c < nctas; c += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += part[(size_t)c * NV + k];
-  block_sum<NV>(v, scratch, o);
+  __shared__ double tot[NV];
+  __shared__ double A[S * S];
+  __shared__ int ok;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int k = warp; k < NV; k += nwarps) {
+    double v = 0.0;
+    for (int c = lane; c < nctas; c += 32) v += part[(size_t)c * NV + k];
+    v = warp_sum(v);
+    if (lane == 0) tot[k] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int k = 0;
-    for (int s = 0; s < S; ++s)
-      for (int t = s; t < S; ++t) {
-        scal[OFF_G + s * S + t] = o[k];
-        scal[OFF_G + t * S + s] = o[k];
+    for (int a = 0; a < S; ++a)
+      for (int b = a; b < S; ++b) {
+        scal[OFF_G + a * S + b] = tot[k];
+        scal[OFF_G + b * S + a] = tot[k];
+        A[a * S + b] = A[b * S + a] = (a == b ? 1.0 : 0.0) + tot[k] / tau;
         ++k;
       }
-    for (int s = 0; s < S; ++s) scal[OFF_UV + s] = o[NG + s];
-    for (int col = 0; col < S; ++col) {
-      double A[S * S], e[S];
-      for (int i = 0; i < S; ++i)
-        for (int j = 0; j < S; ++j) A[i * S + j] = (i == j ? 1.0 : 0.0) + scal[OFF_G + i * S + j] / tau;
-      for (int i = 0; i < S; ++i) e[i] = (i == col) ? 1.0 : 0.0;
-      chol_solve<S>(A, e);
-      for (int i = 0; i < S; ++i) scal[OFF_M + i * S + col] = e[i];
+    for (int a = 0; a < S; ++a) scal[OFF_UV + a] = tot[NG + a];
+    // lower Cholesky factor in place
+    ok = 1;
+    for (int j = 0; j < S; ++j) {
+      double d = A[j * S + j];
+      for (int q = 0; q < j; ++q) d -= A[j * S + q] * A[j * S + q];
+      if (!(d > 0.0)) { ok = 0; break; }
+      const double l = sqrt(d);
+      A[j * S + j] = l;
+      for (int i = j + 1; i < S; ++i) {
+        double t = A[i * S + j];
+        for (int q = 0; q < j; ++q) t -= A[i * S + q] * A[j * S + q];
+        A[i * S + j] = t / l;
+      }
     }
+  }
+  __syncthreads();
+  const int col = threadIdx.x;
+  if (col < S) {
+    double b[S];
+    for (int i = 0; i < S; ++i) b[i] = (i == col) ? 1.0 : 0.0;
+    if (ok) {
+      for (int i = 0; i < S; ++i) {
+        double t = b[i];
+        for (int q = 0; q < i; ++q) t -= A[i * S + q] * b[q];
+        b[i] = t / A[i * S + i];
+      }
+      for (int i = S - 1; i >= 0; --i) {
+        double t = b[i];
+        for (int q = i + 1; q < S; ++q) t -= A[q * S + i] * b[q];
+        b[i] = t / A[i * S + i];
+      }
+    }
+    for (int i = 0; i < S; ++i) scal[OFF_M + i * S + col] = b[i];
   }
 }
 

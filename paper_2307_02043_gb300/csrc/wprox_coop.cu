@@ -27,6 +27,19 @@ namespace {
 constexpr int WP_THREADS = 256;
 constexpr int NW = WP_THREADS / 32;
 constexpr int NVMAX = 44;     // S + S(S+1)/2 for S = 8
+// Trace layout (long long pairs): pair 0 = (barriers passed, start time),
+// pairs 1..TR_ACC-1 = (tag, time) per barrier, pairs from TR_ACC on hold block
+// 0's accumulated times: [2 TR_ACC] dual update, [+1] work before the dual
+// update, [+2] Newton evaluation pass, [+3] Newton decision (thread 0),
+// [+4] divergence pass, [+5] waiting in grid barriers.
+constexpr int TR_ACC = 1000;
+constexpr int TR_SLOTS = 6;
+// Grid barriers that carry sums reduce in two levels: groups of WP_GS
+// consecutive blocks (the last block of a group to arrive sums its group's
+// partials), then the last group reducer sums the group sums.  At most
+// WP_MAXG groups.
+constexpr int WP_GS = 16;
+constexpr int WP_MAXG = 64;
 
 struct WpArgs {
   const float* v;
@@ -37,15 +50,19 @@ struct WpArgs {
   float* x;
   float* xout;
   const float* mom;
-  double* part;           // [NVMAX][gridDim.x] (value-major)
+  double* part;           // [gridDim.x][NVMAX] block partials, then [WP_MAXG][NVMAX] group sums
   double* tot;            // [NVMAX]
-  unsigned* count;        // arrivals (monotonic)
+  unsigned* count;        // arrivals at barriers without sums (monotonic)
   unsigned* gen;          // released barrier generation
+  unsigned* count_groups; // group sums finished (monotonic)
+  unsigned* gcount;       // [WP_MAXG] arrivals per group (monotonic)
   int* err;
   double* stat;           // [0] last newton count, [1] max, [2] total, [3] evaluations
   unsigned char* status;  // per voxel: 1 if the last evaluated z was strictly inside the box
   int n, N, J;
   double tau, c;
+  double inv_tau, c_tau, c_tau2;   // 1/tau, c/tau, c/tau^2 (FP64 divisions are slow on the device)
+  float cdt;                       // (float) c/tau
   float lo, hi, step;
   double tol;
   int maxit;
@@ -66,6 +83,11 @@ MQ_D long long globaltimer() {
   return t;
 }
 
+MQ_D bool tracer(const WpArgs& a) { return a.trace && blockIdx.x == 0 && threadIdx.x == 0; }
+MQ_D void tr_add(const WpArgs& a, int slot, long long dt) {
+  if (tracer(a)) a.trace[2 * TR_ACC + slot] += dt;
+}
+
 // Four consecutive floats as an addressable array.
 struct F4 {
   float v[4];
@@ -84,64 +106,121 @@ struct F4 {
   }
 };
 
-// Grid-wide barrier with an optional sum of NV doubles per block (blk[], shared).
-// Partials are stored value-major, part[k * gridDim.x + b]; the last block to
-// arrive reduces value k in warp k % nwarps: lane sums a fixed stripe of blocks,
-// then a fixed shuffle tree, so the order is deterministic.  The totals land in
-// sh_tot (shared) for every thread.
-template <int NV>
-MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, unsigned& epoch, int tag) {
-  __shared__ int s_last, s_ok;
-  __syncthreads();
-  if constexpr (NV > 0) {
-    if (threadIdx.x < NV) a.part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = blk[threadIdx.x];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned old = atomicAdd(a.count, 1u);
-    s_last = (old == (epoch + 1) * gridDim.x - 1) ? 1 : 0;
-    s_ok = 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    if constexpr (NV > 0) {
-      __threadfence();
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      const int nb = gridDim.x;
-      for (int k = warp; k < NV; k += NW) {
-        const double* p = a.part + (size_t)k * nb;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int b = lane;
-        for (; b + 96 < nb; b += 128) {
-          a0 += __ldcg(p + b);
-          a1 += __ldcg(p + b + 32);
-          a2 += __ldcg(p + b + 64);
-          a3 += __ldcg(p + b + 96);
-        }
-        for (; b < nb; b += 32) a0 += __ldcg(p + b);
-        const double s = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) a.tot[k] = s;
-      }
-      __syncthreads();
+// Barrier counters of one launch: every block passes the same sequence of
+// barriers, so these agree across blocks.
+struct Epochs {
+  unsigned all = 0;    // barriers passed (the released generation)
+  unsigned flat = 0;   // barriers without sums
+  unsigned hier = 0;   // barriers with sums
+};
+
+MQ_D bool wait_generation(const WpArgs& a, unsigned target) {
+  const long long t0 = clock64();
+  while (ld_acquire_u32(a.gen) < target) {
+    if (*((volatile int*)a.err) != 0) return false;
+    if (clock64() - t0 > a.limit) {
+      atomicExch(a.err, 1);
+      return false;
     }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Grid-wide barrier with an optional sum of NV doubles per block (blk[],
+// shared).  NV = 0: one arrival counter, the last block releases.  NV > 0:
+// each block stores its partials (block-major); the last block of each group
+// of WP_GS blocks sums the group's partials in block order, and the last group
+// to finish sums the group sums in group order and releases the others, so the
+// totals are deterministic.  The totals land in sh_tot (shared) for every
+// thread.
+template <int NV>
+MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs& ep, int tag) {
+  __shared__ int s_role, s_ok;   // role: 0 waits, 1 group reducer, 2 releases
+  const long long t_in = tracer(a) ? globaltimer() : 0;
+  __syncthreads();
+  const unsigned target = ep.all + 1;
+  if constexpr (NV == 0) {
     if (threadIdx.x == 0) {
       __threadfence();
-      st_release_u32(a.gen, epoch + 1);
+      const unsigned old = atomicAdd(a.count, 1u);
+      s_role = (old == (ep.flat + 1) * gridDim.x - 1) ? 2 : 0;
+      s_ok = 1;
+      if (s_role == 2) {
+        __threadfence();
+        st_release_u32(a.gen, target);
+      } else if (!wait_generation(a, target)) {
+        s_ok = 0;
+      }
     }
-  } else if (threadIdx.x == 0) {
-    const long long t0 = clock64();
-    while (ld_acquire_u32(a.gen) < epoch + 1) {
-      if (*((volatile int*)a.err) != 0) { s_ok = 0; break; }
-      if (clock64() - t0 > a.limit) { atomicExch(a.err, 1); s_ok = 0; break; }
-      __nanosleep(32);
+    __syncthreads();
+    ep.flat += 1;
+  } else {
+    if (threadIdx.x < NV) a.part[(size_t)blockIdx.x * NVMAX + threadIdx.x] = blk[threadIdx.x];
+    __syncthreads();
+    const int g = blockIdx.x / WP_GS, g0 = g * WP_GS;
+    const int gsize = min(WP_GS, (int)gridDim.x - g0);
+    const int ngroups = ((int)gridDim.x + WP_GS - 1) / WP_GS;
+    double* gpart = a.part + (size_t)gridDim.x * NVMAX;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned old = atomicAdd(a.gcount + g, 1u);
+      s_role = (old == (ep.hier + 1) * (unsigned)gsize - 1) ? 1 : 0;
+      s_ok = 1;
     }
+    __syncthreads();
+    if (s_role == 1) {
+      __threadfence();
+      if (threadIdx.x < NV) {
+        double vals[WP_GS];
+#pragma unroll
+        for (int j = 0; j < WP_GS; ++j)
+          vals[j] = (j < gsize) ? __ldcg(a.part + (size_t)(g0 + j) * NVMAX + threadIdx.x) : 0.0;
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < WP_GS; ++j) acc += vals[j];
+        gpart[(size_t)g * NVMAX + threadIdx.x] = acc;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(a.count_groups, 1u);
+        if (old == (ep.hier + 1) * (unsigned)ngroups - 1) s_role = 2;
+      }
+      __syncthreads();
+      if (s_role == 2) {
+        __threadfence();
+        if (threadIdx.x < NV) {
+          double acc = 0.0;
+          for (int q0 = 0; q0 < ngroups; q0 += 8) {
+            double vals[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              vals[q] = (q0 + q < ngroups) ? __ldcg(gpart + (size_t)(q0 + q) * NVMAX + threadIdx.x) : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc += vals[q];
+          }
+          a.tot[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          st_release_u32(a.gen, target);
+        }
+      }
+    }
+    if (s_role != 2 && threadIdx.x == 0 && !wait_generation(a, target)) s_ok = 0;
+    __syncthreads();
+    ep.hier += 1;
   }
-  __syncthreads();
-  epoch += 1;
-  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && (int)epoch < a.trace_cap) {
-    a.trace[2 * epoch] = tag;
-    a.trace[2 * epoch + 1] = globaltimer();
+  ep.all += 1;
+  if (tracer(a)) {
+    const long long t = globaltimer();
+    if ((int)ep.all < TR_ACC) {
+      a.trace[2 * ep.all] = tag;
+      a.trace[2 * ep.all + 1] = t;
+    }
+    a.trace[2 * TR_ACC + 5] += t - t_in;
   }
   if (!s_ok) return false;
   if constexpr (NV > 0) {
@@ -199,43 +278,55 @@ MQ_D void project(float& px, float& py, float& pz) {
   }
 }
 
+// Cholesky factor of a small SPD matrix in place (lower triangle), with the
+// reciprocals of the diagonal in rd.  One FP64 division and one square root per
+// column: FP64 division is a long instruction sequence on this device.
 template <int S>
-MQ_D bool chol_solve(double (&A)[S * S], double (&b)[S]) {
+MQ_D bool chol_factor(double (&A)[S * S], double (&rd)[S]) {
   for (int j = 0; j < S; ++j) {
     double s = A[j * S + j];
     for (int k = 0; k < j; ++k) s -= A[j * S + k] * A[j * S + k];
     if (!(s > 0.0)) return false;
-    const double l = sqrt(s);
-    A[j * S + j] = l;
+    const double r = 1.0 / sqrt(s);
+    A[j * S + j] = s * r;
+    rd[j] = r;
     for (int i = j + 1; i < S; ++i) {
       double t = A[i * S + j];
       for (int k = 0; k < j; ++k) t -= A[i * S + k] * A[j * S + k];
-      A[i * S + j] = t / l;
+      A[i * S + j] = t * r;
     }
-  }
-  for (int i = 0; i < S; ++i) {
-    double t = b[i];
-    for (int k = 0; k < i; ++k) t -= A[i * S + k] * b[k];
-    b[i] = t / A[i * S + i];
-  }
-  for (int i = S - 1; i >= 0; --i) {
-    double t = b[i];
-    for (int k = i + 1; k < S; ++k) t -= A[k * S + i] * b[k];
-    b[i] = t / A[i * S + i];
   }
   return true;
 }
 
-// M = (I + G/tau)^{-1} column by column (S x S, FP64).  Called by one thread;
-// kept out of line so its scratch does not cost the streaming loops registers.
+// Solve (L L^T) b = b with the factor of chol_factor.
 template <int S>
-__device__ __noinline__ void form_woodbury(const double* G, double tau, double* M) {
+MQ_D void chol_apply(const double (&A)[S * S], const double (&rd)[S], double (&b)[S]) {
+  for (int i = 0; i < S; ++i) {
+    double t = b[i];
+    for (int k = 0; k < i; ++k) t -= A[i * S + k] * b[k];
+    b[i] = t * rd[i];
+  }
+  for (int i = S - 1; i >= 0; --i) {
+    double t = b[i];
+    for (int k = i + 1; k < S; ++k) t -= A[k * S + i] * b[k];
+    b[i] = t * rd[i];
+  }
+}
+
+// M = (I + G/tau)^{-1} (S x S, FP64): one factorisation, S solves.  Called by
+// one thread; kept out of line so its scratch does not cost the streaming loops
+// registers.
+template <int S>
+__device__ __noinline__ void form_woodbury(const double* G, double inv_tau, double* M) {
+  double A[S * S], rd[S];
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) A[i * S + j] = (i == j ? 1.0 : 0.0) + G[i * S + j] * inv_tau;
+  const bool ok = chol_factor<S>(A, rd);
   for (int col = 0; col < S; ++col) {
-    double A[S * S], e[S];
-    for (int i = 0; i < S; ++i)
-      for (int j = 0; j < S; ++j) A[i * S + j] = (i == j ? 1.0 : 0.0) + G[i * S + j] / tau;
+    double e[S];
     for (int i = 0; i < S; ++i) e[i] = (i == col) ? 1.0 : 0.0;
-    chol_solve<S>(A, e);
+    if (ok) chol_apply<S>(A, rd, e);
     for (int i = 0; i < S; ++i) M[i * S + col] = e[i];
   }
 }
@@ -261,7 +352,7 @@ struct NewtonState {
 // ||phi|| <= tol_abs, else take the Newton step -H^{-1} phi from the accepted
 // point, H = I + htri/tau; a rejected trial is halved.  Returns 1 when done.
 template <int S>
-__device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, const double* htri, double tau,
+__device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, const double* htri, double inv_tau,
                                           double tol_abs, int maxit, bool out_of_evals) {
   double phi[S], nphi = 0.0;
   for (int s = 0; s < S; ++s) {
@@ -288,13 +379,15 @@ __device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, 
   int k = 0;
   for (int s = 0; s < S; ++s)
     for (int t = s; t < S; ++t) {
-      const double hst = htri[k++] / tau + (s == t ? 1.0 : 0.0);
+      const double hst = htri[k++] * inv_tau + (s == t ? 1.0 : 0.0);
       H[s * S + t] = hst;
       H[t * S + s] = hst;
     }
   double rhs[S];
   for (int s = 0; s < S; ++s) rhs[s] = -phi[s];
-  if (!chol_solve<S>(H, rhs)) return 1;
+  double rd[S];
+  if (!chol_factor<S>(H, rd)) return 1;
+  chol_apply<S>(H, rd, rhs);
   for (int s = 0; s < S; ++s) {
     ns.dir[s] = rhs[s];
     ns.beta_eval[s] = ns.beta[s] + rhs[s];
@@ -400,7 +493,7 @@ __device__ __noinline__ void pass_x(const WpArgs* pa, const float* src, float* x
   const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
   const int n = a.n, N = a.N, N4 = a.N / 4;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const float cdt = (float)(a.c / a.tau);
+  const float cdt = a.cdt;
   for (int k4 = tid; k4 < N4; k4 += stride) {
     int x0, y, z;
     coords4(k4, n, x0, y, z);
@@ -424,7 +517,7 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const int gw = tid >> 5, nwt = stride >> 5;
-  const float cdt = (float)(a.c / a.tau);
+  const float cdt = a.cdt;
   int ps0 = 0, pt0 = 0, ps1 = 0, pt1 = 0;   // this lane's pairs: lane, lane + 32
   {
     int k = 0;
@@ -520,7 +613,7 @@ template <int S>
 __device__ __noinline__ void pass_fixup(Shared<S>* sh, float* xw) {
   const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
   const int N4 = a.N / 4, tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const float cdt = (float)(a.c / a.tau);
+  const float cdt = a.cdt;
   float th[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) th[s] = sh->theta[s];
@@ -620,16 +713,15 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
   if (threadIdx.x == 0) sh.a = args;
   __syncthreads();
   const WpArgs& a = sh.a;
-  unsigned epoch = 0;
-  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+  Epochs ep;
+  if (tracer(a)) {
     a.trace[1] = globaltimer();
-    a.trace[2 * 1000] = 0;
-    a.trace[2 * 1000 + 1] = 0;
+    for (int k = 0; k < TR_SLOTS; ++k) a.trace[2 * TR_ACC + k] = 0;
   }
 
   if constexpr (S > 0) {
     pass_gram<S>(&sh);
-    if (!grid_reduce<NG + S>(sh.blk, sh.tot, a, epoch, 1)) return;
+    if (!grid_reduce<NG + S>(sh.blk, sh.tot, a, ep, 1)) return;
     if (threadIdx.x == 0) {
       int k = 0;
       for (int s = 0; s < S; ++s)
@@ -640,7 +732,7 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
           ++k;
         }
       for (int s = 0; s < S; ++s) sh.Uv[s] = sh.tot[NG + s];
-      form_woodbury<S>(sh.G, a.tau, sh.M);
+      form_woodbury<S>(sh.G, a.inv_tau, sh.M);
       for (int s = 0; s < S; ++s) sh.beta[s] = 0.0;
     }
     __syncthreads();
@@ -653,19 +745,21 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
     float* xw = final_eval ? a.xout : a.x;
     if constexpr (S == 0) {
       pass_x(&sh.a, src, xw);
-      if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, epoch, 2)) return;
+      if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, ep, 2)) return;
     } else {
+      long long t0 = tracer(a) ? globaltimer() : 0;
       pass_div<S>(&sh, src);
-      if (!grid_reduce<S>(sh.blk, sh.tot, a, epoch, 3)) return;
+      if (tracer(a)) tr_add(a, 4, globaltimer() - t0);
+      if (!grid_reduce<S>(sh.blk, sh.tot, a, ep, 3)) return;
       if (threadIdx.x == 0) {
         double nrm = 0.0;
         for (int s = 0; s < S; ++s) {
           double g = 0.0;
           for (int t = 0; t < S; ++t) g += sh.M[s * S + t] * sh.tot[t];
-          sh.gamma[s] = a.c / (a.tau * a.tau) * g;
+          sh.gamma[s] = a.c_tau2 * g;
         }
         for (int s = 0; s < S; ++s) {
-          double g = sh.Uv[s] - a.c / a.tau * sh.tot[s];
+          double g = sh.Uv[s] - a.c_tau * sh.tot[s];
           for (int t = 0; t < S; ++t) g += sh.G[s * S + t] * sh.gamma[t];
           nrm += g * g;       // (U^T w)_s
         }
@@ -687,22 +781,26 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
       int my_evals = 0;
       while (true) {
         if (threadIdx.x < S) {
-          sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta_eval[threadIdx.x] / a.tau);
+          sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta_eval[threadIdx.x] * a.inv_tau);
           sh.gam[threadIdx.x] = (float)sh.gamma[threadIdx.x];
         }
         __syncthreads();
+        t0 = tracer(a) ? globaltimer() : 0;
         pass_newton<S>(&sh, xw);
-        if (!grid_reduce<NV>(sh.blk, sh.tot, a, epoch, 4)) return;
+        if (tracer(a)) tr_add(a, 2, globaltimer() - t0);
+        if (!grid_reduce<NV>(sh.blk, sh.tot, a, ep, 4)) return;
         ++my_evals;
         if (threadIdx.x < NG) sh.Htot[threadIdx.x] += sh.tot[S + threadIdx.x];
         __syncthreads();
         if (threadIdx.x == 0) {
+          t0 = tracer(a) ? globaltimer() : 0;
           NewtonState<S> ns{sh.beta, sh.beta_eval, sh.dir, sh.phi_cur, &sh.nphi_cur, &sh.tstep, &sh.halvings,
                             &sh.accepted, &sh.first, &sh.accepted_last};
-          const int done = newton_decide<S>(ns, sh.tot, sh.Htot, a.tau, a.tol * sh.scale, a.maxit,
+          const int done = newton_decide<S>(ns, sh.tot, sh.Htot, a.inv_tau, a.tol * sh.scale, a.maxit,
                                             my_evals >= max_evals);
           sh.done = done;
           if (done) last_newton = sh.accepted;
+          if (tracer(a)) tr_add(a, 3, globaltimer() - t0);
         }
         __syncthreads();
         if (sh.done) break;
@@ -714,29 +812,29 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
       evals += my_evals;
       if (!sh.accepted_last) {
         // the last evaluation was a rejected trial: write x for the accepted beta
-        if (threadIdx.x < S) sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta[threadIdx.x] / a.tau);
+        if (threadIdx.x < S) sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta[threadIdx.x] * a.inv_tau);
         __syncthreads();
         pass_fixup<S>(&sh, xw);
-        if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, epoch, 5)) return;
+        if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, ep, 5)) return;
       }
     }
     if (final_eval) break;
     long long t_pre = 0;
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) t_pre = globaltimer();
+    if (tracer(a)) t_pre = globaltimer();
     pass_dual<TV>(&sh.a, a.mom[j]);
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (tracer(a)) {
       // block 0's own time in the dual update and in the work since the last barrier
       const long long t_post = globaltimer();
-      a.trace[2 * 1000] += t_post - t_pre;
-      a.trace[2 * 1000 + 1] += t_pre - a.trace[2 * epoch + 1];
+      a.trace[2 * TR_ACC] += t_post - t_pre;
+      if ((int)ep.all < TR_ACC) a.trace[2 * TR_ACC + 1] += t_pre - a.trace[2 * ep.all + 1];
     }
-    if (!grid_reduce<0>(nullptr, nullptr, a, epoch, 6)) return;
+    if (!grid_reduce<0>(nullptr, nullptr, a, ep, 6)) return;
   }
-  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
-    a.trace[0] = epoch;                 // number of barriers passed; entry 0 also holds the start time
-    if ((int)epoch + 1 < a.trace_cap) {
-      a.trace[2 * (epoch + 1)] = 99;    // end of kernel
-      a.trace[2 * (epoch + 1) + 1] = globaltimer();
+  if (tracer(a)) {
+    a.trace[0] = ep.all;                // number of barriers passed; entry 0 also holds the start time
+    if ((int)ep.all + 1 < TR_ACC) {
+      a.trace[2 * (ep.all + 1)] = 99;   // end of kernel
+      a.trace[2 * (ep.all + 1) + 1] = globaltimer();
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -754,6 +852,7 @@ cudaError_t launch_wprox(mqnpm_handle* h, WpArgs& a) {
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   const int blocks = h->wp.nsm * std::min(per_sm, 2);
+  if (blocks > WP_GS * WP_MAXG) return cudaErrorInvalidConfiguration;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((void*)k_wprox<S, TV>, dim3(blocks), dim3(WP_THREADS), args, 0, h->stream);
 }
@@ -803,7 +902,7 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   }
   CK(cudaMemcpyAsync(h->wp.R, h->wp.Pd, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(h->wp.err, 0, sizeof(int), s));
-  CK(cudaMemsetAsync(h->wp.barrier, 0, 2 * sizeof(unsigned), s));
+  CK(cudaMemsetAsync(h->wp.barrier, 0, wprox_barrier_words() * sizeof(unsigned), s));
   if (S_eff > 0) CK(cudaMemsetAsync(h->wp.status, 1, N, s));
   WpArgs a;
   a.v = v;
@@ -818,6 +917,8 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.tot = h->wp.tot;
   a.count = h->wp.barrier;
   a.gen = h->wp.barrier + 1;
+  a.count_groups = h->wp.barrier + 2;
+  a.gcount = h->wp.barrier + 3;
   a.err = h->wp.err;
   a.stat = h->wp.stat;
   a.status = h->wp.status;
@@ -826,6 +927,10 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.J = J;
   a.tau = tau;
   a.c = c;
+  a.inv_tau = 1.0 / tau;
+  a.c_tau = c / tau;
+  a.c_tau2 = c / (tau * tau);
+  a.cdt = (float)(c / tau);
   a.lo = (float)h->lo;
   a.hi = (float)h->hi;
   a.step = (float)(tau / (4.0 * 3.0 * c));
@@ -863,3 +968,5 @@ std::vector<float> wprox_momentum(int J) {
 }
 
 int wprox_part_len() { return NVMAX; }
+size_t wprox_part_count(int max_blocks) { return (size_t)(max_blocks + WP_MAXG) * NVMAX; }
+int wprox_barrier_words() { return 3 + WP_MAXG; }
