@@ -74,7 +74,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
   }
   if (c.ev) cudaEventRecord(c.ev[2], s);
   {
-    // one CTA per (kx tile, ky) column set; the batch is looped inside (TMA double buffer)
+    // one CTA per (kx tile, ky) column set; the batch is looped inside (one TMA tile buffer)
     dim3 grid(P / CS::C, P);
     const int smem = (int)Pass3Smem<P>::bytes(c.n);
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);

@@ -220,43 +220,54 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
 }
 
 // ------------------------------------- pass 3: z forward, * K_hat, z inverse
-// One CTA per (kx tile, ky) column set, looping over the batch slots: the
-// K_hat tile of the column set (P x C values) is read once into shared
-// memory and reused for every slot, and the input tile of the next slot
-// (rows z < n, C columns, 16 KB at n = 128) is fetched by one TMA tensor load
-// into the other half of a double buffer while the current slot is
-// transformed.  In place on T2/T3 [b][z][ky][kx]; only rows z < n are read
-// and written.
+// One CTA per (kx tile of C columns, ky) column set, looping over the batch
+// slots.  K_hat is even in kz, so the CTA keeps only the folded half of its
+// columns' spectrum (n + 1 rows) in shared memory, read once for all slots.
+// A slot's input tile (rows z < n of the C columns, 16 KB at n = 128) arrives
+// by one TMA tensor copy; as soon as the first transform stage has consumed
+// it, the copy of the next active slot's tile is issued into the same buffer,
+// so it overlaps the remaining three stages.  One tile buffer (instead of two)
+// keeps shared memory at 68 KB for P = 256: three CTAs per SM.  In place on
+// T2/T3 [b][z][ky][kx]; only rows z < n are read and written.
 template <int P>
 struct Pass3Smem {
   using SH = ColShape<P>;
   static constexpr int C = SH::C;
-  static MQ_HD size_t tw_off() { return 0; }
-  static MQ_HD size_t kh_off() { return P * sizeof(float2); }
-  static MQ_HD size_t ex_off() { return kh_off() + (size_t)P * C * sizeof(float2); }
-  static MQ_HD size_t in_off() {   // 1 KB aligned TMA destinations
+  static constexpr int KH = P / 2 + 1;   // folded kz rows of K_hat
+  static constexpr MQ_HD size_t tw_off() { return 0; }
+  static constexpr MQ_HD size_t kh_off() { return P * sizeof(float2); }
+  static constexpr MQ_HD size_t ex_off() { return kh_off() + (size_t)KH * C * sizeof(float2); }
+  static constexpr MQ_HD size_t in_off() {   // 1 KB aligned TMA destination
     const size_t o = ex_off() + (size_t)P * C * sizeof(float2);
     return (o + 1023) & ~(size_t)1023;
   }
-  static MQ_HD size_t in_bytes(int n) { return (size_t)n * C * sizeof(float2); }
-  static MQ_HD size_t bar_off(int n) { return in_off() + 2 * in_bytes(n); }
-  static MQ_HD size_t bytes(int n) { return bar_off(n) + 2 * sizeof(uint64_t) + 1024; }   // + base alignment slack
+  static constexpr MQ_HD size_t in_bytes(int n) { return (size_t)n * C * sizeof(float2); }
+  static constexpr MQ_HD size_t bar_off(int n) { return in_off() + in_bytes(n); }
+  static constexpr MQ_HD size_t bytes(int n) { return bar_off(n) + sizeof(uint64_t) + 1024; }   // + base alignment slack
+};
+
+// Blocks per SM the pass-3 kernel is compiled for (register cap): three when
+// its shared memory allows it.
+template <int P>
+struct Pass3Occ {
+  static constexpr size_t SMEM = Pass3Smem<P>::in_off() + (size_t)(P / 2) * Pass3Smem<P>::C * sizeof(float2) + 1032;
+  static constexpr int MIN_BLOCKS = (3 * SMEM <= 220 * 1024 && ColShape<P>::THREADS <= 256) ? 3 : 2;
 };
 
 template <int P, bool CONJ>
-__global__ void __launch_bounds__(ColShape<P>::THREADS)
+__global__ void __launch_bounds__(ColShape<P>::THREADS, Pass3Occ<P>::MIN_BLOCKS)
 k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int n,
         int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
   using PL = Plan<P>;
   using SH = ColShape<P>;
   using SM = Pass3Smem<P>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C, KH = SM::KH;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   float2* tw = reinterpret_cast<float2*>(sm + SM::tw_off());
   float2* kh = reinterpret_cast<float2*>(sm + SM::kh_off());
   float2* ex = reinterpret_cast<float2*>(sm + SM::ex_off());
-  float2* in0 = reinterpret_cast<float2*>(sm + SM::in_off());
+  float2* in = reinterpret_cast<float2*>(sm + SM::in_off());
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::bar_off(n));
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
   const int kx0 = blockIdx.x * C, kx = kx0 + c;
@@ -269,45 +280,33 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   while (b < nb && !active(b)) ++b;
   if (b >= nb) return;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(bar, 1);
     fence_mbar_init();
     fence_proxy_async();
-    mbar_expect_tx(&bar[0], tile_bytes);
-    tma_load_3d(in0, &tmap, &bar[0], kx0, ky, b * n);
+    mbar_expect_tx(bar, tile_bytes);
+    tma_load_3d(in, &tmap, bar, kx0, ky, b * n);
   }
   for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
   {
     const int fx = kx <= n ? kx : P - kx;
     const int fy = ky <= n ? ky : P - ky;
     const float2* kcol = khat + (size_t)fy * m1 + fx;
-    for (int kz = t; kz < P; kz += T) {
-      const int fz = kz <= n ? kz : P - kz;
+    for (int fz = t; fz < KH; fz += T) {
       float2 v = kcol[(size_t)fz * m1 * m1];
       if (CONJ) v.y = -v.y;
-      kh[kz * C + c] = v;
+      kh[fz * C + c] = v;
     }
   }
   __syncthreads();
-  uint32_t phase[2] = {0u, 0u};
-  int buf = 0;
+  uint32_t phase = 0u;
   while (b < nb) {
-    int next = b + 1;
-    while (next < nb && !active(next)) ++next;
-    if (next < nb && threadIdx.x == 0) {
-      // the other buffer was last read before the closing barrier of the previous slot
-      mbar_expect_tx(&bar[buf ^ 1], tile_bytes);
-      tma_load_3d(reinterpret_cast<unsigned char*>(in0) + (buf ^ 1) * tile_bytes, &tmap, &bar[buf ^ 1], kx0, ky,
-                  next * n);
-    }
-    if (!mbar_wait_bounded(&bar[buf], phase[buf], 1 << 22)) {
+    if (!mbar_wait_bounded(bar, phase, 1 << 22)) {
       if (threadIdx.x == 0) atomicExch(err, 1);
-      // let any other copy in flight land before the CTA exits (bounded as well)
-      if (next < nb) mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1], 1 << 22);
+      // the copy given up on is the only one in flight: give it one more bounded wait
+      mbar_wait_bounded(bar, phase, 1 << 22);
       return;
     }
-    phase[buf] ^= 1u;
-    const float2* in = reinterpret_cast<const float2*>(reinterpret_cast<const unsigned char*>(in0) + buf * tile_bytes);
+    phase ^= 1u;
     float2* col = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
     // forward stage 1 (n2-threads), inputs z = R2 n1 + n2 < n from the TMA tile [z][c]
 #pragma unroll
@@ -323,7 +322,14 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) ex[(n2 * R1 + k1) * C + c] = cmul(a[k1], tw[n2 * k1]);
     }
-    __syncthreads();
+    __syncthreads();   // the tile is consumed: fetch the next active slot's into the same buffer
+    int next = b + 1;
+    while (next < nb && !active(next)) ++next;
+    if (next < nb && threadIdx.x == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar, tile_bytes);
+      tma_load_3d(in, &tmap, bar, kx0, ky, next * n);
+    }
     // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread)
     float2 zb[R1 / T][R2];
 #pragma unroll
@@ -334,7 +340,10 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       for (int n2 = 0; n2 < R2; ++n2) a[n2] = ex[(n2 * R1 + k1) * C + c];
       dft<R2, false>(a);
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) a[k2] = cmul(a[k2], kh[(k1 + R1 * k2) * C + c]);
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const int kz = k1 + R1 * k2;
+        a[k2] = cmul(a[k2], kh[(kz <= P / 2 ? kz : P - kz) * C + c]);
+      }
       dft<R2, true>(a);   // over k2 -> j1
 #pragma unroll
       for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = cmul(a[j1], cconj(tw[j1 * k1]));
@@ -358,8 +367,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
 #pragma unroll
       for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(j1 + R2 * j2) * zs] = a[j2];
     }
-    __syncthreads();   // ex and the current input buffer are free again
+    __syncthreads();   // ex is free again for the next slot's first stage
     b = next;
-    buf ^= 1;
   }
 }
