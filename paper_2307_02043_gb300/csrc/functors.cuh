@@ -61,10 +61,13 @@ struct Pro<PRO_BICG_P> {
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
     const size_t i = g.vox(b, x, y, z);
-    const float2 beta = make_float2((float)st[b].beta_re, (float)st[b].beta_im);
-    const float2 omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
-    const float2 pv = csub(a.w[i], cmul(omega, a.v[i]));       // p - omega v
-    const float2 pn = caxpy(beta, pv, a.r[i]);                  // r + beta (p - omega v)
+    float2 pn = a.r[i];                                         // first iteration: p_1 = r_0
+    if (st[b].iters > 0) {
+      const float2 beta = make_float2((float)st[b].beta_re, (float)st[b].beta_im);
+      const float2 omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
+      const float2 pv = csub(a.w[i], cmul(omega, a.v[i]));     // p - omega v
+      pn = caxpy(beta, pv, pn);                                 // r + beta (p - omega v)
+    }
     a.w[i] = pn;
     return cscale(pn, a.x[g.vox0(x, y, z)]);
   }

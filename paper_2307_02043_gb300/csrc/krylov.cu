@@ -54,7 +54,7 @@ __global__ void k_fin_init(KState* st, const double* part, int nctas, double tol
     k.rho_re = s[0];
     k.alpha_re = 1.0;
     k.omega_re = 1.0;
-    k.beta_re = 0.0;   // p = v = 0, so p_1 = r_0
+    k.beta_re = 0.0;   // the first iteration takes p_1 = r_0 (iters == 0)
     k.rnorm2 = s[0];
     k.bnorm2 = bnorm2_fwd > 0.0 ? bnorm2_fwd : s[0];
     k.tol2 = tol2;
@@ -387,8 +387,6 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   k_init_uin<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->tab, w.illum, h->n, N);
-  CK(cudaMemsetAsync(w.p, 0, nb * N * sizeof(float2), s));
-  CK(cudaMemsetAsync(w.v, 0, nb * N * sizeof(float2), s));
   GreenCall c = base_call(h, nb, false);
   c.pro = PRO_BORN;                    // r_0 = u_in - A u_in = G(x u_in)
   c.pa.x = x;
@@ -412,8 +410,6 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   CK(cudaMemsetAsync(w.zs, 0, nb * N * sizeof(float2), s));
-  CK(cudaMemsetAsync(w.p, 0, nb * N * sizeof(float2), s));
-  CK(cudaMemsetAsync(w.v, 0, nb * N * sizeof(float2), s));
   GreenCall c = base_call(h, nb, true);
   c.pro = PRO_LIFT;
   c.pa.rdet = w.rdet;

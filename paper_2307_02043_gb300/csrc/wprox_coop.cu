@@ -314,6 +314,48 @@ MQ_D void chol_apply(const double (&A)[S * S], const double (&rd)[S], double (&b
   }
 }
 
+// The same in FP32 for the Newton direction of Algorithm 4.3: H = I + U^T D U / tau
+// is symmetric positive definite with eigenvalues >= 1, and the direction only
+// needs to be approximate (the step is accepted on ||phi|| evaluated in FP64).
+template <int S>
+MQ_D bool chol_factor_f(float (&A)[S * S], float (&rd)[S]) {
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    float s = A[j * S + j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s = fmaf(-A[j * S + k], A[j * S + k], s);
+    if (!(s > 0.f)) return false;
+    const float r = rsqrtf(s);
+    rd[j] = r;
+#pragma unroll
+    for (int i = j + 1; i < S; ++i) {
+      float t = A[i * S + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t = fmaf(-A[i * S + k], A[j * S + k], t);
+      A[i * S + j] = t * r;
+    }
+  }
+  return true;
+}
+
+template <int S>
+MQ_D void chol_apply_f(const float (&A)[S * S], const float (&rd)[S], float (&b)[S]) {
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    float t = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = fmaf(-A[i * S + k], b[k], t);
+    b[i] = t * rd[i];
+  }
+#pragma unroll
+  for (int i = S - 1; i >= 0; --i) {
+    float t = b[i];
+#pragma unroll
+    for (int k = i + 1; k < S; ++k) t = fmaf(-A[k * S + i], b[k], t);
+    b[i] = t * rd[i];
+  }
+}
+
 // M = (I + G/tau)^{-1} (S x S, FP64): one factorisation, S solves.  Called by
 // one thread; kept out of line so its scratch does not cost the streaming loops
 // registers.
@@ -375,22 +417,25 @@ __device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, 
   }
   *ns.nphi_cur = nphi;
   if (nphi <= tol_abs || *ns.accepted >= maxit || out_of_evals || !isfinite(nphi)) return 1;
-  double H[S * S];
+  // Newton direction -H^{-1} phi, solved in FP32 (see chol_factor_f)
+  float H[S * S];
   int k = 0;
+#pragma unroll
   for (int s = 0; s < S; ++s)
+#pragma unroll
     for (int t = s; t < S; ++t) {
-      const double hst = htri[k++] * inv_tau + (s == t ? 1.0 : 0.0);
+      const float hst = (float)(htri[k++] * inv_tau) + (s == t ? 1.f : 0.f);
       H[s * S + t] = hst;
       H[t * S + s] = hst;
     }
-  double rhs[S];
-  for (int s = 0; s < S; ++s) rhs[s] = -phi[s];
-  double rd[S];
-  if (!chol_factor<S>(H, rd)) return 1;
-  chol_apply<S>(H, rd, rhs);
+  float rhs[S], rd[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) rhs[s] = (float)(-phi[s]);
+  if (!chol_factor_f<S>(H, rd)) return 1;
+  chol_apply_f<S>(H, rd, rhs);
   for (int s = 0; s < S; ++s) {
-    ns.dir[s] = rhs[s];
-    ns.beta_eval[s] = ns.beta[s] + rhs[s];
+    ns.dir[s] = (double)rhs[s];
+    ns.beta_eval[s] = ns.beta[s] + (double)rhs[s];
   }
   *ns.tstep = 1.0;
   *ns.halvings = 0;
