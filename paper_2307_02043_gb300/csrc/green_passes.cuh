@@ -262,9 +262,10 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   using SH = ColShape<P>;
   using SM = Pass3Smem<P>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C, KH = SM::KH;
+  static_assert(R1 * R2 == P && R2 % 2 == 0, "two-stage plan with an even second factor");
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
-  float2* tw = reinterpret_cast<float2*>(sm + SM::tw_off());
+  float2* tw = reinterpret_cast<float2*>(sm + SM::tw_off());   // [R2][R1]: W_P^(a b)
   float2* kh = reinterpret_cast<float2*>(sm + SM::kh_off());
   float2* ex = reinterpret_cast<float2*>(sm + SM::ex_off());
   float2* in = reinterpret_cast<float2*>(sm + SM::in_off());
@@ -286,7 +287,12 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     mbar_expect_tx(bar, tile_bytes);
     tma_load_3d(in, &tmap, bar, kx0, ky, b * n);
   }
-  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+  // Twiddles as an R2 x R1 table, so that every thread reads its row (stage 1)
+  // or its column (inverse stage A) at compile-time offsets from one base.
+  for (int i = threadIdx.x; i < R1 * R2; i += blockDim.x) {
+    const int r = i / R1, q = i - (i / R1) * R1;
+    tw[i] = twg[r * q];
+  }
   {
     const int fx = kx <= n ? kx : P - kx;
     const int fy = ky <= n ? ky : P - ky;
@@ -307,7 +313,6 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       return;
     }
     phase ^= 1u;
-    float2* col = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
     // forward stage 1 (n2-threads), inputs z = R2 n1 + n2 < n from the TMA tile [z][c]
 #pragma unroll
     for (int i = 0; i < R2 / T; ++i) {
@@ -319,8 +324,10 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
         if (n1 < R1 / 2) a[n1] = in[(R2 * n1 + n2) * C + c];
       }
       dft<R1, false>(a);
+      const float2* twr = tw + n2 * R1;
+      float2* exw = ex + (n2 * R1) * C + c;
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) ex[(n2 * R1 + k1) * C + c] = cmul(a[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < R1; ++k1) exw[k1 * C] = (k1 == 0) ? a[0] : cmul(a[k1], twr[k1]);
     }
     __syncthreads();   // the tile is consumed: fetch the next active slot's into the same buffer
     int next = b + 1;
@@ -330,42 +337,51 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       mbar_expect_tx(bar, tile_bytes);
       tma_load_3d(in, &tmap, bar, kx0, ky, next * n);
     }
-    // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread)
+    // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread).
+    // K_hat row of kz = k1 + R1 k2: kz itself for k2 < R2/2, else the folded P - kz.
     float2 zb[R1 / T][R2];
 #pragma unroll
     for (int i = 0; i < R1 / T; ++i) {
       const int k1 = t + T * i;
       float2 a[R2];
+      const float2* exr = ex + k1 * C + c;
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) a[n2] = ex[(n2 * R1 + k1) * C + c];
+      for (int n2 = 0; n2 < R2; ++n2) a[n2] = exr[n2 * R1 * C];
       dft<R2, false>(a);
+      const float2* khA = kh + k1 * C + c;
+      const float2* khB = kh + (P - k1) * C + c;
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) {
-        const int kz = k1 + R1 * k2;
-        a[k2] = cmul(a[k2], kh[(kz <= P / 2 ? kz : P - kz) * C + c]);
-      }
+      for (int k2 = 0; k2 < R2; ++k2)
+        a[k2] = cmul(a[k2], k2 < R2 / 2 ? khA[k2 * R1 * C] : khB[-k2 * R1 * C]);
       dft<R2, true>(a);   // over k2 -> j1
+      const float2* twc = tw + k1;
 #pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = cmul(a[j1], cconj(tw[j1 * k1]));
+      for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = (j1 == 0) ? a[0] : cmul(a[j1], cconj(twc[j1 * R1]));
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < R1 / T; ++i) {
-      const int k1 = t + T * i;
+      float2* exw = ex + ((t + T * i) * R2) * C + c;
 #pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) ex[(k1 * R2 + j1) * C + c] = zb[i][j1];
+      for (int j1 = 0; j1 < R2; ++j1) exw[j1 * C] = zb[i][j1];
     }
     __syncthreads();
     // inverse stage B (j1-threads): outputs z = j1 + R2 j2 for j2 < R1/2
+    float2* colb = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
 #pragma unroll
     for (int i = 0; i < R2 / T; ++i) {
       const int j1 = t + T * i;
       float2 a[R1];
+      const float2* exr = ex + j1 * C + c;
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) a[k1] = ex[(k1 * R2 + j1) * C + c];
+      for (int k1 = 0; k1 < R1; ++k1) a[k1] = exr[k1 * R2 * C];
       dft<R1, true>(a);
+      float2* col = colb + (size_t)j1 * zs;
 #pragma unroll
-      for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(j1 + R2 * j2) * zs] = a[j2];
+      for (int j2 = 0; j2 < R1 / 2; ++j2) {
+        *col = a[j2];
+        col += (size_t)R2 * zs;
+      }
     }
     __syncthreads();   // ex is free again for the next slot's first stage
     b = next;
