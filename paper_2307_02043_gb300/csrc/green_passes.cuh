@@ -66,6 +66,20 @@ MQ_D void write_partials(const Parts<K>& p, double* partials, int b, int cta, in
 
 MQ_D bool slot_active(const KState* st, int b) { return st == nullptr || st[b].active != 0; }
 
+// Twiddles W_P^(r q) as an R2 x R1 table in shared memory (r < R2, q < R1): a
+// thread whose first-stage index n2 is fixed reads row n2 at compile-time
+// offsets, with no per-element index arithmetic.  Only for the column passes,
+// whose warps hold two values of n2 (the row passes keep a linear table: their
+// warps hold sixteen, and rows 128 bytes apart would share banks).
+template <int P>
+MQ_D void load_twiddle_table(float2* tw, const float2* __restrict__ twg) {
+  constexpr int R1 = Plan<P>::R1, R2 = Plan<P>::R2;
+  for (int i = threadIdx.x; i < R1 * R2; i += blockDim.x) {
+    const int r = i / R1, q = i - (i / R1) * R1;
+    tw[i] = twg[r * q];
+  }
+}
+
 // ------------------------------------------------------- pass 1: x forward
 template <int P, class Pro>
 __global__ void __launch_bounds__(RowShape<P>::THREADS)
@@ -182,7 +196,7 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
   float2* ex = sm + P;
   const int b = blockIdx.z;
   if (!slot_active(st, b)) return;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+  load_twiddle_table<P>(tw, twg);
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
   const int kx = blockIdx.x * C + c;
   const int z = blockIdx.y;
@@ -202,7 +216,7 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
     dft<R1, INV>(a);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
-      const float2 w = tw[n2 * k1];
+      const float2 w = tw[n2 * R1 + k1];
       ex[(n2 * R1 + k1) * C + c] = cmul(a[k1], INV ? cconj(w) : w);
     }
   }
@@ -287,12 +301,9 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     mbar_expect_tx(bar, tile_bytes);
     tma_load_3d(in, &tmap, bar, kx0, ky, b * n);
   }
-  // Twiddles as an R2 x R1 table, so that every thread reads its row (stage 1)
-  // or its column (inverse stage A) at compile-time offsets from one base.
-  for (int i = threadIdx.x; i < R1 * R2; i += blockDim.x) {
-    const int r = i / R1, q = i - (i / R1) * R1;
-    tw[i] = twg[r * q];
-  }
+  // every thread reads its twiddle row (stage 1) or column (inverse stage A)
+  // at compile-time offsets from one base
+  load_twiddle_table<P>(tw, twg);
   {
     const int fx = kx <= n ? kx : P - kx;
     const int fy = ky <= n ? ky : P - ky;
