@@ -88,6 +88,11 @@ typedef struct mqnpm_config {
   size_t hbm_budget_bytes; /* 0: no limit; else create fails with MQNPM_ERR_BUDGET  */
   int device;              /* CUDA device ordinal                                   */
   void* stream;            /* cudaStream_t for all work (NULL: legacy default)      */
+  /* --- Krylov initial guess (the paper leaves it open) */
+  int warm_start;          /* 1: each LS forward solve starts from the field last
+                              computed for the same illumination (kept on the
+                              device, L x N complex, and in checkpoints);
+                              0: from u_in                                     */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;
@@ -176,8 +181,10 @@ int mqnpm_lipschitz(mqnpm_handle* h, const int* illum, int nb, double scale, con
                     int iters, double* alpha_out);
 
 /* Checkpoint of the outer-loop state (k, tau_s, rank flags, xbar_s, gbar_s,
- * u_s, dual field).  With buf == NULL, *size receives the byte count; else buf
- * (host, *size bytes) receives the state.  load restores it exactly. */
+ * u_s, dual field and, with warm_start, the stored forward fields).  With
+ * buf == NULL, *size receives the byte count; else buf (host, *size bytes)
+ * receives the state.  load restores it exactly; it rejects a state written
+ * by a handle of another n, S, L or warm_start. */
 int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size);
 int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size);
 

@@ -148,6 +148,7 @@ void mqnpm_destroy(mqnpm_handle* h) {
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_nactive) cudaFreeHost(h->w.h_nactive);
   if (h->w.h_illum) cudaFreeHost(h->w.h_illum);
+  if (h->w.h_warm) cudaFreeHost(h->w.h_warm);
   if (h->w.h_scal) cudaFreeHost(h->w.h_scal);
   cudaSetDevice(dev);
   delete h;
@@ -203,6 +204,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->max_batch = cfg->max_batch;
   h->device = cfg->device;
   h->stream = static_cast<cudaStream_t>(cfg->stream);
+  h->warm_start = cfg->warm_start != 0;
   h->budget = cfg->hbm_budget_bytes;
   h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
   h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);
@@ -248,6 +250,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
   need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * 44 + 200) * 8 + wprox_part_count(wp_blocks) * 8;   // wprox
   need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
+  if (h->warm_start && h->model == MQNPM_MODEL_LS) need += (size_t)h->L * N * 8;     // stored fields
   if (h->budget > 0 && need > h->budget) {
     char msg[160];
     snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds the budget of %zu bytes", need, h->budget);
@@ -278,6 +281,9 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(w.st, B);
   AL(w.gerr, 1);
   AL(w.illum, B);
+  AL(w.warm, B);
+  if (h->warm_start && h->model == MQNPM_MODEL_LS) AL(h->ufield, (size_t)h->L * N);
+  h->have_field.assign(h->L, 0);
   AL(w.nactive, 1);
   AL(w.dscal, 64);
   WproxWork& wp = h->wp;
@@ -306,6 +312,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
 #undef AL
   if ((e = cudaMallocHost(&w.h_nactive, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_illum, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
+  if ((e = cudaMallocHost(&w.h_warm, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_scal, 64 * sizeof(double))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
 
   // ---- tables: twiddles W_P^j and incident-field axis factors, built in FP64
@@ -570,7 +577,7 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
 // ---- checkpoint: header, then xbar, gbar, U (S x N floats each), P (3N floats)
 struct StateHeader {
   unsigned magic;
-  int n, S, k, have_P;
+  int n, S, k, have_P, warm, L;
   int has_u[MQNPM_MAX_S];
   double tau[MQNPM_MAX_S];
 };
@@ -578,7 +585,9 @@ struct StateHeader {
 int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size) {
   if (!h || !size) return MQNPM_ERR_INVALID_ARG;
   const size_t N = h->N;
-  const size_t need = sizeof(StateHeader) + (3 * (size_t)h->S * N + 3 * N) * sizeof(float);
+  const bool warm = h->ufield != nullptr;
+  const size_t need = sizeof(StateHeader) + (3 * (size_t)h->S * N + 3 * N) * sizeof(float) +
+                      (warm ? (size_t)h->L * (sizeof(int) + N * sizeof(float2)) : 0);
   if (!buf) {
     *size = need;
     return MQNPM_OK;
@@ -586,10 +595,12 @@ int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size) {
   if (*size < need) return set_error(h, MQNPM_ERR_INVALID_ARG, "save_state: buffer too small");
   CK(cudaSetDevice(h->device));
   StateHeader hd{};
-  hd.magic = 0x4d514e50u;
+  hd.magic = 0x4d514e51u;
   hd.n = h->n;
   hd.S = h->S;
   hd.k = h->k;
+  hd.warm = warm ? 1 : 0;
+  hd.L = h->L;
   hd.have_P = h->have_P ? 1 : 0;
   for (int s = 0; s < h->S; ++s) {
     hd.has_u[s] = h->has_u[s];
@@ -603,6 +614,12 @@ int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size) {
   CK(cudaMemcpyAsync(p, h->gbar, SN, cudaMemcpyDeviceToHost, h->stream)); p += SN;
   CK(cudaMemcpyAsync(p, h->U, SN, cudaMemcpyDeviceToHost, h->stream)); p += SN;
   CK(cudaMemcpyAsync(p, h->Pwarm, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  p += 3 * N * sizeof(float);
+  if (warm) {
+    std::memcpy(p, h->have_field.data(), (size_t)h->L * sizeof(int));
+    p += (size_t)h->L * sizeof(int);
+    CK(cudaMemcpyAsync(p, h->ufield, (size_t)h->L * N * sizeof(float2), cudaMemcpyDeviceToHost, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   *size = need;
   return MQNPM_OK;
@@ -611,11 +628,13 @@ int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size) {
 int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size) {
   if (!h || !buf) return MQNPM_ERR_INVALID_ARG;
   const size_t N = h->N;
-  const size_t need = sizeof(StateHeader) + (3 * (size_t)h->S * N + 3 * N) * sizeof(float);
-  if (size < need) return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: buffer too small");
+  const bool warm = h->ufield != nullptr;
+  const size_t need = sizeof(StateHeader) + (3 * (size_t)h->S * N + 3 * N) * sizeof(float) +
+                      (warm ? (size_t)h->L * (sizeof(int) + N * sizeof(float2)) : 0);
+  if (size < sizeof(StateHeader) || size < need) return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: buffer too small");
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof hd);
-  if (hd.magic != 0x4d514e50u || hd.n != h->n || hd.S != h->S)
+  if (hd.magic != 0x4d514e51u || hd.n != h->n || hd.S != h->S || hd.L != h->L || hd.warm != (warm ? 1 : 0))
     return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: state does not match this handle");
   CK(cudaSetDevice(h->device));
   const char* p = static_cast<const char*>(buf) + sizeof hd;
@@ -624,6 +643,12 @@ int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size) {
   CK(cudaMemcpyAsync(h->gbar, p, SN, cudaMemcpyHostToDevice, h->stream)); p += SN;
   CK(cudaMemcpyAsync(h->U, p, SN, cudaMemcpyHostToDevice, h->stream)); p += SN;
   CK(cudaMemcpyAsync(h->Pwarm, p, 3 * N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  p += 3 * N * sizeof(float);
+  if (warm) {
+    std::memcpy(h->have_field.data(), p, (size_t)h->L * sizeof(int));
+    p += (size_t)h->L * sizeof(int);
+    CK(cudaMemcpyAsync(h->ufield, p, (size_t)h->L * N * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   h->k = hd.k;
   h->have_P = hd.have_P != 0;

@@ -162,6 +162,22 @@ struct Epi<EPI_INIT> {
   }
 };
 
+// Residual of a start u: r_0 = u_in - (I - G X) u = u_in - u + G(x u).
+template <>
+struct Epi<EPI_INIT_WARM> {
+  static constexpr int NPART = 1;
+  EpiArgs a;
+  Geo g;
+  template <class Pt>
+  MQ_D void store(int b, int x, int y, int z, float2 gv, Pt& parts) const {
+    const size_t i = g.vox(b, x, y, z);
+    const float2 r = cadd(csub(incident(a.tab, a.illum[b], g.n, x, y, z), a.a[i]), gv);
+    a.out[i] = r;
+    a.out2[i] = r;
+    parts.v[0] += cabs2(r);
+  }
+};
+
 template <>
 struct Epi<EPI_DETECT> {
   static constexpr int NPART = 1;

@@ -104,6 +104,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     case EPI_V: e = launch5<EPI_V>(c, s); break;
     case EPI_T: e = launch5<EPI_T>(c, s); break;
     case EPI_INIT: e = launch5<EPI_INIT>(c, s); break;
+    case EPI_INIT_WARM: e = launch5<EPI_INIT_WARM>(c, s); break;
     case EPI_DETECT: e = launch5<EPI_DETECT>(c, s); break;
     default: return cudaErrorInvalidValue;
   }

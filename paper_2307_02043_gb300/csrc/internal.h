@@ -71,6 +71,8 @@ struct Workspace {
   int* nactive = nullptr;                // device counter
   int* h_nactive = nullptr;              // pinned host mirror
   int* h_illum = nullptr;                // pinned staging of slot illuminations
+  int* warm = nullptr;                   // [max_batch]: slot starts from a stored field
+  int* h_warm = nullptr;                 // pinned staging of warm
   double* h_scal = nullptr;              // pinned scalar staging (64 doubles)
   double* dscal = nullptr;               // device scalar scratch (64 doubles)
   int ctas_row = 0, ctas_upd = 0, ctas_vec = 0;
@@ -116,6 +118,10 @@ struct mqnpm_handle {
   bool have_meas = false;
   Workspace w;
   WproxWork wp;
+  // Krylov warm start: last forward field per illumination
+  bool warm_start = false;
+  float2* ufield = nullptr;      // [L][N]
+  std::vector<int> have_field;   // [L]
   // outer-loop state (Algorithm 4.1)
   int k = 0;
   float *xbar = nullptr, *gbar = nullptr, *U = nullptr, *g = nullptr, *vq = nullptr, *Pwarm = nullptr;

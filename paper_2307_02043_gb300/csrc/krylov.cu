@@ -205,6 +205,26 @@ __global__ void k_init_uin(float2* u, const float2* tab, const int* illum, int n
     u[(size_t)b * N + i] = incident_at(tab, l, n, i);
 }
 
+// Start fields of a warm-started forward solve: the field stored for the
+// slot's illumination where there is one, else u_in.
+__global__ void k_init_u_warm(float2* u, const float2* __restrict__ ufield, const int* warm, const float2* tab,
+                              const int* illum, int n, size_t N) {
+  const int b = blockIdx.y;
+  const int l = illum[b];
+  const bool w = warm[b] != 0;
+  const float2* src = ufield + (size_t)l * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    u[(size_t)b * N + i] = w ? src[i] : incident_at(tab, l, n, i);
+}
+
+// Keep each slot's converged field for its illumination's next solve.
+__global__ void k_store_field(float2* __restrict__ ufield, const float2* __restrict__ u, const int* illum, size_t N) {
+  const int b = blockIdx.y;
+  float2* dst = ufield + (size_t)illum[b] * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = u[(size_t)b * N + i];
+}
+
 // Detector of the LS field: usc = (u - u_in) on z = n-1; r_det = usc - y (or usc if y == NULL).
 __global__ void k_detect_ls(const float2* u, const float2* tab, const int* illum, const float2* ymeas,
                             float2* out, int n, size_t N, double* part) {
@@ -386,22 +406,44 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
   const size_t N = h->N;
-  k_init_uin<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->tab, w.illum, h->n, N);
   GreenCall c = base_call(h, nb, false);
-  c.pro = PRO_BORN;                    // r_0 = u_in - A u_in = G(x u_in)
-  c.pa.x = x;
-  c.pa.tab = h->tab;
-  c.pa.illum = w.illum;
-  c.epi = EPI_INIT;
+  if (h->ufield) {
+    // warm start: u_0 = the stored field (or u_in), r_0 = u_in - u_0 + G(x u_0)
+    for (int b = 0; b < nb; ++b) w.h_warm[b] = h->have_field[w.h_illum[b]] ? 1 : 0;
+    CK(cudaMemcpyAsync(w.warm, w.h_warm, nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_init_u_warm<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->ufield, w.warm, h->tab, w.illum, h->n, N);
+    c.pro = PRO_CONTRAST;
+    c.pa.x = x;
+    c.pa.q = w.u;
+    c.epi = EPI_INIT_WARM;
+    c.ea.a = w.u;
+    c.ea.tab = h->tab;
+    c.ea.illum = w.illum;
+  } else {
+    k_init_uin<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->tab, w.illum, h->n, N);
+    c.pro = PRO_BORN;                    // r_0 = u_in - A u_in = G(x u_in)
+    c.pa.x = x;
+    c.pa.tab = h->tab;
+    c.pa.illum = w.illum;
+    c.epi = EPI_INIT;
+  }
   c.ea.out = w.r;
   c.ea.out2 = w.rhat;
   CK(glaunch(h, c, s));
   k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, (double)N);
   CK(cudaGetLastError());
-  h->launches += 2;   // init_uin, fin_init
+  h->launches += 2;   // init, fin_init
   int rc = krylov_iterate(h, nb, x, w.u, false);
   if (rc != MQNPM_OK) return rc;
-  return collect_states(h, nb, iters, stride, offset);
+  if (h->ufield) {
+    k_store_field<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(h->ufield, w.u, w.illum, N);
+    CK(cudaGetLastError());
+    h->launches += 1;
+  }
+  rc = collect_states(h, nb, iters, stride, offset);
+  if (h->ufield)
+    for (int b = 0; b < nb; ++b) h->have_field[w.h_illum[b]] = (rc == MQNPM_ERR_NONFINITE) ? 0 : 1;
+  return rc;
 }
 
 // Adjoint solve for nb slots: z = (I - G^H X)^{-1} G^H S^T r_det.

@@ -41,6 +41,7 @@ enum EpiKind {
   EPI_T = 2,            // t = s - g; partials <t, s>, ||t||^2
   EPI_INIT = 3,         // r = rhat = g; partial ||g||^2
   EPI_DETECT = 4,       // z = n-1: r_det = g - y_meas(l_b); partial ||r_det||^2
+  EPI_INIT_WARM = 5,    // r = rhat = u_in(l_b) - u + g (start u); partial ||r||^2
 };
 
 struct ProArgs {
@@ -61,4 +62,5 @@ struct EpiArgs {
   float2* out2;          // second output (rhat for EPI_INIT, r_det for EPI_DETECT)
   const float2* ymeas;   // [L][n*n]
   const int* illum;
+  const float2* tab;     // incident-field axis tables [l][3][n]
 };

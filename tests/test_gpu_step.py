@@ -53,11 +53,15 @@ def ls32():
     return w, kd, om, ys, subs, so, alpha, opt, xs
 
 
-def test_step_trajectory_matches_oracle(ls32):
+@pytest.mark.parametrize("warm", [False, True])
+def test_step_trajectory_matches_oracle(ls32, warm):
     """Config 1 (32^3, LS, L = 8, S = 4, 10 iterations): per-iterate error and the
-    objective trajectory against the FP64 oracle run with the same inputs."""
+    objective trajectory against the FP64 oracle run with the same inputs.  With
+    warm starts the forward solves begin at the fields of the previous visit of
+    each subset; the solutions stay within the Krylov tolerance, so the same
+    bounds hold."""
     w, kd, om, ys, subs, so, alpha, opt, xs = ls32
-    h = handle(w, kd, so, alpha)
+    h = handle(w, kd, so, alpha, warm_start=warm)
     h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
     x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
     for k in range(1, w.outer_iters + 1):
@@ -74,10 +78,11 @@ def test_step_trajectory_matches_oracle(ls32):
     h.close()
 
 
-def test_checkpoint_resume_is_bit_identical(ls32):
+@pytest.mark.parametrize("warm", [False, True])
+def test_checkpoint_resume_is_bit_identical(ls32, warm):
     w, kd, om, ys, subs, so, alpha, opt, xs = ls32
     y = torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1)
-    h = handle(w, kd, so, alpha)
+    h = handle(w, kd, so, alpha, warm_start=warm)
     h.set_measurements(y)
     x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
     for _ in range(w.S + 1):
@@ -86,7 +91,7 @@ def test_checkpoint_resume_is_bit_identical(ls32):
     x_saved = x.clone()
     for _ in range(2):
         h.step(x)
-    h2 = handle(w, kd, so, alpha)
+    h2 = handle(w, kd, so, alpha, warm_start=warm)
     h2.set_measurements(y)
     h2.load_state(blob)
     x2 = x_saved.clone()
@@ -95,6 +100,34 @@ def test_checkpoint_resume_is_bit_identical(ls32):
     assert torch.equal(x, x2)
     h.close()
     h2.close()
+
+
+def test_warm_start_solves_to_the_same_tolerance(ls32):
+    """A forward solve started from the stored field of a nearby contrast needs
+    no more BiCGSTAB iterations and returns the same data to the tolerance."""
+    w, kd, om, ys, subs, so, alpha, opt, xs = ls32
+    hw = handle(w, kd, so, alpha, warm_start=True, krylov_tol=1e-7)
+    hc = handle(w, kd, so, alpha, krylov_tol=1e-7)
+    x1 = f32(xs[w.S]).reshape(-1)
+    x2 = f32(xs[w.S + 1]).reshape(-1)
+    illum = list(range(w.L))
+    hw.forward(x1, illum)                      # stores the fields
+    yw, itw = hw.forward(x2, illum)            # warm
+    yc, itc = hc.forward(x2, illum)            # cold
+    assert sum(itw) <= sum(itc), (itw, itc)
+    for l in illum:
+        ref = om.forward(xs[w.S + 1], l)
+        ew = np.linalg.norm(yw[l].cpu().numpy() - ref)
+        ec = np.linalg.norm(yc[l].cpu().numpy() - ref)
+        # the detector data is the small scattered part of u, so a residual
+        # tolerance of 1e-7 leaves ~1e-5 relative error in it, warm or cold
+        assert ew <= 2e-5 * np.linalg.norm(ref), (l, ew, ec)
+    blob_w = hw.save_state()
+    h3 = handle(w, kd, so, alpha)              # cold handle: a warm checkpoint does not match it
+    with pytest.raises(binding.MQNPMError):
+        h3.load_state(blob_w)
+    for hh in (hw, hc, h3):
+        hh.close()
 
 
 def test_failures_are_reported():
