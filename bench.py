@@ -384,6 +384,34 @@ def green_only(args, torch, binding):
     h.close()
 
 
+def grad_only(args, torch, binding):
+    """Mini-batch gradients of the workload (a small case for profiler captures:
+    no set-up solves, zero measurements, x = phantom / 2): prints per-pass times."""
+    w = synth.workload(args.workload)
+    dev = torch.device("cuda", 0)
+    subs = synth.subsets(w)
+    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, model=w.model,
+                      krylov_tol=w.krylov_tol, max_batch=max(len(q) for q in subs))
+    h.set_measurements(torch.zeros(w.L * w.n * w.n, dtype=torch.complex64, device=dev))
+    x = 0.5 * torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
+    illum = [int(i) for i in subs[0]]
+    for _ in range(args.warmup):
+        h.grad_batch(x, illum, 1.0)
+    h.profile_begin(4096)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    its = None
+    for _ in range(args.steps):
+        _, _, its = h.grad_batch(x, illum, 1.0)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = h.profile_end()
+    print(json.dumps({"workload": w.name, "illuminations": len(illum), "ms_per_gradient": round(
+        e0.elapsed_time(e1) / args.steps, 3), "krylov_iters": its, "applies": prof["calls"],
+        "pass_ms": [round(t, 3) for t in prof["pass_ms"]]}), flush=True)
+    h.close()
+
+
 # ---------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -397,6 +425,8 @@ def main():
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
+    ap.add_argument("--grad-only", action="store_true",
+                    help="small case for profiler captures: mini-batch gradients of the workload")
     ap.add_argument("--prox-only", action="store_true",
                     help="small case for profiler captures: weighted proximal mappings on the workload grid")
     args = ap.parse_args()
@@ -415,6 +445,9 @@ def main():
         return
     if args.prox_only:
         prox_only(args, torch, binding)
+        return
+    if args.grad_only:
+        grad_only(args, torch, binding)
         return
 
     if args.warmup < 3:

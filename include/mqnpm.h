@@ -158,6 +158,26 @@ int mqnpm_forward(mqnpm_handle* h, const float* x, const int* illum, int nb,
 int mqnpm_grad_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
                      float* grad_out, double* loss_out, int* krylov_iters_out);
 
+/* Data term of a mini-batch without its gradient (Eq. 4.1, the forward half of
+ * mqnpm_grad_batch): *loss_out = scale * sum_{l in illum} f_l(x).  x: device N
+ * floats; illum, loss_out (host); krylov_iters_out: host nb ints (forward
+ * solves) or NULL.  When nb <= max_batch the forward fields and detector
+ * residuals stay in the workspace for a following mqnpm_grad_fields; any other
+ * data-term, forward, step or lipschitz call, or new measurements, drop them.
+ * Errors as mqnpm_grad_batch. */
+int mqnpm_loss_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
+                     double* loss_out, int* krylov_iters_out);
+
+/* Gradient of the same data term (the backward half): grad_out (device N
+ * floats) = scale * sum grad f_l(x).  With reuse != 0, and when the workspace
+ * still holds the fields of the last mqnpm_loss_batch for the same x pointer
+ * and illumination list, only the adjoint solves run (the caller guarantees
+ * that the contents of x did not change in between); otherwise the forward
+ * fields are recomputed, chunk by chunk.  *reused_out (host, may be NULL) is 1
+ * when the stored fields were used. */
+int mqnpm_grad_fields(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
+                      float* grad_out, int reuse, int* reused_out);
+
 /* Weighted proximal mapping of c*TV + iota_C under B = tau_star I + U U^T
  * (Eq. 4.5, Theorem 3.1, Lemma 4.1, Algorithm 4.3):
  *   x_out ~= argmin_{x in C} 1/2 ||x - v||_B^2 + c TV(x)

@@ -78,6 +78,10 @@ SIGNATURES = {
     "mqnpm_grad_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                         ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_loss_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_grad_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mqnpm_wprox": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "mqnpm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
@@ -285,6 +289,36 @@ class MQNPM:
         rc = self.lib.mqnpm_grad_batch(self._h, _ptr(x), il, nb, float(scale), _ptr(out), ctypes.byref(loss), its)
         self._raise(rc, allow_not_converged)
         return out, loss.value, [(its[2 * b], its[2 * b + 1]) for b in range(nb)]
+
+    def loss_batch(self, x: torch.Tensor, illum: Sequence[int], scale: float, allow_not_converged=False):
+        """scale * sum f_l(x) without the gradient; keeps the fields of a single
+        chunk for grad_fields."""
+        _check_cuda(x, torch.float32, self.N, "x", self.device)
+        nb = len(illum)
+        il = (ctypes.c_int * nb)(*[int(i) for i in illum])
+        its = (ctypes.c_int * nb)()
+        loss = ctypes.c_double()
+        self._stream()
+        rc = self.lib.mqnpm_loss_batch(self._h, _ptr(x), il, nb, float(scale), ctypes.byref(loss), its)
+        self._raise(rc, allow_not_converged)
+        return loss.value, list(its)
+
+    def grad_fields(self, x: torch.Tensor, illum: Sequence[int], scale: float, reuse: bool = True,
+                    out: Optional[torch.Tensor] = None, allow_not_converged=False):
+        """scale * sum grad f_l(x), reusing the fields of the last loss_batch
+        when allowed; returns (gradient, reused)."""
+        _check_cuda(x, torch.float32, self.N, "x", self.device)
+        if out is None:
+            out = torch.empty_like(x)
+        _check_cuda(out, torch.float32, self.N, "grad_out", self.device)
+        nb = len(illum)
+        il = (ctypes.c_int * nb)(*[int(i) for i in illum])
+        reused = ctypes.c_int()
+        self._stream()
+        rc = self.lib.mqnpm_grad_fields(self._h, _ptr(x), il, nb, float(scale), _ptr(out), int(bool(reuse)),
+                                        ctypes.byref(reused))
+        self._raise(rc, allow_not_converged)
+        return out, bool(reused.value)
 
     def wprox(self, v: torch.Tensor, tau: float, U: Optional[torch.Tensor], c: float,
               P_warm: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:

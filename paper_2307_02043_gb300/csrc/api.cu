@@ -350,6 +350,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
 int mqnpm_set_measurements(mqnpm_handle* h, const float* y) {
   if (!h || !y) return MQNPM_ERR_INVALID_ARG;
   CK(cudaSetDevice(h->device));
+  h->fields_valid = false;   // stored residuals refer to the old data
   CK(cudaMemcpyAsync(h->ymeas, y, (size_t)h->L * h->M * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
   h->have_meas = true;
   return MQNPM_OK;
@@ -403,6 +404,26 @@ int mqnpm_grad_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, 
     if (illum[b] < 0 || illum[b] >= h->L) return set_error(h, MQNPM_ERR_INVALID_ARG, "grad_batch: illumination index");
   CK(cudaSetDevice(h->device));
   return grad_batch_impl(h, x, illum, nb, scale, grad_out, loss_out, krylov_iters_out, true, nullptr);
+}
+
+int mqnpm_loss_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, double* loss_out,
+                     int* krylov_iters_out) {
+  if (!h || !x || !illum || !loss_out || nb < 1) return set_error(h, MQNPM_ERR_INVALID_ARG, "loss_batch: bad arguments");
+  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "loss_batch: measurements not set");
+  for (int b = 0; b < nb; ++b)
+    if (illum[b] < 0 || illum[b] >= h->L) return set_error(h, MQNPM_ERR_INVALID_ARG, "loss_batch: illumination index");
+  CK(cudaSetDevice(h->device));
+  return loss_batch_impl(h, x, illum, nb, scale, loss_out, krylov_iters_out);
+}
+
+int mqnpm_grad_fields(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad_out,
+                      int reuse, int* reused_out) {
+  if (!h || !x || !illum || !grad_out || nb < 1) return set_error(h, MQNPM_ERR_INVALID_ARG, "grad_fields: bad arguments");
+  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "grad_fields: measurements not set");
+  for (int b = 0; b < nb; ++b)
+    if (illum[b] < 0 || illum[b] >= h->L) return set_error(h, MQNPM_ERR_INVALID_ARG, "grad_fields: illumination index");
+  CK(cudaSetDevice(h->device));
+  return grad_fields_impl(h, x, illum, nb, scale, grad_out, reuse != 0, reused_out);
 }
 
 int mqnpm_wprox(mqnpm_handle* h, const float* v, double tau_star, const float* U, int S_eff, double c, float* P_warm,

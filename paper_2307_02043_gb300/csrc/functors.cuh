@@ -26,6 +26,7 @@ struct Pro<PRO_PLAIN> {
   static constexpr int NPART = 0;
   ProArgs a;
   Geo g;
+  MQ_D void begin(int) {}
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const { return a.q[g.vox(b, x, y, z)]; }
 };
@@ -35,6 +36,7 @@ struct Pro<PRO_CONTRAST> {
   static constexpr int NPART = 0;
   ProArgs a;
   Geo g;
+  MQ_D void begin(int) {}
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
     return cscale(a.q[g.vox(b, x, y, z)], a.x[g.vox0(x, y, z)]);
@@ -46,6 +48,7 @@ struct Pro<PRO_BORN> {
   static constexpr int NPART = 0;
   ProArgs a;
   Geo g;
+  MQ_D void begin(int) {}
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
     return cscale(incident(a.tab, a.illum[b], g.n, x, y, z), a.x[g.vox0(x, y, z)]);
@@ -58,13 +61,18 @@ struct Pro<PRO_BICG_P> {
   ProArgs a;
   Geo g;
   const KState* st;
+  float2 beta, omega;   // slot scalars, rounded once per thread by begin()
+  bool first;
+  MQ_D void begin(int b) {
+    first = st[b].iters == 0;
+    beta = make_float2((float)st[b].beta_re, (float)st[b].beta_im);
+    omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
+  }
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
     const size_t i = g.vox(b, x, y, z);
     float2 pn = a.r[i];                                         // first iteration: p_1 = r_0
-    if (st[b].iters > 0) {
-      const float2 beta = make_float2((float)st[b].beta_re, (float)st[b].beta_im);
-      const float2 omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
+    if (!first) {
       const float2 pv = csub(a.w[i], cmul(omega, a.v[i]));     // p - omega v
       pn = caxpy(beta, pv, pn);                                 // r + beta (p - omega v)
     }
@@ -79,10 +87,11 @@ struct Pro<PRO_BICG_S> {
   ProArgs a;
   Geo g;
   const KState* st;
+  float2 alpha;         // slot scalar, rounded once per thread by begin()
+  MQ_D void begin(int b) { alpha = make_float2((float)st[b].alpha_re, (float)st[b].alpha_im); }
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt& parts) const {
     const size_t i = g.vox(b, x, y, z);
-    const float2 alpha = make_float2((float)st[b].alpha_re, (float)st[b].alpha_im);
     const float2 s = caxpy(make_float2(-alpha.x, -alpha.y), a.v[i], a.r[i]);   // r - alpha v
     a.w[i] = s;
     parts.v[0] += cabs2(s);
@@ -95,6 +104,7 @@ struct Pro<PRO_LIFT> {
   static constexpr int NPART = 0;
   ProArgs a;
   Geo g;
+  MQ_D void begin(int) {}
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
     if (z != g.n - 1) return make_float2(0.f, 0.f);

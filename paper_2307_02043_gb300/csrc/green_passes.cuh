@@ -93,6 +93,7 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
   float2* ex = sm + P;
   const int b = blockIdx.y;
   if (!slot_active(st, b)) return;
+  pro.begin(b);
   for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
   const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
   const int line = blockIdx.x * SH::LPB + l;

@@ -118,6 +118,10 @@ struct mqnpm_handle {
   bool have_meas = false;
   Workspace w;
   WproxWork wp;
+  // forward fields and residuals of the last loss-only call (for its gradient)
+  bool fields_valid = false;
+  const float* fields_x = nullptr;
+  std::vector<int> fields_illum;
   // Krylov warm start: last forward field per illumination
   bool warm_start = false;
   float2* ufield = nullptr;      // [L][N]
@@ -143,6 +147,10 @@ cudaEvent_t* profile_slot(mqnpm_handle* h, int nb);
 // krylov.cu
 int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
                     float* grad, double* loss, int* iters, bool want_grad, float2* y_out);
+int loss_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, double* loss,
+                    int* iters);
+int grad_fields_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad,
+                     bool reuse, int* reused);
 int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, const float* start,
                    int iters, double* alpha_out);
 cudaError_t vec_reduce(mqnpm_handle* h, int kind, const float* a, const float* b, const float* c,

@@ -467,73 +467,146 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   return collect_states(h, nb, iters, stride, offset);
 }
 
+namespace {
+
+// Stage the illuminations of one chunk (pinned staging, then the device copy).
+int chunk_illum(mqnpm_handle* h, const int* illum, int c0, int m) {
+  Workspace& w = h->w;
+  CK(cudaStreamSynchronize(h->stream));
+  for (int b = 0; b < m; ++b) w.h_illum[b] = illum[c0 + b];
+  CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  return MQNPM_OK;
+}
+
+// Forward fields and detector residuals of one chunk (slots [0, m)); the
+// residual norm lands in w.h_scal[0] after the next synchronisation.
+int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2* det_out, const float2* ym) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  int worst = MQNPM_OK;
+  if (h->model == MQNPM_MODEL_LS) {
+    int rc = forward_ls(h, m, x, it_chunk, 2, 0);
+    if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
+    if (rc != MQNPM_OK) worst = rc;
+    k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, ym, det_out, h->n, N, w.partd);
+  } else {
+    GreenCall c = base_call(h, m, false);
+    c.pro = PRO_BORN;
+    c.pa.x = x;
+    c.pa.tab = h->tab;
+    c.pa.illum = w.illum;
+    c.epi = EPI_DETECT;
+    c.ea.out2 = det_out;
+    c.ea.ymeas = ym;
+    c.ea.illum = w.illum;
+    c.part_epi = w.partd;
+    CK(glaunch(h, c, s));
+  }
+  CK(cudaGetLastError());
+  k_sum_all<<<1, 256, 0, s>>>(w.partd, m * w.ctas_row, w.dscal);
+  CK(cudaMemcpyAsync(w.h_scal, w.dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + 1;
+  return worst;
+}
+
+// Adjoint solves and gradient assembly of one chunk from the fields and
+// residuals in the workspace; accumulate adds to grad.
+int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, double scale, float* grad, bool accumulate) {
+  Workspace& w = h->w;
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  int worst = MQNPM_OK;
+  if (h->model == MQNPM_MODEL_LS) {
+    int rc = adjoint_ls(h, m, x, it_chunk, 2, 1);
+    if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
+    if (rc != MQNPM_OK) worst = rc;
+    k_grad<<<w.ctas_vec, 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, accumulate);
+  } else {
+    GreenCall c = base_call(h, m, true);
+    c.pro = PRO_LIFT;
+    c.pa.rdet = w.rdet;
+    c.epi = EPI_PLAIN;
+    c.ea.out = w.zs;
+    CK(glaunch(h, c, s));
+    k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, accumulate);
+  }
+  CK(cudaGetLastError());
+  h->launches += 1;
+  return worst;
+}
+
+int check_tile_waits(mqnpm_handle* h) {
+  int gerr = 0;
+  CK(cudaMemcpy(&gerr, h->w.gerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (gerr) return set_error(h, MQNPM_ERR_TIMEOUT, "a bounded wait for a transform tile load gave up");
+  return MQNPM_OK;
+}
+
+}  // namespace
+
 int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad,
                     double* loss, int* iters, bool want_grad, float2* y_out) {
   Workspace& w = h->w;
-  cudaStream_t s = h->stream;
-  const size_t N = h->N, M = (size_t)h->M;
+  const size_t M = (size_t)h->M;
   double total = 0.0;
   int worst = MQNPM_OK;
+  h->fields_valid = false;
   h->last_iters.assign(2 * nb, 0);
   for (int c0 = 0; c0 < nb; c0 += h->max_batch) {
     const int m = std::min(h->max_batch, nb - c0);
-    CK(cudaStreamSynchronize(s));
-    for (int b = 0; b < m; ++b) w.h_illum[b] = illum[c0 + b];
-    CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, s));
+    int rc = chunk_illum(h, illum, c0, m);
+    if (rc != MQNPM_OK) return rc;
     int* it_chunk = h->last_iters.data() + 2 * c0;
     float2* det_out = y_out ? y_out + (size_t)c0 * M : w.rdet;
     const float2* ym = y_out ? nullptr : h->ymeas;
-    // ---- forward field and detector residual
-    if (h->model == MQNPM_MODEL_LS) {
-      int rc = forward_ls(h, m, x, it_chunk, 2, 0);
+    rc = chunk_forward(h, x, m, it_chunk, det_out, ym);
+    if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
+    if (rc != MQNPM_OK) worst = rc;
+    if (!y_out && want_grad) {
+      rc = chunk_adjoint(h, x, m, it_chunk, scale, grad, c0 > 0);
       if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
       if (rc != MQNPM_OK) worst = rc;
-      k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, ym, det_out, h->n, N, w.partd);
-    } else {
-      GreenCall c = base_call(h, m, false);
-      c.pro = PRO_BORN;
-      c.pa.x = x;
-      c.pa.tab = h->tab;
-      c.pa.illum = w.illum;
-      c.epi = EPI_DETECT;
-      c.ea.out2 = det_out;
-      c.ea.ymeas = ym;
-      c.ea.illum = w.illum;
-      c.part_epi = w.partd;
-      CK(glaunch(h, c, s));
     }
-    CK(cudaGetLastError());
-    k_sum_all<<<1, 256, 0, s>>>(w.partd, m * w.ctas_row, w.dscal);
-    CK(cudaMemcpyAsync(w.h_scal, w.dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (!y_out && want_grad) {
-      // ---- adjoint and gradient
-      if (h->model == MQNPM_MODEL_LS) {
-        int rc = adjoint_ls(h, m, x, it_chunk, 2, 1);
-        if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
-        if (rc != MQNPM_OK) worst = rc;
-        k_grad<<<w.ctas_vec, 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, c0 > 0);
-      } else {
-        GreenCall c = base_call(h, m, true);
-        c.pro = PRO_LIFT;
-        c.pa.rdet = w.rdet;
-        c.epi = EPI_PLAIN;
-        c.ea.out = w.zs;
-        CK(glaunch(h, c, s));
-        k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, c0 > 0);
-      }
-      CK(cudaGetLastError());
-    }
-    CK(cudaStreamSynchronize(s));
+    CK(cudaStreamSynchronize(h->stream));
     total += 0.5 * w.h_scal[0];
-    // detector (LS) + loss sum + gradient assembly (when requested)
-    h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + 1 + ((!y_out && want_grad) ? 1 : 0);
   }
   if (loss) *loss = scale * total;
   if (iters) std::memcpy(iters, h->last_iters.data(), 2 * nb * sizeof(int));
-  int gerr = 0;
-  CK(cudaMemcpy(&gerr, w.gerr, sizeof(int), cudaMemcpyDeviceToHost));
-  if (gerr) return set_error(h, MQNPM_ERR_TIMEOUT, "a bounded wait for a transform tile load gave up");
-  return worst;
+  const int rc = check_tile_waits(h);
+  return rc != MQNPM_OK ? rc : worst;
+}
+
+// Data term without the gradient; a single chunk keeps its fields for
+// grad_fields_impl.
+int loss_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, double* loss,
+                    int* iters) {
+  const int rc = grad_batch_impl(h, x, illum, nb, scale, nullptr, loss, nullptr, false, nullptr);
+  if (iters)
+    for (int b = 0; b < nb; ++b) iters[b] = h->last_iters[2 * b];
+  if ((rc == MQNPM_OK || rc == MQNPM_ERR_NOT_CONVERGED) && nb <= h->max_batch) {
+    h->fields_valid = true;
+    h->fields_x = x;
+    h->fields_illum.assign(illum, illum + nb);
+  }
+  return rc;
+}
+
+// Gradient of the data term, reusing the fields of the last loss_batch_impl
+// when allowed and they match (same x pointer and illuminations).
+int grad_fields_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad,
+                     bool reuse, int* reused) {
+  const bool match = reuse && h->fields_valid && h->fields_x == x && (int)h->fields_illum.size() == nb &&
+                     std::equal(illum, illum + nb, h->fields_illum.begin());
+  if (reused) *reused = match ? 1 : 0;
+  if (!match) return grad_batch_impl(h, x, illum, nb, scale, grad, nullptr, nullptr, true, nullptr);
+  h->fields_valid = false;   // the adjoint solve reuses the Krylov workspace
+  std::vector<int> it(2 * nb, 0);
+  int rc = chunk_adjoint(h, x, nb, it.data(), scale, grad, false);
+  if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  const int rt = check_tile_waits(h);
+  return rt != MQNPM_OK ? rt : rc;
 }
 
 cudaError_t vec_reduce(mqnpm_handle* h, int /*kind*/, const float* a, const float* b, const float* c,
@@ -557,6 +630,7 @@ int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, cons
   float* q = h->vq;   // current unit vector
   float* a = h->g;    // operator output
   double d3[3];
+  h->fields_valid = false;   // the power steps reuse the slot workspace
   CK(vec_reduce(h, 0, start, nullptr, nullptr, nullptr, d3));
   if (!(d3[0] > 0.0)) return set_error(h, MQNPM_ERR_INVALID_ARG, "lipschitz: zero start vector");
   k_scale_real<<<w.ctas_vec, 256, 0, s>>>(start, q, N, (float)(1.0 / std::sqrt(d3[0])));

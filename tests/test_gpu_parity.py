@@ -185,3 +185,55 @@ def test_wprox_matches_oracle(kind, S_eff, n):
     assert rel(xg.cpu().numpy().reshape(xo.shape), xo) < 1e-5, rel(xg.cpu().numpy().reshape(xo.shape), xo)
     assert rel(Pw.cpu().numpy().reshape(Po.shape), Po) < 1e-4
     h.close()
+
+
+# ------------------------------------------------------------------ autograd
+@pytest.mark.parametrize("model", ["ls", "born"])
+@pytest.mark.parametrize("nb,max_batch", [(3, 4), (5, 2)])
+def test_autograd_split_matches_grad_batch_and_oracle(model, nb, max_batch):
+    """LSGradient: forward = loss only, backward = adjoint solves.  With the
+    batch inside the workspace the backward reuses the forward fields; with a
+    larger batch it recomputes them.  Both give grad_batch's loss and gradient
+    and the oracle's to the gradient tolerance."""
+    from paper_2307_02043_gb300.autograd import LSGradient
+
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, model, L=6, batch=3)
+    h = make_handle(n, kd, so, [1.0] * w.S, model=model, krylov_tol=1e-6, max_batch=max_batch)
+    h.set_measurements(c64(ys).reshape(-1))
+    x = (0.7 * f32(xt)).reshape(n, n, n).requires_grad_(True)
+    illum = list(range(nb))
+    scale = w.S / w.L
+    loss = LSGradient.apply(x, h, illum, scale)
+    loss.backward()
+    assert h.last_backward_reused == (nb <= max_batch)
+    g_ref, l_ref, _ = h.grad_batch(x.detach().reshape(-1).contiguous(), illum, scale)
+    assert abs(float(loss.detach()) - l_ref) <= 1e-7 * abs(l_ref)
+    assert rel(x.grad.reshape(-1).cpu().numpy(), g_ref.cpu().numpy()) < 1e-6
+    lo, go = om.batch_loss_grad(0.7 * xt, illum, ys, scale)
+    assert rel(x.grad.cpu().numpy().reshape(go.shape), go) < 1e-4
+    assert abs(float(loss.detach()) - lo) <= 1e-5 * abs(lo)
+    h.close()
+
+
+def test_grad_fields_recomputes_after_other_calls():
+    """Stored fields are dropped by any other use of the workspace: the
+    gradient is then recomputed and still equal."""
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, "ls", L=6, batch=3)
+    h = make_handle(n, kd, so, [1.0] * w.S, krylov_tol=1e-6, max_batch=4)
+    h.set_measurements(c64(ys).reshape(-1))
+    x = f32(0.7 * xt).reshape(-1)
+    h.loss_batch(x, [0, 1], 1.0)
+    h.forward(x, [2])                                   # uses the workspace
+    g1, reused = h.grad_fields(x, [0, 1], 1.0)
+    assert not reused
+    h.loss_batch(x, [0, 1], 1.0)
+    g2, reused = h.grad_fields(x, [0, 1], 1.0)
+    assert reused
+    g3, reused = h.grad_fields(x, [0, 1], 1.0)          # the adjoint solve used the workspace
+    assert not reused
+    ref, _, _ = h.grad_batch(x, [0, 1], 1.0)
+    for g in (g1, g2, g3):
+        assert rel(g.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+    h.close()

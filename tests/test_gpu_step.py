@@ -78,6 +78,26 @@ def test_step_trajectory_matches_oracle(ls32, warm):
     h.close()
 
 
+def test_strategy2_trajectory_matches_oracle(ls32):
+    """Strategy II (s' drawn uniformly, seeded draws passed to both sides) on
+    config 1: per-iterate error against the FP64 oracle."""
+    w, kd, om, ys, subs, so, alpha, _, _ = ls32
+    draws = synth.strategy2_draws(w, w.outer_iters)
+    opt = bqnpm.BQNPM(om, ys, subs, alpha, lam=w.lam, box=w.box, kind=w.tv, dual_iters=w.dual_iters,
+                      gamma=w.gamma, step=w.step, strategy=2, draws=draws)
+    xs = opt.run(np.zeros((w.n,) * 3), w.outer_iters)
+    h = handle(w, kd, so, alpha, strategy=2, draws=[int(d) for d in draws])
+    h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+    x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+    for k in range(1, w.outer_iters + 1):
+        info = h.step(x)
+        assert info["subset"] == opt.history[k - 1]["s"]
+        xg = x.cpu().numpy().astype(np.float64).reshape(xs[k].shape)
+        err = np.linalg.norm(xg - xs[k]) / np.linalg.norm(xs[k])
+        assert err < 2e-3, (k, err)
+    h.close()
+
+
 @pytest.mark.parametrize("warm", [False, True])
 def test_checkpoint_resume_is_bit_identical(ls32, warm):
     w, kd, om, ys, subs, so, alpha, opt, xs = ls32
