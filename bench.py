@@ -532,8 +532,10 @@ def main():
     bytes_dom = per_slot[dom] * prof["slot_launches"] + (8 * (n + 1) ** 3 * prof["calls"] if dom == 2 else 0)
     peak, peak_kind = peaks()
     achieved = bytes_dom / (pms[dom] / 1e3) / 1e9 if pms[dom] > 0 else 0.0
+    # GB/s only where the bytes per slot do not depend on the fused prologue or
+    # epilogue (the x passes move 20-52 N bytes per slot depending on the kind)
     passes = {nm: {"ms": round(t, 3), "GB/s": round(per_slot[i] * prof["slot_launches"] / (t / 1e3) / 1e9, 1)
-                   if t > 0 else None} for i, (nm, t) in enumerate(zip(names, pms))}
+                   if t > 0 and nm not in ("x_fwd", "x_inv") else None} for i, (nm, t) in enumerate(zip(names, pms))}
     kit = [i["krylov_iters_max"] for i in infos]
     kit_per_illum = [i["krylov_iters_total"] / max(1, i["n_illum"]) for i in infos]
     out = {
