@@ -50,7 +50,7 @@ enum { MQNPM_MODEL_BORN = 0, MQNPM_MODEL_LS = 1 };
 enum { MQNPM_TV_ISO = 0, MQNPM_TV_ANISO = 1 };
 
 /* Largest number of subsets S (rank of the quasi-Newton metric) supported. */
-#define MQNPM_MAX_S 8
+#define MQNPM_MAX_S 16
 
 typedef struct mqnpm_config {
   /* --- forward model (Section 6; discretisation is the library's stated reading) */

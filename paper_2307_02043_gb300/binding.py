@@ -24,7 +24,7 @@ STATUS = {
 }
 MODEL = {"born": 0, "ls": 1}
 TV = {"iso": 0, "aniso": 1}
-MAX_S = 8
+MAX_S = 16
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 192)
 
 

@@ -248,7 +248,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   need += B * ((size_t)n * n * P + (size_t)n * P * P) * 8; // T1, T2
   need += B * M * 8;                                       // rdet
   need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
-  need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * 44 + 200) * 8 + wprox_part_count(wp_blocks) * 8;   // wprox
+  need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * wprox_part_len() + 600) * 8 + wprox_part_count(wp_blocks) * 8;   // wprox
   need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
   if (h->warm_start && h->model == MQNPM_MODEL_LS) need += (size_t)h->L * N * 8;     // stored fields
   if (h->budget > 0 && need > h->budget) {
@@ -291,7 +291,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(wp.part, wprox_part_count(wp_blocks));
   AL(wp.tot, (size_t)wprox_part_len());
   AL(wp.stat, 4);
-  AL(wp.gram, (size_t)wp.ctas_vec * 44);
+  AL(wp.gram, (size_t)wp.ctas_vec * wprox_part_len());
   AL(wp.scal, (size_t)woodbury_scal_count());
   AL(wp.barrier, (size_t)wprox_barrier_words());
   AL(wp.err, 1);

@@ -130,7 +130,7 @@ MQ_D void block_sum(double (&v)[K], double* scratch, double (&out)[K]) {
 // Sum K per-thread float partials over the block: the warp tree runs in FP32
 // (GB300's FP64 rate is a small fraction of its FP32 rate), the per-warp
 // results are combined in FP64 in warp order.  Thread 0 receives out[].
-// scratch: >= 32*K doubles.
+// scratch: >= (warps + 1) * K doubles (33 * K covers any block size).
 template <int K>
 MQ_D void block_sum_f(const float (&v)[K], double* scratch, double (&out)[K]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -143,12 +143,12 @@ MQ_D void block_sum_f(const float (&v)[K], double* scratch, double (&out)[K]) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += scratch[w * K + k];
-    scratch[32 * K + k] = s;
+    scratch[nw * K + k] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = scratch[32 * K + k];
+    for (int k = 0; k < K; ++k) out[k] = scratch[nw * K + k];
   }
   __syncthreads();
 }

@@ -12,13 +12,14 @@
 
 namespace {
 
-constexpr int OFF_G = 0;       // U^T U        (8 x 8)
-constexpr int OFF_M = 64;      // (I + U^T U / tau)^{-1}
-constexpr int OFF_UV = 128;    // U^T g
+constexpr int SM2 = MQNPM_MAX_S * MQNPM_MAX_S;
+constexpr int OFF_G = 0;          // U^T U        (S x S, row stride S)
+constexpr int OFF_M = SM2;        // (I + U^T U / tau)^{-1}
+constexpr int OFF_UV = 2 * SM2;   // U^T g
 
 template <int S>
 MQ_D void block_reduce_store(float (&acc)[S], double* dst) {
-  __shared__ double scratch[33 * S];
+  __shared__ double scratch[9 * S];   // 8 warps + totals
   double o[S];
   block_sum_f<S>(acc, scratch, o);
   if (threadIdx.x == 0) {
@@ -161,9 +162,17 @@ int qn_point_impl(mqnpm_handle* h, const float* x, const float* g, const UPtrs& 
     case 6: e = qn_point<6>(h, x, g, U, tau, aS, v); break;
     case 7: e = qn_point<7>(h, x, g, U, tau, aS, v); break;
     case 8: e = qn_point<8>(h, x, g, U, tau, aS, v); break;
+    case 9: e = qn_point<9>(h, x, g, U, tau, aS, v); break;
+    case 10: e = qn_point<10>(h, x, g, U, tau, aS, v); break;
+    case 11: e = qn_point<11>(h, x, g, U, tau, aS, v); break;
+    case 12: e = qn_point<12>(h, x, g, U, tau, aS, v); break;
+    case 13: e = qn_point<13>(h, x, g, U, tau, aS, v); break;
+    case 14: e = qn_point<14>(h, x, g, U, tau, aS, v); break;
+    case 15: e = qn_point<15>(h, x, g, U, tau, aS, v); break;
+    case 16: e = qn_point<16>(h, x, g, U, tau, aS, v); break;
     default: return set_error(h, MQNPM_ERR_INVALID_ARG, "qn_point: S_eff out of range");
   }
   return e == cudaSuccess ? MQNPM_OK : set_cuda_error(h, e, "qn_point");
 }
 
-int woodbury_scal_count() { return 136; }
+int woodbury_scal_count() { return 2 * SM2 + MQNPM_MAX_S; }

@@ -22,11 +22,13 @@
 #include "internal.h"
 #include "mqnpm.h"
 
+cudaError_t wprox_dispatch_high(mqnpm_handle* h, int S, int tv, void* args);
+
 namespace {
 
 constexpr int WP_THREADS = 256;
 constexpr int NW = WP_THREADS / 32;
-constexpr int NVMAX = 44;     // S + S(S+1)/2 for S = 8
+constexpr int NVMAX = MQNPM_MAX_S + MQNPM_MAX_S * (MQNPM_MAX_S + 1) / 2;   // S + S(S+1)/2
 // Trace layout (long long pairs): pair 0 = (barriers passed, start time),
 // pairs 1..TR_ACC-1 = (tag, time) per barrier, pairs from TR_ACC on hold block
 // 0's accumulated times: [2 TR_ACC] dual update, [+1] work before the dual
@@ -446,7 +448,7 @@ __device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, 
 // Block-level sum of K floats per thread into thread 0's out[] (FP64).
 template <int K>
 MQ_D void block_partial(const float (&acc)[K], double (&out)[K]) {
-  __shared__ double scratch[33 * (K > 0 ? K : 1)];
+  __shared__ double scratch[(NW + 1) * (K > 0 ? K : 1)];
   block_sum_f<K>(acc, scratch, out);
 }
 
@@ -563,13 +565,17 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const int gw = tid >> 5, nwt = stride >> 5;
   const float cdt = a.cdt;
-  int ps0 = 0, pt0 = 0, ps1 = 0, pt1 = 0;   // this lane's pairs: lane, lane + 32
+  constexpr int NGL = (NG + 31) / 32;      // pairs (s, t) per lane: lane + 32 j
+  int ps[NGL], pt[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) { ps[j] = 0; pt[j] = 0; }
   {
     int k = 0;
     for (int s = 0; s < S; ++s)
       for (int t = s; t < S; ++t) {
-        if (k == lane) { ps0 = s; pt0 = t; }
-        if (k == lane + 32) { ps1 = s; pt1 = t; }
+#pragma unroll
+        for (int j = 0; j < NGL; ++j)
+          if (k == lane + 32 * j) { ps[j] = s; pt[j] = t; }
         ++k;
       }
   }
@@ -579,7 +585,9 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
   float acc[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) acc[s] = 0.f;
-  float dH0 = 0.f, dH1 = 0.f;
+  float dH[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) dH[j] = 0.f;
   const float* __restrict__ din = a.d;
   float* __restrict__ xout = xw;
   uchar4* __restrict__ stat = reinterpret_cast<uchar4*>(a.status);
@@ -632,8 +640,9 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
           const int jl = __ffs(flips) - 1;
           flips &= flips - 1;
           const float sg = sh->trSign[wib][jl];
-          if (lane < NG) dH0 = fmaf(sg * sh->trU[wib][ps0][jl], sh->trU[wib][pt0][jl], dH0);
-          if (lane + 32 < NG) dH1 = fmaf(sg * sh->trU[wib][ps1][jl], sh->trU[wib][pt1][jl], dH1);
+#pragma unroll
+          for (int j = 0; j < NGL; ++j)
+            if (lane + 32 * j < NG) dH[j] = fmaf(sg * sh->trU[wib][ps[j]][jl], sh->trU[wib][pt[j]][jl], dH[j]);
         }
         __syncwarp();
       }
@@ -643,8 +652,9 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
   block_partial<S>(acc, o);
   if (threadIdx.x == 0)
     for (int k = 0; k < S; ++k) sh->blk[k] = o[k];
-  if (lane < NG) sh->dH[wib][lane] = dH0;
-  if (lane + 32 < NG) sh->dH[wib][lane + 32] = dH1;
+#pragma unroll
+  for (int j = 0; j < NGL; ++j)
+    if (lane + 32 * j < NG) sh->dH[wib][lane + 32 * j] = dH[j];
   __syncthreads();
   if (threadIdx.x < NG) {
     double sacc = 0.0;
@@ -902,6 +912,23 @@ cudaError_t launch_wprox(mqnpm_handle* h, WpArgs& a) {
   return cudaLaunchCooperativeKernel((void*)k_wprox<S, TV>, dim3(blocks), dim3(WP_THREADS), args, 0, h->stream);
 }
 
+#ifdef MQ_WP_HIGH
+template <int TV>
+cudaError_t dispatch_high_tv(mqnpm_handle* h, int S, WpArgs& a) {
+  switch (S) {
+    case 9: return launch_wprox<9, TV>(h, a);
+    case 10: return launch_wprox<10, TV>(h, a);
+    case 11: return launch_wprox<11, TV>(h, a);
+    case 12: return launch_wprox<12, TV>(h, a);
+    case 13: return launch_wprox<13, TV>(h, a);
+    case 14: return launch_wprox<14, TV>(h, a);
+    case 15: return launch_wprox<15, TV>(h, a);
+    case 16: return launch_wprox<16, TV>(h, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+#else
 template <int TV>
 cudaError_t dispatch(mqnpm_handle* h, int S, WpArgs& a) {
   switch (S) {
@@ -914,9 +941,10 @@ cudaError_t dispatch(mqnpm_handle* h, int S, WpArgs& a) {
     case 6: return launch_wprox<6, TV>(h, a);
     case 7: return launch_wprox<7, TV>(h, a);
     case 8: return launch_wprox<8, TV>(h, a);
-    default: return cudaErrorInvalidValue;
+    default: return wprox_dispatch_high(h, S, TV, &a);
   }
 }
+#endif
 
 #define CK(call)                                                \
   do {                                                          \
@@ -925,6 +953,16 @@ cudaError_t dispatch(mqnpm_handle* h, int S, WpArgs& a) {
   } while (0)
 
 }  // namespace
+
+#ifdef MQ_WP_HIGH
+// Ranks 9-16, instantiated in a second compilation of this file (MQ_WP_HIGH)
+// to keep each translation unit's build short.  args points to the WpArgs of
+// the calling unit (the same definition, compiled from this file).
+cudaError_t wprox_dispatch_high(mqnpm_handle* h, int S, int tv, void* args) {
+  WpArgs& a = *static_cast<WpArgs*>(args);
+  return tv == MQNPM_TV_ISO ? dispatch_high_tv<MQNPM_TV_ISO>(h, S, a) : dispatch_high_tv<MQNPM_TV_ANISO>(h, S, a);
+}
+#else
 
 int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int S_eff, double c, float* P_warm,
                bool warm, float* x_out) {
@@ -1015,3 +1053,4 @@ std::vector<float> wprox_momentum(int J) {
 int wprox_part_len() { return NVMAX; }
 size_t wprox_part_count(int max_blocks) { return (size_t)(max_blocks + WP_MAXG) * NVMAX; }
 int wprox_barrier_words() { return 3 + WP_MAXG; }
+#endif

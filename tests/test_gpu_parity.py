@@ -168,9 +168,9 @@ def test_lipschitz_matches_oracle():
 
 
 # ------------------------------------------------------------ proximal map
-@pytest.mark.parametrize("kind", ["iso", "aniso"])
-@pytest.mark.parametrize("S_eff", [0, 1, 3, 4])
-@pytest.mark.parametrize("n", [8, 24])
+@pytest.mark.parametrize("kind,S_eff,n", [(k, s, m) for k in ("iso", "aniso") for s in (0, 1, 3, 4)
+                                          for m in (8, 24)] + [("iso", 9, 8), ("aniso", 12, 8), ("iso", 16, 8),
+                                                               ("iso", 16, 24)])
 def test_wprox_matches_oracle(kind, S_eff, n):
     rng = np.random.default_rng(10 * S_eff + n)
     v = rng.uniform(-0.02, 0.07, (n, n, n))

@@ -98,6 +98,28 @@ def test_strategy2_trajectory_matches_oracle(ls32):
     h.close()
 
 
+def test_step_trajectory_rank_above_8():
+    """S = 12 subsets (L = 24, b = 2 at 16^3: the subset counts of the uneven
+    request mix go up to 15): the rank-12 metric and prox follow the oracle."""
+    w = synth.small("ls32", n=16, L=24, batch=2, outer_iters=26)
+    assert w.S == 12
+    kd, om, xt, ys, subs, so = setup(w)
+    alpha = [om.lipschitz(s, w.S / w.L, synth.power_start(w), 10) for s in subs]
+    opt = bqnpm.BQNPM(om, ys, subs, alpha, lam=w.lam, box=w.box, kind=w.tv, dual_iters=w.dual_iters,
+                      gamma=w.gamma, step=w.step)
+    xs = opt.run(np.zeros((w.n,) * 3), w.outer_iters)
+    h = handle(w, kd, so, alpha)
+    h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+    x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+    for k in range(1, w.outer_iters + 1):
+        info = h.step(x)
+        xg = x.cpu().numpy().astype(np.float64).reshape(xs[k].shape)
+        err = np.linalg.norm(xg - xs[k]) / np.linalg.norm(xs[k])
+        assert err < 2e-3, (k, err, info)
+    assert info["rank"] > 8
+    h.close()
+
+
 @pytest.mark.parametrize("warm", [False, True])
 def test_checkpoint_resume_is_bit_identical(ls32, warm):
     w, kd, om, ys, subs, so, alpha, opt, xs = ls32
