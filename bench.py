@@ -412,6 +412,100 @@ def grad_only(args, torch, binding):
     h.close()
 
 
+def serve_uneven(args, torch, binding):
+    """Uneven request mix (16 reconstructions, grids 64^3-160^3, L in {24, 48, 60},
+    mini-batch 4-8): requests are admitted while their workspace fits the HBM
+    budget (the library's own budget check at create), served round-robin one
+    MQNPM iteration at a time, and retired after `outer_iters` iterations, which
+    admits queued requests.  Prints throughput and per-iteration latency
+    percentiles as one JSON line."""
+    dev = torch.device("cuda", 0)
+    reqs = synth.uneven_requests()
+    budget = int(args.hbm_budget_gb * 2 ** 30)
+    # measurements and alpha_s of every request (set-up, not timed)
+    prepared = []
+    for w in reqs:
+        subs = synth.subsets(w)
+        kd = synth.illumination_dirs(w)
+        so = subset_of(w)
+        xt = torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
+        mb = max(len(q) for q in subs)
+        setup = binding.MQNPM(w.n, kd, so, [1.0] * w.S, krylov_tol=1e-6, krylov_maxit=1000, max_batch=mb)
+        ys = [setup.forward(xt, list(range(c0, min(w.L, c0 + mb))))[0] for c0 in range(0, w.L, mb)]
+        y = torch.cat(ys)
+        noise = torch.from_numpy(synth.noise_draws(w).astype(np.complex64)).to(dev)
+        sigma = torch.linalg.vector_norm(y, dim=1, keepdim=True) / math.sqrt(w.n * w.n) * 10 ** (-w.snr_db / 20)
+        y = (y + sigma * noise).contiguous()
+        start = torch.from_numpy(synth.power_start(w).astype(np.float32)).to(dev).reshape(-1)
+        alpha = [setup.lipschitz(list(q), w.S / w.L, start, iters=10) for q in subs]
+        setup.close()
+        del xt
+        prepared.append((w, kd, so, alpha, y, mb))
+    torch.cuda.synchronize()
+    queue = list(range(len(reqs)))
+    active = {}        # request index -> (handle, x, iterations done)
+    used = 0
+    lat_ms, illum_done, admitted_order, peak_used = [], 0, [], 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def admit():
+        nonlocal used, peak_used
+        while queue:
+            i = queue[0]
+            w, kd, so, alpha, y, mb = prepared[i]
+            if budget - used <= 0:                   # a zero budget would mean "no limit"
+                return
+            try:
+                h = binding.MQNPM(w.n, kd, so, alpha, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=w.krylov_tol,
+                                  krylov_maxit=1000, dual_iters=w.dual_iters, gamma=w.gamma, step=w.step,
+                                  max_batch=mb, warm_start=True, hbm_budget_bytes=budget - used)
+            except binding.MQNPMError as err:
+                if err.code == 2 and active:     # over budget: wait for a retirement
+                    return
+                raise
+            h.set_measurements(y.reshape(-1))
+            used += h.workspace_bytes
+            peak_used = max(peak_used, used)
+            active[i] = (h, torch.zeros(w.N, dtype=torch.float32, device=dev), 0)
+            admitted_order.append(i)
+            queue.pop(0)
+
+    admit()
+    admitted_first = len(active)
+    t0.record()
+    while active:
+        for i in list(active):
+            h, x, done = active[i]
+            e0.record()
+            info = h.step(x, allow_not_converged=True)
+            e1.record()
+            e1.synchronize()
+            lat_ms.append(e0.elapsed_time(e1))
+            illum_done += info["n_illum"]
+            done += 1
+            if done >= prepared[i][0].outer_iters:
+                used -= h.workspace_bytes
+                h.close()
+                del active[i]
+                admit()
+            else:
+                active[i] = (h, x, done)
+    t1.record()
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    lat = np.array(lat_ms)
+    print(json.dumps({
+        "workload": "uneven16", "requests": len(reqs), "grids": sorted({w.n for w in reqs}),
+        "hbm_budget_gb": args.hbm_budget_gb, "peak_workspace_gb": round(peak_used / 2 ** 30, 2),
+        "admitted_at_start": admitted_first, "admission_order": admitted_order, "iterations": int(lat.size),
+        "illum_gradients_per_s": round(illum_done / (total_ms / 1e3), 2),
+        "iteration_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                 "p99": round(float(np.percentile(lat, 99)), 3),
+                                 "max": round(float(lat.max()), 3)},
+        "total_ms": round(total_ms, 1)}), flush=True)
+
+
 # ---------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -425,6 +519,9 @@ def main():
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
+    ap.add_argument("--serve-uneven", action="store_true",
+                    help="uneven request mix: admission by HBM budget, round-robin iterations, latency percentiles")
+    ap.add_argument("--hbm-budget-gb", type=float, default=24.0, help="HBM budget of --serve-uneven")
     ap.add_argument("--grad-only", action="store_true",
                     help="small case for profiler captures: mini-batch gradients of the workload")
     ap.add_argument("--prox-only", action="store_true",
@@ -448,6 +545,9 @@ def main():
         return
     if args.grad_only:
         grad_only(args, torch, binding)
+        return
+    if args.serve_uneven:
+        serve_uneven(args, torch, binding)
         return
 
     if args.warmup < 3:
