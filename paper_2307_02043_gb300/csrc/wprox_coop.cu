@@ -193,14 +193,16 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
       if (s_role == 2) {
         __threadfence();
         if (threadIdx.x < NV) {
+          // all group sums of a chunk are loaded before any is added (one
+          // round trip for up to 24 groups: 384 blocks)
           double acc = 0.0;
-          for (int q0 = 0; q0 < ngroups; q0 += 8) {
-            double vals[8];
+          for (int q0 = 0; q0 < ngroups; q0 += 24) {
+            double vals[24];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < 24; ++q)
               vals[q] = (q0 + q < ngroups) ? __ldcg(gpart + (size_t)(q0 + q) * NVMAX + threadIdx.x) : 0.0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc += vals[q];
+            for (int q = 0; q < 24; ++q) acc += vals[q];
           }
           a.tot[threadIdx.x] = acc;
         }

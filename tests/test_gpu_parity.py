@@ -237,3 +237,49 @@ def test_grad_fields_recomputes_after_other_calls():
     for g in (g1, g2, g3):
         assert rel(g.cpu().numpy(), ref.cpu().numpy()) < 1e-6
     h.close()
+
+
+@pytest.mark.parametrize("case", ["no_dual_iterations", "point_box", "tiny_c", "large_tau"])
+def test_wprox_degenerate_cases(case):
+    """Degenerate proximal problems against the oracle: J = 0 (x = prox of the
+    box under B at the warm dual field), lo = hi (x is the constant), c -> 0
+    (x -> box projection under B), and tau* >> |U|^2 (B ~ tau* I)."""
+    n, S_eff = 8, 3
+    rng = np.random.default_rng(77)
+    v = rng.uniform(-0.02, 0.07, (n, n, n))
+    U = rng.standard_normal((S_eff, n, n, n)) * 0.05
+    P0 = rng.uniform(-0.5, 0.5, (3, n, n, n))
+    tau, c, J, lo, hi, kind = 1.5, 2e-3, 6, 0.0, 0.05, "iso"
+    if case == "no_dual_iterations":
+        J = 0
+    elif case == "point_box":
+        lo = hi = 0.03
+    elif case == "tiny_c":
+        c, kind = 1e-12, "aniso"
+    elif case == "large_tau":
+        tau = 1e4
+    xo, Po, _ = owprox.wprox(v, tau, U, c, lo, hi, kind, J, P0=P0, newton_tol=1e-6)
+    h = make_handle(n, cone(2), [0, 0], [1.0], tv=kind, box=(lo, hi), dual_iters=J, newton_tol=1e-6)
+    Pw = f32(P0).reshape(-1).clone()
+    xg = h.wprox(f32(v).reshape(-1), tau, f32(U).reshape(-1), c, P_warm=Pw).cpu().numpy().reshape(xo.shape)
+    if case == "point_box":
+        assert np.all(xg == np.float32(0.03))
+    else:
+        assert rel(xg, xo) < 1e-5, rel(xg, xo)
+    h.close()
+
+
+def test_empty_and_invalid_batches_are_rejected():
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, "ls")
+    h = make_handle(n, kd, so, [1.0] * w.S)
+    h.set_measurements(c64(ys).reshape(-1))
+    x = f32(xt).reshape(-1)
+    lib = h.lib
+    g = torch.empty_like(x)
+    il = (binding.ctypes.c_int * 1)(0)
+    assert lib.mqnpm_grad_batch(h._h, binding._ptr(x), il, 0, 1.0, binding._ptr(g), None, None) == 1
+    bad = (binding.ctypes.c_int * 1)(w.L)
+    assert lib.mqnpm_grad_batch(h._h, binding._ptr(x), bad, 1, 1.0, binding._ptr(g), None, None) == 1
+    assert lib.mqnpm_loss_batch(h._h, binding._ptr(x), il, 0, 1.0, None, None) == 1
+    h.close()
