@@ -51,6 +51,9 @@ enum { MQNPM_TV_ISO = 0, MQNPM_TV_ANISO = 1 };
 
 /* Largest number of subsets S (rank of the quasi-Newton metric) supported. */
 #define MQNPM_MAX_S 16
+/* Largest workspace batch (illuminations solved together); larger mini-batches
+ * run in chunks of max_batch. */
+#define MQNPM_MAX_BATCH 64
 
 typedef struct mqnpm_config {
   /* --- forward model (Section 6; discretisation is the library's stated reading) */
@@ -84,7 +87,8 @@ typedef struct mqnpm_config {
   double newton_tol;       /* semi-smooth Newton tolerance (Algorithm 4.3)          */
   int newton_maxit;
   /* --- resources */
-  int max_batch;           /* illuminations solved together (workspace sizing)      */
+  int max_batch;           /* illuminations solved together (workspace sizing),
+                              1..MQNPM_MAX_BATCH                                    */
   size_t hbm_budget_bytes; /* 0: no limit; else create fails with MQNPM_ERR_BUDGET  */
   int device;              /* CUDA device ordinal                                   */
   void* stream;            /* cudaStream_t for all work (NULL: legacy default)      */

@@ -166,6 +166,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   // ---- validation
   if (cfg->n < 4 || cfg->L < 1 || cfg->S < 1 || cfg->S > MQNPM_MAX_S || cfg->S > cfg->L || !cfg->kdir ||
       !cfg->subset_of || !cfg->alpha || !(cfg->h > 0) || !(cfg->kb > 0) || cfg->max_batch < 1 ||
+      cfg->max_batch > MQNPM_MAX_BATCH ||
       !(cfg->box_lo <= cfg->box_hi) || !(cfg->lambda >= 0) || !(cfg->step > 0) || cfg->dual_iters < 0 ||
       !(cfg->krylov_tol > 0) || cfg->krylov_maxit < 1 || (cfg->model != MQNPM_MODEL_LS && cfg->model != MQNPM_MODEL_BORN) ||
       (cfg->tv != MQNPM_TV_ISO && cfg->tv != MQNPM_TV_ANISO) || (cfg->strategy != 1 && cfg->strategy != 2) ||

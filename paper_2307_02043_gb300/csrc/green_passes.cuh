@@ -291,10 +291,11 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   const size_t zs = (size_t)P * P;
   const int m1 = n + 1;
   const uint32_t tile_bytes = (uint32_t)SM::in_bytes(n);
-  auto active = [&](int b) { return st == nullptr || st[b].active != 0; };
-  int b = 0;
-  while (b < nb && !active(b)) ++b;
-  if (b >= nb) return;
+  unsigned long long act = 0ull;   // active slots as a bit mask (nb <= 64)
+  for (int q = 0; q < nb; ++q)
+    if (st == nullptr || st[q].active != 0) act |= 1ull << q;
+  if (act == 0ull) return;
+  int b = __ffsll((long long)act) - 1;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -317,7 +318,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   }
   __syncthreads();
   uint32_t phase = 0u;
-  while (b < nb) {
+  while (true) {
     if (!mbar_wait_bounded(bar, phase, 1 << 22)) {
       if (threadIdx.x == 0) atomicExch(err, 1);
       // the copy given up on is the only one in flight: give it one more bounded wait
@@ -342,8 +343,8 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       for (int k1 = 0; k1 < R1; ++k1) exw[k1 * C] = (k1 == 0) ? a[0] : cmul(a[k1], twr[k1]);
     }
     __syncthreads();   // the tile is consumed: fetch the next active slot's into the same buffer
-    int next = b + 1;
-    while (next < nb && !active(next)) ++next;
+    const unsigned long long rest = act & ~((2ull << b) - 1ull);
+    const int next = rest ? __ffsll((long long)rest) - 1 : nb;
     if (next < nb && threadIdx.x == 0) {
       fence_proxy_async();
       mbar_expect_tx(bar, tile_bytes);
@@ -396,6 +397,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       }
     }
     __syncthreads();   // ex is free again for the next slot's first stage
+    if (next >= nb) break;
     b = next;
   }
 }

@@ -182,6 +182,9 @@ def test_failures_are_reported():
     with pytest.raises(binding.MQNPMError) as e:
         binding.MQNPM(16, kd, so, [1.0, -1.0])
     assert e.value.code == 1
+    with pytest.raises(binding.MQNPMError) as e:
+        binding.MQNPM(16, kd, so, [1.0, 1.0], max_batch=65)   # above MQNPM_MAX_BATCH
+    assert e.value.code == 1
     # budget below the workspace
     with pytest.raises(binding.MQNPMError) as e:
         handle(w, kd, so, [1.0, 1.0], hbm_budget_bytes=1 << 20)
