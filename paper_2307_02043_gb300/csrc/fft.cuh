@@ -38,15 +38,32 @@ constexpr int first_factor(int R) {
                                                                                            : (R % 5 == 0 && R > 5) ? 5 : R;
 }
 
-// In-place DFT of length R on registers, natural order in and out.
-template <int R, bool INV>
+// In-place DFT of length R on registers, natural order in and out.  NZ < R
+// declares a[NZ..R) zero (the zero-padded half of a pruned transform): the
+// butterflies that only add those zeros are left out.
+template <int R, bool INV, int NZ = R>
 MQ_D void dft(float2 (&a)[R]) {
+  static_assert(NZ >= 1 && NZ <= R, "NZ in [1, R]");
   if constexpr (R == 1) {
     return;
+  } else if constexpr (R == 2 && NZ == 1) {
+    a[1] = a[0];
   } else if constexpr (R == 2) {
     float2 t = a[0];
     a[0] = cadd(t, a[1]);
     a[1] = csub(t, a[1]);
+  } else if constexpr (R == 4 && NZ == 1) {
+    a[1] = a[0];
+    a[2] = a[0];
+    a[3] = a[0];
+  } else if constexpr (R == 4 && NZ == 2) {
+    // inputs (a0, a1, 0, 0): y_k = a0 + W^k a1
+    const float2 a0 = a[0], a1 = a[1];
+    const float2 r = INV ? make_float2(-a1.y, a1.x) : make_float2(a1.y, -a1.x);   // -i a1 (fwd)
+    a[0] = cadd(a0, a1);
+    a[2] = csub(a0, a1);
+    a[1] = cadd(a0, r);
+    a[3] = csub(a0, r);
   } else if constexpr (R == 3) {
     constexpr float h = 0.86602540378443864676f;   // sqrt(3)/2
     float2 s = cadd(a[1], a[2]);
@@ -93,9 +110,12 @@ MQ_D void dft(float2 (&a)[R]) {
     float2 y[R];  // y[n2 * A + k1]
     static_for<B>([&](auto n2c) {
       constexpr int n2 = decltype(n2c)::value;
+      // nonzero inputs of this sub-transform: n1 with B n1 + n2 < NZ
+      constexpr int NZT0 = (NZ - n2 + B - 1) / B;
+      constexpr int NZT = NZT0 < 1 ? 1 : (NZT0 > A ? A : NZT0);
       float2 t[A];
       static_for<A>([&](auto n1c) { t[decltype(n1c)::value] = a[B * decltype(n1c)::value + n2]; });
-      dft<A, INV>(t);
+      dft<A, INV, NZT>(t);
       static_for<A>([&](auto k1c) {
         constexpr int k1 = decltype(k1c)::value;
         y[n2 * A + k1] = tw_mul<(long)n2 * k1, R, INV>(t[k1]);

@@ -112,7 +112,7 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
       a[n1] = make_float2(0.f, 0.f);
       if (n1 < R1 / 2 && valid) a[n1] = pro.load(b, R2 * n1 + n2, y, z, parts);
     }
-    dft<R1, false>(a);
+    dft<R1, false, R1 / 2>(a);   // inputs n1 >= R1/2 are the zero padding
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) exl[n2 * SH::PITCH + k1] = cmul(a[k1], tw[n2 * k1]);
   }
@@ -214,7 +214,7 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
       a[n1] = make_float2(0.f, 0.f);
       if (INV || n1 < R1 / 2) a[n1] = src[(size_t)(R2 * n1 + n2) * P];
     }
-    dft<R1, INV>(a);
+    dft<R1, INV, INV ? R1 : R1 / 2>(a);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       const float2 w = tw[n2 * R1 + k1];
@@ -336,7 +336,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
         a[n1] = make_float2(0.f, 0.f);
         if (n1 < R1 / 2) a[n1] = in[(R2 * n1 + n2) * C + c];
       }
-      dft<R1, false>(a);
+      dft<R1, false, R1 / 2>(a);   // inputs n1 >= R1/2 are the zero padding
       const float2* twr = tw + n2 * R1;
       float2* exw = ex + (n2 * R1) * C + c;
 #pragma unroll
