@@ -60,14 +60,42 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def fp32_peak_tflops():
+    """FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32
+    lanes x 2 flops per FMA x the maximum SM clock (MEASURED_PEAKS.json, else
+    the nominal 2070 MHz)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
 # ---------------------------------------------------------------- clocks
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of k_pass3 at
 # n = 128 from one ncu capture of 4 slots per launch (profiles/
 # k_pass3_ls128_batch4.md), per slot.  It applies only while the sources the
 # kernel is compiled from are the captured ones (digest below); otherwise the
 # bench reports traffic as null.
-PASS3_CAPTURE = {"n": 128, "bytes_per_slot": 126694784, "sources_sha256_16": "ed4ea0d4e3978d4b"}
+PASS3_CAPTURE = {"n": 128, "bytes_per_slot": 126668608, "sources_sha256_16": "77f4dab900a63162"}
 PASS3_SOURCES = ("common.cuh", "fft.cuh", "green_passes.cuh", "green_inst.cu")
+
+
+def pass3_alu_view(n: int, prof: dict, ms: float):
+    """Pass 3 as the FP32-issue-bound kernel it is: FFT flops by the usual
+    convention (5 P log2 P per P-point complex transform, two per column, plus
+    6 per point for the K_hat product) over its live time, against the FP32
+    FMA peak.  The convention counts the full transforms, so it is an upper
+    estimate of the arithmetic done by the pruned ones."""
+    P = 2 * n
+    flops_slot = P * P * (2 * 5 * P * math.log2(P) + 6 * P)
+    achieved = flops_slot * prof["slot_launches"] / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    peak = fp32_peak_tflops()
+    return {"bound": "alu", "kernel": "k_pass3", "achieved": round(achieved, 2), "peak": round(peak, 1),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "flops_per_slot": int(flops_slot),
+            "convention": "5 P log2 P per transform + 6 per K_hat product; peak = 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"}
 
 
 def pass3_traffic(n: int, slots_per_launch: float):
@@ -643,7 +671,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)", "data": "synthetic",
         "config": {"workload": w.name, "n": n, "padded": 2 * n, "L": w.L, "batch": max(len(s) for s in subs),
-                   "S": w.S, "model": "lippmann-schwinger", "krylov_tol": w.krylov_tol, "dual_iters": w.dual_iters,
+                   "S": w.S, "model": "lippmann-schwinger" if w.model == "ls" else "first-born",
+                   "krylov_tol": w.krylov_tol if w.model == "ls" else None, "dual_iters": w.dual_iters,
                    "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
                    "krylov_start": "forward solves warm-started from each illumination's last field",
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
@@ -656,6 +685,7 @@ def main():
                      "algorithmic_bytes_per_slot": per_slot[dom],
                      "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof["calls"])),
                      "launches": prof["calls"], "slots_per_launch": round(prof["slot_launches"] / max(1, prof["calls"]), 2)},
+        "roofline_alu": pass3_alu_view(n, prof, pms[2]),
         "passes": passes,
         "green_applies": prof["calls"],
         "phase_ms": {k: round(statistics.mean(i["ms_" + k] for i in infos), 3) for k in ("gradient", "metric", "prox")},
