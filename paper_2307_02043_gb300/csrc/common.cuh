@@ -153,40 +153,12 @@ MQ_D void block_sum_f(const float (&v)[K], double* scratch, double (&out)[K]) {
   __syncthreads();
 }
 
-// ------------------------------------------------------------ grid barrier
-// Barrier for cooperative launches (all blocks co-resident).  `count` is a
-// monotonically increasing arrival counter zeroed before the launch; `epoch`
-// is the number of barriers this block has passed.  The wait is bounded by
-// `limit_cycles`; on expiry the block raises *err and returns false, and every
-// caller leaves its loop, so the kernel ends instead of hanging.
+// Acquire load of a flag written with a release store by another block.
 MQ_D unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-MQ_D bool grid_barrier(unsigned* count, unsigned nblocks, unsigned& epoch, int* err,
-                       long long limit_cycles) {
-  __syncthreads();
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    epoch += 1;
-    __threadfence();
-    atomicAdd(count, 1u);
-    const unsigned target = epoch * nblocks;
-    const long long t0 = clock64();
-    int ok = 1;
-    while (ld_acquire_u32(count) < target) {
-      if (*((volatile int*)err) != 0) { ok = 0; break; }
-      if (clock64() - t0 > limit_cycles) { atomicExch(err, 1); ok = 0; break; }
-      __nanosleep(64);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // ------------------------------------------------------- TMA and mbarriers
 // Tensor-memory-accelerator tile loads into shared memory, completed on an
 // mbarrier (transaction count = bytes).  Waits are bounded: the caller gets
