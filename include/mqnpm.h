@@ -97,6 +97,9 @@ typedef struct mqnpm_config {
                               computed for the same illumination (kept on the
                               device, L x N complex, and in checkpoints);
                               0: from u_in                                     */
+  int direct_launches;     /* 0: a BiCGSTAB iteration (14 kernels) is captured
+                              once per batch shape as a CUDA graph and replayed;
+                              1: its kernels are launched one by one          */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;

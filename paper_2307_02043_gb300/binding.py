@@ -50,7 +50,7 @@ class Config(ctypes.Structure):
         ("delta2", ctypes.c_double), ("krylov_tol", ctypes.c_double), ("krylov_maxit", ctypes.c_int),
         ("dual_iters", ctypes.c_int), ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
-        ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int),
+        ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
     ]
 
 
@@ -166,7 +166,8 @@ class MQNPM:
                  step: float = 1.0, strategy: int = 1, draws: Optional[Sequence[int]] = None,
                  gamma: float = 0.8, tau_max: float = 0.0, krylov_tol: float = 1e-6, krylov_maxit: int = 500,
                  dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
-                 hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False):
+                 hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
+                 direct_launches: bool = False):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -208,6 +209,7 @@ class MQNPM:
         cfg.max_batch = max_batch
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.warm_start = int(bool(warm_start))
+        cfg.direct_launches = int(bool(direct_launches))
         cfg.device = self.device
         with torch.cuda.device(self.device):
             cfg.stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)

@@ -70,6 +70,9 @@ void profile_clear(mqnpm_handle* h) {
   h->prof.nb.clear();
   h->prof.used = 0;
   h->prof.on = false;
+  for (double& v : h->prof.acc_ms) v = 0.0;
+  h->prof.acc_slots = 0;
+  h->prof.acc_calls = 0;
 }
 
 }  // namespace
@@ -107,8 +110,8 @@ int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches
   if (!h || !pass_ms) return MQNPM_ERR_INVALID_ARG;
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->stream));
-  for (int p = 0; p < 5; ++p) pass_ms[p] = 0.0;
-  long long slots = 0;
+  for (int p = 0; p < 5; ++p) pass_ms[p] = h->prof.acc_ms[p];
+  long long slots = h->prof.acc_slots;
   for (int g = 0; g < h->prof.used; ++g) {
     for (int p = 0; p < 5; ++p) {
       float ms = 0.f;
@@ -118,7 +121,7 @@ int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches
     slots += h->prof.nb[g];
   }
   if (slot_launches) *slot_launches = slots;
-  if (calls) *calls = h->prof.used;
+  if (calls) *calls = h->prof.used + h->prof.acc_calls;
   profile_clear(h);
   return MQNPM_OK;
 }
@@ -143,6 +146,12 @@ void mqnpm_destroy(mqnpm_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   profile_clear(h);
+  for (KrylovGraph& g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev)
+      if (e) cudaEventDestroy(e);
+  }
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   for (cudaEvent_t ev : h->step_ev)
     if (ev) cudaEventDestroy(ev);
   for (void* p : h->allocations) cudaFree(p);
@@ -206,6 +215,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->device = cfg->device;
   h->stream = static_cast<cudaStream_t>(cfg->stream);
   h->warm_start = cfg->warm_start != 0;
+  h->direct_launches = cfg->direct_launches != 0;
   h->budget = cfg->hbm_budget_bytes;
   h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
   h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);

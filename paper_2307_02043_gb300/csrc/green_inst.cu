@@ -53,7 +53,15 @@ int MQ_CAT(green_row_ctas_P, MQ_P)(int n) { return ceil_div(n * n, RS::LPB); }
 cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
   if (2 * c.n != P) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
-  if (c.ev) cudaEventRecord(c.ev[0], s);
+  // inside a stream capture the records must be external to become event-record
+  // nodes of the graph; outside one they are plain records
+  unsigned rec_flags = cudaEventRecordDefault;
+  if (c.ev) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+  }
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[0], s, rec_flags)) != cudaSuccess) return e;
   switch (c.pro) {
     case PRO_PLAIN: e = launch1<PRO_PLAIN>(c, s); break;
     case PRO_CONTRAST: e = launch1<PRO_CONTRAST>(c, s); break;
@@ -64,7 +72,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
-  if (c.ev) cudaEventRecord(c.ev[1], s);
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[1], s, rec_flags)) != cudaSuccess) return e;
   {
     auto kern = k_pass_y<P, false>;
     if ((e = set_smem(kern, CS::SMEM)) != cudaSuccess) return e;
@@ -72,7 +80,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     kern<<<grid, CS::THREADS, CS::SMEM, s>>>(c.T1, c.T2, c.n, c.tw, c.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (c.ev) cudaEventRecord(c.ev[2], s);
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[2], s, rec_flags)) != cudaSuccess) return e;
   {
     // one CTA per (kx tile, ky) column set; the batch is looped inside (one TMA tile buffer)
     dim3 grid(P / CS::C, P);
@@ -90,7 +98,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (c.ev) cudaEventRecord(c.ev[3], s);
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[3], s, rec_flags)) != cudaSuccess) return e;
   {
     auto kern = k_pass_y<P, true>;
     if ((e = set_smem(kern, CS::SMEM)) != cudaSuccess) return e;
@@ -98,7 +106,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     kern<<<grid, CS::THREADS, CS::SMEM, s>>>(c.T2, c.T1, c.n, c.tw, c.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (c.ev) cudaEventRecord(c.ev[4], s);
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[4], s, rec_flags)) != cudaSuccess) return e;
   switch (c.epi) {
     case EPI_PLAIN: e = launch5<EPI_PLAIN>(c, s); break;
     case EPI_V: e = launch5<EPI_V>(c, s); break;
@@ -108,7 +116,7 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     case EPI_DETECT: e = launch5<EPI_DETECT>(c, s); break;
     default: return cudaErrorInvalidValue;
   }
-  if (c.ev && e == cudaSuccess) cudaEventRecord(c.ev[5], s);
+  if (c.ev && e == cudaSuccess) e = cudaEventRecordWithFlags(c.ev[5], s, rec_flags);
   if (c.launches) *c.launches += 5;
   return e;
 }

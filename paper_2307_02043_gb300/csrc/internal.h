@@ -39,7 +39,21 @@ struct Profiler {
   std::vector<cudaEvent_t> ev;   // groups of 6
   int used = 0;                  // groups recorded
   std::vector<int> nb;           // batch slots of each recorded call
+  double acc_ms[5] = {0, 0, 0, 0, 0};   // applies replayed inside CUDA graphs, summed per pass
+  long long acc_slots = 0;
+  int acc_calls = 0;
   cudaEvent_t* next();
+};
+
+// One BiCGSTAB iteration captured as a CUDA graph for a batch shape.
+struct KrylovGraph {
+  int nb = 0;
+  bool adjoint = false, prof = false;
+  const float* x = nullptr;
+  const float2* xs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[12] = {};       // pass boundaries of the two applies (when profiled)
+  long long kernels = 0;         // kernels per replay
 };
 
 // Number of CTAs pass 1 / pass 5 use per slot (partials layout).
@@ -137,6 +151,9 @@ struct mqnpm_handle {
   int last_newton_max = 0, last_newton_total = 0;
   int last_status = 0;
   Profiler prof;
+  bool direct_launches = false;
+  cudaStream_t capture_stream = nullptr;   // stream the iteration graphs are captured on
+  std::vector<KrylovGraph> graphs;         // captured iterations (a few batch shapes)
   long long launches = 0;        // kernels launched by this handle since creation
   cudaEvent_t step_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // phase timing of mqnpm_step
 };

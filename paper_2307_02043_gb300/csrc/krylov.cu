@@ -320,13 +320,15 @@ __global__ void k_scale_real(const float* a, float* out, size_t N, float s) {
     if (e_ != cudaSuccess) return set_cuda_error(h, e_, #call); \
   } while (0)
 
-cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
-  c.ev = profile_slot(h, c.nb);
+cudaError_t glaunch_ev(mqnpm_handle* h, GreenCall c, cudaStream_t s, cudaEvent_t* ev) {
+  c.ev = ev;
   c.launches = &h->launches;
   c.tmap = h->w.t2map;
   c.err = h->w.gerr;
   return green_launch(c, s);
 }
+
+cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) { return glaunch_ev(h, c, s, profile_slot(h, c.nb)); }
 
 GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
   GreenCall c;
@@ -343,37 +345,122 @@ GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
   return c;
 }
 
-// Run BiCGSTAB iterations for the nb slots initialised by k_fin_init.
+// One BiCGSTAB iteration of the nb slots on stream s; evA and evB receive the
+// pass boundaries of its two Green's applies (or are null).
+int iteration_body(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint, cudaStream_t s,
+                   cudaEvent_t* evA, cudaEvent_t* evB) {
+  Workspace& w = h->w;
+  const size_t N = h->N;
+  GreenCall c = base_call(h, nb, adjoint);
+  c.st = w.st;
+  c.pro = PRO_BICG_P;
+  c.pa.x = x;
+  c.pa.w = w.p;
+  c.pa.r = w.r;
+  c.pa.v = w.v;
+  c.epi = EPI_V;
+  c.ea.out = w.v;
+  c.ea.a = w.p;
+  c.ea.rhat = w.rhat;
+  CK(glaunch_ev(h, c, s, evA));
+  k_fin_alpha<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row);
+  c.pro = PRO_BICG_S;
+  c.pa.w = w.s;
+  c.epi = EPI_T;
+  c.ea.out = w.t;
+  c.ea.a = w.s;
+  CK(glaunch_ev(h, c, s, evB));
+  k_fin_omega<<<nb, 256, 0, s>>>(w.st, w.part1, w.part5, w.ctas_row);
+  k_update<<<dim3(w.ctas_upd, nb), 256, 0, s>>>(w.st, xs, w.r, w.p, w.s, w.t, w.rhat, N, w.partu);
+  CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), s));
+  k_fin_rho<<<nb, 256, 0, s>>>(w.st, w.partu, w.ctas_upd, h->krylov_maxit, w.nactive);
+  CK(cudaGetLastError());
+  h->launches += 4;   // fin_alpha, fin_omega, update, fin_rho
+  return MQNPM_OK;
+}
+
+void destroy_graph(KrylovGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (cudaEvent_t& e : g.ev)
+    if (e) cudaEventDestroy(e);
+  g = KrylovGraph{};
+}
+
+// The iteration of this batch shape as a replayable CUDA graph, captured on a
+// private stream at first use (the caller's stream may be the legacy default
+// stream, which cannot be captured).  The graph ends with the copy of the
+// active-slot count to the host.
+int iteration_graph(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint, KrylovGraph** out) {
+  for (KrylovGraph& g : h->graphs)
+    if (g.nb == nb && g.adjoint == adjoint && g.x == x && g.xs == xs && g.prof == h->prof.on) {
+      *out = &g;
+      return MQNPM_OK;
+    }
+  if (!h->capture_stream) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+  if (h->graphs.size() >= 8) {   // a few shapes at a time: drop the oldest
+    destroy_graph(h->graphs.front());
+    h->graphs.erase(h->graphs.begin());
+  }
+  KrylovGraph g;
+  g.nb = nb;
+  g.adjoint = adjoint;
+  g.x = x;
+  g.xs = xs;
+  g.prof = h->prof.on;
+  if (g.prof)
+    for (cudaEvent_t& e : g.ev) CK(cudaEventCreate(&e));
+  cudaStream_t cs = h->capture_stream;
+  const long long before = h->launches;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  int rc = iteration_body(h, nb, x, xs, adjoint, cs, g.prof ? g.ev : nullptr, g.prof ? g.ev + 6 : nullptr);
+  cudaError_t e = cudaMemcpyAsync(h->w.h_nactive, h->w.nactive, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+  g.kernels = h->launches - before;
+  h->launches = before;
+  if (rc == MQNPM_OK && e == cudaSuccess && ee == cudaSuccess)
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != MQNPM_OK || e != cudaSuccess || ee != cudaSuccess) {
+    destroy_graph(g);
+    if (rc != MQNPM_OK) return rc;
+    return set_cuda_error(h, e != cudaSuccess ? e : ee, "capture of the BiCGSTAB iteration");
+  }
+  h->graphs.push_back(g);
+  *out = &h->graphs.back();
+  return MQNPM_OK;
+}
+
+// Run BiCGSTAB iterations for the nb slots initialised by k_fin_init; the
+// host reads the number of active slots after every iteration.
 int krylov_iterate(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
-  const size_t N = h->N;
+  if (!h->direct_launches) {
+    KrylovGraph* g = nullptr;
+    const int rc = iteration_graph(h, nb, x, xs, adjoint, &g);
+    if (rc != MQNPM_OK) return rc;
+    for (int it = 0; it < h->krylov_maxit; ++it) {
+      CK(cudaGraphLaunch(g->exec, s));
+      h->launches += g->kernels;
+      CK(cudaStreamSynchronize(s));
+      if (g->prof) {   // pass times of the two applies of this replay
+        for (int a = 0; a < 2; ++a)
+          for (int p = 0; p < 5; ++p) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, g->ev[6 * a + p], g->ev[6 * a + p + 1]));
+            h->prof.acc_ms[p] += ms;
+          }
+        h->prof.acc_slots += 2 * (long long)nb;
+        h->prof.acc_calls += 2;
+      }
+      if (*w.h_nactive == 0) break;
+    }
+    return MQNPM_OK;
+  }
   for (int it = 0; it < h->krylov_maxit; ++it) {
-    GreenCall c = base_call(h, nb, adjoint);
-    c.st = w.st;
-    c.pro = PRO_BICG_P;
-    c.pa.x = x;
-    c.pa.w = w.p;
-    c.pa.r = w.r;
-    c.pa.v = w.v;
-    c.epi = EPI_V;
-    c.ea.out = w.v;
-    c.ea.a = w.p;
-    c.ea.rhat = w.rhat;
-    CK(glaunch(h, c, s));
-    k_fin_alpha<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row);
-    c.pro = PRO_BICG_S;
-    c.pa.w = w.s;
-    c.epi = EPI_T;
-    c.ea.out = w.t;
-    c.ea.a = w.s;
-    CK(glaunch(h, c, s));
-    k_fin_omega<<<nb, 256, 0, s>>>(w.st, w.part1, w.part5, w.ctas_row);
-    k_update<<<dim3(w.ctas_upd, nb), 256, 0, s>>>(w.st, xs, w.r, w.p, w.s, w.t, w.rhat, N, w.partu);
-    CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), s));
-    k_fin_rho<<<nb, 256, 0, s>>>(w.st, w.partu, w.ctas_upd, h->krylov_maxit, w.nactive);
-    CK(cudaGetLastError());
-    h->launches += 4;   // fin_alpha, fin_omega, update, fin_rho
+    const int rc = iteration_body(h, nb, x, xs, adjoint, s, profile_slot(h, nb), profile_slot(h, nb));
+    if (rc != MQNPM_OK) return rc;
     if ((it + 1) % h->check_every == 0 || it + 1 == h->krylov_maxit) {
       CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));

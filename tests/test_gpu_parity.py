@@ -283,3 +283,27 @@ def test_empty_and_invalid_batches_are_rejected():
     assert lib.mqnpm_grad_batch(h._h, binding._ptr(x), bad, 1, 1.0, binding._ptr(g), None, None) == 1
     assert lib.mqnpm_loss_batch(h._h, binding._ptr(x), il, 0, 1.0, None, None) == 1
     h.close()
+
+
+@pytest.mark.parametrize("model", ["ls", "born"])
+def test_graph_replay_equals_direct_launches(model):
+    """BiCGSTAB iterations replayed from captured CUDA graphs launch the same
+    kernels as direct launches: identical gradients, losses, iteration counts,
+    kernel counts and profiled applies."""
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, model, L=6, batch=3)
+    outs = []
+    for direct in (False, True):
+        h = make_handle(n, kd, so, [1.0] * w.S, model=model, krylov_tol=1e-6, max_batch=2, direct_launches=direct)
+        h.set_measurements(c64(ys).reshape(-1))
+        x = f32(0.7 * xt).reshape(-1)
+        h.grad_batch(x, [0, 1, 2], 1.0)                 # captures (graph path)
+        k0 = h.launch_count
+        h.profile_begin(64)
+        g, loss, its = h.grad_batch(x, [0, 1, 2], 1.0)
+        prof = h.profile_end()
+        outs.append((g.cpu().numpy(), loss, its, h.launch_count - k0, prof["calls"], prof["slot_launches"]))
+        h.close()
+    (ga, la, ia, ka, ca, sa), (gb, lb, ib, kb, cb, sb) = outs
+    assert np.array_equal(ga, gb) and la == lb and ia == ib
+    assert ka == kb and ca == cb and sa == sb
