@@ -73,12 +73,12 @@ def fp32_peak_tflops():
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
-# ---------------------------------------------------------------- clocks
+# ------------------------------------------------------- pass-3 DRAM traffic
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of k_pass3 at
-# n = 128 from one ncu capture of 4 slots per launch (profiles/
-# k_pass3_ls128_batch4.md), per slot.  It applies only while the sources the
-# kernel is compiled from are the captured ones (digest below); otherwise the
-# bench reports traffic as null.
+# n = 128 from one ncu capture of `bench.py --green-only --batch 4` (4 slots
+# per launch), per slot.  It applies only while the sources the kernel is
+# compiled from are the captured ones (digest below); otherwise the bench
+# reports traffic as null.
 PASS3_CAPTURE = {"n": 128, "bytes_per_slot": 126668608, "sources_sha256_16": "77f4dab900a63162"}
 PASS3_SOURCES = ("common.cuh", "fft.cuh", "green_passes.cuh", "green_inst.cu")
 
