@@ -100,6 +100,11 @@ typedef struct mqnpm_config {
   int direct_launches;     /* 0: a BiCGSTAB iteration (14 kernels) is captured
                               once per batch shape as a CUDA graph and replayed;
                               1: its kernels are launched one by one          */
+  const float* green_hat;  /* host, (n+1)^3 complex64 [fz][fy][fx] or NULL: the
+                              first octant of DFT_P of the P-periodic Green's
+                              kernel (even in every axis; any discretisation of
+                              G, e.g. a truncated kernel), used instead of the
+                              library's own (Section 6 reading)              */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;
@@ -120,10 +125,11 @@ typedef struct mqnpm_step_info {
   double ms_prox;          /* device time of the weighted proximal mapping         */
 } mqnpm_step_info;
 
-/* Create a handle: validates cfg, builds the Green's kernel spectrum and the
- * incident-field tables, and allocates the workspace for max_batch
- * illuminations.  Host arrays in cfg are copied.  Errors: INVALID_ARG,
- * UNSUPPORTED (n), BUDGET, CUDA.  On error *out is NULL. */
+/* Create a handle: validates cfg, builds the Green's kernel spectrum (or
+ * scales cfg->green_hat by 1/P^3 and rounds it once) and the incident-field
+ * tables, and allocates the workspace for max_batch illuminations.  Host
+ * arrays in cfg are copied.  Errors: INVALID_ARG (also a non-finite
+ * green_hat value), UNSUPPORTED (n), BUDGET, CUDA.  On error *out is NULL. */
 int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out);
 
 /* Release the workspace.  NULL is accepted. */

@@ -51,6 +51,7 @@ class Config(ctypes.Structure):
         ("dual_iters", ctypes.c_int), ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
+        ("green_hat", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -167,7 +168,7 @@ class MQNPM:
                  gamma: float = 0.8, tau_max: float = 0.0, krylov_tol: float = 1e-6, krylov_maxit: int = 500,
                  dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
-                 direct_launches: bool = False):
+                 direct_launches: bool = False, green_hat: Optional[np.ndarray] = None):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -210,6 +211,12 @@ class MQNPM:
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.warm_start = int(bool(warm_start))
         cfg.direct_launches = int(bool(direct_launches))
+        if green_hat is not None:
+            gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
+            if gh.size != (self.n + 1) ** 3:
+                raise ValueError("green_hat must hold (n+1)^3 complex values")
+            self._keep = self._keep + (gh,)
+            cfg.green_hat = gh.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         cfg.device = self.device
         with torch.cuda.device(self.device):
             cfg.stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)

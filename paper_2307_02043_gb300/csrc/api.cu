@@ -188,6 +188,15 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
     delete h;
     return MQNPM_ERR_UNSUPPORTED;
   }
+  if (cfg->green_hat) {
+    const size_t m = (size_t)cfg->n + 1, cnt = 2 * m * m * m;
+    for (size_t i = 0; i < cnt; ++i)
+      if (!std::isfinite(cfg->green_hat[i])) {
+        fprintf(stderr, "mqnpm_create: green_hat holds a non-finite value\n");
+        delete h;
+        return MQNPM_ERR_INVALID_ARG;
+      }
+  }
   h->n = cfg->n;
   h->P = 2 * cfg->n;
   h->N = (size_t)cfg->n * cfg->n * cfg->n;
@@ -347,7 +356,8 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   }
   if ((e = cudaMemcpyAsync(h->tw, tw.data(), P * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = build_khat(n, h->h, h->kb, h->khat, s)) != cudaSuccess) {
+      (e = (cfg->green_hat ? upload_khat(cfg->green_hat, n, h->khat, s) : build_khat(n, h->h, h->kb, h->khat, s))) !=
+          cudaSuccess) {
     set_cuda_error(h, e, "create tables");
     return fail(MQNPM_ERR_CUDA);
   }

@@ -192,3 +192,20 @@ cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_
   cudaFreeAsync(dcos, s);
   return e;
 }
+
+// A caller-provided spectrum: the first octant [fz][fy][fx] of the
+// unnormalised DFT_P, complex64 on the host.  Scaled by 1/P^3 in FP64 and
+// rounded once, like the library's own construction.
+cudaError_t upload_khat(const float* host, int n, float2* khat_out, cudaStream_t s) {
+  const int P = 2 * n;
+  const size_t big = (size_t)(n + 1) * (n + 1) * (n + 1);
+  const double scale = 1.0 / ((double)P * P * P);
+  std::vector<float2> v(big);
+  for (size_t i = 0; i < big; ++i) {
+    const double re = host[2 * i], im = host[2 * i + 1];
+    v[i] = make_float2((float)(re * scale), (float)(im * scale));
+  }
+  cudaError_t e = cudaMemcpyAsync(khat_out, v.data(), big * sizeof(float2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the staging vector goes out of scope
+  return e;
+}

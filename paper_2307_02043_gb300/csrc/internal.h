@@ -69,6 +69,7 @@ MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
 
 // K_hat octant in FP64 by separable even (cosine) sums, rounded to complex64.
 cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s);
+cudaError_t upload_khat(const float* host, int n, float2* khat_out, cudaStream_t s);
 cudaError_t build_khat_scratch(int n, double h, double kb, float2* khat_out, double2* a, double2* b, double* dcos,
                                cudaStream_t s);
 

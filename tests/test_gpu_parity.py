@@ -95,6 +95,43 @@ def test_green_apply_full_size_sampled():
 
 
 # ---------------------------------------------------------------- forward/grad
+@pytest.mark.parametrize("n", [12, 32])
+def test_green_apply_with_host_spectrum(n):
+    """A caller-provided spectrum replaces the built one: the octant of the
+    oracle's DFT_P at another wavenumber gives that wavenumber's G, and the
+    octant at the handle's own wavenumber reproduces the built spectrum."""
+    rng = np.random.default_rng(300 + n)
+    nb = 2
+    v = rng.standard_normal((nb, n, n, n)) + 1j * rng.standard_normal((nb, n, n, n))
+    kb2 = math.pi / 3
+    kh2 = physics.green_hat(n, kb2)
+    h = make_handle(n, cone(2), [0, 0], [1.0], max_batch=nb, green_hat=kh2[:n + 1, :n + 1, :n + 1])
+    for adjoint in (False, True):
+        out = h.green_apply(c64(v).reshape(-1), adjoint=adjoint).cpu().numpy().reshape(nb, n, n, n)
+        for b in range(nb):
+            ref = physics.green_apply(v[b], kh2, adjoint=adjoint)
+            assert relmax(out[b], ref) < 2e-6, (n, adjoint, b, relmax(out[b], ref))
+    h.close()
+    kh = physics.green_hat(n, KB)
+    ha = make_handle(n, cone(2), [0, 0], [1.0], max_batch=nb, green_hat=kh[:n + 1, :n + 1, :n + 1])
+    hb = make_handle(n, cone(2), [0, 0], [1.0], max_batch=nb)
+    oa = ha.green_apply(c64(v).reshape(-1)).cpu().numpy()
+    ob = hb.green_apply(c64(v).reshape(-1)).cpu().numpy()
+    assert relmax(oa, ob) < 1e-6
+    ha.close()
+    hb.close()
+
+
+def test_host_spectrum_rejects_bad_input():
+    n = 8
+    bad = physics.green_hat(n, KB)[:n + 1, :n + 1, :n + 1].copy()
+    bad[1, 2, 3] = np.nan
+    with pytest.raises(binding.MQNPMError):
+        make_handle(n, cone(2), [0, 0], [1.0], green_hat=bad)
+    with pytest.raises(ValueError):
+        make_handle(n, cone(2), [0, 0], [1.0], green_hat=bad[:n])
+
+
 def problem(n, model, L=4, batch=2, contrast=None, seed_name="ls32"):
     w = synth.small(seed_name, n=n, L=L, batch=batch, model=model)
     if contrast is not None:
