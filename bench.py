@@ -495,12 +495,14 @@ def serve_uneven(args, torch, binding):
                     return
                 raise
             h.set_measurements(y.reshape(-1))
+            tiles[str(w.n)] = h.tile_info()["tile"]
             used += h.workspace_bytes
             peak_used = max(peak_used, used)
             active[i] = (h, torch.zeros(w.N, dtype=torch.float32, device=dev), 0)
             admitted_order.append(i)
             queue.pop(0)
 
+    tiles = {}
     admit()
     admitted_first = len(active)
     t0.record()
@@ -533,7 +535,7 @@ def serve_uneven(args, torch, binding):
         "iteration_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                                  "p99": round(float(np.percentile(lat, 99)), 3),
                                  "max": round(float(lat.max()), 3)},
-        "total_ms": round(total_ms, 1)}), flush=True)
+        "total_ms": round(total_ms, 1), "green_tile_per_grid": tiles}), flush=True)
 
 
 # ---------------------------------------------------------------------- main
@@ -597,6 +599,8 @@ def main():
     for _ in range(args.warmup):
         h.step(x, allow_not_converged=True)
     torch.cuda.synchronize()
+    # the end-to-end run below repeats the same iterations from this state
+    state0, x0 = h.save_state(), x.cpu()
     # ---- timed region: inputs resident in HBM
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -630,17 +634,21 @@ def main():
     prof = h.profile_end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    # ---- end-to-end through the public call with host buffers
+    # ---- end-to-end through the public call with host buffers, same iterations
+    h.load_state(state0)
+    del state0
     xh = torch.empty(w.N, dtype=torch.float32).pin_memory()
-    xh.copy_(x.cpu())
+    xh.copy_(x0)
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     xd = torch.empty_like(x)
     e2e_illum = 0
+    e2e_infos = []
     f0.record(stream)
     for _ in range(args.steps):
         xd.copy_(xh, non_blocking=True)
         info = h.step(xd, allow_not_converged=True)
+        e2e_infos.append(info)
         e2e_illum += len(subs[info["subset"]])
         xh.copy_(xd, non_blocking=True)
     f1.record(stream)
@@ -690,6 +698,7 @@ def main():
         "roofline_alu": pass3_alu_view(n, prof, pms[2]),
         "passes": passes,
         "green_applies": prof["calls"],
+        "green_tile": h.tile_info(),
         "phase_ms": {k: round(statistics.mean(i["ms_" + k] for i in infos), 3) for k in ("gradient", "metric", "prox")},
         "newton_iters_max": [i["newton_iters_max"] for i in infos],
         "prox_trace_us": prox_trace,
@@ -697,7 +706,11 @@ def main():
         "krylov_iters_per_illum": [round(k, 2) for k in kit_per_illum],
         "gpu_launches": None,
         "clocks": clk,
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N},
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+                "iterations": "the timed k = %d..%d again, from a checkpoint" % (infos[0]["k"], infos[-1]["k"]),
+                "pass_events": "none (the timed region above records 6 per Green's apply for the pass timings)",
+                "same_krylov_iters": [i["krylov_iters_total"] for i in e2e_infos] ==
+                                     [i["krylov_iters_total"] for i in infos]},
     }
     out["gpu_launches"] = int(launches)
     out["config"]["iterations"] = "k = %d..%d from x0 = 0" % (infos[0]["k"], infos[-1]["k"])

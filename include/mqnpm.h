@@ -105,6 +105,13 @@ typedef struct mqnpm_config {
                               kernel (even in every axis; any discretisation of
                               G, e.g. a truncated kernel), used instead of the
                               library's own (Section 6 reading)              */
+  int tile;                /* launch shapes of the Green's passes: -1 picks the
+                              fastest of 0..7 by timing at create (cached per
+                              device, n and batch slots); 0..7 fixes them, bit 0
+                              the alternative lines per CTA of the x passes,
+                              bit 1 the alternative columns per CTA of the y/z
+                              passes, bit 2 two exchange buffers in the z pass
+                              (0 = the built-in defaults)                     */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;
@@ -242,6 +249,12 @@ int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count);
 
 /* Number of CUDA kernels this handle has launched since creation. */
 long long mqnpm_launch_count(const mqnpm_handle* h);
+
+/* Launch shapes the handle uses: *tile (0..7), lines per CTA of the x passes
+ * and columns per CTA of the y/z passes; ms (8 doubles, may be NULL) receives
+ * the autotuner's time of one Green's apply per tile, -1 where none was taken
+ * (a fixed tile).  Returns MQNPM_OK or INVALID_ARG. */
+int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* lines, int* cols, double* ms);
 
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);
 int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls);

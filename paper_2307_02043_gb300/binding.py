@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
         ("dual_iters", ctypes.c_int), ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
         ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
-        ("green_hat", ctypes.POINTER(ctypes.c_float)),
+        ("green_hat", ctypes.POINTER(ctypes.c_float)), ("tile", ctypes.c_int),
     ]
 
 
@@ -91,6 +91,8 @@ SIGNATURES = {
     "mqnpm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "mqnpm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "mqnpm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "mqnpm_tile_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_prox_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int)]),
     "mqnpm_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -168,7 +170,7 @@ class MQNPM:
                  gamma: float = 0.8, tau_max: float = 0.0, krylov_tol: float = 1e-6, krylov_maxit: int = 500,
                  dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
-                 direct_launches: bool = False, green_hat: Optional[np.ndarray] = None):
+                 direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -211,6 +213,7 @@ class MQNPM:
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.warm_start = int(bool(warm_start))
         cfg.direct_launches = int(bool(direct_launches))
+        cfg.tile = int(tile)
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
             if gh.size != (self.n + 1) ** 3:
@@ -259,6 +262,14 @@ class MQNPM:
     def launch_count(self) -> int:
         """Kernels launched by this handle since creation."""
         return int(self.lib.mqnpm_launch_count(self._h))
+
+    def tile_info(self) -> dict:
+        """Launch shapes of the Green's passes and the autotuner's timings (ms per apply)."""
+        tile, lines, cols = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 8)()
+        self._raise(self.lib.mqnpm_tile_info(self._h, ctypes.byref(tile), ctypes.byref(lines), ctypes.byref(cols), ms))
+        return {"tile": tile.value, "lines_per_cta": lines.value, "columns_per_cta": cols.value,
+                "tuned_ms": [round(m, 4) if m >= 0 else None for m in ms]}
 
     # -- calls -------------------------------------------------------------
     def set_measurements(self, y: torch.Tensor):

@@ -130,6 +130,15 @@ const char* mqnpm_last_error(const mqnpm_handle* h) { return h ? h->err.c_str() 
 
 long long mqnpm_launch_count(const mqnpm_handle* h) { return h ? h->launches : 0; }
 
+int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* lines, int* cols, double* ms) {
+  if (!h || !tile || !lines || !cols) return MQNPM_ERR_INVALID_ARG;
+  *tile = h->tile;
+  green_shape(h->n, h->tile, lines, cols);
+  if (ms)
+    for (int i = 0; i < MQ_TILES; ++i) ms[i] = h->tune_ms[i];
+  return MQNPM_OK;
+}
+
 size_t mqnpm_workspace_bytes(const mqnpm_handle* h) { return h ? h->bytes : 0; }
 
 int mqnpm_set_stream(mqnpm_handle* h, void* stream) {
@@ -179,7 +188,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
       !(cfg->box_lo <= cfg->box_hi) || !(cfg->lambda >= 0) || !(cfg->step > 0) || cfg->dual_iters < 0 ||
       !(cfg->krylov_tol > 0) || cfg->krylov_maxit < 1 || (cfg->model != MQNPM_MODEL_LS && cfg->model != MQNPM_MODEL_BORN) ||
       (cfg->tv != MQNPM_TV_ISO && cfg->tv != MQNPM_TV_ANISO) || (cfg->strategy != 1 && cfg->strategy != 2) ||
-      !(cfg->gamma > 0 && cfg->gamma <= 1.0)) {
+      !(cfg->gamma > 0 && cfg->gamma <= 1.0) || cfg->tile < -1 || cfg->tile >= MQ_TILES) {
     fprintf(stderr, "mqnpm_create: invalid configuration\n");
     delete h;
     return MQNPM_ERR_INVALID_ARG;
@@ -251,7 +260,16 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   if (nsm <= 0) nsm = 1;
   const size_t N = h->N, M = h->M, B = h->max_batch;
   const int n = h->n, P = h->P;
-  h->w.ctas_row = green_row_ctas(n);
+  h->tile = cfg->tile < 0 ? 0 : cfg->tile;
+  if (!green_tile_fits(n, h->tile, h->device)) {
+    char msg[120];
+    snprintf(msg, sizeof msg, "tile %d needs more shared memory per block than the device has at n = %d", h->tile, n);
+    h->err = msg;
+    *out = nullptr;
+    delete h;
+    return MQNPM_ERR_INVALID_ARG;
+  }
+  h->w.ctas_row = green_row_ctas_max(n);   // partials sized for every tile variant
   h->w.ctas_vec = (int)std::min<long long>(ceil_div_ll((long long)N, 256LL * 8), 8LL * nsm);
   h->w.ctas_upd = (int)std::min<long long>(ceil_div_ll((long long)N, 256LL * 8), 4LL * nsm);
   if (h->w.ctas_vec < 1) h->w.ctas_vec = 1;
@@ -349,7 +367,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
         tab[((size_t)l * 3 + ax) * n + i] = make_float2((float)std::cos(ph), (float)std::sin(ph));
       }
   cudaStream_t s = h->stream;
-  if ((e = make_t2_tensor_map(w.T2, n, (int)B, w.t2map)) != cudaSuccess ||
+  if ((e = make_t2_tensor_map(w.T2, n, (int)B, h->tile, w.t2map)) != cudaSuccess ||
       (e = cudaMemsetAsync(w.gerr, 0, sizeof(int), s)) != cudaSuccess) {
     set_cuda_error(h, e, "tensor map of the transform buffer");
     return fail(MQNPM_ERR_CUDA);
@@ -364,6 +382,8 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->tau.assign(h->alpha.begin(), h->alpha.end());
   h->has_u.assign(h->S, 0);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { set_cuda_error(h, e, "create sync"); return fail(MQNPM_ERR_CUDA); }
+  if (cfg->tile < 0 && (rc = autotune_tile(h)) != MQNPM_OK) return fail(rc);
+  w.ctas_row = green_row_ctas(n, h->tile);
   *out = h;
   return MQNPM_OK;
 }
@@ -396,6 +416,7 @@ int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int a
   c.part_epi = h->w.part5;
   c.ev = profile_slot(h, nb);
   c.launches = &h->launches;
+  c.tile = h->tile;
   c.tmap = h->w.t2map;
   c.err = h->w.gerr;
   CK(green_launch(c, h->stream));

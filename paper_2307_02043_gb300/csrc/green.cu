@@ -11,6 +11,7 @@
 //   Kf(f) = k(0) + 2 sum_{d=1}^{n-1} k(d) cos(2 pi f d / P),  f = 0..n.
 // These sums run in FP64 on the device; the result, scaled by 1/P^3 (the
 // normalisation of the inverse transform), is rounded to complex64.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -33,14 +34,41 @@ bool green_supported(int n) {
   }
 }
 
-int green_row_ctas(int n) {
+void green_shape(int n, int tile, int* lines, int* cols, size_t* smem) {
+  *lines = 0;
+  *cols = 0;
+  size_t m = 0;
   switch (2 * n) {
-#define MQ_CASE(P) case P: return green_row_ctas_P##P(n);
+#define MQ_CASE(P) case P: green_shape_P##P(tile, n, lines, cols, &m); break;
     MQ_DISPATCH(MQ_CASE)
 #undef MQ_CASE
     default:
-      return 0;
+      break;
   }
+  if (smem) *smem = m;
+}
+
+bool green_tile_fits(int n, int tile, int device) {
+  int lines = 0, cols = 0, optin = 0;
+  size_t smem = 0;
+  green_shape(n, tile, &lines, &cols, &smem);
+  if (lines <= 0 || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+    return false;
+  return smem <= (size_t)optin;
+}
+
+int green_row_ctas(int n, int tile) {
+  int lines = 0, cols = 0;
+  green_shape(n, tile, &lines, &cols);
+  return lines > 0 ? (n * n + lines - 1) / lines : 0;
+}
+
+int green_row_ctas_max(int n) { return std::max(green_row_ctas(n, 0), green_row_ctas(n, 1)); }
+
+int green_col_width(int n, int tile) {
+  int lines = 0, cols = 0;
+  green_shape(n, tile, &lines, &cols);
+  return cols;
 }
 
 cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
@@ -58,16 +86,10 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
 // z = slot * n + z (max_batch * n).  Pass 3 loads boxes of C x 1 x n: one
 // column set of one slot.  The encoder comes from the driver through the
 // runtime's entry-point query, so the library does not link libcuda.
-cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, void* map_out) {
+cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, int tile, void* map_out) {
   const int P = 2 * n;
-  int C = 0;
-  switch (P) {
-#define MQ_CASE(PP) case PP: C = ColShape<PP>::C; break;
-    MQ_DISPATCH(MQ_CASE)
-#undef MQ_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+  const int C = green_col_width(n, tile);
+  if (C <= 0) return cudaErrorInvalidValue;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;

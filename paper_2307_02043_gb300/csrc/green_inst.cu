@@ -12,21 +12,20 @@
 
 namespace {
 constexpr int P = MQ_P;
-using RS = RowShape<P>;
-using CS = ColShape<P>;
 
 template <class K>
 cudaError_t set_smem(K kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int KIND>
+template <int RV, int KIND>
 cudaError_t launch1(const GreenCall& c, cudaStream_t s) {
+  using RS = RowShape<P, RV>;
   Pro<KIND> pro;
   pro.a = c.pa;
   pro.g = Geo{c.n};
   if constexpr (KIND == PRO_BICG_P || KIND == PRO_BICG_S) pro.st = c.st;
-  auto kern = k_pass1<P, Pro<KIND>>;
+  auto kern = k_pass1<P, RV, Pro<KIND>>;
   cudaError_t e = set_smem(kern, RS::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(c.n * c.n, RS::LPB), c.nb);
@@ -34,24 +33,100 @@ cudaError_t launch1(const GreenCall& c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int KIND>
+template <int RV, int KIND>
 cudaError_t launch5(const GreenCall& c, cudaStream_t s) {
+  using RS = RowShape<P, RV>;
   Epi<KIND> epi;
   epi.a = c.ea;
   epi.g = Geo{c.n};
-  auto kern = k_pass5<P, Epi<KIND>>;
+  auto kern = k_pass5<P, RV, Epi<KIND>>;
   cudaError_t e = set_smem(kern, RS::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(c.n * c.n, RS::LPB), c.nb);
   kern<<<grid, RS::THREADS, RS::SMEM, s>>>(epi, c.T1, c.n, c.tw, c.st, c.part_epi);
   return cudaGetLastError();
 }
+
+template <int RV>
+cudaError_t pass1(const GreenCall& c, cudaStream_t s) {
+  switch (c.pro) {
+    case PRO_PLAIN: return launch1<RV, PRO_PLAIN>(c, s);
+    case PRO_CONTRAST: return launch1<RV, PRO_CONTRAST>(c, s);
+    case PRO_BORN: return launch1<RV, PRO_BORN>(c, s);
+    case PRO_BICG_P: return launch1<RV, PRO_BICG_P>(c, s);
+    case PRO_BICG_S: return launch1<RV, PRO_BICG_S>(c, s);
+    case PRO_LIFT: return launch1<RV, PRO_LIFT>(c, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int RV>
+cudaError_t pass5(const GreenCall& c, cudaStream_t s) {
+  switch (c.epi) {
+    case EPI_PLAIN: return launch5<RV, EPI_PLAIN>(c, s);
+    case EPI_V: return launch5<RV, EPI_V>(c, s);
+    case EPI_T: return launch5<RV, EPI_T>(c, s);
+    case EPI_INIT: return launch5<RV, EPI_INIT>(c, s);
+    case EPI_INIT_WARM: return launch5<RV, EPI_INIT_WARM>(c, s);
+    case EPI_DETECT: return launch5<RV, EPI_DETECT>(c, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int CV, bool INV>
+cudaError_t pass_y(const GreenCall& c, const float2* in, float2* out, cudaStream_t s) {
+  using CS = ColShape<P, CV>;
+  auto kern = k_pass_y<P, CV, INV>;
+  cudaError_t e = set_smem(kern, CS::SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid(P / CS::C, c.n, c.nb);
+  kern<<<grid, CS::THREADS, CS::SMEM, s>>>(in, out, c.n, c.tw, c.st);
+  return cudaGetLastError();
+}
+
+// one CTA per (kx tile, ky) column set; the batch is looped inside (one TMA tile buffer)
+template <int CV, bool DB, bool CONJ>
+cudaError_t pass3(const GreenCall& c, cudaStream_t s) {
+  using CS = ColShape<P, CV>;
+  const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);
+  if (tm == nullptr || c.err == nullptr) return cudaErrorInvalidValue;
+  auto kern = k_pass3<P, CV, DB, CONJ>;
+  const int smem = (int)Pass3Smem<P, CV, DB>::bytes(c.n);
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(P / CS::C, P);
+  kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.n, c.nb, c.tw, c.st, c.err);
+  return cudaGetLastError();
+}
+
+template <int CV, bool DB>
+cudaError_t columns(const GreenCall& c, cudaStream_t s, unsigned rec_flags) {
+  cudaError_t e;
+  if ((e = pass_y<CV, false>(c, c.T1, c.T2, s)) != cudaSuccess) return e;
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[2], s, rec_flags)) != cudaSuccess) return e;
+  if ((e = c.adjoint ? pass3<CV, DB, true>(c, s) : pass3<CV, DB, false>(c, s)) != cudaSuccess) return e;
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[3], s, rec_flags)) != cudaSuccess) return e;
+  return pass_y<CV, true>(c, c.T2, c.T1, s);
+}
 }  // namespace
 
-int MQ_CAT(green_row_ctas_P, MQ_P)(int n) { return ceil_div(n * n, RS::LPB); }
+void MQ_CAT(green_shape_P, MQ_P)(int tile, int n, int* lines, int* cols, size_t* smem) {
+  *lines = (tile & 1) ? RowShape<P, 1>::LPB : RowShape<P, 0>::LPB;
+  *cols = (tile & 2) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
+  size_t m = 0;   // the largest dynamic shared memory of the tile's five passes
+  switch ((tile >> 1) & 3) {
+    case 0: m = Pass3Smem<P, 0, false>::bytes(n); break;
+    case 1: m = Pass3Smem<P, 1, false>::bytes(n); break;
+    case 2: m = Pass3Smem<P, 0, true>::bytes(n); break;
+    default: m = Pass3Smem<P, 1, true>::bytes(n); break;
+  }
+  const size_t ys = (tile & 2) ? ColShape<P, 1>::SMEM : ColShape<P, 0>::SMEM;
+  const size_t rs = (tile & 1) ? RowShape<P, 1>::SMEM : RowShape<P, 0>::SMEM;
+  *smem = m > ys ? (m > rs ? m : rs) : (ys > rs ? ys : rs);
+}
 
 cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
-  if (2 * c.n != P) return cudaErrorInvalidValue;
+  if (2 * c.n != P || c.tile < 0 || c.tile >= MQ_TILES) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   // inside a stream capture the records must be external to become event-record
   // nodes of the graph; outside one they are plain records
@@ -61,62 +136,21 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
     if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
   }
+  const bool row_alt = (c.tile & 1) != 0;
+  const int col = (c.tile >> 1) & 3;   // bit 1: column shape, bit 2: pass-3 exchange buffers
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[0], s, rec_flags)) != cudaSuccess) return e;
-  switch (c.pro) {
-    case PRO_PLAIN: e = launch1<PRO_PLAIN>(c, s); break;
-    case PRO_CONTRAST: e = launch1<PRO_CONTRAST>(c, s); break;
-    case PRO_BORN: e = launch1<PRO_BORN>(c, s); break;
-    case PRO_BICG_P: e = launch1<PRO_BICG_P>(c, s); break;
-    case PRO_BICG_S: e = launch1<PRO_BICG_S>(c, s); break;
-    case PRO_LIFT: e = launch1<PRO_LIFT>(c, s); break;
-    default: return cudaErrorInvalidValue;
+  if ((e = row_alt ? pass1<1>(c, s) : pass1<0>(c, s)) != cudaSuccess) return e;
+  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[1], s, rec_flags)) != cudaSuccess) return e;
+  switch (col) {
+    case 0: e = columns<0, false>(c, s, rec_flags); break;
+    case 1: e = columns<1, false>(c, s, rec_flags); break;
+    case 2: e = columns<0, true>(c, s, rec_flags); break;
+    default: e = columns<1, true>(c, s, rec_flags); break;
   }
   if (e != cudaSuccess) return e;
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[1], s, rec_flags)) != cudaSuccess) return e;
-  {
-    auto kern = k_pass_y<P, false>;
-    if ((e = set_smem(kern, CS::SMEM)) != cudaSuccess) return e;
-    dim3 grid(P / CS::C, c.n, c.nb);
-    kern<<<grid, CS::THREADS, CS::SMEM, s>>>(c.T1, c.T2, c.n, c.tw, c.st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[2], s, rec_flags)) != cudaSuccess) return e;
-  {
-    // one CTA per (kx tile, ky) column set; the batch is looped inside (one TMA tile buffer)
-    dim3 grid(P / CS::C, P);
-    const int smem = (int)Pass3Smem<P>::bytes(c.n);
-    const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);
-    if (tm == nullptr || c.err == nullptr) return cudaErrorInvalidValue;
-    if (c.adjoint) {
-      auto kern = k_pass3<P, true>;
-      if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-      kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.n, c.nb, c.tw, c.st, c.err);
-    } else {
-      auto kern = k_pass3<P, false>;
-      if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-      kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.n, c.nb, c.tw, c.st, c.err);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[3], s, rec_flags)) != cudaSuccess) return e;
-  {
-    auto kern = k_pass_y<P, true>;
-    if ((e = set_smem(kern, CS::SMEM)) != cudaSuccess) return e;
-    dim3 grid(P / CS::C, c.n, c.nb);
-    kern<<<grid, CS::THREADS, CS::SMEM, s>>>(c.T2, c.T1, c.n, c.tw, c.st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[4], s, rec_flags)) != cudaSuccess) return e;
-  switch (c.epi) {
-    case EPI_PLAIN: e = launch5<EPI_PLAIN>(c, s); break;
-    case EPI_V: e = launch5<EPI_V>(c, s); break;
-    case EPI_T: e = launch5<EPI_T>(c, s); break;
-    case EPI_INIT: e = launch5<EPI_INIT>(c, s); break;
-    case EPI_INIT_WARM: e = launch5<EPI_INIT_WARM>(c, s); break;
-    case EPI_DETECT: e = launch5<EPI_DETECT>(c, s); break;
-    default: return cudaErrorInvalidValue;
-  }
-  if (c.ev && e == cudaSuccess) e = cudaEventRecordWithFlags(c.ev[5], s, rec_flags);
+  if ((e = row_alt ? pass5<1>(c, s) : pass5<0>(c, s)) != cudaSuccess) return e;
+  if (c.ev) e = cudaEventRecordWithFlags(c.ev[5], s, rec_flags);
   if (c.launches) *c.launches += 5;
   return e;
 }

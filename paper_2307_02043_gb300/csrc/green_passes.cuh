@@ -21,23 +21,41 @@
 #include "kstate.h"
 
 // ----------------------------------------------------------- CTA shapes
+// Every transform length has two row shapes (lines per CTA of passes 1 and 5)
+// and two column shapes (columns per CTA of passes 2-4).  V = 0 is the
+// default; V = 1 halves it, or doubles it where the default CTA has fewer than
+// 128 threads.  The autotuner times the four combinations per handle.
 template <int P>
-struct RowShape {
+struct RowBase {
   using PL = Plan<P>;
   static constexpr int PITCH = PL::R1 + 1;                 // padded exchange row
   static constexpr int PER_LINE = PL::R2 * PITCH;
   static constexpr int LPB0 = 256 / PL::T;
-  static constexpr int LPB = (LPB0 * PER_LINE * 8 > 40960) ? (40960 / (PER_LINE * 8) >= 16 ? 16 : 8) : LPB0;
-  static constexpr int THREADS = LPB * PL::T;
-  static constexpr int SMEM = (P + LPB * PER_LINE) * 8;
+  static constexpr int LPB_DEF = (LPB0 * PER_LINE * 8 > 40960) ? (40960 / (PER_LINE * 8) >= 16 ? 16 : 8) : LPB0;
+  static constexpr int LPB_ALT = LPB_DEF * PL::T >= 128 ? LPB_DEF / 2 : 2 * LPB_DEF;
+};
+template <int P, int V = 0>
+struct RowShape : RowBase<P> {
+  static_assert(V == 0 || V == 1, "two row shapes");
+  static constexpr int LPB = V == 0 ? RowBase<P>::LPB_DEF : RowBase<P>::LPB_ALT;
+  static constexpr int THREADS = LPB * Plan<P>::T;
+  static constexpr int SMEM = (P + LPB * RowBase<P>::PER_LINE) * 8;
 };
 template <int P>
-struct ColShape {
+struct ColBase {
   using PL = Plan<P>;
   static constexpr int C0 = 256 / PL::T;
   static constexpr int C1 = C0 > P ? P : C0;
-  static constexpr int C = (C1 * P * 8 > 40960) ? 16 : C1;
-  static constexpr int THREADS = C * PL::T;
+  static constexpr int C_DEF = (C1 * P * 8 > 40960) ? 16 : C1;
+  static constexpr int C_UP = 2 * C_DEF;
+  static constexpr int C_ALT = (C_DEF * PL::T < 128 && C_UP <= P && P % C_UP == 0) ? C_UP : C_DEF / 2;
+};
+template <int P, int V = 0>
+struct ColShape : ColBase<P> {
+  static_assert(V == 0 || V == 1, "two column shapes");
+  static constexpr int C = V == 0 ? ColBase<P>::C_DEF : ColBase<P>::C_ALT;
+  static_assert(P % C == 0 && C % 2 == 0, "column tiles divide P; TMA rows of 16-byte multiples");
+  static constexpr int THREADS = C * Plan<P>::T;
   static constexpr int SMEM = (P + P * C) * 8;
 };
 
@@ -81,12 +99,12 @@ MQ_D void load_twiddle_table(float2* tw, const float2* __restrict__ twg) {
 }
 
 // ------------------------------------------------------- pass 1: x forward
-template <int P, class Pro>
-__global__ void __launch_bounds__(RowShape<P>::THREADS)
+template <int P, int RV, class Pro>
+__global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
 k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
         const KState* __restrict__ st, double* __restrict__ partials) {
   using PL = Plan<P>;
-  using SH = RowShape<P>;
+  using SH = RowShape<P, RV>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T;
   extern __shared__ float2 sm[];
   float2* tw = sm;
@@ -134,12 +152,12 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
 }
 
 // ------------------------------------------------------- pass 5: x inverse
-template <int P, class Epi>
-__global__ void __launch_bounds__(RowShape<P>::THREADS)
+template <int P, int RV, class Epi>
+__global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
 k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict__ twg,
         const KState* __restrict__ st, double* __restrict__ partials) {
   using PL = Plan<P>;
-  using SH = RowShape<P>;
+  using SH = RowShape<P, RV>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T;
   extern __shared__ float2 sm[];
   float2* tw = sm;
@@ -185,12 +203,12 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
 // ------------------------------------------------- passes 2 and 4: y columns
 // INV = false: T1 [b][z][y < n][kx] -> T2 [b][z][ky < P][kx]
 // INV = true : T3 [b][z][ky < P][kx] -> T4 [b][z][y < n][kx]
-template <int P, bool INV>
-__global__ void __launch_bounds__(ColShape<P>::THREADS)
+template <int P, int CV, bool INV>
+__global__ void __launch_bounds__(ColShape<P, CV>::THREADS)
 k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
          const float2* __restrict__ twg, const KState* __restrict__ st) {
   using PL = Plan<P>;
-  using SH = ColShape<P>;
+  using SH = ColShape<P, CV>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C;
   extern __shared__ float2 sm[];
   float2* tw = sm;
@@ -241,19 +259,26 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
 // A slot's input tile (rows z < n of the C columns, 16 KB at n = 128) arrives
 // by one TMA tensor copy; as soon as the first transform stage has consumed
 // it, the copy of the next active slot's tile is issued into the same buffer,
-// so it overlaps the remaining three stages.  One tile buffer (instead of two)
-// keeps shared memory at 68 KB for P = 256: three CTAs per SM.  In place on
-// T2/T3 [b][z][ky][kx]; only rows z < n are read and written.
-template <int P>
+// so it overlaps the remaining three stages.  In place on T2/T3
+// [b][z][ky][kx]; only rows z < n are read and written.
+//
+// Two exchange schemes (DB): with one exchange buffer the middle stage keeps
+// its inverse-stage-A results in registers until every thread has read the
+// buffer (four barriers per slot; 68 KB of shared memory at P = 256, three
+// CTAs per SM).  With two, the middle stage writes them straight into the
+// second buffer (two barriers per slot, no register-held stage: the choice for
+// lengths whose threads carry several columns of a stage, e.g. P = 192, 320).
+template <int P, int CV, bool DB>
 struct Pass3Smem {
-  using SH = ColShape<P>;
+  using SH = ColShape<P, CV>;
   static constexpr int C = SH::C;
   static constexpr int KH = P / 2 + 1;   // folded kz rows of K_hat
   static constexpr MQ_HD size_t tw_off() { return 0; }
   static constexpr MQ_HD size_t kh_off() { return P * sizeof(float2); }
   static constexpr MQ_HD size_t ex_off() { return kh_off() + (size_t)KH * C * sizeof(float2); }
+  static constexpr MQ_HD size_t ex2_off() { return ex_off() + (size_t)P * C * sizeof(float2); }
   static constexpr MQ_HD size_t in_off() {   // 1 KB aligned TMA destination
-    const size_t o = ex_off() + (size_t)P * C * sizeof(float2);
+    const size_t o = ex_off() + (size_t)(DB ? 2 : 1) * P * C * sizeof(float2);
     return (o + 1023) & ~(size_t)1023;
   }
   static constexpr MQ_HD size_t in_bytes(int n) { return (size_t)n * C * sizeof(float2); }
@@ -263,19 +288,21 @@ struct Pass3Smem {
 
 // Blocks per SM the pass-3 kernel is compiled for (register cap): three when
 // its shared memory allows it.
-template <int P>
+template <int P, int CV, bool DB>
 struct Pass3Occ {
-  static constexpr size_t SMEM = Pass3Smem<P>::in_off() + (size_t)(P / 2) * Pass3Smem<P>::C * sizeof(float2) + 1032;
-  static constexpr int MIN_BLOCKS = (3 * SMEM <= 220 * 1024 && ColShape<P>::THREADS <= 256) ? 3 : 2;
+  using SM = Pass3Smem<P, CV, DB>;
+  static constexpr size_t SMEM = SM::in_off() + (size_t)(P / 2) * SM::C * sizeof(float2) + 1032;
+  static constexpr int MIN_BLOCKS = (3 * SMEM <= 220 * 1024 && ColShape<P, CV>::THREADS <= 256) ? 3
+                                    : (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
-template <int P, bool CONJ>
-__global__ void __launch_bounds__(ColShape<P>::THREADS, Pass3Occ<P>::MIN_BLOCKS)
+template <int P, int CV, bool DB, bool CONJ>
+__global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB>::MIN_BLOCKS)
 k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int n,
         int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
   using PL = Plan<P>;
-  using SH = ColShape<P>;
-  using SM = Pass3Smem<P>;
+  using SH = ColShape<P, CV>;
+  using SM = Pass3Smem<P, CV, DB>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C, KH = SM::KH;
   static_assert(R1 * R2 == P && R2 % 2 == 0, "two-stage plan with an even second factor");
   extern __shared__ unsigned char smraw[];
@@ -283,6 +310,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   float2* tw = reinterpret_cast<float2*>(sm + SM::tw_off());   // [R2][R1]: W_P^(a b)
   float2* kh = reinterpret_cast<float2*>(sm + SM::kh_off());
   float2* ex = reinterpret_cast<float2*>(sm + SM::ex_off());
+  float2* ex2 = DB ? reinterpret_cast<float2*>(sm + SM::ex2_off()) : ex;   // inverse-stage exchange
   float2* in = reinterpret_cast<float2*>(sm + SM::in_off());
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::bar_off(n));
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
@@ -352,7 +380,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     }
     // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread).
     // K_hat row of kz = k1 + R1 k2: kz itself for k2 < R2/2, else the folded P - kz.
-    float2 zb[R1 / T][R2];
+    float2 zb[DB ? 1 : R1 / T][R2];
 #pragma unroll
     for (int i = 0; i < R1 / T; ++i) {
       const int k1 = t + T * i;
@@ -368,24 +396,32 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
         a[k2] = cmul(a[k2], k2 < R2 / 2 ? khA[k2 * R1 * C] : khB[-k2 * R1 * C]);
       dft<R2, true>(a);   // over k2 -> j1
       const float2* twc = tw + k1;
+      if constexpr (DB) {
+        float2* exw = ex2 + (k1 * R2) * C + c;
 #pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = (j1 == 0) ? a[0] : cmul(a[j1], cconj(twc[j1 * R1]));
+        for (int j1 = 0; j1 < R2; ++j1) exw[j1 * C] = (j1 == 0) ? a[0] : cmul(a[j1], cconj(twc[j1 * R1]));
+      } else {
+#pragma unroll
+        for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = (j1 == 0) ? a[0] : cmul(a[j1], cconj(twc[j1 * R1]));
+      }
     }
     __syncthreads();
+    if constexpr (!DB) {
 #pragma unroll
-    for (int i = 0; i < R1 / T; ++i) {
-      float2* exw = ex + ((t + T * i) * R2) * C + c;
+      for (int i = 0; i < R1 / T; ++i) {
+        float2* exw = ex + ((t + T * i) * R2) * C + c;
 #pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) exw[j1 * C] = zb[i][j1];
+        for (int j1 = 0; j1 < R2; ++j1) exw[j1 * C] = zb[i][j1];
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // inverse stage B (j1-threads): outputs z = j1 + R2 j2 for j2 < R1/2
     float2* colb = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
 #pragma unroll
     for (int i = 0; i < R2 / T; ++i) {
       const int j1 = t + T * i;
       float2 a[R1];
-      const float2* exr = ex + j1 * C + c;
+      const float2* exr = ex2 + j1 * C + c;
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) a[k1] = exr[k1 * R2 * C];
       dft<R1, true>(a);
@@ -396,7 +432,12 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
         col += (size_t)R2 * zs;
       }
     }
-    __syncthreads();   // ex is free again for the next slot's first stage
+    // one buffer: ex is free again for the next slot's first stage only after
+    // this barrier.  Two buffers: the next slot's first stage writes ex, which
+    // every thread finished reading before the barrier above, and its middle
+    // stage writes ex2 only after the next first-stage barrier, which no thread
+    // passes before finishing this stage.
+    if constexpr (!DB) __syncthreads();
     if (next >= nb) break;
     b = next;
   }

@@ -28,10 +28,15 @@ struct GreenCall {
   long long* launches = nullptr; // optional kernel-launch counter (+5 per apply)
   const void* tmap = nullptr;    // CUtensorMap of T2 for the pass-3 tile loads
   int* err = nullptr;            // device flag raised when a bounded wait gives up
+  int tile = 0;                  // launch shapes: bit 0 alternative row shape, bit 1 alternative column
+                                 // shape, bit 2 two pass-3 exchange buffers
 };
 
-// Tensor map of the pass-3 buffer T2 = [max_batch * n][P][P] complex64, box C x 1 x n.
-cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, void* map_out /* CUtensorMap, 64 B aligned */);
+constexpr int MQ_TILES = 8;      // launch-shape variants of the Green's passes
+
+// Tensor map of the pass-3 buffer T2 = [max_batch * n][P][P] complex64, box C x 1 x n
+// with C the column width of the tile's column shape.
+cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, int tile, void* map_out /* CUtensorMap, 64 B aligned */);
 
 // Per-pass timing (opt-in tracing): events recorded around every Green's apply.
 struct Profiler {
@@ -56,13 +61,23 @@ struct KrylovGraph {
   long long kernels = 0;         // kernels per replay
 };
 
-// Number of CTAs pass 1 / pass 5 use per slot (partials layout).
-int green_row_ctas(int n);
+// Number of CTAs pass 1 / pass 5 use per slot (partials layout) for a tile
+// variant; green_row_ctas_max covers every variant.
+int green_row_ctas(int n, int tile);
+int green_row_ctas_max(int n);
+// Lines per CTA of passes 1/5 and columns per CTA of passes 2-4 (0 if n is
+// unsupported), and the largest dynamic shared memory of the tile's passes.
+void green_shape(int n, int tile, int* lines, int* cols, size_t* smem = nullptr);
+// Whether a tile's passes fit the device's shared memory per block.
+bool green_tile_fits(int n, int tile, int device);
+int green_col_width(int n, int tile);
 bool green_supported(int n);
 cudaError_t green_launch(const GreenCall& c, cudaStream_t s);
 
 // Per-P entry points (one translation unit each).
-#define MQ_DECL(P) cudaError_t green_launch_P##P(const GreenCall& c, cudaStream_t s); int green_row_ctas_P##P(int n);
+#define MQ_DECL(P)                                                   \
+  cudaError_t green_launch_P##P(const GreenCall& c, cudaStream_t s); \
+  void green_shape_P##P(int tile, int n, int* lines, int* cols, size_t* smem);
 MQ_DECL(16) MQ_DECL(24) MQ_DECL(32) MQ_DECL(48) MQ_DECL(64) MQ_DECL(96) MQ_DECL(128)
 MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
 #undef MQ_DECL
@@ -153,6 +168,8 @@ struct mqnpm_handle {
   int last_status = 0;
   Profiler prof;
   bool direct_launches = false;
+  int tile = 0;                            // launch shapes of the Green's passes (GreenCall::tile)
+  double tune_ms[MQ_TILES] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0};   // autotuner timings (-1: not timed)
   cudaStream_t capture_stream = nullptr;   // stream the iteration graphs are captured on
   std::vector<KrylovGraph> graphs;         // captured iterations (a few batch shapes)
   long long launches = 0;        // kernels launched by this handle since creation
@@ -187,6 +204,9 @@ int wprox_part_len();
 size_t wprox_part_count(int max_blocks);   // doubles of the partials buffer
 int wprox_barrier_words();                // unsigned words of the barrier counters
 int woodbury_scal_count();
+
+// tune.cu: pick the launch shapes of the Green's passes by timing
+int autotune_tile(mqnpm_handle* h);
 
 // status helpers (api.cu)
 int set_cuda_error(mqnpm_handle* h, cudaError_t e, const char* where);

@@ -323,6 +323,7 @@ __global__ void k_scale_real(const float* a, float* out, size_t N, float s) {
 cudaError_t glaunch_ev(mqnpm_handle* h, GreenCall c, cudaStream_t s, cudaEvent_t* ev) {
   c.ev = ev;
   c.launches = &h->launches;
+  c.tile = h->tile;
   c.tmap = h->w.t2map;
   c.err = h->w.gerr;
   return green_launch(c, s);

@@ -93,7 +93,7 @@ extern "C" int mqnpm_green_apply_noalloc(int n, double h, double kb, const float
         build_khat_scratch(n, h, kb, khat, reinterpret_cast<double2*>(d.base + NA_KA),
                            reinterpret_cast<double2*>(d.base + NA_KB), reinterpret_cast<double*>(d.base + NA_COS),
                            s) != cudaSuccess ||
-        make_t2_tensor_map(T2, n, 1, d.tmap) != cudaSuccess)
+        make_t2_tensor_map(T2, n, 1, 0, d.tmap) != cudaSuccess)
       return MQNPM_ERR_CUDA;
     d.n = n;
     d.h = h;

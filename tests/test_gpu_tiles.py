@@ -1,0 +1,136 @@
+"""Launch-shape variants of the Green's apply and the autotuner that picks one.
+
+Every tile runs the same arithmetic per line and per column (only the number
+of lines or columns per CTA and the pass-3 exchange scheme change), so a plain
+Green's apply must be bit-identical across the eight tiles at every transform
+length; reductions inside the Krylov solves regroup with the row shape, so
+gradients agree to rounding and against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import synth  # noqa: E402
+from oracle import physics  # noqa: E402
+from paper_2307_02043_gb300 import binding  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+KB = math.pi / 2
+TILES = range(8)
+
+
+def cone(L, deg=30.0):
+    t = math.radians(deg)
+    return np.array([[math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)]
+                     for p in 2 * math.pi * np.arange(L) / L])
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).to(DEV)
+
+
+@pytest.mark.parametrize("n", [8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 192])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_every_tile_gives_the_same_apply(n, adjoint):
+    rng = np.random.default_rng(500 + n)
+    nb = 2 if n >= 128 else 3
+    v = c64(rng.standard_normal((nb, n, n, n)) + 1j * rng.standard_normal((nb, n, n, n))).reshape(-1)
+    ref = None
+    skipped = []
+    for t in TILES:
+        try:
+            h = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=nb, tile=t)
+        except binding.MQNPMError as err:   # the tile's shared memory exceeds the device's
+            assert err.code == 1
+            skipped.append(t)
+            continue
+        info = h.tile_info()
+        assert info["tile"] == t and info["tuned_ms"] == [None] * 8
+        out = h.green_apply(v, adjoint=adjoint).cpu()
+        h.close()
+        if ref is None:
+            ref = out
+        else:
+            assert torch.equal(out, ref), (n, t)
+    # only the two-buffer z pass with the wide column shape can outgrow shared memory (P = 320)
+    assert set(skipped) <= {6, 7}, skipped
+    if n <= 32:
+        vh = v.cpu().numpy().reshape(nb, n, n, n)
+        kh = physics.green_hat(n, KB)
+        got = ref.numpy().reshape(nb, n, n, n)
+        for b in range(nb):
+            want = physics.green_apply(vh[b], kh, adjoint=adjoint)
+            assert np.max(np.abs(got[b] - want)) / np.max(np.abs(want)) < 2e-6
+
+
+def test_shapes_reported_per_tile():
+    """Bit 0 switches the lines per CTA of the x passes, bit 1 the columns per
+    CTA of the y/z passes, bit 2 neither (the pass-3 exchange scheme)."""
+    n = 128
+    shape = {}
+    for t in TILES:
+        h = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=1, tile=t)
+        info = h.tile_info()
+        h.close()
+        shape[t] = (info["lines_per_cta"], info["columns_per_cta"])
+    for t in TILES:
+        assert shape[t] == shape[t & 3]
+        assert shape[t][0] == shape[t & 1][0] and shape[t][1] == shape[t & 2][1]
+    assert shape[0][0] != shape[1][0] and shape[0][1] != shape[2][1]
+
+
+def test_autotuner_picks_the_fastest_and_caches():
+    n, nb = 64, 4
+    h1 = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=nb)
+    a = h1.tile_info()
+    ms = a["tuned_ms"]
+    assert all(m is not None and m > 0 for m in ms), ms
+    assert a["tile"] == int(np.argmin(ms))
+    h2 = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=nb)
+    assert h2.tile_info() == a          # same (device, n, slots): cached, not re-timed
+    h1.close()
+    h2.close()
+
+
+def test_invalid_tile_is_rejected():
+    for t in (-2, 8):
+        with pytest.raises(binding.MQNPMError):
+            binding.MQNPM(16, cone(2), [0, 0], [1.0], tile=t)
+
+
+@pytest.mark.parametrize("model", ["ls", "born"])
+def test_gradient_agrees_across_tiles_and_with_oracle(model):
+    """Row shapes regroup the per-CTA partial sums of the Krylov inner
+    products: the gradients agree to rounding, and with the oracle."""
+    n = 16
+    w = synth.small("ls32", n=n, L=6, batch=3, model=model)
+    kd = synth.illumination_dirs(w)
+    xt = synth.phantom(w)
+    om = physics.Model(n, kd, model, tol=1e-12)
+    ys = physics.simulate(om, xt, synth.noise_draws(w), w.snr_db)
+    so = np.zeros(w.L, dtype=np.int32)
+    for s_, ii in enumerate(synth.subsets(w)):
+        so[ii] = s_
+    x = 0.7 * xt
+    illum = [0, 1, 2]
+    scale = w.S / w.L
+    lo, go = om.batch_loss_grad(x, illum, ys, scale)
+    xd = torch.from_numpy(np.ascontiguousarray(x).astype(np.float32).reshape(-1)).to(DEV)
+    grads = []
+    for t in (0, 1, 6, 7):
+        h = binding.MQNPM(n, kd, so, [1.0] * w.S, model=model, krylov_tol=1e-6, max_batch=2, tile=t)
+        h.set_measurements(c64(ys).reshape(-1))
+        g, loss, _ = h.grad_batch(xd, illum, scale)
+        h.close()
+        g = g.cpu().numpy().astype(np.float64).reshape(go.shape)
+        assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), (model, t)
+        assert abs(loss - lo) <= 1e-5 * abs(lo), (model, t)
+        grads.append(g)
+    for g in grads[1:]:
+        assert np.linalg.norm(g - grads[0]) <= 1e-5 * np.linalg.norm(grads[0]), model
