@@ -250,11 +250,13 @@ int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count);
 /* Number of CUDA kernels this handle has launched since creation. */
 long long mqnpm_launch_count(const mqnpm_handle* h);
 
-/* Launch shapes the handle uses: *tile (0..7), lines per CTA of the x passes
- * and columns per CTA of the y/z passes; ms (8 doubles, may be NULL) receives
- * the autotuner's time of one Green's apply per tile, -1 where none was taken
- * (a fixed tile).  Returns MQNPM_OK or INVALID_ARG. */
-int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* lines, int* cols, double* ms);
+/* Launch shapes the handle uses: *tile (0..7); shape (4 ints) receives the
+ * lines per CTA and threads per line of the x passes, then the columns per CTA
+ * and threads per column of the y/z passes; ms (8 doubles, may be NULL)
+ * receives the autotuner's time of one Green's apply per tile, -1 where none
+ * was taken (a fixed tile, or one whose shared memory does not fit).
+ * Returns MQNPM_OK or INVALID_ARG. */
+int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms);
 
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);
 int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls);

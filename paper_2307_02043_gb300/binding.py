@@ -92,7 +92,7 @@ SIGNATURES = {
     "mqnpm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "mqnpm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "mqnpm_tile_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_prox_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int)]),
     "mqnpm_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -265,10 +265,12 @@ class MQNPM:
 
     def tile_info(self) -> dict:
         """Launch shapes of the Green's passes and the autotuner's timings (ms per apply)."""
-        tile, lines, cols = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        tile = ctypes.c_int()
+        shape = (ctypes.c_int * 4)()
         ms = (ctypes.c_double * 8)()
-        self._raise(self.lib.mqnpm_tile_info(self._h, ctypes.byref(tile), ctypes.byref(lines), ctypes.byref(cols), ms))
-        return {"tile": tile.value, "lines_per_cta": lines.value, "columns_per_cta": cols.value,
+        self._raise(self.lib.mqnpm_tile_info(self._h, ctypes.byref(tile), shape, ms))
+        return {"tile": tile.value, "lines_per_cta": shape[0], "threads_per_line": shape[1],
+                "columns_per_cta": shape[2], "threads_per_column": shape[3],
                 "tuned_ms": [round(m, 4) if m >= 0 else None for m in ms]}
 
     # -- calls -------------------------------------------------------------

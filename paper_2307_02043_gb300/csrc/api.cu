@@ -130,10 +130,10 @@ const char* mqnpm_last_error(const mqnpm_handle* h) { return h ? h->err.c_str() 
 
 long long mqnpm_launch_count(const mqnpm_handle* h) { return h ? h->launches : 0; }
 
-int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* lines, int* cols, double* ms) {
-  if (!h || !tile || !lines || !cols) return MQNPM_ERR_INVALID_ARG;
+int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms) {
+  if (!h || !tile || !shape) return MQNPM_ERR_INVALID_ARG;
   *tile = h->tile;
-  green_shape(h->n, h->tile, lines, cols);
+  green_shape(h->n, h->tile, shape);
   if (ms)
     for (int i = 0; i < MQ_TILES; ++i) ms[i] = h->tune_ms[i];
   return MQNPM_OK;

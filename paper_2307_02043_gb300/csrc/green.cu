@@ -34,12 +34,11 @@ bool green_supported(int n) {
   }
 }
 
-void green_shape(int n, int tile, int* lines, int* cols, size_t* smem) {
-  *lines = 0;
-  *cols = 0;
+void green_shape(int n, int tile, int* shape, size_t* smem) {
+  shape[0] = shape[1] = shape[2] = shape[3] = 0;
   size_t m = 0;
   switch (2 * n) {
-#define MQ_CASE(P) case P: green_shape_P##P(tile, n, lines, cols, &m); break;
+#define MQ_CASE(P) case P: green_shape_P##P(tile, n, shape, &m); break;
     MQ_DISPATCH(MQ_CASE)
 #undef MQ_CASE
     default:
@@ -49,26 +48,26 @@ void green_shape(int n, int tile, int* lines, int* cols, size_t* smem) {
 }
 
 bool green_tile_fits(int n, int tile, int device) {
-  int lines = 0, cols = 0, optin = 0;
+  int shape[4], optin = 0;
   size_t smem = 0;
-  green_shape(n, tile, &lines, &cols, &smem);
-  if (lines <= 0 || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+  green_shape(n, tile, shape, &smem);
+  if (shape[0] <= 0 || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return false;
   return smem <= (size_t)optin;
 }
 
 int green_row_ctas(int n, int tile) {
-  int lines = 0, cols = 0;
-  green_shape(n, tile, &lines, &cols);
-  return lines > 0 ? (n * n + lines - 1) / lines : 0;
+  int shape[4];
+  green_shape(n, tile, shape);
+  return shape[0] > 0 ? (n * n + shape[0] - 1) / shape[0] : 0;
 }
 
 int green_row_ctas_max(int n) { return std::max(green_row_ctas(n, 0), green_row_ctas(n, 1)); }
 
 int green_col_width(int n, int tile) {
-  int lines = 0, cols = 0;
-  green_shape(n, tile, &lines, &cols);
-  return cols;
+  int shape[4];
+  green_shape(n, tile, shape);
+  return shape[2];
 }
 
 cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {

@@ -110,9 +110,11 @@ cudaError_t columns(const GreenCall& c, cudaStream_t s, unsigned rec_flags) {
 }
 }  // namespace
 
-void MQ_CAT(green_shape_P, MQ_P)(int tile, int n, int* lines, int* cols, size_t* smem) {
-  *lines = (tile & 1) ? RowShape<P, 1>::LPB : RowShape<P, 0>::LPB;
-  *cols = (tile & 2) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
+void MQ_CAT(green_shape_P, MQ_P)(int tile, int n, int* shape, size_t* smem) {
+  shape[0] = (tile & 1) ? RowShape<P, 1>::LPB : RowShape<P, 0>::LPB;
+  shape[1] = (tile & 1) ? RowShape<P, 1>::T : RowShape<P, 0>::T;
+  shape[2] = (tile & 2) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
+  shape[3] = (tile & 2) ? ColShape<P, 1>::T : ColShape<P, 0>::T;
   size_t m = 0;   // the largest dynamic shared memory of the tile's five passes
   switch ((tile >> 1) & 3) {
     case 0: m = Pass3Smem<P, 0, false>::bytes(n); break;

@@ -21,41 +21,59 @@
 #include "kstate.h"
 
 // ----------------------------------------------------------- CTA shapes
-// Every transform length has two row shapes (lines per CTA of passes 1 and 5)
-// and two column shapes (columns per CTA of passes 2-4).  V = 0 is the
-// default; V = 1 halves it, or doubles it where the default CTA has fewer than
-// 128 threads.  The autotuner times the four combinations per handle.
+// Every transform length has two row shapes (passes 1 and 5) and two column
+// shapes (passes 2-4); V = 0 is the default, V = 1 the alternative the
+// autotuner also times.  Where the plan's threads per line T is below R2 (T
+// is limited to a common divisor of R1 and R2), the alternative gives every
+// line or column R1 threads, one middle-stage DFT each (the other stage leaves
+// R1 - R2 of them idle); elsewhere it halves the lines or columns per CTA, or
+// doubles them where the default CTA has fewer than 128 threads.
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
 template <int P>
 struct RowBase {
   using PL = Plan<P>;
   static constexpr int PITCH = PL::R1 + 1;                 // padded exchange row
   static constexpr int PER_LINE = PL::R2 * PITCH;
+  static constexpr bool WIDE = PL::T < PL::R2;
   static constexpr int LPB0 = 256 / PL::T;
   static constexpr int LPB_DEF = (LPB0 * PER_LINE * 8 > 40960) ? (40960 / (PER_LINE * 8) >= 16 ? 16 : 8) : LPB0;
-  static constexpr int LPB_ALT = LPB_DEF * PL::T >= 128 ? LPB_DEF / 2 : 2 * LPB_DEF;
+  static constexpr int T_ALT = WIDE ? PL::R1 : PL::T;
+  // wide: the most lines, in steps that keep whole warps, with at most 320
+  // threads and 48 KB of shared memory
+  static constexpr int Q = 32 / gcd_c(T_ALT, 32);
+  static constexpr int LPB_W0 = 320 / T_ALT < (49152 / 8 - P) / PER_LINE ? 320 / T_ALT : (49152 / 8 - P) / PER_LINE;
+  static constexpr int LPB_W = (LPB_W0 / Q) * Q;
+  static constexpr int LPB_ALT = WIDE ? LPB_W : (LPB_DEF * PL::T >= 128 ? LPB_DEF / 2 : 2 * LPB_DEF);
 };
 template <int P, int V = 0>
 struct RowShape : RowBase<P> {
   static_assert(V == 0 || V == 1, "two row shapes");
+  static constexpr int T = V == 0 ? Plan<P>::T : RowBase<P>::T_ALT;
   static constexpr int LPB = V == 0 ? RowBase<P>::LPB_DEF : RowBase<P>::LPB_ALT;
-  static constexpr int THREADS = LPB * Plan<P>::T;
+  static constexpr int THREADS = LPB * T;
+  static_assert(LPB >= 1 && THREADS % 32 == 0, "whole warps (the partial sums reduce per warp)");
   static constexpr int SMEM = (P + LPB * RowBase<P>::PER_LINE) * 8;
 };
 template <int P>
 struct ColBase {
   using PL = Plan<P>;
+  static constexpr bool WIDE = PL::T < PL::R2;
   static constexpr int C0 = 256 / PL::T;
   static constexpr int C1 = C0 > P ? P : C0;
   static constexpr int C_DEF = (C1 * P * 8 > 40960) ? 16 : C1;
   static constexpr int C_UP = 2 * C_DEF;
-  static constexpr int C_ALT = (C_DEF * PL::T < 128 && C_UP <= P && P % C_UP == 0) ? C_UP : C_DEF / 2;
+  static constexpr int C_ALT = WIDE ? C_DEF
+                               : (C_DEF * PL::T < 128 && C_UP <= P && P % C_UP == 0) ? C_UP : C_DEF / 2;
+  static constexpr int T_ALT = WIDE ? PL::R1 : PL::T;
 };
 template <int P, int V = 0>
 struct ColShape : ColBase<P> {
   static_assert(V == 0 || V == 1, "two column shapes");
+  static constexpr int T = V == 0 ? Plan<P>::T : ColBase<P>::T_ALT;
   static constexpr int C = V == 0 ? ColBase<P>::C_DEF : ColBase<P>::C_ALT;
   static_assert(P % C == 0 && C % 2 == 0, "column tiles divide P; TMA rows of 16-byte multiples");
-  static constexpr int THREADS = C * Plan<P>::T;
+  static constexpr int THREADS = C * T;
   static constexpr int SMEM = (P + P * C) * 8;
 };
 
@@ -105,7 +123,8 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
         const KState* __restrict__ st, double* __restrict__ partials) {
   using PL = Plan<P>;
   using SH = RowShape<P, RV>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T;
+  constexpr int I1 = (R2 + T - 1) / T, I2 = (R1 + T - 1) / T;   // sub-DFTs per thread and stage
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* ex = sm + P;
@@ -122,8 +141,9 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
   parts.zero();
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < R2 / T; ++i) {
+  for (int i = 0; i < I1; ++i) {
     const int n2 = t + T * i;
+    if (R2 % T != 0 && n2 >= R2) continue;   // idle in this stage
     float2 a[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
@@ -136,8 +156,9 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < R1 / T; ++i) {
+  for (int i = 0; i < I2; ++i) {
     const int k1 = t + T * i;
+    if (R1 % T != 0 && k1 >= R1) continue;
     float2 a[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) a[n2] = exl[n2 * SH::PITCH + k1];
@@ -158,7 +179,8 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
         const KState* __restrict__ st, double* __restrict__ partials) {
   using PL = Plan<P>;
   using SH = RowShape<P, RV>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T;
+  constexpr int I1 = (R2 + T - 1) / T, I2 = (R1 + T - 1) / T;   // sub-DFTs per thread and stage
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* ex = sm + P;
@@ -175,8 +197,9 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
   parts.zero();
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < R2 / T; ++i) {
+  for (int i = 0; i < I1; ++i) {
     const int n2 = t + T * i;
+    if (R2 % T != 0 && n2 >= R2) continue;   // idle in this stage
     float2 a[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) a[n1] = valid ? src[R2 * n1 + n2] : make_float2(0.f, 0.f);
@@ -186,8 +209,9 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < R1 / T; ++i) {
+  for (int i = 0; i < I2; ++i) {
     const int k1 = t + T * i;
+    if (R1 % T != 0 && k1 >= R1) continue;
     float2 a[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) a[n2] = exl[n2 * SH::PITCH + k1];
@@ -209,7 +233,8 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
          const float2* __restrict__ twg, const KState* __restrict__ st) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T, C = SH::C;
+  constexpr int I1 = (R2 + T - 1) / T, I2 = (R1 + T - 1) / T;   // sub-DFTs per thread and stage
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* ex = sm + P;
@@ -224,8 +249,9 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
   float2* dst = out + ((size_t)b * n + z) * len_out * P + kx;
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < R2 / T; ++i) {
+  for (int i = 0; i < I1; ++i) {
     const int n2 = t + T * i;
+    if (R2 % T != 0 && n2 >= R2) continue;   // idle in this stage
     float2 a[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
@@ -241,8 +267,9 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < R1 / T; ++i) {
+  for (int i = 0; i < I2; ++i) {
     const int k1 = t + T * i;
+    if (R1 % T != 0 && k1 >= R1) continue;
     float2 a[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) a[n2] = ex[(n2 * R1 + k1) * C + c];
@@ -303,7 +330,8 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
   using SM = Pass3Smem<P, CV, DB>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, T = PL::T, C = SH::C, KH = SM::KH;
+  constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T, C = SH::C, KH = SM::KH;
+  constexpr int I1 = (R2 + T - 1) / T, I2 = (R1 + T - 1) / T;   // sub-DFTs per thread and stage
   static_assert(R1 * R2 == P && R2 % 2 == 0, "two-stage plan with an even second factor");
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
@@ -356,8 +384,9 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     phase ^= 1u;
     // forward stage 1 (n2-threads), inputs z = R2 n1 + n2 < n from the TMA tile [z][c]
 #pragma unroll
-    for (int i = 0; i < R2 / T; ++i) {
+    for (int i = 0; i < I1; ++i) {
       const int n2 = t + T * i;
+      if (R2 % T != 0 && n2 >= R2) continue;   // idle in this stage
       float2 a[R1];
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) {
@@ -380,10 +409,11 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     }
     // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread).
     // K_hat row of kz = k1 + R1 k2: kz itself for k2 < R2/2, else the folded P - kz.
-    float2 zb[DB ? 1 : R1 / T][R2];
+    float2 zb[DB ? 1 : I2][R2];
 #pragma unroll
-    for (int i = 0; i < R1 / T; ++i) {
+    for (int i = 0; i < I2; ++i) {
       const int k1 = t + T * i;
+      if (R1 % T != 0 && k1 >= R1) continue;
       float2 a[R2];
       const float2* exr = ex + k1 * C + c;
 #pragma unroll
@@ -408,7 +438,8 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     __syncthreads();
     if constexpr (!DB) {
 #pragma unroll
-      for (int i = 0; i < R1 / T; ++i) {
+      for (int i = 0; i < I2; ++i) {
+        if (R1 % T != 0 && t + T * i >= R1) continue;
         float2* exw = ex + ((t + T * i) * R2) * C + c;
 #pragma unroll
         for (int j1 = 0; j1 < R2; ++j1) exw[j1 * C] = zb[i][j1];
@@ -418,8 +449,9 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     // inverse stage B (j1-threads): outputs z = j1 + R2 j2 for j2 < R1/2
     float2* colb = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
 #pragma unroll
-    for (int i = 0; i < R2 / T; ++i) {
+    for (int i = 0; i < I1; ++i) {
       const int j1 = t + T * i;
+      if (R2 % T != 0 && j1 >= R2) continue;
       float2 a[R1];
       const float2* exr = ex2 + j1 * C + c;
 #pragma unroll

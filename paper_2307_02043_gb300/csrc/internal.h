@@ -65,9 +65,10 @@ struct KrylovGraph {
 // variant; green_row_ctas_max covers every variant.
 int green_row_ctas(int n, int tile);
 int green_row_ctas_max(int n);
-// Lines per CTA of passes 1/5 and columns per CTA of passes 2-4 (0 if n is
-// unsupported), and the largest dynamic shared memory of the tile's passes.
-void green_shape(int n, int tile, int* lines, int* cols, size_t* smem = nullptr);
+// shape[4] = lines per CTA and threads per line of passes 1/5, columns per
+// CTA and threads per column of passes 2-4 (zeros if n is unsupported); smem =
+// the largest dynamic shared memory of the tile's passes.
+void green_shape(int n, int tile, int* shape, size_t* smem = nullptr);
 // Whether a tile's passes fit the device's shared memory per block.
 bool green_tile_fits(int n, int tile, int device);
 int green_col_width(int n, int tile);
@@ -77,7 +78,7 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s);
 // Per-P entry points (one translation unit each).
 #define MQ_DECL(P)                                                   \
   cudaError_t green_launch_P##P(const GreenCall& c, cudaStream_t s); \
-  void green_shape_P##P(int tile, int n, int* lines, int* cols, size_t* smem);
+  void green_shape_P##P(int tile, int n, int* shape, size_t* smem);
 MQ_DECL(16) MQ_DECL(24) MQ_DECL(32) MQ_DECL(48) MQ_DECL(64) MQ_DECL(96) MQ_DECL(128)
 MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
 #undef MQ_DECL

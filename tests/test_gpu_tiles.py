@@ -69,20 +69,27 @@ def test_every_tile_gives_the_same_apply(n, adjoint):
             assert np.max(np.abs(got[b] - want)) / np.max(np.abs(want)) < 2e-6
 
 
-def test_shapes_reported_per_tile():
-    """Bit 0 switches the lines per CTA of the x passes, bit 1 the columns per
-    CTA of the y/z passes, bit 2 neither (the pass-3 exchange scheme)."""
-    n = 128
+@pytest.mark.parametrize("n", [128, 160])
+def test_shapes_reported_per_tile(n):
+    """Bit 0 switches the x-pass shape, bit 1 the y/z-pass shape, bit 2 neither
+    (the pass-3 exchange scheme).  At n = 128 the alternatives halve the lines
+    or columns per CTA; at n = 160 (P = 320 = 20 x 16, four threads per line by
+    default) they give every line and column 20 threads."""
     shape = {}
     for t in TILES:
-        h = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=1, tile=t)
+        try:
+            h = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=1, tile=t)
+        except binding.MQNPMError:
+            continue
         info = h.tile_info()
         h.close()
-        shape[t] = (info["lines_per_cta"], info["columns_per_cta"])
-    for t in TILES:
+        shape[t] = (info["lines_per_cta"], info["threads_per_line"], info["columns_per_cta"], info["threads_per_column"])
+    for t in shape:
         assert shape[t] == shape[t & 3]
-        assert shape[t][0] == shape[t & 1][0] and shape[t][1] == shape[t & 2][1]
-    assert shape[0][0] != shape[1][0] and shape[0][1] != shape[2][1]
+        assert shape[t][:2] == shape[t & 1][:2] and shape[t][2:] == shape[t & 2][2:]
+    assert shape[0][:2] != shape[1][:2] and shape[0][2:] != shape[2][2:]
+    if n == 160:
+        assert shape[0][1] == 4 and shape[1][1] == 20 and shape[0][3] == 4 and shape[2][3] == 20
 
 
 def test_autotuner_picks_the_fastest_and_caches():
