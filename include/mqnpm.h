@@ -106,12 +106,12 @@ typedef struct mqnpm_config {
                               G, e.g. a truncated kernel), used instead of the
                               library's own (Section 6 reading)              */
   int tile;                /* launch shapes of the Green's passes: -1 picks the
-                              fastest of 0..7 by timing at create (cached per
-                              device, n and batch slots); 0..7 fixes them, bit 0
-                              the alternative lines per CTA of the x passes,
-                              bit 1 the alternative columns per CTA of the y/z
-                              passes, bit 2 two exchange buffers in the z pass
-                              (0 = the built-in defaults)                     */
+                              fastest of 0..15 by timing at create (cached per
+                              device, n and batch slots); 0..15 fixes them: bits
+                              0, 1, 2 select the alternative shape (lines or
+                              columns per CTA, threads per line or column) of
+                              the x, y and z passes, bit 3 two exchange buffers
+                              in the z pass (0 = the built-in defaults)       */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;
@@ -250,12 +250,12 @@ int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count);
 /* Number of CUDA kernels this handle has launched since creation. */
 long long mqnpm_launch_count(const mqnpm_handle* h);
 
-/* Launch shapes the handle uses: *tile (0..7); shape (4 ints) receives the
+/* Launch shapes the handle uses: *tile (0..15); shape (6 ints) receives the
  * lines per CTA and threads per line of the x passes, then the columns per CTA
- * and threads per column of the y/z passes; ms (8 doubles, may be NULL)
- * receives the autotuner's time of one Green's apply per tile, -1 where none
- * was taken (a fixed tile, or one whose shared memory does not fit).
- * Returns MQNPM_OK or INVALID_ARG. */
+ * and threads per column of the y passes and of the z pass; ms (16 doubles,
+ * may be NULL) receives the autotuner's time of one Green's apply per tile,
+ * -1 where none was taken (a fixed tile, or one whose shared memory does not
+ * fit).  Returns MQNPM_OK or INVALID_ARG. */
 int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms);
 
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);

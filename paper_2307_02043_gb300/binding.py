@@ -266,11 +266,13 @@ class MQNPM:
     def tile_info(self) -> dict:
         """Launch shapes of the Green's passes and the autotuner's timings (ms per apply)."""
         tile = ctypes.c_int()
-        shape = (ctypes.c_int * 4)()
-        ms = (ctypes.c_double * 8)()
+        shape = (ctypes.c_int * 6)()
+        ms = (ctypes.c_double * 16)()
         self._raise(self.lib.mqnpm_tile_info(self._h, ctypes.byref(tile), shape, ms))
-        return {"tile": tile.value, "lines_per_cta": shape[0], "threads_per_line": shape[1],
-                "columns_per_cta": shape[2], "threads_per_column": shape[3],
+        return {"tile": tile.value, "x": {"lines_per_cta": shape[0], "threads_per_line": shape[1]},
+                "y": {"columns_per_cta": shape[2], "threads_per_column": shape[3]},
+                "z": {"columns_per_cta": shape[4], "threads_per_column": shape[5],
+                      "exchange_buffers": 2 if tile.value & 8 else 1},
                 "tuned_ms": [round(m, 4) if m >= 0 else None for m in ms]}
 
     # -- calls -------------------------------------------------------------

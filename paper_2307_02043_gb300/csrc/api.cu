@@ -261,6 +261,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   const size_t N = h->N, M = h->M, B = h->max_batch;
   const int n = h->n, P = h->P;
   h->tile = cfg->tile < 0 ? 0 : cfg->tile;
+  std::fill(h->tune_ms, h->tune_ms + MQ_TILES, -1.0);
   if (!green_tile_fits(n, h->tile, h->device)) {
     char msg[120];
     snprintf(msg, sizeof msg, "tile %d needs more shared memory per block than the device has at n = %d", h->tile, n);

@@ -35,7 +35,7 @@ bool green_supported(int n) {
 }
 
 void green_shape(int n, int tile, int* shape, size_t* smem) {
-  shape[0] = shape[1] = shape[2] = shape[3] = 0;
+  for (int i = 0; i < 6; ++i) shape[i] = 0;
   size_t m = 0;
   switch (2 * n) {
 #define MQ_CASE(P) case P: green_shape_P##P(tile, n, shape, &m); break;
@@ -48,7 +48,7 @@ void green_shape(int n, int tile, int* shape, size_t* smem) {
 }
 
 bool green_tile_fits(int n, int tile, int device) {
-  int shape[4], optin = 0;
+  int shape[6], optin = 0;
   size_t smem = 0;
   green_shape(n, tile, shape, &smem);
   if (shape[0] <= 0 || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
@@ -57,17 +57,17 @@ bool green_tile_fits(int n, int tile, int device) {
 }
 
 int green_row_ctas(int n, int tile) {
-  int shape[4];
+  int shape[6];
   green_shape(n, tile, shape);
   return shape[0] > 0 ? (n * n + shape[0] - 1) / shape[0] : 0;
 }
 
 int green_row_ctas_max(int n) { return std::max(green_row_ctas(n, 0), green_row_ctas(n, 1)); }
 
-int green_col_width(int n, int tile) {
-  int shape[4];
+int green_col_width(int n, int tile) {   // columns per CTA of pass 3 (the tensor-map box)
+  int shape[6];
   green_shape(n, tile, shape);
-  return shape[2];
+  return shape[4];
 }
 
 cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {

@@ -99,14 +99,14 @@ cudaError_t pass3(const GreenCall& c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int CV, bool DB>
+template <int YV, int ZV, bool DB>
 cudaError_t columns(const GreenCall& c, cudaStream_t s, unsigned rec_flags) {
   cudaError_t e;
-  if ((e = pass_y<CV, false>(c, c.T1, c.T2, s)) != cudaSuccess) return e;
+  if ((e = pass_y<YV, false>(c, c.T1, c.T2, s)) != cudaSuccess) return e;
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[2], s, rec_flags)) != cudaSuccess) return e;
-  if ((e = c.adjoint ? pass3<CV, DB, true>(c, s) : pass3<CV, DB, false>(c, s)) != cudaSuccess) return e;
+  if ((e = c.adjoint ? pass3<ZV, DB, true>(c, s) : pass3<ZV, DB, false>(c, s)) != cudaSuccess) return e;
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[3], s, rec_flags)) != cudaSuccess) return e;
-  return pass_y<CV, true>(c, c.T2, c.T1, s);
+  return pass_y<YV, true>(c, c.T2, c.T1, s);
 }
 }  // namespace
 
@@ -115,8 +115,10 @@ void MQ_CAT(green_shape_P, MQ_P)(int tile, int n, int* shape, size_t* smem) {
   shape[1] = (tile & 1) ? RowShape<P, 1>::T : RowShape<P, 0>::T;
   shape[2] = (tile & 2) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
   shape[3] = (tile & 2) ? ColShape<P, 1>::T : ColShape<P, 0>::T;
+  shape[4] = (tile & 4) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
+  shape[5] = (tile & 4) ? ColShape<P, 1>::T : ColShape<P, 0>::T;
   size_t m = 0;   // the largest dynamic shared memory of the tile's five passes
-  switch ((tile >> 1) & 3) {
+  switch ((tile >> 2) & 3) {
     case 0: m = Pass3Smem<P, 0, false>::bytes(n); break;
     case 1: m = Pass3Smem<P, 1, false>::bytes(n); break;
     case 2: m = Pass3Smem<P, 0, true>::bytes(n); break;
@@ -139,15 +141,19 @@ cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
   }
   const bool row_alt = (c.tile & 1) != 0;
-  const int col = (c.tile >> 1) & 3;   // bit 1: column shape, bit 2: pass-3 exchange buffers
+  const int col = (c.tile >> 1) & 7;   // bit 1: y-pass shape, bit 2: z-pass shape, bit 3: its two buffers
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[0], s, rec_flags)) != cudaSuccess) return e;
   if ((e = row_alt ? pass1<1>(c, s) : pass1<0>(c, s)) != cudaSuccess) return e;
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[1], s, rec_flags)) != cudaSuccess) return e;
   switch (col) {
-    case 0: e = columns<0, false>(c, s, rec_flags); break;
-    case 1: e = columns<1, false>(c, s, rec_flags); break;
-    case 2: e = columns<0, true>(c, s, rec_flags); break;
-    default: e = columns<1, true>(c, s, rec_flags); break;
+    case 0: e = columns<0, 0, false>(c, s, rec_flags); break;
+    case 1: e = columns<1, 0, false>(c, s, rec_flags); break;
+    case 2: e = columns<0, 1, false>(c, s, rec_flags); break;
+    case 3: e = columns<1, 1, false>(c, s, rec_flags); break;
+    case 4: e = columns<0, 0, true>(c, s, rec_flags); break;
+    case 5: e = columns<1, 0, true>(c, s, rec_flags); break;
+    case 6: e = columns<0, 1, true>(c, s, rec_flags); break;
+    default: e = columns<1, 1, true>(c, s, rec_flags); break;
   }
   if (e != cudaSuccess) return e;
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[4], s, rec_flags)) != cudaSuccess) return e;

@@ -28,11 +28,11 @@ struct GreenCall {
   long long* launches = nullptr; // optional kernel-launch counter (+5 per apply)
   const void* tmap = nullptr;    // CUtensorMap of T2 for the pass-3 tile loads
   int* err = nullptr;            // device flag raised when a bounded wait gives up
-  int tile = 0;                  // launch shapes: bit 0 alternative row shape, bit 1 alternative column
-                                 // shape, bit 2 two pass-3 exchange buffers
+  int tile = 0;                  // launch shapes: alternative shape of bit 0 the x passes, bit 1 the
+                                 // y passes, bit 2 the z pass; bit 3 two z-pass exchange buffers
 };
 
-constexpr int MQ_TILES = 8;      // launch-shape variants of the Green's passes
+constexpr int MQ_TILES = 16;     // launch-shape variants of the Green's passes
 
 // Tensor map of the pass-3 buffer T2 = [max_batch * n][P][P] complex64, box C x 1 x n
 // with C the column width of the tile's column shape.
@@ -65,9 +65,9 @@ struct KrylovGraph {
 // variant; green_row_ctas_max covers every variant.
 int green_row_ctas(int n, int tile);
 int green_row_ctas_max(int n);
-// shape[4] = lines per CTA and threads per line of passes 1/5, columns per
-// CTA and threads per column of passes 2-4 (zeros if n is unsupported); smem =
-// the largest dynamic shared memory of the tile's passes.
+// shape[6] = lines per CTA and threads per line of passes 1/5, columns per
+// CTA and threads per column of passes 2/4, then of pass 3 (zeros if n is
+// unsupported); smem = the largest dynamic shared memory of the tile's passes.
 void green_shape(int n, int tile, int* shape, size_t* smem = nullptr);
 // Whether a tile's passes fit the device's shared memory per block.
 bool green_tile_fits(int n, int tile, int device);
@@ -170,7 +170,7 @@ struct mqnpm_handle {
   Profiler prof;
   bool direct_launches = false;
   int tile = 0;                            // launch shapes of the Green's passes (GreenCall::tile)
-  double tune_ms[MQ_TILES] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0};   // autotuner timings (-1: not timed)
+  double tune_ms[MQ_TILES] = {};   // autotuner timings (-1: not timed; set at create)
   cudaStream_t capture_stream = nullptr;   // stream the iteration graphs are captured on
   std::vector<KrylovGraph> graphs;         // captured iterations (a few batch shapes)
   long long launches = 0;        // kernels launched by this handle since creation

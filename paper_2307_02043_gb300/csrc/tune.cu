@@ -1,13 +1,15 @@
 // Launch-shape autotuner of the Green's apply.
 //
-// Each transform length has two row shapes (lines per CTA of the x passes),
-// two column shapes (columns per CTA of the y and z passes) and two exchange
-// schemes of pass 3 (one or two shared-memory buffers), so eight tiles.  The tuner times a plain apply of min(max_batch, 8) slots for each
-// tile on the handle's own buffers (zero input: the passes do the same work
-// for any values), round-robin over three rounds after one warm-up round so
-// that clock ramp-up does not favour a late candidate, and keeps the tile with
-// the smallest best time.  The choice is cached per (device, n, slots) for
-// the life of the process, so handles of the same shape are not re-timed.
+// Each transform length has two shapes for the x passes, two for the y
+// passes and two for the z pass (lines or columns per CTA and threads per
+// line or column), and two exchange schemes of the z pass (one or two
+// shared-memory buffers): sixteen tiles.  The tuner times a plain apply of
+// min(max_batch, 8) slots for each tile on the handle's own buffers (zero
+// input: the passes do the same work for any values), round-robin over two
+// rounds after one warm-up round so that clock ramp-up does not favour a late
+// candidate, and keeps the tile with the smallest best time.  The choice is
+// cached per (device, n, slots) for the life of the process, so handles of the
+// same shape are not re-timed.
 #include <array>
 #include <map>
 #include <mutex>
@@ -76,7 +78,7 @@ int autotune_tile(mqnpm_handle* h) {
     ms.fill(1e30);
     bool fits[MQ_TILES];
     for (int t = 0; t < MQ_TILES; ++t) fits[t] = green_tile_fits(h->n, t, h->device);
-    for (int round = 0; round < 4 && e == cudaSuccess; ++round)
+    for (int round = 0; round < 3 && e == cudaSuccess; ++round)
       for (int t = 0; t < MQ_TILES && e == cudaSuccess; ++t) {
         if (!fits[t]) continue;
         c.tile = t;

@@ -22,7 +22,7 @@ from paper_2307_02043_gb300 import binding  # noqa: E402
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 KB = math.pi / 2
-TILES = range(8)
+TILES = range(16)
 
 
 def cone(L, deg=30.0):
@@ -51,15 +51,15 @@ def test_every_tile_gives_the_same_apply(n, adjoint):
             skipped.append(t)
             continue
         info = h.tile_info()
-        assert info["tile"] == t and info["tuned_ms"] == [None] * 8
+        assert info["tile"] == t and info["tuned_ms"] == [None] * 16
         out = h.green_apply(v, adjoint=adjoint).cpu()
         h.close()
         if ref is None:
             ref = out
         else:
             assert torch.equal(out, ref), (n, t)
-    # only the two-buffer z pass with the wide column shape can outgrow shared memory (P = 320)
-    assert set(skipped) <= {6, 7}, skipped
+    # only the two-buffer z pass with the alternative shape can outgrow shared memory (P = 320)
+    assert all(t & 12 == 12 for t in skipped), skipped
     if n <= 32:
         vh = v.cpu().numpy().reshape(nb, n, n, n)
         kh = physics.green_hat(n, KB)
@@ -71,10 +71,10 @@ def test_every_tile_gives_the_same_apply(n, adjoint):
 
 @pytest.mark.parametrize("n", [128, 160])
 def test_shapes_reported_per_tile(n):
-    """Bit 0 switches the x-pass shape, bit 1 the y/z-pass shape, bit 2 neither
-    (the pass-3 exchange scheme).  At n = 128 the alternatives halve the lines
-    or columns per CTA; at n = 160 (P = 320 = 20 x 16, four threads per line by
-    default) they give every line and column 20 threads."""
+    """Bits 0, 1, 2 switch the x-, y- and z-pass shapes, bit 3 the z-pass
+    exchange scheme.  At n = 128 the alternatives halve the lines or columns
+    per CTA; at n = 160 (P = 320 = 20 x 16, four threads per line by default)
+    they give every line and column 20 threads."""
     shape = {}
     for t in TILES:
         try:
@@ -83,13 +83,18 @@ def test_shapes_reported_per_tile(n):
             continue
         info = h.tile_info()
         h.close()
-        shape[t] = (info["lines_per_cta"], info["threads_per_line"], info["columns_per_cta"], info["threads_per_column"])
+        shape[t] = (info["x"], info["y"], info["z"])
     for t in shape:
-        assert shape[t] == shape[t & 3]
-        assert shape[t][:2] == shape[t & 1][:2] and shape[t][2:] == shape[t & 2][2:]
-    assert shape[0][:2] != shape[1][:2] and shape[0][2:] != shape[2][2:]
+        assert shape[t][0] == shape[t & 1][0] and shape[t][1] == shape[t & 2][1]
+        assert {k: v for k, v in shape[t][2].items() if k != "exchange_buffers"} == \
+               {k: v for k, v in shape[t & 4][2].items() if k != "exchange_buffers"}
+        assert shape[t][2]["exchange_buffers"] == (2 if t & 8 else 1)
+    assert shape[0][0] != shape[1][0] and shape[0][1] != shape[2][1]
+    assert shape[0][2]["columns_per_cta"] != shape[4][2]["columns_per_cta"] or \
+        shape[0][2]["threads_per_column"] != shape[4][2]["threads_per_column"]
     if n == 160:
-        assert shape[0][1] == 4 and shape[1][1] == 20 and shape[0][3] == 4 and shape[2][3] == 20
+        assert shape[0][0]["threads_per_line"] == 4 and shape[1][0]["threads_per_line"] == 20
+        assert shape[2][1]["threads_per_column"] == 20 and shape[4][2]["threads_per_column"] == 20
 
 
 def test_autotuner_picks_the_fastest_and_caches():
@@ -106,7 +111,7 @@ def test_autotuner_picks_the_fastest_and_caches():
 
 
 def test_invalid_tile_is_rejected():
-    for t in (-2, 8):
+    for t in (-2, 16):
         with pytest.raises(binding.MQNPMError):
             binding.MQNPM(16, cone(2), [0, 0], [1.0], tile=t)
 
@@ -130,7 +135,7 @@ def test_gradient_agrees_across_tiles_and_with_oracle(model):
     lo, go = om.batch_loss_grad(x, illum, ys, scale)
     xd = torch.from_numpy(np.ascontiguousarray(x).astype(np.float32).reshape(-1)).to(DEV)
     grads = []
-    for t in (0, 1, 6, 7):
+    for t in (0, 1, 6, 15):
         h = binding.MQNPM(n, kd, so, [1.0] * w.S, model=model, krylov_tol=1e-6, max_batch=2, tile=t)
         h.set_measurements(c64(ys).reshape(-1))
         g, loss, _ = h.grad_batch(xd, illum, scale)
