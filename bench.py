@@ -75,11 +75,12 @@ def fp32_peak_tflops():
 
 # ------------------------------------------------------- pass-3 DRAM traffic
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of k_pass3 at
-# n = 128 from one ncu capture of `bench.py --green-only --batch 4` (4 slots
-# per launch), per slot.  It applies only while the sources the kernel is
-# compiled from are the captured ones (digest below); otherwise the bench
-# reports traffic as null.
-PASS3_CAPTURE = {"n": 128, "bytes_per_slot": 126668608, "sources_sha256_16": "77f4dab900a63162"}
+# n = 128 from one ncu capture of `bench.py --green-only --batch 4 --tile 0`
+# (4 slots per launch, the default z-pass shape), per slot.  It applies only
+# while the sources the kernel is compiled from are the captured ones (digest
+# below) and the run uses the captured z-pass shape (tile bits 2-3);
+# otherwise the bench reports traffic as null.
+PASS3_CAPTURE = {"n": 128, "bytes_per_slot": 126649600, "z_tile_bits": 0, "sources_sha256_16": "8b1d45e675aa3dc8"}
 PASS3_SOURCES = ("common.cuh", "fft.cuh", "green_passes.cuh", "green_inst.cu")
 
 
@@ -98,8 +99,10 @@ def pass3_alu_view(n: int, prof: dict, ms: float):
             "convention": "5 P log2 P per transform + 6 per K_hat product; peak = 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"}
 
 
-def pass3_traffic(n: int, slots_per_launch: float):
+def pass3_traffic(n: int, slots_per_launch: float, tile: int):
     """Captured per-slot traffic x slots per launch, or None if stale."""
+    if (tile >> 2) & 3 != PASS3_CAPTURE["z_tile_bits"]:
+        return None
     import hashlib
     d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2307_02043_gb300", "csrc")
     hsh = hashlib.sha256()
@@ -186,7 +189,7 @@ def subset_of(w):
     return so
 
 
-def make_problem(w, dev, torch, binding, seed_shift=0):
+def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1):
     """Synthetic measurements and alpha_s, produced with the library itself."""
     kd = synth.illumination_dirs(w)
     so = subset_of(w)
@@ -195,7 +198,7 @@ def make_problem(w, dev, torch, binding, seed_shift=0):
     common = dict(model=w.model, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=w.krylov_tol,
                   dual_iters=w.dual_iters, gamma=w.gamma, step=w.step, max_batch=max(len(s) for s in subs),
                   krylov_maxit=1000)
-    setup = binding.MQNPM(w.n, kd, so, [1.0] * w.S, **dict(common, krylov_tol=1e-6))
+    setup = binding.MQNPM(w.n, kd, so, [1.0] * w.S, **dict(common, krylov_tol=1e-6, tile=tile))
     ys = []
     for c0 in range(0, w.L, setup.max_batch):
         il = list(range(c0, min(w.L, c0 + setup.max_batch)))
@@ -208,7 +211,7 @@ def make_problem(w, dev, torch, binding, seed_shift=0):
     start = torch.from_numpy(synth.power_start(w).astype(np.float32)).to(dev).reshape(-1)
     alpha = [setup.lipschitz(list(s), w.S / w.L, start, iters=10) for s in subs]
     setup.close()
-    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, **common)
+    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, **common)
     h.set_measurements(y.reshape(-1))
     return h, y, alpha, kd, so, subs
 
@@ -395,7 +398,8 @@ def green_only(args, torch, binding):
     captures): prints per-pass times and achieved GB/s as one JSON line."""
     w = synth.workload(args.workload)
     dev = torch.device("cuda", 0)
-    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, max_batch=args.batch)
+    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, max_batch=args.batch,
+                      tile=args.tile)
     g = torch.Generator(device=dev).manual_seed(0)
     v = torch.randn(args.batch * w.N, dtype=torch.complex64, device=dev, generator=g)
     for _ in range(args.warmup):
@@ -421,7 +425,7 @@ def grad_only(args, torch, binding):
     dev = torch.device("cuda", 0)
     subs = synth.subsets(w)
     h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, model=w.model,
-                      krylov_tol=w.krylov_tol, max_batch=max(len(q) for q in subs))
+                      krylov_tol=w.krylov_tol, max_batch=max(len(q) for q in subs), tile=args.tile)
     h.set_measurements(torch.zeros(w.L * w.n * w.n, dtype=torch.complex64, device=dev))
     x = 0.5 * torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
     illum = [int(i) for i in subs[0]]
@@ -551,6 +555,8 @@ def main():
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="launch-shape tile of the Green's passes (-1: autotuned when a handle is created)")
     ap.add_argument("--serve-uneven", action="store_true",
                     help="uneven request mix: admission by HBM budget, round-robin iterations, latency percentiles")
     ap.add_argument("--hbm-budget-gb", type=float, default=24.0, help="HBM budget of --serve-uneven")
@@ -589,7 +595,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     w = synth.workload(args.workload)
-    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding)
+    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile)
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
     # Set-up iterations from x0 = 0: the S initial steps of Algorithm 4.1 and the
     # reconstruction up to iteration SETUP_ITERS, so that the warm-up and timed
@@ -690,7 +696,8 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_pass3 (" + names[dom] + ")" if dom == 2 else names[dom],
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": pass3_traffic(n, prof["slot_launches"] / max(1, prof["calls"])) if dom == 2 else None,
+                     "traffic": pass3_traffic(n, prof["slot_launches"] / max(1, prof["calls"]), h.tile_info()["tile"])
+                     if dom == 2 else None,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_slot": per_slot[dom],
                      "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof["calls"])),
