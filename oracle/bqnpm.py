@@ -72,6 +72,20 @@ class BQNPM:
             f += 0.5 * float(np.vdot(r, r).real)
         return f / self.L + self.lam * tvops.tv(x, self.kind)
 
+    def bias_error(self, x_prev: np.ndarray, s_prime: int) -> float:
+        """e_k^2 of the convergence validation (Section 6), taken literally:
+        || (1/S) sum_{s != s'} (grad F_s(x_{k-1}) - g_s^k) ||^2 with
+        g_s^k = grad F_{s'}(x_{k-1}) for every s (strategies I and II,
+        Section 4.2)."""
+        _, g_sp = self.grad_F(x_prev, s_prime)
+        acc = np.zeros_like(g_sp)
+        for s in range(self.S):
+            if s != s_prime:
+                _, g_s = self.grad_F(x_prev, s)
+                acc += g_s - g_sp
+        acc /= self.S
+        return float(np.vdot(acc, acc).real)
+
     def pick(self, k: int) -> int:
         if k <= self.S:
             return k - 1

@@ -99,3 +99,26 @@ def test_bqnpm_strategy2_uses_draws():
                       draws=draws, dual_iters=5)
     opt.run(np.zeros((6, 6, 6)), 5)
     assert [h["s"] for h in opt.history][2:] == list(draws[:3])
+
+
+def test_bias_error_pins():
+    """e_k^2 of Section 6, summed literally over s != s', against: the
+    identity (1/S) sum_{s != s'} (grad F_s - grad F_{s'}) = grad F - grad F_{s'}
+    with grad F the full-batch gradient (1/L) sum_l grad f_l (F_s = (S/L) sum
+    over S_s, Eq. 4.1); zero for one subset; zero when every subset holds the
+    same illuminations."""
+    w, m, xt, ys = tiny_setup()
+    subs = synth.subsets(w)
+    opt = bqnpm.BQNPM(m, ys, subs, [1.0] * len(subs), lam=1e-4, box=w.box)
+    x = 0.5 * xt
+    for sp in range(len(subs)):
+        e2 = opt.bias_error(x, sp)
+        _, g_full = m.batch_loss_grad(x, np.arange(w.L), ys, 1.0 / w.L)
+        _, g_sp = opt.grad_F(x, sp)
+        d = g_full - g_sp
+        assert e2 > 0
+        assert abs(e2 - float(np.vdot(d, d).real)) <= 1e-12 * e2
+    one = bqnpm.BQNPM(m, ys, [np.arange(w.L)], [1.0], lam=1e-4, box=w.box)
+    assert one.bias_error(x, 0) == 0.0
+    same = bqnpm.BQNPM(m, ys, [subs[0], subs[0]], [1.0, 1.0], lam=1e-4, box=w.box)
+    assert same.bias_error(x, 1) <= 1e-30
