@@ -220,6 +220,17 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info);
 int mqnpm_lipschitz(mqnpm_handle* h, const int* illum, int nb, double scale, const float* start,
                     int iters, double* alpha_out);
 
+/* Convergence diagnostics of Section 6 (off the hot path: one full and one
+ * subset gradient).  x_prev = x_{k-1}, x_cur = x_k (device N floats; x_cur may
+ * be NULL), s_prime = the subset iteration k used (mqnpm_step_info.subset).
+ * out (host, 3 doubles): out[0] = e_k^2 = ||(1/S) sum_{s != s'} (grad F_s(x_{k-1})
+ * - g_s^k)||^2 with g_s^k = grad F_{s'}(x_{k-1}) (strategies I and II), computed
+ * as ||grad F - grad F_{s'}||^2 with grad F = (1/L) sum_l grad f_l; out[1] =
+ * ||x_k - x_{k-1}||^2 (0 without x_cur); out[2] = (1/L) sum_l f_l(x_{k-1}).
+ * With warm_start the forward solves start from, and refresh, the stored
+ * fields.  Requires mqnpm_set_measurements; NOT_CONVERGED as mqnpm_grad_batch. */
+int mqnpm_diagnostics(mqnpm_handle* h, const float* x_prev, const float* x_cur, int s_prime, double* out);
+
 /* Checkpoint of the outer-loop state (k, tau_s, rank flags, xbar_s, gbar_s,
  * u_s, dual field and, with warm_start, the stored forward fields).  With
  * buf == NULL, *size receives the byte count; else buf (host, *size bytes)

@@ -91,6 +91,8 @@ SIGNATURES = {
     "mqnpm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "mqnpm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "mqnpm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "mqnpm_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_tile_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_prox_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
@@ -262,6 +264,20 @@ class MQNPM:
     def launch_count(self) -> int:
         """Kernels launched by this handle since creation."""
         return int(self.lib.mqnpm_launch_count(self._h))
+
+    def diagnostics(self, x_prev: torch.Tensor, s_prime: int, x_cur: Optional[torch.Tensor] = None,
+                    allow_not_converged: bool = False) -> dict:
+        """Section 6 convergence diagnostics at iteration k: the bias error e_k^2,
+        ||x_k - x_{k-1}||^2 and the full data term at x_{k-1}."""
+        _check_cuda(x_prev, torch.float32, self.N, "x_prev", self.device)
+        if x_cur is not None:
+            _check_cuda(x_cur, torch.float32, self.N, "x_cur", self.device)
+        out = (ctypes.c_double * 3)()
+        self._stream()
+        rc = self.lib.mqnpm_diagnostics(self._h, _ptr(x_prev), _ptr(x_cur) if x_cur is not None else None,
+                                        int(s_prime), out)
+        self._raise(rc, allow_not_converged)
+        return {"bias_error": out[0], "step_sq": out[1], "data_term": out[2]}
 
     def tile_info(self) -> dict:
         """Launch shapes of the Green's passes and the autotuner's timings (ms per apply)."""

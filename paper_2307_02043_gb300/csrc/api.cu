@@ -449,6 +449,30 @@ int mqnpm_grad_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, 
   return grad_batch_impl(h, x, illum, nb, scale, grad_out, loss_out, krylov_iters_out, true, nullptr);
 }
 
+int mqnpm_diagnostics(mqnpm_handle* h, const float* x_prev, const float* x_cur, int s_prime, double* out) {
+  if (!h || !x_prev || !out || s_prime < 0 || s_prime >= h->S)
+    return set_error(h, MQNPM_ERR_INVALID_ARG, "diagnostics: bad arguments");
+  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "diagnostics: measurements not set");
+  CK(cudaSetDevice(h->device));
+  // h->g and h->vq hold a step's gradient and quasi-Newton point only within
+  // mqnpm_step, so they serve as scratch here
+  std::vector<int> all(h->L);
+  for (int l = 0; l < h->L; ++l) all[l] = l;
+  double loss = 0.0;
+  int rc = grad_batch_impl(h, x_prev, all.data(), h->L, 1.0 / h->L, h->g, &loss, nullptr, true, nullptr);
+  if (rc != MQNPM_OK && rc != MQNPM_ERR_NOT_CONVERGED) return rc;
+  const std::vector<int>& sub = h->subsets[s_prime];
+  const int rc2 = grad_batch_impl(h, x_prev, sub.data(), (int)sub.size(), (double)h->S / h->L, h->vq, nullptr,
+                                  nullptr, true, nullptr);
+  if (rc2 != MQNPM_OK && rc2 != MQNPM_ERR_NOT_CONVERGED) return rc2;
+  double d3[3];
+  CK(vec_reduce(h, 1, h->g, h->vq, x_cur ? x_cur : x_prev, x_prev, d3));
+  out[0] = d3[0];
+  out[1] = x_cur ? d3[2] : 0.0;
+  out[2] = loss;
+  return rc != MQNPM_OK ? rc : rc2;
+}
+
 int mqnpm_loss_batch(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, double* loss_out,
                      int* krylov_iters_out) {
   if (!h || !x || !illum || !loss_out || nb < 1) return set_error(h, MQNPM_ERR_INVALID_ARG, "loss_batch: bad arguments");

@@ -78,6 +78,35 @@ def test_step_trajectory_matches_oracle(ls32, warm):
     h.close()
 
 
+def test_diagnostics_match_oracle(ls32):
+    """Section 6 convergence diagnostics on the oracle's own iterates: the bias
+    error e_k^2 (summed literally over s != s' by the oracle), the squared step
+    ||x_k - x_{k-1}||^2 and the full data term."""
+    w, kd, om, ys, subs, so, alpha, opt, xs = ls32
+    h = handle(w, kd, so, alpha)
+    h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+    for k in (w.S + 1, w.outer_iters):
+        sp = opt.history[k - 1]["s"]
+        d = h.diagnostics(f32(xs[k - 1]).reshape(-1), sp, f32(xs[k]).reshape(-1))
+        e2 = opt.bias_error(xs[k - 1], sp)
+        dx2 = float(np.sum((xs[k].astype(np.float32).astype(np.float64)
+                            - xs[k - 1].astype(np.float32).astype(np.float64)) ** 2))
+        data = opt.full_cost(xs[k - 1]) - w.lam * physics_tv(xs[k - 1], w.tv)
+        assert abs(d["bias_error"] - e2) <= 2e-4 * e2, (k, d, e2)
+        assert abs(d["step_sq"] - dx2) <= 1e-5 * dx2, (k, d, dx2)
+        assert abs(d["data_term"] - data) <= 1e-4 * abs(data), (k, d, data)   # objective bound
+    # without x_k the step term is zero; a subset index out of range is rejected
+    assert h.diagnostics(f32(xs[1]).reshape(-1), 0)["step_sq"] == 0.0
+    with pytest.raises(binding.MQNPMError):
+        h.diagnostics(f32(xs[1]).reshape(-1), w.S)
+    h.close()
+
+
+def physics_tv(x, kind):
+    from oracle import tv as otv
+    return otv.tv(x, kind)
+
+
 def test_strategy2_trajectory_matches_oracle(ls32):
     """Strategy II (s' drawn uniformly, seeded draws passed to both sides) on
     config 1: per-iterate error against the FP64 oracle."""
