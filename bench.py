@@ -195,7 +195,7 @@ def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1):
     so = subset_of(w)
     subs = synth.subsets(w)
     xt = torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
-    common = dict(model=w.model, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=w.krylov_tol,
+    common = dict(model=w.model, h=w.h, kb=w.kb, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=w.krylov_tol,
                   dual_iters=w.dual_iters, gamma=w.gamma, step=w.step, max_batch=max(len(s) for s in subs),
                   krylov_maxit=1000)
     setup = binding.MQNPM(w.n, kd, so, [1.0] * w.S, **dict(common, krylov_tol=1e-6, tile=tile))
@@ -230,7 +230,7 @@ class PlainPath:
         self.dev = dev
         self.kd = kd
         self.y = y.view(w.L, w.n, w.n)
-        n, P, kb = self.n, self.P, w.kb
+        n, P, kb = self.n, self.P, w.kb * w.h   # dimensionless: lengths in voxels
         idx = torch.arange(P, device=dev, dtype=torch.float64)
         off = torch.where(idx < n, idx, idx - P)
         dz, dy, dx = torch.meshgrid(off, off, off, indexing="ij")
@@ -257,7 +257,7 @@ class PlainPath:
 
     def uin(self, l):
         k = self.kd[l]
-        ph = self.w.kb * (k[0] * self.X + k[1] * self.Y + k[2] * self.Z)
+        ph = self.w.kb * self.w.h * (k[0] * self.X + k[1] * self.Y + k[2] * self.Z)
         return self.t.exp(1j * ph).to(self.t.complex64)
 
     def bicgstab(self, A, b, x0, tol, maxit=1000):
@@ -319,7 +319,7 @@ def oracle_sample(w, x_np, seconds_hint=20.0):
     forward solve at the workload size (K_hat set-up excluded)."""
     from oracle import physics
     kd = synth.illumination_dirs(w)
-    m = physics.Model(w.n, kd[:1], "ls", tol=1e-30, maxit=1)
+    m = physics.Model(w.n, kd[:1], "ls", kb=w.kb, h=w.h, tol=1e-30, maxit=1)
     uin = m.u_in(0)
     A = lambda p: p - m.G(x_np * p)  # noqa: E731
     physics.bicgstab(A, uin, uin, 1e-30, 1)       # warm caches / first-touch
@@ -340,7 +340,7 @@ def run_reference(args, world, rank):
     x_np = synth.phantom(w)
     from oracle import physics
     kd = synth.illumination_dirs(w)
-    m = physics.Model(w.n, kd[:1], "ls", tol=1e-30, maxit=1)
+    m = physics.Model(w.n, kd[:1], "ls", kb=w.kb, h=w.h, tol=1e-30, maxit=1)
     uin = m.u_in(0)
     A = lambda p: p - m.G(x_np * p)  # noqa: E731
     for _ in range(args.warmup):
@@ -398,7 +398,7 @@ def green_only(args, torch, binding):
     captures): prints per-pass times and achieved GB/s as one JSON line."""
     w = synth.workload(args.workload)
     dev = torch.device("cuda", 0)
-    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, max_batch=args.batch,
+    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, max_batch=args.batch, h=w.h, kb=w.kb,
                       tile=args.tile)
     g = torch.Generator(device=dev).manual_seed(0)
     v = torch.randn(args.batch * w.N, dtype=torch.complex64, device=dev, generator=g)
@@ -424,7 +424,7 @@ def grad_only(args, torch, binding):
     w = synth.workload(args.workload)
     dev = torch.device("cuda", 0)
     subs = synth.subsets(w)
-    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, model=w.model,
+    h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, model=w.model, h=w.h, kb=w.kb,
                       krylov_tol=w.krylov_tol, max_batch=max(len(q) for q in subs), tile=args.tile)
     h.set_measurements(torch.zeros(w.L * w.n * w.n, dtype=torch.complex64, device=dev))
     x = 0.5 * torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)

@@ -4,7 +4,10 @@ The workloads mirror the shapes of the paper's optical-diffraction-tomography
 experiments (Section 6: spheres/ellipsoids immersed in a homogeneous medium,
 plane waves on an illumination cone, complex noisy fields on a detector
 plane), at the grid sizes used for parity and measurement.  Units: voxel
-h = 1, background wavelength = 4 voxels, so k_b = pi/2 per voxel.
+h = 1, background wavelength = 4 voxels, so k_b = pi/2 per voxel, except for
+the workloads in physical units (the geometry of the paper's simulated 64^3
+and real-data 96^3 experiments), where h is the voxel edge in metres and
+k_b = 2 pi eta_m / lambda_vacuum.
 """
 from __future__ import annotations
 
@@ -45,6 +48,9 @@ class Workload:
     gamma: float = 0.8
     step: float = 1.0           # a_k (constant)
     margin: int = 2             # voxels kept free of objects at every face
+    voxel_m: float = 0.0        # physical units: voxel edge (m); 0 = the lambda/4 voxel convention
+    wavelength_m: float = 0.0   # vacuum wavelength (m)
+    eta_m: float = 0.0          # refractive index of the medium
 
     @property
     def S(self) -> int:
@@ -60,7 +66,13 @@ class Workload:
 
     @property
     def kb(self) -> float:
+        if self.voxel_m > 0:
+            return 2.0 * math.pi * self.eta_m / self.wavelength_m
         return math.pi / 2.0
+
+    @property
+    def h(self) -> float:
+        return self.voxel_m if self.voxel_m > 0 else 1.0
 
     def with_(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)
@@ -87,6 +99,26 @@ WORKLOADS: Dict[str, Workload] = {
         contrast_max=0.04, background=(0.005, 128 / 6), snr_db=30.0, batch=8,
         tv="iso", lam=1e-3, box=(0.0, 0.06), krylov_tol=1e-4, dual_iters=20,
         outer_iters=10),
+    # The paper's simulated strongly scattering experiment in physical units
+    # (Section 6): 64^3 voxels of 50 nm, vacuum wavelength 406 nm, medium index
+    # 1.333, maximal index 1.43 (contrast (1.43/1.333)^2 - 1), 60 plane waves on
+    # a 42-degree cone, S = 4, lambda = 1/64^3.
+    "sim64": Workload(
+        name="sim64", config_id=6, n=64, model="ls", L=60, cone_deg=42.0,
+        shape="ellipsoid", n_objects=8, size_range=(3.0, 12.0),
+        contrast_max=(1.43 / 1.333) ** 2 - 1, background=(0.0, 0.0), snr_db=30.0, batch=15,
+        tv="iso", lam=1.0 / 64 ** 3, box=(0.0, 0.16), krylov_tol=1e-5, dual_iters=20,
+        outer_iters=20, voxel_m=50e-9, wavelength_m=406e-9, eta_m=1.333),
+    # Geometry of the paper's real-data experiment (a yeast cell, Section 6):
+    # 96^3 voxels of 99 nm, 532 nm, medium 1.338, 60 plane waves on a 35-degree
+    # cone, lambda = 2/96^3; the cell is a synthetic ellipsoid cluster (the
+    # measured data are not available).
+    "yeast96": Workload(
+        name="yeast96", config_id=7, n=96, model="ls", L=60, cone_deg=35.0,
+        shape="ellipsoid", n_objects=6, size_range=(4.0, 20.0),
+        contrast_max=(1.40 / 1.338) ** 2 - 1, background=(0.0, 0.0), snr_db=30.0, batch=15,
+        tv="iso", lam=2.0 / 96 ** 3, box=(0.0, 0.1), krylov_tol=1e-5, dual_iters=20,
+        outer_iters=20, voxel_m=99e-9, wavelength_m=532e-9, eta_m=1.338),
     # Large strong-scattering case.
     "ls192": Workload(
         name="ls192", config_id=5, n=192, model="ls", L=120, cone_deg=60.0,

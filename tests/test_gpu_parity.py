@@ -179,6 +179,35 @@ def test_grad_batch_matches_oracle(model, n, nb, max_batch):
     h.close()
 
 
+def test_physical_units_strong_scattering_matches_oracle():
+    """The paper's simulated set-up in physical units (50 nm voxels, 406 nm,
+    medium index 1.333, contrast up to (1.43/1.333)^2 - 1 = 0.15) on a 32^3
+    grid: forward fields and the mini-batch gradient against the oracle with
+    the same h (metres) and k_b (per metre)."""
+    n = 32
+    w = synth.small("sim64", n=n, L=4, batch=2)
+    kd = synth.illumination_dirs(w)
+    xt = synth.phantom(w)
+    assert xt.max() > 0.1
+    om = physics.Model(n, kd, "ls", kb=w.kb, h=w.h, tol=1e-12)
+    ys = physics.simulate(om, xt, synth.noise_draws(w), w.snr_db)
+    so = np.zeros(w.L, dtype=np.int32)
+    for s_, ii in enumerate(synth.subsets(w)):
+        so[ii] = s_
+    h = make_handle(n, kd, so, [1.0] * w.S, h=w.h, kb=w.kb, krylov_tol=1e-6, max_batch=2)
+    h.set_measurements(c64(ys).reshape(-1))
+    y, its = h.forward(f32(xt).reshape(-1), [0, 1])
+    y = y.cpu().numpy()
+    for b, l in enumerate([0, 1]):
+        assert rel(y[b], om.forward(xt, l)) < 1e-4, (l, its)
+    x = 0.7 * xt
+    g, loss, its = h.grad_batch(f32(x).reshape(-1), [0, 1], w.S / w.L)
+    lo, go = om.batch_loss_grad(x, [0, 1], ys, w.S / w.L)
+    assert rel(g.cpu().numpy().reshape(go.shape), go) < 1e-4
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+    h.close()
+
+
 def test_grad_edge_cases():
     """Zero contrast (Krylov converges at start), zero residual (adjoint RHS 0)."""
     n = 16

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 from scipy import integrate
 
+import synth
 from oracle import physics as ph
 
 KB = math.pi / 2.0
@@ -187,3 +188,24 @@ def test_detector_and_lift_are_adjoint():
     v = rand_c(rng, (n, n, n))
     r = rand_c(rng, n * n)
     assert abs(np.vdot(r, m.detect(v)) - np.vdot(m.lift(r), v)) < 1e-12
+
+
+def test_physical_units_enter_only_through_kb_h():
+    """Dimensional analysis of the discretisation (Section 6 reading): with the
+    voxel edge h in metres and k_b = 2 pi eta_m / lambda, the Green's weights
+    k_b^2 h^3 e^{j k_b |D| h} / (4 pi |D| h), the equal-volume self term and the
+    incident phases depend on k_b h only, so the paper's 50 nm / 406 nm / 1.333
+    set-up equals the unit-voxel model with k_b = k_b h."""
+    n = 8
+    w = synth.small("sim64", n=n, L=2, batch=1)
+    kd = synth.illumination_dirs(w)
+    x = synth.phantom(w)
+    assert x.max() > 0.1                       # strong scattering: (1.43/1.333)^2 - 1
+    kbh = w.kb * w.h
+    assert abs(kbh - 2 * math.pi * 1.333 * 50 / 406) < 1e-12
+    mp = ph.Model(n, kd, model="ls", kb=w.kb, h=w.h, tol=1e-13)
+    mu = ph.Model(n, kd, model="ls", kb=kbh, h=1.0, tol=1e-13)
+    assert np.allclose(mp.khat, mu.khat, rtol=0, atol=1e-12 * np.abs(mu.khat).max())
+    for l in range(2):
+        yp, yu = mp.forward(x, l), mu.forward(x, l)
+        assert np.max(np.abs(yp - yu)) <= 1e-10 * np.max(np.abs(yu))
