@@ -15,8 +15,13 @@ and in the CUDA library alike:
   w_0 = [exp(j k_b a)(1 - j k_b a) - 1] / k_b^2, a = (3/(4 pi))^(1/3) h, the
   exact integral of the Green's function over the sphere of volume h^3;
 * LS: u = u_in + G (x * u); Born: u_sc = G (x * u_in);
-* detector: the scattered field u - u_in on the last z-slice (M = n^2);
-* gradient: grad f = Re(conj(u) * z), z = (I - G^H X)^{-1} G^H S^T r.
+* detector: the scattered field u - u_in on the last z-slice (M = n^2), or,
+  with a remote detector, that slice carried a distance d further along z by
+  the angular spectrum with a pupil of numerical aperture na (relative to the
+  medium): D = F^-1 diag(H) F with H = exp(j k_z d) 1[kx^2 + ky^2 <= (na k_b)^2],
+  k_z = sqrt(k_b^2 - kx^2 - ky^2) on the branch with Im k_z >= 0, F the 2D DFT
+  of the n x n slice (periodic; frequencies 2 pi fftfreq(n, h));
+* gradient: grad f = Re(conj(u) * z), z = (I - G^H X)^{-1} G^H S^T D^H r.
 
 Arrays are indexed [z, y, x] (x fastest in memory).
 """
@@ -81,6 +86,21 @@ def green_apply(v: np.ndarray, khat: np.ndarray, adjoint: bool = False) -> np.nd
     return out[:n, :n, :n]
 
 
+def transfer_function(n: int, kb: float, h: float, distance: float, na: float) -> np.ndarray:
+    """H[ky, kx] of the angular-spectrum propagation over `distance` with the
+    pupil kx^2 + ky^2 <= (na kb)^2 (remote-detector reading of Section 6)."""
+    f = 2.0 * math.pi * np.fft.fftfreq(n, d=h)
+    KY, KX = np.meshgrid(f, f, indexing="ij")
+    k2 = KX * KX + KY * KY
+    kz = np.sqrt((kb * kb - k2).astype(np.complex128))   # principal root: Im >= 0
+    return np.where(k2 <= (na * kb) ** 2, np.exp(1j * kz * distance), 0.0)
+
+
+def propagate(field: np.ndarray, H: np.ndarray, adjoint: bool = False) -> np.ndarray:
+    """D f = F^-1 (H F f) on an n x n slice; D^H uses conj(H)."""
+    return np.fft.ifft2((np.conj(H) if adjoint else H) * np.fft.fft2(field))
+
+
 def incident_field(n: int, kdir: Sequence[float], kb: float, h: float = 1.0) -> np.ndarray:
     """u_in(r) = exp(j kb <kdir, r>), r = (idx - n/2) h, shape (n, n, n) [z, y, x]."""
     c = (np.arange(n) - n / 2.0) * h
@@ -131,7 +151,8 @@ class Model:
 
     def __init__(self, n: int, kdirs: np.ndarray, model: str = "ls",
                  kb: float | None = None, h: float = 1.0,
-                 tol: float = 1e-12, maxit: int = 2000):
+                 tol: float = 1e-12, maxit: int = 2000,
+                 det_distance: float = 0.0, det_na: float = 0.0):
         self.n = n
         self.h = h
         self.kb = kb_default(h) if kb is None else kb
@@ -140,6 +161,8 @@ class Model:
         self.tol = tol
         self.maxit = maxit
         self.khat = green_hat(n, self.kb, h)
+        # remote detector (det_na > 0): angular-spectrum transfer function
+        self.H = transfer_function(n, self.kb, h, det_distance, det_na) if det_na > 0 else None
 
     # -- operators ---------------------------------------------------------
     def G(self, v: np.ndarray) -> np.ndarray:
@@ -160,13 +183,21 @@ class Model:
         return u, it
 
     def detect(self, usc: np.ndarray) -> np.ndarray:
-        """S: last z-slice of the scattered field, flattened [y, x] (M = n^2)."""
-        return usc[-1].reshape(-1).copy()
+        """S (then D for a remote detector): last z-slice of the scattered
+        field, flattened [y, x] (M = n^2)."""
+        sl = usc[-1]
+        if self.H is not None:
+            sl = propagate(sl, self.H)
+        return sl.reshape(-1).copy()
 
     def lift(self, r: np.ndarray) -> np.ndarray:
-        """S^T: embed a detector vector into the last z-slice of a zero volume."""
+        """S^T (after D^H for a remote detector): embed a detector vector into
+        the last z-slice of a zero volume."""
+        r2 = r.reshape(self.n, self.n)
+        if self.H is not None:
+            r2 = propagate(r2, self.H, adjoint=True)
         out = np.zeros((self.n,) * 3, dtype=np.complex128)
-        out[-1] = r.reshape(self.n, self.n)
+        out[-1] = r2
         return out
 
     def forward(self, x: np.ndarray, l: int) -> np.ndarray:

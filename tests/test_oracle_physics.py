@@ -128,10 +128,12 @@ def _jvp(m, x, l, dx, h=1e-6):
     return (m.forward(x + h * dx, l) - m.forward(x - h * dx, l)) / (2 * h)
 
 
-@pytest.mark.parametrize("model", ["ls", "born"])
-def test_gradient_central_differences(model):
+@pytest.mark.parametrize("model,remote", [("ls", False), ("born", False), ("ls", True)])
+def test_gradient_central_differences(model, remote):
     n = 5
     x, m = small_problem(n, contrast=0.4, model=model)
+    if remote:   # remote detector: the gradient must carry D^H through the lift
+        m = ph.Model(n, m.kdirs, model=model, det_distance=3.0, det_na=0.8)
     rng = np.random.default_rng(7)
     y = rand_c(rng, n * n) * 0.05
     f0, g, _ = m.loss_grad(x, 1, y)
@@ -209,3 +211,39 @@ def test_physical_units_enter_only_through_kb_h():
     for l in range(2):
         yp, yu = mp.forward(x, l), mu.forward(x, l)
         assert np.max(np.abs(yp - yu)) <= 1e-10 * np.max(np.abs(yu))
+
+
+def test_remote_detector_propagation_pins():
+    """Angular-spectrum remote detector: identity at zero distance with an open
+    pupil; a grid plane wave inside the pupil gains exactly exp(j k_z d) (sign of
+    the exp(j <k, r>) convention); two distances compose; D is unitary on the
+    pupil band; <D a, b> = <a, D^H b>; the data term's adjoint (lift) is the
+    transpose of detect."""
+    n, h = 16, 1.0
+    kb = ph.kb_default(h)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    b = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H0 = ph.transfer_function(n, kb, h, 0.0, 100.0)
+    assert np.allclose(ph.propagate(a, H0), a, atol=1e-13)
+    d = 7.5
+    H = ph.transfer_function(n, kb, h, d, 0.9)
+    fx, fy = 2, 1                                # grid frequency inside the pupil
+    kx, ky = 2 * math.pi * fx / (n * h), 2 * math.pi * fy / (n * h)
+    assert kx * kx + ky * ky <= (0.9 * kb) ** 2
+    yy, xx = np.meshgrid(np.arange(n) * h, np.arange(n) * h, indexing="ij")
+    pw = np.exp(1j * (kx * xx + ky * yy))
+    kz = math.sqrt(kb * kb - kx * kx - ky * ky)
+    assert np.allclose(ph.propagate(pw, H), np.exp(1j * kz * d) * pw, atol=1e-12)
+    H1, H2 = ph.transfer_function(n, kb, h, 3.0, 0.9), ph.transfer_function(n, kb, h, 4.5, 0.9)
+    assert np.allclose(ph.propagate(ph.propagate(a, H1), H2), ph.propagate(a, H), atol=1e-12)
+    band = ph.propagate(a, ph.transfer_function(n, kb, h, 0.0, 0.9))   # pupil-limited field
+    assert abs(np.linalg.norm(ph.propagate(band, H)) - np.linalg.norm(band)) < 1e-12 * np.linalg.norm(band)
+    lhs = np.vdot(b, ph.propagate(a, H))
+    rhs = np.vdot(ph.propagate(b, H, adjoint=True), a)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    kd = np.array([[0.0, 0.0, 1.0]])
+    m = ph.Model(n, kd, "born", det_distance=d, det_na=0.9)
+    v = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    r = rng.standard_normal(n * n) + 1j * rng.standard_normal(n * n)
+    assert abs(np.vdot(r, m.detect(v)) - np.vdot(m.lift(r), v)) < 1e-12 * np.linalg.norm(r) * np.linalg.norm(v)
