@@ -112,6 +112,12 @@ typedef struct mqnpm_config {
                               columns per CTA, threads per line or column) of
                               the x, y and z passes, bit 3 two exchange buffers
                               in the z pass (0 = the built-in defaults)       */
+  double det_distance;     /* remote detector (det_na > 0): distance from the last
+                              z-slice to the detector plane, units of h        */
+  double det_na;           /* 0: the detector is the last z-slice; > 0: that
+                              slice propagated by the angular spectrum over
+                              det_distance with the pupil kx^2 + ky^2 <=
+                              (det_na kb)^2 (Section 6 reading)               */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;

@@ -52,6 +52,7 @@ class Config(ctypes.Structure):
         ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
         ("green_hat", ctypes.POINTER(ctypes.c_float)), ("tile", ctypes.c_int),
+        ("det_distance", ctypes.c_double), ("det_na", ctypes.c_double),
     ]
 
 
@@ -172,7 +173,8 @@ class MQNPM:
                  gamma: float = 0.8, tau_max: float = 0.0, krylov_tol: float = 1e-6, krylov_maxit: int = 500,
                  dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
-                 direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1):
+                 direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1,
+                 det_distance: float = 0.0, det_na: float = 0.0):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -216,6 +218,8 @@ class MQNPM:
         cfg.warm_start = int(bool(warm_start))
         cfg.direct_launches = int(bool(direct_launches))
         cfg.tile = int(tile)
+        cfg.det_distance = float(det_distance)
+        cfg.det_na = float(det_na)
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
             if gh.size != (self.n + 1) ** 3:

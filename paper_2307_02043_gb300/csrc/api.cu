@@ -188,7 +188,8 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
       !(cfg->box_lo <= cfg->box_hi) || !(cfg->lambda >= 0) || !(cfg->step > 0) || cfg->dual_iters < 0 ||
       !(cfg->krylov_tol > 0) || cfg->krylov_maxit < 1 || (cfg->model != MQNPM_MODEL_LS && cfg->model != MQNPM_MODEL_BORN) ||
       (cfg->tv != MQNPM_TV_ISO && cfg->tv != MQNPM_TV_ANISO) || (cfg->strategy != 1 && cfg->strategy != 2) ||
-      !(cfg->gamma > 0 && cfg->gamma <= 1.0) || cfg->tile < -1 || cfg->tile >= MQ_TILES) {
+      !(cfg->gamma > 0 && cfg->gamma <= 1.0) || cfg->tile < -1 || cfg->tile >= MQ_TILES ||
+      !(cfg->det_na >= 0.0 && std::isfinite(cfg->det_na)) || !std::isfinite(cfg->det_distance)) {
     fprintf(stderr, "mqnpm_create: invalid configuration\n");
     delete h;
     return MQNPM_ERR_INVALID_ARG;
@@ -286,6 +287,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   need += 8 * B * N * 8;                                   // u zs r rhat p v s t
   need += B * ((size_t)n * n * P + (size_t)n * P * P) * 8; // T1, T2
   need += B * M * 8;                                       // rdet
+  if (cfg->det_na > 0) need += 3 * B * M * 8 + M * 8 + (size_t)n * 8;   // remote detector
   need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
   need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * wprox_part_len() + 600) * 8 + wprox_part_count(wp_blocks) * 8;   // wprox
   need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
@@ -313,6 +315,11 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(w.T1, B * (size_t)n * n * P);
   AL(w.T2, B * (size_t)n * P * P);
   AL(w.rdet, B * M);
+  h->remote = cfg->det_na > 0;
+  if (h->remote) {
+    AL(w.dtmp1, B * M); AL(w.dtmp2, B * M); AL(w.rlift, B * M);
+    AL(h->Hdet, M); AL(h->twn, (size_t)n);
+  }
   AL(w.part1, B * (size_t)w.ctas_row * 1);
   AL(w.part5, B * (size_t)w.ctas_row * 3);
   AL(w.partd, B * (size_t)w.ctas_row);
@@ -378,6 +385,10 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
       (e = (cfg->green_hat ? upload_khat(cfg->green_hat, n, h->khat, s) : build_khat(n, h->h, h->kb, h->khat, s))) !=
           cudaSuccess) {
     set_cuda_error(h, e, "create tables");
+    return fail(MQNPM_ERR_CUDA);
+  }
+  if (h->remote && (e = detector_tables(h, cfg->det_distance, cfg->det_na)) != cudaSuccess) {
+    set_cuda_error(h, e, "remote detector tables");
     return fail(MQNPM_ERR_CUDA);
   }
   h->tau.assign(h->alpha.begin(), h->alpha.end());

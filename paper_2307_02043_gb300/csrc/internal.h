@@ -96,6 +96,7 @@ struct Workspace {
          *s = nullptr, *t = nullptr;
   float2 *T1 = nullptr, *T2 = nullptr;   // transform scratch
   float2* rdet = nullptr;                // [max_batch][M]
+  float2 *dtmp1 = nullptr, *dtmp2 = nullptr, *rlift = nullptr;   // remote detector: [max_batch][M] each
   double *part1 = nullptr, *part5 = nullptr, *partu = nullptr, *partd = nullptr;
   KState* st = nullptr;                  // [max_batch]
   int* illum = nullptr;                  // [max_batch]
@@ -146,6 +147,8 @@ struct mqnpm_handle {
   std::vector<void*> allocations;
   // device tables
   float2 *khat = nullptr, *tw = nullptr, *tab = nullptr, *ymeas = nullptr;
+  bool remote = false;                    // detector behind an angular-spectrum propagation
+  float2 *twn = nullptr, *Hdet = nullptr;  // W_n^j (n) and H / n^2 ([ky][kx], M)
   bool have_meas = false;
   Workspace w;
   WproxWork wp;
@@ -205,6 +208,13 @@ int wprox_part_len();
 size_t wprox_part_count(int max_blocks);   // doubles of the partials buffer
 int wprox_barrier_words();                // unsigned words of the barrier counters
 int woodbury_scal_count();
+
+// detector.cu: remote detector D = F^-1 diag(H) F on the n x n slices
+cudaError_t detector_tables(mqnpm_handle* h, double distance, double na);
+// det (m slices) <- D(det) - y_meas(illum) (y_meas may be null), partials in w.partd
+cudaError_t detector_forward(mqnpm_handle* h, float2* det, int m, const float2* ym, const int* illum);
+// out <- D^H r (m slices)
+cudaError_t detector_adjoint(mqnpm_handle* h, const float2* r, float2* out, int m);
 
 // tune.cu: pick the launch shapes of the Green's passes by timing
 int autotune_tile(mqnpm_handle* h);

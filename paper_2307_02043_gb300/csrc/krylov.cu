@@ -543,6 +543,10 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   GreenCall c = base_call(h, nb, true);
   c.pro = PRO_LIFT;
   c.pa.rdet = w.rdet;
+  if (h->remote) {                     // S^T D^H r_det
+    CK(detector_adjoint(h, w.rdet, w.rlift, nb));
+    c.pa.rdet = w.rlift;
+  }
   c.epi = EPI_INIT;                    // r_0 = b = G^H S^T r_det (start z_0 = 0)
   c.ea.out = w.r;
   c.ea.out2 = w.rhat;
@@ -577,7 +581,8 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     int rc = forward_ls(h, m, x, it_chunk, 2, 0);
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
     if (rc != MQNPM_OK) worst = rc;
-    k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, ym, det_out, h->n, N, w.partd);
+    k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, h->remote ? nullptr : ym, det_out,
+                                                     h->n, N, w.partd);
   } else {
     GreenCall c = base_call(h, m, false);
     c.pro = PRO_BORN;
@@ -586,12 +591,13 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     c.pa.illum = w.illum;
     c.epi = EPI_DETECT;
     c.ea.out2 = det_out;
-    c.ea.ymeas = ym;
+    c.ea.ymeas = h->remote ? nullptr : ym;
     c.ea.illum = w.illum;
     c.part_epi = w.partd;
     CK(glaunch(h, c, s));
   }
   CK(cudaGetLastError());
+  if (h->remote) CK(detector_forward(h, det_out, m, ym, w.illum));   // D(slice) - y, partials replaced
   k_sum_all<<<1, 256, 0, s>>>(w.partd, m * w.ctas_row, w.dscal);
   CK(cudaMemcpyAsync(w.h_scal, w.dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
   h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + 1;
@@ -614,6 +620,10 @@ int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, double 
     GreenCall c = base_call(h, m, true);
     c.pro = PRO_LIFT;
     c.pa.rdet = w.rdet;
+    if (h->remote) {
+      CK(detector_adjoint(h, w.rdet, w.rlift, m));
+      c.pa.rdet = w.rlift;
+    }
     c.epi = EPI_PLAIN;
     c.ea.out = w.zs;
     CK(glaunch(h, c, s));
@@ -743,6 +753,11 @@ int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, cons
       GreenCall c2 = base_call(h, m, true);
       c2.pro = PRO_LIFT;                // G^H S^T (.)
       c2.pa.rdet = w.rdet;
+      if (h->remote) {                  // J = D S G(. u_in): D, then D^H before the lift
+        CK(detector_forward(h, w.rdet, m, nullptr, w.illum));
+        CK(detector_adjoint(h, w.rdet, w.rlift, m));
+        c2.pa.rdet = w.rlift;
+      }
       c2.epi = EPI_PLAIN;
       c2.ea.out = w.zs;
       CK(glaunch(h, c2, s));
