@@ -127,6 +127,31 @@ def test_strategy2_trajectory_matches_oracle(ls32):
     h.close()
 
 
+def test_full_batch_variant_matches_oracle():
+    """S = 1 (every illumination in one subset: the full-batch variant of the
+    method, Section 4.2): every iteration after the first takes the SR1 branch
+    on the full gradient; per-iterate error against the FP64 oracle."""
+    w = synth.small("ls32", n=16, L=4, batch=4)
+    assert w.S == 1
+    kd, om, xt, ys, subs, so = setup(w)
+    alpha = [om.lipschitz(subs[0], 1.0 / w.L, synth.power_start(w), 20)]
+    iters = 6
+    opt = bqnpm.BQNPM(om, ys, subs, alpha, lam=w.lam, box=w.box, kind=w.tv, dual_iters=w.dual_iters,
+                      gamma=w.gamma, step=w.step)
+    xs = opt.run(np.zeros((w.n,) * 3), iters)
+    assert all("sr1" in hh for hh in opt.history[1:])
+    h = handle(w, kd, so, alpha)
+    h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+    x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+    for k in range(1, iters + 1):
+        info = h.step(x)
+        assert info["subset"] == 0
+        xg = x.cpu().numpy().astype(np.float64).reshape(xs[k].shape)
+        err = np.linalg.norm(xg - xs[k]) / np.linalg.norm(xs[k])
+        assert err < 2e-3, (k, err)
+    h.close()
+
+
 def test_step_trajectory_rank_above_8():
     """S = 12 subsets (L = 24, b = 2 at 16^3: the subset counts of the uneven
     request mix go up to 15): the rank-12 metric and prox follow the oracle."""
