@@ -86,8 +86,15 @@ MQ_D long long globaltimer() {
 }
 
 MQ_D bool tracer(const WpArgs& a) { return a.trace && blockIdx.x == 0 && threadIdx.x == 0; }
+// Block 0's phase accumulators and the time of the last barrier live in shared
+// memory while the kernel runs (written to the trace at its end), so the
+// tracing thread does no global read-modify-write on the barrier path.
+MQ_D long long* tr_acc() {
+  __shared__ long long acc[TR_SLOTS + 1];   // [TR_SLOTS] = time of the last barrier
+  return acc;
+}
 MQ_D void tr_add(const WpArgs& a, int slot, long long dt) {
-  if (tracer(a)) a.trace[2 * TR_ACC + slot] += dt;
+  if (tracer(a)) tr_acc()[slot] += dt;
 }
 
 // Four consecutive floats as an addressable array.
@@ -224,7 +231,8 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
       a.trace[2 * ep.all] = tag;
       a.trace[2 * ep.all + 1] = t;
     }
-    a.trace[2 * TR_ACC + 5] += t - t_in;
+    tr_acc()[5] += t - t_in;
+    tr_acc()[TR_SLOTS] = t;
   }
   if (!s_ok) return false;
   if constexpr (NV > 0) {
@@ -393,19 +401,21 @@ struct NewtonState {
 };
 
 // One decision of Algorithm 4.3 after phi was evaluated at beta_eval
-// (tot[0..S) = U^T(w - clip(z))) with htri = sum_{inner} u u^T (upper triangle).
-// Accept the trial if it reduces ||phi|| (or halving is exhausted), stop at
-// ||phi|| <= tol_abs, else take the Newton step -H^{-1} phi from the accepted
-// point, H = I + htri/tau; a rejected trial is halved.  Returns 1 when done.
+// (tot[0..S) = U^T(w - clip(z))) with hf = sum_{inner} u u^T / tau (upper
+// triangle, FP32).  Accept the trial if it reduces ||phi|| (or halving is
+// exhausted), stop at ||phi||^2 <= tol2, else take the Newton step -H^{-1} phi
+// from the accepted point, H = I + hf; a rejected trial is halved.  The norms
+// are compared squared (no FP64 square root: a long sequence on this device).
+// tol2 is the squared tolerance.  Returns 1 when done.
 template <int S>
-__device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, const double* htri, double inv_tau,
-                                          double tol_abs, int maxit, bool out_of_evals) {
-  double phi[S], nphi = 0.0;
+__device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, const float* hf, double tol2,
+                                          int maxit, bool out_of_evals) {
+  double phi[S], nphi = 0.0;   // nphi: ||phi||^2
+#pragma unroll
   for (int s = 0; s < S; ++s) {
     phi[s] = tot[s] + ns.beta_eval[s];
-    nphi += phi[s] * phi[s];
+    nphi = fma(phi[s], phi[s], nphi);
   }
-  nphi = sqrt(nphi);
   const bool accept = *ns.first || nphi < *ns.nphi_cur || *ns.halvings >= 30 || !isfinite(*ns.nphi_cur);
   *ns.first = false;
   *ns.accepted_last = accept ? 1 : 0;
@@ -420,7 +430,7 @@ __device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, 
     ns.phi_cur[s] = phi[s];
   }
   *ns.nphi_cur = nphi;
-  if (nphi <= tol_abs || *ns.accepted >= maxit || out_of_evals || !isfinite(nphi)) return 1;
+  if (nphi <= tol2 || *ns.accepted >= maxit || out_of_evals || !isfinite(nphi)) return 1;
   // Newton direction -H^{-1} phi, solved in FP32 (see chol_factor_f)
   float H[S * S];
   int k = 0;
@@ -428,7 +438,7 @@ __device__ __noinline__ int newton_decide(NewtonState<S> ns, const double* tot, 
   for (int s = 0; s < S; ++s)
 #pragma unroll
     for (int t = s; t < S; ++t) {
-      const float hst = (float)(htri[k++] * inv_tau) + (s == t ? 1.f : 0.f);
+      const float hst = hf[k++] + (s == t ? 1.f : 0.f);
       H[s * S + t] = hst;
       H[t * S + s] = hst;
     }
@@ -469,12 +479,13 @@ struct Shared {
   float trSign[NW][32];
   float dH[NW][NGG];
   double Htot[NGG];        // sum_{status inner} u u^T (upper triangle)
+  float Hf[NGG];           // Htot / tau* in FP32 for the Newton direction
   double G[SS * SS], M[SS * SS], Uv[SS];
   double gamma[SS], beta[SS], beta_eval[SS], dir[SS], phi_cur[SS];
   double tot[NVMAX], blk[NVMAX];
   float theta[SS], gam[SS];
   int done, accepted_last, halvings, accepted;
-  double scale, nphi_cur, tstep;
+  double scale, nphi_cur, tstep;   // max(1, ||U^T w||^2), ||phi||^2 of the accepted point, step
   bool first;
 };
 
@@ -772,8 +783,10 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
   const WpArgs& a = sh.a;
   Epochs ep;
   if (tracer(a)) {
-    a.trace[1] = globaltimer();
-    for (int k = 0; k < TR_SLOTS; ++k) a.trace[2 * TR_ACC + k] = 0;
+    const long long t0 = globaltimer();
+    a.trace[1] = t0;
+    for (int k = 0; k < TR_SLOTS; ++k) tr_acc()[k] = 0;
+    tr_acc()[TR_SLOTS] = t0;
   }
 
   if constexpr (S > 0) {
@@ -808,19 +821,25 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
       pass_div<S>(&sh, src);
       if (tracer(a)) tr_add(a, 4, globaltimer() - t0);
       if (!grid_reduce<S>(sh.blk, sh.tot, a, ep, 3)) return;
+      // S threads in parallel: gamma = c/tau^2 M U^T d, then (U^T w)_s
+      if (threadIdx.x < S) {
+        const int s = threadIdx.x;
+        double g = 0.0;
+        for (int t = 0; t < S; ++t) g = fma(sh.M[s * S + t], sh.tot[t], g);
+        sh.gamma[s] = a.c_tau2 * g;
+      }
+      __syncthreads();
+      if (threadIdx.x < S) {
+        const int s = threadIdx.x;
+        double g = sh.Uv[s] - a.c_tau * sh.tot[s];
+        for (int t = 0; t < S; ++t) g = fma(sh.G[s * S + t], sh.gamma[t], g);
+        sh.phi_cur[s] = g * g;   // scratch until the reset below
+      }
+      __syncthreads();
       if (threadIdx.x == 0) {
-        double nrm = 0.0;
-        for (int s = 0; s < S; ++s) {
-          double g = 0.0;
-          for (int t = 0; t < S; ++t) g += sh.M[s * S + t] * sh.tot[t];
-          sh.gamma[s] = a.c_tau2 * g;
-        }
-        for (int s = 0; s < S; ++s) {
-          double g = sh.Uv[s] - a.c_tau * sh.tot[s];
-          for (int t = 0; t < S; ++t) g += sh.G[s * S + t] * sh.gamma[t];
-          nrm += g * g;       // (U^T w)_s
-        }
-        sh.scale = fmax(1.0, sqrt(nrm));
+        double nrm = 0.0;        // ||U^T w||^2
+        for (int s = 0; s < S; ++s) nrm += sh.phi_cur[s];
+        sh.scale = fmax(1.0, nrm);   // the stopping test compares squared norms
         for (int s = 0; s < S; ++s) {
           sh.beta_eval[s] = sh.beta[s];
           sh.dir[s] = 0.0;
@@ -847,13 +866,17 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
         if (tracer(a)) tr_add(a, 2, globaltimer() - t0);
         if (!grid_reduce<NV>(sh.blk, sh.tot, a, ep, 4)) return;
         ++my_evals;
-        if (threadIdx.x < NG) sh.Htot[threadIdx.x] += sh.tot[S + threadIdx.x];
+        if (threadIdx.x < NG) {   // the thread-parallel part of the decision: H's off-identity terms
+          const double hv = sh.Htot[threadIdx.x] + sh.tot[S + threadIdx.x];
+          sh.Htot[threadIdx.x] = hv;
+          sh.Hf[threadIdx.x] = (float)(hv * a.inv_tau);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
           t0 = tracer(a) ? globaltimer() : 0;
           NewtonState<S> ns{sh.beta, sh.beta_eval, sh.dir, sh.phi_cur, &sh.nphi_cur, &sh.tstep, &sh.halvings,
                             &sh.accepted, &sh.first, &sh.accepted_last};
-          const int done = newton_decide<S>(ns, sh.tot, sh.Htot, a.inv_tau, a.tol * sh.scale, a.maxit,
+          const int done = newton_decide<S>(ns, sh.tot, sh.Hf, a.tol * a.tol * sh.scale, a.maxit,
                                             my_evals >= max_evals);
           sh.done = done;
           if (done) last_newton = sh.accepted;
@@ -882,12 +905,13 @@ __global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
     if (tracer(a)) {
       // block 0's own time in the dual update and in the work since the last barrier
       const long long t_post = globaltimer();
-      a.trace[2 * TR_ACC] += t_post - t_pre;
-      if ((int)ep.all < TR_ACC) a.trace[2 * TR_ACC + 1] += t_pre - a.trace[2 * ep.all + 1];
+      tr_acc()[0] += t_post - t_pre;
+      tr_acc()[1] += t_pre - tr_acc()[TR_SLOTS];
     }
     if (!grid_reduce<0>(nullptr, nullptr, a, ep, 6)) return;
   }
   if (tracer(a)) {
+    for (int k = 0; k < TR_SLOTS; ++k) a.trace[2 * TR_ACC + k] = tr_acc()[k];
     a.trace[0] = ep.all;                // number of barriers passed; entry 0 also holds the start time
     if ((int)ep.all + 1 < TR_ACC) {
       a.trace[2 * (ep.all + 1)] = 99;   // end of kernel
