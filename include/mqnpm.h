@@ -118,6 +118,10 @@ typedef struct mqnpm_config {
                               slice propagated by the angular spectrum over
                               det_distance with the pupil kx^2 + ky^2 <=
                               (det_na kb)^2 (Section 6 reading)               */
+  size_t guard_bytes;      /* debugging: 0 = off; else every workspace buffer is
+                              framed by guard bands of this many bytes (rounded
+                              up to 256) filled with 0xA5, checked by
+                              mqnpm_check_guards                              */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;
@@ -266,6 +270,15 @@ int mqnpm_prox_trace(mqnpm_handle* h, long long* out, int cap, int* count);
 
 /* Number of CUDA kernels this handle has launched since creation. */
 long long mqnpm_launch_count(const mqnpm_handle* h);
+
+/* Guard bands (guard_bytes > 0): *corrupted receives the number of bands, of
+ * the two around every workspace buffer, whose bytes are no longer 0xA5 (0 when
+ * no kernel wrote outside its buffers; also 0 without guards).  Synchronises
+ * the handle's stream.  mqnpm_debug_poke_guard overwrites one byte of band
+ * `band` (0-based) so that a test can see the check fire; it returns
+ * INVALID_ARG for a band that does not exist. */
+int mqnpm_check_guards(mqnpm_handle* h, int* corrupted);
+int mqnpm_debug_poke_guard(mqnpm_handle* h, int band);
 
 /* Launch shapes the handle uses: *tile (0..15); shape (6 ints) receives the
  * lines per CTA and threads per line of the x passes, then the columns per CTA

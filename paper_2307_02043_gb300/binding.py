@@ -52,7 +52,7 @@ class Config(ctypes.Structure):
         ("max_batch", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
         ("green_hat", ctypes.POINTER(ctypes.c_float)), ("tile", ctypes.c_int),
-        ("det_distance", ctypes.c_double), ("det_na", ctypes.c_double),
+        ("det_distance", ctypes.c_double), ("det_na", ctypes.c_double), ("guard_bytes", ctypes.c_size_t),
     ]
 
 
@@ -92,6 +92,8 @@ SIGNATURES = {
     "mqnpm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "mqnpm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "mqnpm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "mqnpm_check_guards": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_debug_poke_guard": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mqnpm_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_tile_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -174,7 +176,7 @@ class MQNPM:
                  dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
                  direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1,
-                 det_distance: float = 0.0, det_na: float = 0.0):
+                 det_distance: float = 0.0, det_na: float = 0.0, guard_bytes: int = 0):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -220,6 +222,7 @@ class MQNPM:
         cfg.tile = int(tile)
         cfg.det_distance = float(det_distance)
         cfg.det_na = float(det_na)
+        cfg.guard_bytes = int(guard_bytes)
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
             if gh.size != (self.n + 1) ** 3:
@@ -282,6 +285,13 @@ class MQNPM:
                                         int(s_prime), out)
         self._raise(rc, allow_not_converged)
         return {"bias_error": out[0], "step_sq": out[1], "data_term": out[2]}
+
+    def check_guards(self) -> int:
+        """Guard bands (guard_bytes > 0) no longer holding their fill pattern."""
+        bad = ctypes.c_int()
+        self._stream()
+        self._raise(self.lib.mqnpm_check_guards(self._h, ctypes.byref(bad)))
+        return bad.value
 
     def tile_info(self) -> dict:
         """Launch shapes of the Green's passes and the autotuner's timings (ms per apply)."""

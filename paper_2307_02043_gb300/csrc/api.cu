@@ -33,13 +33,28 @@ namespace {
 template <class T>
 int dalloc(mqnpm_handle* h, T** p, size_t count) {
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  const size_t G = h->guard;
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaError_t e = cudaMalloc(&q, bytes + 2 * G);
   if (e != cudaSuccess) return set_cuda_error(h, e, "cudaMalloc");
   h->allocations.push_back(q);
-  h->bytes += bytes;
-  *p = static_cast<T*>(q);
+  h->bytes += bytes + 2 * G;
+  unsigned char* raw = static_cast<unsigned char*>(q);
+  if (G > 0) {   // bands before and after the buffer
+    if ((e = cudaMemset(raw, 0xA5, G)) != cudaSuccess || (e = cudaMemset(raw + G + bytes, 0xA5, G)) != cudaSuccess)
+      return set_cuda_error(h, e, "guard bands");
+    h->guards.push_back({raw, G});
+    h->guards.push_back({raw + G + bytes, G});
+  }
+  *p = reinterpret_cast<T*>(raw + G);
   return MQNPM_OK;
+}
+
+__global__ void k_check_guards(unsigned char* const* bands, size_t len, int* bad) {
+  const unsigned char* b = bands[blockIdx.x];
+  int wrong = 0;
+  for (size_t i = threadIdx.x; i < len; i += blockDim.x) wrong |= (b[i] != 0xA5);
+  if (__syncthreads_or(wrong) && threadIdx.x == 0) bad[blockIdx.x] = 1;
 }
 
 struct Sizes {
@@ -129,6 +144,29 @@ int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches
 const char* mqnpm_last_error(const mqnpm_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
 long long mqnpm_launch_count(const mqnpm_handle* h) { return h ? h->launches : 0; }
+
+int mqnpm_check_guards(mqnpm_handle* h, int* corrupted) {
+  if (!h || !corrupted) return MQNPM_ERR_INVALID_ARG;
+  *corrupted = 0;
+  if (h->guards.empty()) return MQNPM_OK;
+  CK(cudaSetDevice(h->device));
+  const int nb = (int)h->guards.size();
+  CK(cudaMemsetAsync(h->guard_bad, 0, nb * sizeof(int), h->stream));
+  k_check_guards<<<nb, 256, 0, h->stream>>>(h->guard_ptr, h->guard, h->guard_bad);
+  CK(cudaGetLastError());
+  std::vector<int> bad(nb);
+  CK(cudaMemcpyAsync(bad.data(), h->guard_bad, nb * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int v : bad) *corrupted += v;
+  return MQNPM_OK;
+}
+
+int mqnpm_debug_poke_guard(mqnpm_handle* h, int band) {
+  if (!h || band < 0 || band >= (int)h->guards.size()) return MQNPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemsetAsync(h->guards[band].first + h->guards[band].second / 2, 0x00, 1, h->stream));
+  return MQNPM_OK;
+}
 
 int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms) {
   if (!h || !tile || !shape) return MQNPM_ERR_INVALID_ARG;
@@ -236,6 +274,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->warm_start = cfg->warm_start != 0;
   h->direct_launches = cfg->direct_launches != 0;
   h->budget = cfg->hbm_budget_bytes;
+  h->guard = (cfg->guard_bytes + 255) / 256 * 256;
   h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
   h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);
   h->subset_of.assign(cfg->subset_of, cfg->subset_of + cfg->L);
@@ -356,6 +395,22 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(h->xbar, (size_t)h->S * N); AL(h->gbar, (size_t)h->S * N); AL(h->U, (size_t)h->S * N);
   AL(h->g, N); AL(h->vq, N); AL(h->Pwarm, 3 * N);
 #undef AL
+  if (!h->guards.empty()) {   // device table of the guard bands (itself unguarded)
+    const size_t nb = h->guards.size();
+    std::vector<unsigned char*> ptrs(nb);
+    for (size_t i = 0; i < nb; ++i) ptrs[i] = h->guards[i].first;
+    void* q = nullptr;
+    if ((e = cudaMalloc(&q, nb * sizeof(unsigned char*))) != cudaSuccess) { set_cuda_error(h, e, "guard table"); return fail(MQNPM_ERR_CUDA); }
+    h->allocations.push_back(q);
+    h->guard_ptr = static_cast<unsigned char**>(q);
+    if ((e = cudaMalloc(&q, nb * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "guard flags"); return fail(MQNPM_ERR_CUDA); }
+    h->allocations.push_back(q);
+    h->guard_bad = static_cast<int*>(q);
+    if ((e = cudaMemcpy(h->guard_ptr, ptrs.data(), nb * sizeof(unsigned char*), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      set_cuda_error(h, e, "guard table");
+      return fail(MQNPM_ERR_CUDA);
+    }
+  }
   if ((e = cudaMallocHost(&w.h_nactive, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_illum, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_warm, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }

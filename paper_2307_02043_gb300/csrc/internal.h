@@ -145,6 +145,10 @@ struct mqnpm_handle {
   std::string err;
   size_t bytes = 0, budget = 0;
   std::vector<void*> allocations;
+  size_t guard = 0;                               // guard-band bytes per side (0: none)
+  std::vector<std::pair<unsigned char*, size_t>> guards;   // device guard bands
+  unsigned char** guard_ptr = nullptr;            // device table of the bands (check kernel)
+  int* guard_bad = nullptr;                       // device flags, one per band
   // device tables
   float2 *khat = nullptr, *tw = nullptr, *tab = nullptr, *ymeas = nullptr;
   bool remote = false;                    // detector behind an angular-spectrum propagation
