@@ -586,6 +586,8 @@ def main():
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
+    ap.add_argument("--log-jsonl", default=None,
+                    help="write one JSON line per timed MQNPM iteration (step info) to this file")
     ap.add_argument("--tile", type=int, default=-1,
                     help="launch-shape tile of the Green's passes (-1: autotuned when a handle is created)")
     ap.add_argument("--serve-uneven", action="store_true",
@@ -691,6 +693,10 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
+    if args.log_jsonl and rank == 0:
+        with open(args.log_jsonl, "w") as f:
+            for i in infos:
+                f.write(json.dumps({k: (round(v, 6) if isinstance(v, float) else v) for k, v in i.items()}) + "\n")
     wprox_ratio = weighted_vs_unweighted_prox(torch, h, x, infos, w)
     # ---- max over ranks
     t_max, ms_e2e, illum_total, e2e_total = aggregate_ranks(torch, dist if world > 1 else None, dev, ms, ms_e2e,
