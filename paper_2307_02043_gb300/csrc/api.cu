@@ -317,7 +317,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   if (h->w.ctas_upd < 1) h->w.ctas_upd = 1;
   h->wp.ctas_vec = h->w.ctas_vec;
   h->wp.nsm = nsm;
-  const int wp_blocks = 2 * nsm;   // the cooperative prox kernel runs at most 2 blocks per SM
+  const int wp_blocks = wprox_blocks_per_sm() * nsm;   // blocks of the cooperative prox kernel, at most
 
   // ---- budget (every device allocation of the handle)
   const size_t m1 = (size_t)(n + 1);

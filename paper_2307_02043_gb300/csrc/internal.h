@@ -209,6 +209,7 @@ int qn_point_impl(mqnpm_handle* h, const float* x, const float* g, const UPtrs& 
                   double aS, float* v);
 std::vector<float> wprox_momentum(int J);
 int wprox_part_len();
+int wprox_blocks_per_sm();                // co-resident blocks per SM of the cooperative prox kernel
 size_t wprox_part_count(int max_blocks);   // doubles of the partials buffer
 int wprox_barrier_words();                // unsigned words of the barrier counters
 int woodbury_scal_count();

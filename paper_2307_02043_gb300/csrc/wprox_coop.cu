@@ -27,6 +27,7 @@ cudaError_t wprox_dispatch_high(mqnpm_handle* h, int S, int tv, void* args);
 namespace {
 
 constexpr int WP_THREADS = 256;
+constexpr int WP_BPS = 2;        // co-resident blocks per SM the kernel is compiled and launched for
 constexpr int NW = WP_THREADS / 32;
 constexpr int NVMAX = MQNPM_MAX_S + MQNPM_MAX_S * (MQNPM_MAX_S + 1) / 2;   // S + S(S+1)/2
 // Trace layout (long long pairs): pair 0 = (barriers passed, start time),
@@ -774,7 +775,7 @@ __device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
 }
 
 template <int S, int TV>
-__global__ void __launch_bounds__(WP_THREADS, 2) k_wprox(WpArgs args) {
+__global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
   constexpr int NG = S * (S + 1) / 2;
   constexpr int NV = S + NG;
   __shared__ Shared<S> sh;
@@ -932,7 +933,7 @@ cudaError_t launch_wprox(mqnpm_handle* h, WpArgs& a) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wprox<S, TV>, WP_THREADS, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  const int blocks = h->wp.nsm * std::min(per_sm, 2);
+  const int blocks = h->wp.nsm * std::min(per_sm, WP_BPS);
   if (blocks > WP_GS * WP_MAXG) return cudaErrorInvalidConfiguration;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((void*)k_wprox<S, TV>, dim3(blocks), dim3(WP_THREADS), args, 0, h->stream);
@@ -1077,6 +1078,7 @@ std::vector<float> wprox_momentum(int J) {
 }
 
 int wprox_part_len() { return NVMAX; }
+int wprox_blocks_per_sm() { return WP_BPS; }
 size_t wprox_part_count(int max_blocks) { return (size_t)(max_blocks + WP_MAXG) * NVMAX; }
 int wprox_barrier_words() { return 3 + WP_MAXG; }
 #endif
