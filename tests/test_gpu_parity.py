@@ -244,6 +244,41 @@ def test_remote_detector_matches_oracle(model, n):
     h.close()
 
 
+def test_maximum_batch_of_64_slots():
+    """MQNPM_MAX_BATCH = 64 slots in one launch (the pass-3 slot mask is 64
+    bits wide): every slot's apply against the oracle, and the 64-illumination
+    gradient in one chunk against 13 chunks of 5 and against the oracle."""
+    n, L = 8, 64
+    kd = cone(L, 35.0)
+    so = np.zeros(L, dtype=np.int32)
+    rng = np.random.default_rng(64)
+    h = make_handle(n, kd, so, [1.0], max_batch=64, krylov_tol=1e-7)
+    v = rng.standard_normal((L, n, n, n)) + 1j * rng.standard_normal((L, n, n, n))
+    out = h.green_apply(c64(v).reshape(-1)).cpu().numpy().reshape(L, n, n, n)
+    kh = physics.green_hat(n, KB)
+    for b in (0, 1, 31, 32, 62, 63):
+        assert relmax(out[b], physics.green_apply(v[b], kh)) < 2e-6, b
+    x = 0.02 * rng.random((n, n, n))
+    om = physics.Model(n, kd, "ls", tol=1e-12)
+    ys = np.stack([om.forward(x, l) for l in range(L)])
+    ys = ys + 0.01 * np.abs(ys).max() * (rng.standard_normal(ys.shape) + 1j * rng.standard_normal(ys.shape))
+    h.set_measurements(c64(ys).reshape(-1))
+    illum = list(range(L))
+    g1, l1, its = h.grad_batch(f32(x).reshape(-1), illum, 1.0 / L)
+    h.close()
+    h5 = make_handle(n, kd, so, [1.0], max_batch=5, krylov_tol=1e-7)
+    h5.set_measurements(c64(ys).reshape(-1))
+    g5, l5, _ = h5.grad_batch(f32(x).reshape(-1), illum, 1.0 / L)
+    h5.close()
+    g1 = g1.cpu().numpy().astype(np.float64)
+    assert rel(g1, g5.cpu().numpy()) < 1e-5
+    assert abs(l1 - l5) <= 1e-6 * abs(l5)
+    lo, go = om.batch_loss_grad(x, illum, ys, 1.0 / L)
+    assert rel(g1.reshape(go.shape), go) < 1e-4
+    assert abs(l1 - lo) <= 1e-5 * abs(lo)
+    assert len(its) == L and all(a > 0 and b > 0 for a, b in its)
+
+
 def test_grad_edge_cases():
     """Zero contrast (Krylov converges at start), zero residual (adjoint RHS 0)."""
     n = 16
