@@ -120,7 +120,7 @@ MQ_D void load_twiddle_table(float2* tw, const float2* __restrict__ twg) {
 template <int P, int RV, class Pro>
 __global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
 k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
-        const KState* __restrict__ st, double* __restrict__ partials) {
+        const KState* __restrict__ st, double* __restrict__ partials, int line0, int nlines) {
   using PL = Plan<P>;
   using SH = RowShape<P, RV>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T;
@@ -133,8 +133,8 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
   pro.begin(b);
   for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
   const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
-  const int line = blockIdx.x * SH::LPB + l;
-  const bool valid = line < n * n;
+  const int line = line0 + blockIdx.x * SH::LPB + l;   // rows [line0, line0 + nlines) of [z][y]
+  const bool valid = line < line0 + nlines;
   const int z = line / n, y = line - (line / n) * n;
   float2* exl = ex + l * SH::PER_LINE;
   Parts<Pro::NPART> parts;
@@ -230,7 +230,7 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
 template <int P, int CV, bool INV>
 __global__ void __launch_bounds__(ColShape<P, CV>::THREADS)
 k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
-         const float2* __restrict__ twg, const KState* __restrict__ st) {
+         const float2* __restrict__ twg, const KState* __restrict__ st, int z0) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T, C = SH::C;
@@ -243,7 +243,7 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
   load_twiddle_table<P>(tw, twg);
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
   const int kx = blockIdx.x * C + c;
-  const int z = blockIdx.y;
+  const int z = z0 + blockIdx.y;   // planes [z0, z0 + gridDim.y)
   const int len_in = INV ? P : n, len_out = INV ? n : P;
   const float2* src = in + ((size_t)b * n + z) * len_in * P + kx;
   float2* dst = out + ((size_t)b * n + z) * len_out * P + kx;
@@ -295,7 +295,12 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
 // CTAs per SM).  With two, the middle stage writes them straight into the
 // second buffer (two barriers per slot, no register-held stage: the choice for
 // lengths whose threads carry several columns of a stage, e.g. P = 192, 320).
-template <int P, int CV, bool DB>
+// A third input scheme (PLANE) serves the adjoint right-hand side G^H S^T r,
+// whose input is nonzero on the detector plane z = n - 1 only: the forward z
+// transform of a column is then the ramp v W_P^{(n-1) kz} = v (-1)^kz W_P^{-kz}
+// (P = 2n), so the first stage, the forward half of the middle stage and the
+// input tile are skipped.
+template <int P, int CV, bool DB, bool PLANE = false>
 struct Pass3Smem {
   using SH = ColShape<P, CV>;
   static constexpr int C = SH::C;
@@ -308,29 +313,30 @@ struct Pass3Smem {
     const size_t o = ex_off() + (size_t)(DB ? 2 : 1) * P * C * sizeof(float2);
     return (o + 1023) & ~(size_t)1023;
   }
-  static constexpr MQ_HD size_t in_bytes(int n) { return (size_t)n * C * sizeof(float2); }
+  static constexpr MQ_HD size_t in_bytes(int n) { return PLANE ? 0 : (size_t)n * C * sizeof(float2); }
   static constexpr MQ_HD size_t bar_off(int n) { return in_off() + in_bytes(n); }
   static constexpr MQ_HD size_t bytes(int n) { return bar_off(n) + sizeof(uint64_t) + 1024; }   // + base alignment slack
 };
 
 // Blocks per SM the pass-3 kernel is compiled for (register cap): three when
 // its shared memory allows it.
-template <int P, int CV, bool DB>
+template <int P, int CV, bool DB, bool PLANE = false>
 struct Pass3Occ {
-  using SM = Pass3Smem<P, CV, DB>;
-  static constexpr size_t SMEM = SM::in_off() + (size_t)(P / 2) * SM::C * sizeof(float2) + 1032;
+  using SM = Pass3Smem<P, CV, DB, PLANE>;
+  static constexpr size_t SMEM = SM::in_off() + SM::in_bytes(P / 2) + 1032;
   static constexpr int MIN_BLOCKS = (3 * SMEM <= 220 * 1024 && ColShape<P, CV>::THREADS <= 256) ? 3
                                     : (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
-template <int P, int CV, bool DB, bool CONJ>
-__global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB>::MIN_BLOCKS)
+template <int P, int CV, bool DB, bool CONJ, bool PLANE = false>
+__global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB, PLANE>::MIN_BLOCKS)
 k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int n,
         int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
-  using SM = Pass3Smem<P, CV, DB>;
+  using SM = Pass3Smem<P, CV, DB, PLANE>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T, C = SH::C, KH = SM::KH;
+  static_assert(!PLANE || R1 % 2 == 0, "plane input: (-1)^kz = (-1)^k1 needs an even R1");
   constexpr int I1 = (R2 + T - 1) / T, I2 = (R1 + T - 1) / T;   // sub-DFTs per thread and stage
   static_assert(R1 * R2 == P && R2 % 2 == 0, "two-stage plan with an even second factor");
   extern __shared__ unsigned char smraw[];
@@ -352,7 +358,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     if (st == nullptr || st[q].active != 0) act |= 1ull << q;
   if (act == 0ull) return;
   int b = __ffsll((long long)act) - 1;
-  if (threadIdx.x == 0) {
+  if (!PLANE && threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
     fence_proxy_async();
@@ -375,38 +381,48 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   __syncthreads();
   uint32_t phase = 0u;
   while (true) {
-    if (!mbar_wait_bounded(bar, phase, 1 << 22)) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
-      // the copy given up on is the only one in flight: give it one more bounded wait
-      mbar_wait_bounded(bar, phase, 1 << 22);
-      return;
-    }
-    phase ^= 1u;
-    // forward stage 1 (n2-threads), inputs z = R2 n1 + n2 < n from the TMA tile [z][c]
-#pragma unroll
-    for (int i = 0; i < I1; ++i) {
-      const int n2 = t + T * i;
-      if (R2 % T != 0 && n2 >= R2) continue;   // idle in this stage
-      float2 a[R1];
-#pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) {
-        a[n1] = make_float2(0.f, 0.f);
-        if (n1 < R1 / 2) a[n1] = in[(R2 * n1 + n2) * C + c];
+    int next = nb;
+    float2 vplane = make_float2(0.f, 0.f);
+    if constexpr (PLANE) {
+      // no tile: only the previous slot's last stage must be finished with ex
+      __syncthreads();
+      const unsigned long long rest = act & ~((2ull << b) - 1ull);
+      next = rest ? __ffsll((long long)rest) - 1 : nb;
+      vplane = T2[((size_t)b * n + (n - 1)) * zs + (size_t)ky * P + kx];
+    } else {
+      if (!mbar_wait_bounded(bar, phase, 1 << 22)) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        // the copy given up on is the only one in flight: give it one more bounded wait
+        mbar_wait_bounded(bar, phase, 1 << 22);
+        return;
       }
-      dft<R1, false, R1 / 2>(a);   // inputs n1 >= R1/2 are the zero padding
-      const float2* twr = tw + n2 * R1;
-      float2* exw = ex + (n2 * R1) * C + c;
+      phase ^= 1u;
+      // forward stage 1 (n2-threads), inputs z = R2 n1 + n2 < n from the TMA tile [z][c]
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) exw[k1 * C] = (k1 == 0) ? a[0] : cmul(a[k1], twr[k1]);
-    }
-    __syncthreads();   // the tile is consumed: fetch the next active slot's into the same buffer
-    const unsigned long long rest = act & ~((2ull << b) - 1ull);
-    const int next = rest ? __ffsll((long long)rest) - 1 : nb;
-    if (next < nb && threadIdx.x == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(bar, tile_bytes);
-      tma_load_3d(in, &tmap, bar, kx0, ky, next * n);
-    }
+      for (int i = 0; i < I1; ++i) {
+        const int n2 = t + T * i;
+        if (R2 % T != 0 && n2 >= R2) continue;   // idle in this stage
+        float2 a[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+          a[n1] = make_float2(0.f, 0.f);
+          if (n1 < R1 / 2) a[n1] = in[(R2 * n1 + n2) * C + c];
+        }
+        dft<R1, false, R1 / 2>(a);   // inputs n1 >= R1/2 are the zero padding
+        const float2* twr = tw + n2 * R1;
+        float2* exw = ex + (n2 * R1) * C + c;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) exw[k1 * C] = (k1 == 0) ? a[0] : cmul(a[k1], twr[k1]);
+      }
+      __syncthreads();   // the tile is consumed: fetch the next active slot's into the same buffer
+      const unsigned long long rest = act & ~((2ull << b) - 1ull);
+      next = rest ? __ffsll((long long)rest) - 1 : nb;
+      if (next < nb && threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, tile_bytes);
+        tma_load_3d(in, &tmap, bar, kx0, ky, next * n);
+      }
+    }   // !PLANE
     // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread).
     // K_hat row of kz = k1 + R1 k2: kz itself for k2 < R2/2, else the folded P - kz.
     float2 zb[DB ? 1 : I2][R2];
@@ -415,10 +431,21 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       const int k1 = t + T * i;
       if (R1 % T != 0 && k1 >= R1) continue;
       float2 a[R2];
-      const float2* exr = ex + k1 * C + c;
+      if constexpr (PLANE) {
+        // X[k1 + R1 k2] = v (-1)^k1 conj(W_P^k1) conj(W_R2^k2)
+        const float2 w1 = tw[R1 + k1];   // row 1 of the table: W_P^k1
+        float2 base = cmul(vplane, make_float2(w1.x, -w1.y));
+        if (k1 & 1) base = make_float2(-base.x, -base.y);
+        static_for<R2>([&](auto k2c) {
+          constexpr int k2 = decltype(k2c)::value;
+          a[k2] = tw_mul<k2, R2, true>(base);
+        });
+      } else {
+        const float2* exr = ex + k1 * C + c;
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) a[n2] = exr[n2 * R1 * C];
-      dft<R2, false>(a);
+        for (int n2 = 0; n2 < R2; ++n2) a[n2] = exr[n2 * R1 * C];
+        dft<R2, false>(a);
+      }
       const float2* khA = kh + k1 * C + c;
       const float2* khB = kh + (P - k1) * C + c;
 #pragma unroll

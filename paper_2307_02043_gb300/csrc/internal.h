@@ -28,6 +28,7 @@ struct GreenCall {
   long long* launches = nullptr; // optional kernel-launch counter (+5 per apply)
   const void* tmap = nullptr;    // CUtensorMap of T2 for the pass-3 tile loads
   int* err = nullptr;            // device flag raised when a bounded wait gives up
+  bool plane = false;            // input nonzero on the last z-plane only (the lift S^T r; G^H only)
   int tile = 0;                  // launch shapes: alternative shape of bit 0 the x passes, bit 1 the
                                  // y passes, bit 2 the z pass; bit 3 two z-pass exchange buffers
 };

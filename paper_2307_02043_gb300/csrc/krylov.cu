@@ -329,7 +329,12 @@ cudaError_t glaunch_ev(mqnpm_handle* h, GreenCall c, cudaStream_t s, cudaEvent_t
   return green_launch(c, s);
 }
 
-cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) { return glaunch_ev(h, c, s, profile_slot(h, c.nb)); }
+// The pass timers cover the full applies only: a plane-input apply (the
+// adjoint lift) skips most of passes 1-3, and counting its slots at the full
+// algorithmic bytes would overstate the bandwidth figures.
+cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
+  return glaunch_ev(h, c, s, c.plane ? nullptr : profile_slot(h, c.nb));
+}
 
 GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
   GreenCall c;
@@ -542,6 +547,7 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   CK(cudaMemsetAsync(w.zs, 0, nb * N * sizeof(float2), s));
   GreenCall c = base_call(h, nb, true);
   c.pro = PRO_LIFT;
+  c.plane = true;                      // S^T r: nonzero on the detector plane only
   c.pa.rdet = w.rdet;
   if (h->remote) {                     // S^T D^H r_det
     CK(detector_adjoint(h, w.rdet, w.rlift, nb));
@@ -619,6 +625,7 @@ int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, double 
   } else {
     GreenCall c = base_call(h, m, true);
     c.pro = PRO_LIFT;
+    c.plane = true;
     c.pa.rdet = w.rdet;
     if (h->remote) {
       CK(detector_adjoint(h, w.rdet, w.rlift, m));
@@ -752,6 +759,7 @@ int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, cons
       CK(glaunch(h, c, s));
       GreenCall c2 = base_call(h, m, true);
       c2.pro = PRO_LIFT;                // G^H S^T (.)
+      c2.plane = true;
       c2.pa.rdet = w.rdet;
       if (h->remote) {                  // J = D S G(. u_in): D, then D^H before the lift
         CK(detector_forward(h, w.rdet, m, nullptr, w.illum));
