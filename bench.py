@@ -740,7 +740,7 @@ def main():
                      "algorithmic_bytes_per_slot": per_slot[dom],
                      "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof["calls"])),
                      "launches": prof["calls"], "slots_per_launch": round(prof["slot_launches"] / max(1, prof["calls"]), 2)},
-        "roofline_alu": pass3_alu_view(n, prof, pms[2]),
+        "roofline_alu": pass3_alu_view(n, prof, pms[2]) if prof["calls"] else None,
         "passes": passes,
         "green_applies": prof["calls"],
         "green_tile": h.tile_info(),
@@ -758,6 +758,10 @@ def main():
                 "same_krylov_iters": [i["krylov_iters_total"] for i in e2e_infos] ==
                                      [i["krylov_iters_total"] for i in infos]},
     }
+    if prof["calls"] == 0:
+        out["roofline"] = None
+        out["roofline_note"] = ("every Green's apply of this model touches one z-plane (first-Born data, adjoint "
+                                "right-hand sides); the pass timers cover full applies only")
     out["gpu_launches"] = int(launches)
     out["config"]["iterations"] = "k = %d..%d from x0 = 0" % (infos[0]["k"], infos[-1]["k"])
     if rank == 0 and not args.no_plain:

@@ -256,9 +256,9 @@ int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size);
  * of each pass in pass_ms (host, 5 doubles: x-forward, y-forward,
  * z-forward*K_hat*z-inverse, y-inverse, x-inverse), the number of recorded
  * applies in *calls and the sum of their batch sizes in *slot_launches, and
- * stops recording.  The adjoint right-hand sides G^H S^T r, whose input lies
- * on one z-plane and which skip most of the first three passes, are not
- * recorded. */
+ * stops recording.  Applies that touch one z-plane are not recorded: the
+ * adjoint right-hand sides G^H S^T r (input on the detector plane) and the
+ * first-Born data S G(x u_in) (only the detector plane kept). */
 /* Phase trace of the last weighted proximal mapping: out (host, 2*cap
  * long longs) receives out[1] = start time (ns, GPU global timer) and, for
  * e = 1..*count, the pair (tag, time) stamped when the e-th grid barrier was

@@ -62,6 +62,12 @@ int green_row_ctas(int n, int tile) {
   return shape[0] > 0 ? (n * n + shape[0] - 1) / shape[0] : 0;
 }
 
+int green_plane_ctas(int n, int tile) {
+  int shape[6];
+  green_shape(n, tile, shape);
+  return shape[0] > 0 ? (n + shape[0] - 1) / shape[0] : 0;
+}
+
 int green_row_ctas_max(int n) { return std::max(green_row_ctas(n, 0), green_row_ctas(n, 1)); }
 
 int green_col_width(int n, int tile) {   // columns per CTA of pass 3 (the tensor-map box)

@@ -44,8 +44,9 @@ cudaError_t launch5(const GreenCall& c, cudaStream_t s) {
   auto kern = k_pass5<P, RV, Epi<KIND>>;
   cudaError_t e = set_smem(kern, RS::SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid(ceil_div(c.n * c.n, RS::LPB), c.nb);
-  kern<<<grid, RS::THREADS, RS::SMEM, s>>>(epi, c.T1, c.n, c.tw, c.st, c.part_epi);
+  const int line0 = c.outplane ? (c.n - 1) * c.n : 0, nlines = c.outplane ? c.n : c.n * c.n;
+  dim3 grid(ceil_div(nlines, RS::LPB), c.nb);
+  kern<<<grid, RS::THREADS, RS::SMEM, s>>>(epi, c.T1, c.n, c.tw, c.st, c.part_epi, line0, nlines);
   return cudaGetLastError();
 }
 
@@ -81,20 +82,21 @@ cudaError_t pass_y(const GreenCall& c, const float2* in, float2* out, cudaStream
   auto kern = k_pass_y<P, CV, INV>;
   cudaError_t e = set_smem(kern, CS::SMEM);
   if (e != cudaSuccess) return e;
-  const bool plane = c.plane && !INV;   // forward y pass of a plane input: that plane only
+  // forward y pass of a plane input, inverse y pass of a plane output: that plane only
+  const bool plane = INV ? c.outplane : c.plane;
   dim3 grid(P / CS::C, plane ? 1 : c.n, c.nb);
   kern<<<grid, CS::THREADS, CS::SMEM, s>>>(in, out, c.n, c.tw, c.st, plane ? c.n - 1 : 0);
   return cudaGetLastError();
 }
 
 // one CTA per (kx tile, ky) column set; the batch is looped inside (one TMA tile buffer)
-template <int CV, bool DB, bool CONJ, bool PLANE = false>
+template <int CV, bool DB, bool CONJ, int IO = IO_FULL>
 cudaError_t pass3(const GreenCall& c, cudaStream_t s) {
   using CS = ColShape<P, CV>;
   const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);
   if (tm == nullptr || c.err == nullptr) return cudaErrorInvalidValue;
-  auto kern = k_pass3<P, CV, DB, CONJ, PLANE>;
-  const int smem = (int)Pass3Smem<P, CV, DB, PLANE>::bytes(c.n);
+  auto kern = k_pass3<P, CV, DB, CONJ, IO>;
+  const int smem = (int)Pass3Smem<P, CV, DB, IO>::bytes(c.n);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(P / CS::C, P);
@@ -108,8 +110,11 @@ cudaError_t columns(const GreenCall& c, cudaStream_t s, unsigned rec_flags) {
   if ((e = pass_y<YV, false>(c, c.T1, c.T2, s)) != cudaSuccess) return e;
   if (c.ev && (e = cudaEventRecordWithFlags(c.ev[2], s, rec_flags)) != cudaSuccess) return e;
   if (c.plane) {   // the plane input serves the adjoint lift only
-    if (!c.adjoint) return cudaErrorInvalidValue;
-    e = pass3<ZV, DB, true, true>(c, s);
+    if (!c.adjoint || c.outplane) return cudaErrorInvalidValue;
+    e = pass3<ZV, DB, true, IO_IN>(c, s);
+  } else if (c.outplane) {   // the plane output serves the first-Born data only
+    if (c.adjoint) return cudaErrorInvalidValue;
+    e = pass3<ZV, DB, false, IO_OUT>(c, s);
   } else {
     e = c.adjoint ? pass3<ZV, DB, true>(c, s) : pass3<ZV, DB, false>(c, s);
   }

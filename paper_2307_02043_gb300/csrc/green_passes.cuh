@@ -176,7 +176,7 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
 template <int P, int RV, class Epi>
 __global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
 k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict__ twg,
-        const KState* __restrict__ st, double* __restrict__ partials) {
+        const KState* __restrict__ st, double* __restrict__ partials, int line0, int nlines) {
   using PL = Plan<P>;
   using SH = RowShape<P, RV>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T;
@@ -188,11 +188,11 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
   if (!slot_active(st, b)) return;
   for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
   const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
-  const int line = blockIdx.x * SH::LPB + l;
-  const bool valid = line < n * n;
+  const int line = line0 + blockIdx.x * SH::LPB + l;   // rows [line0, line0 + nlines) of [z][y]
+  const bool valid = line < line0 + nlines;
   const int z = line / n, y = line - (line / n) * n;
   float2* exl = ex + l * SH::PER_LINE;
-  const float2* src = T4 + ((size_t)b * n * n + (valid ? line : 0)) * P;
+  const float2* src = T4 + ((size_t)b * n * n + (valid ? line : line0)) * P;
   Parts<Epi::NPART> parts;
   parts.zero();
   __syncthreads();
@@ -295,12 +295,18 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
 // CTAs per SM).  With two, the middle stage writes them straight into the
 // second buffer (two barriers per slot, no register-held stage: the choice for
 // lengths whose threads carry several columns of a stage, e.g. P = 192, 320).
-// A third input scheme (PLANE) serves the adjoint right-hand side G^H S^T r,
-// whose input is nonzero on the detector plane z = n - 1 only: the forward z
-// transform of a column is then the ramp v W_P^{(n-1) kz} = v (-1)^kz W_P^{-kz}
-// (P = 2n), so the first stage, the forward half of the middle stage and the
-// input tile are skipped.
-template <int P, int CV, bool DB, bool PLANE = false>
+// Two plane modes (IO) serve applies that touch one z-plane.  IO_IN: the
+// adjoint right-hand side G^H S^T r, whose input is nonzero on the detector
+// plane z = n - 1 only: the forward z transform of a column is then the ramp
+// v W_P^{(n-1) kz} = v (-1)^kz W_P^{-kz} (P = 2n), so the first stage, the
+// forward half of the middle stage and the input tile are skipped.  IO_OUT: a
+// forward apply of which only the detector plane is kept (the first-Born data
+// S G(x u_in)): the inverse z transform shrinks to the one output
+// x[n-1] = sum_kz Y[kz] (-1)^kz W_P^kz, a per-thread sum and a column
+// reduction, and only row z = n - 1 is written.
+enum Pass3IO { IO_FULL = 0, IO_IN = 1, IO_OUT = 2 };
+
+template <int P, int CV, bool DB, int IO = IO_FULL>
 struct Pass3Smem {
   using SH = ColShape<P, CV>;
   static constexpr int C = SH::C;
@@ -313,30 +319,33 @@ struct Pass3Smem {
     const size_t o = ex_off() + (size_t)(DB ? 2 : 1) * P * C * sizeof(float2);
     return (o + 1023) & ~(size_t)1023;
   }
-  static constexpr MQ_HD size_t in_bytes(int n) { return PLANE ? 0 : (size_t)n * C * sizeof(float2); }
+  static constexpr MQ_HD size_t in_bytes(int n) { return IO == IO_IN ? 0 : (size_t)n * C * sizeof(float2); }
   static constexpr MQ_HD size_t bar_off(int n) { return in_off() + in_bytes(n); }
-  static constexpr MQ_HD size_t bytes(int n) { return bar_off(n) + sizeof(uint64_t) + 1024; }   // + base alignment slack
+  static constexpr MQ_HD size_t red_off(int n) { return bar_off(n) + 16; }   // IO_OUT: column partials [T][C]
+  static constexpr MQ_HD size_t red_bytes() { return IO == IO_OUT ? (size_t)SH::T * C * sizeof(float2) : 0; }
+  static constexpr MQ_HD size_t bytes(int n) { return red_off(n) + red_bytes() + 1024; }   // + base alignment slack
 };
 
 // Blocks per SM the pass-3 kernel is compiled for (register cap): three when
 // its shared memory allows it.
-template <int P, int CV, bool DB, bool PLANE = false>
+template <int P, int CV, bool DB, int IO = IO_FULL>
 struct Pass3Occ {
-  using SM = Pass3Smem<P, CV, DB, PLANE>;
-  static constexpr size_t SMEM = SM::in_off() + SM::in_bytes(P / 2) + 1032;
+  using SM = Pass3Smem<P, CV, DB, IO>;
+  static constexpr size_t SMEM = SM::in_off() + SM::in_bytes(P / 2) + SM::red_bytes() + 1040;
   static constexpr int MIN_BLOCKS = (3 * SMEM <= 220 * 1024 && ColShape<P, CV>::THREADS <= 256) ? 3
                                     : (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
-template <int P, int CV, bool DB, bool CONJ, bool PLANE = false>
-__global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB, PLANE>::MIN_BLOCKS)
+template <int P, int CV, bool DB, bool CONJ, int IO = IO_FULL>
+__global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB, IO>::MIN_BLOCKS)
 k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int n,
         int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
-  using SM = Pass3Smem<P, CV, DB, PLANE>;
+  using SM = Pass3Smem<P, CV, DB, IO>;
   constexpr int R1 = PL::R1, R2 = PL::R2, T = SH::T, C = SH::C, KH = SM::KH;
-  static_assert(!PLANE || R1 % 2 == 0, "plane input: (-1)^kz = (-1)^k1 needs an even R1");
+  constexpr bool PLANE = IO == IO_IN;
+  static_assert(IO == IO_FULL || R1 % 2 == 0, "plane modes: (-1)^kz = (-1)^k1 needs an even R1");
   constexpr int I1 = (R2 + T - 1) / T, I2 = (R1 + T - 1) / T;   // sub-DFTs per thread and stage
   static_assert(R1 * R2 == P && R2 % 2 == 0, "two-stage plan with an even second factor");
   extern __shared__ unsigned char smraw[];
@@ -426,6 +435,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
     // forward stage 2 (k1-threads) -> multiply -> inverse stage A (same thread).
     // K_hat row of kz = k1 + R1 k2: kz itself for k2 < R2/2, else the folded P - kz.
     float2 zb[DB ? 1 : I2][R2];
+    float2 opart = make_float2(0.f, 0.f);   // IO_OUT: this thread's share of x[n-1]
 #pragma unroll
     for (int i = 0; i < I2; ++i) {
       const int k1 = t + T * i;
@@ -451,6 +461,18 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2)
         a[k2] = cmul(a[k2], k2 < R2 / 2 ? khA[k2 * R1 * C] : khB[-k2 * R1 * C]);
+      if constexpr (IO == IO_OUT) {
+        // sum_k2 Y[k1 + R1 k2] (-1)^k1 W_P^k1 W_R2^k2: no inverse stage A
+        float2 acc = make_float2(0.f, 0.f);
+        static_for<R2>([&](auto k2c) {
+          constexpr int k2 = decltype(k2c)::value;
+          acc = cadd(acc, tw_mul<k2, R2, false>(a[k2]));
+        });
+        acc = cmul(acc, tw[R1 + k1]);
+        if (k1 & 1) acc = make_float2(-acc.x, -acc.y);
+        opart = cadd(opart, acc);
+        continue;
+      }
       dft<R2, true>(a);   // over k2 -> j1
       const float2* twc = tw + k1;
       if constexpr (DB) {
@@ -461,6 +483,21 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
 #pragma unroll
         for (int j1 = 0; j1 < R2; ++j1) zb[i][j1] = (j1 == 0) ? a[0] : cmul(a[j1], cconj(twc[j1 * R1]));
       }
+    }
+    if constexpr (IO == IO_OUT) {
+      // column sums in a fixed thread order; the barrier also ends every
+      // thread's reads of ex, so the next slot's first stage may write it
+      float2* red = reinterpret_cast<float2*>(sm + SM::red_off(n));
+      red[t * C + c] = opart;
+      __syncthreads();
+      if (t == 0) {
+        float2 x = red[c];
+        for (int q = 1; q < T; ++q) x = cadd(x, red[q * C + c]);
+        T2[((size_t)b * n + (n - 1)) * zs + (size_t)ky * P + kx] = x;
+      }
+      if (next >= nb) break;
+      b = next;
+      continue;
     }
     __syncthreads();
     if constexpr (!DB) {

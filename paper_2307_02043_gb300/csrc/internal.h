@@ -29,6 +29,7 @@ struct GreenCall {
   const void* tmap = nullptr;    // CUtensorMap of T2 for the pass-3 tile loads
   int* err = nullptr;            // device flag raised when a bounded wait gives up
   bool plane = false;            // input nonzero on the last z-plane only (the lift S^T r; G^H only)
+  bool outplane = false;         // only the last z-plane of the output is needed (first-Born data; G only)
   int tile = 0;                  // launch shapes: alternative shape of bit 0 the x passes, bit 1 the
                                  // y passes, bit 2 the z pass; bit 3 two z-pass exchange buffers
 };
@@ -66,6 +67,7 @@ struct KrylovGraph {
 // variant; green_row_ctas_max covers every variant.
 int green_row_ctas(int n, int tile);
 int green_row_ctas_max(int n);
+int green_plane_ctas(int n, int tile);     // CTAs per slot of pass 1/5 over one z-plane
 // shape[6] = lines per CTA and threads per line of passes 1/5, columns per
 // CTA and threads per column of passes 2/4, then of pass 3 (zeros if n is
 // unsupported); smem = the largest dynamic shared memory of the tile's passes.

@@ -330,10 +330,11 @@ cudaError_t glaunch_ev(mqnpm_handle* h, GreenCall c, cudaStream_t s, cudaEvent_t
 }
 
 // The pass timers cover the full applies only: a plane-input apply (the
-// adjoint lift) skips most of passes 1-3, and counting its slots at the full
-// algorithmic bytes would overstate the bandwidth figures.
+// adjoint lift) skips most of passes 1-3 and a plane-output apply (first-Born
+// data) most of passes 3-5, so counting their slots at the full algorithmic
+// bytes would overstate the bandwidth figures.
 cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
-  return glaunch_ev(h, c, s, c.plane ? nullptr : profile_slot(h, c.nb));
+  return glaunch_ev(h, c, s, (c.plane || c.outplane) ? nullptr : profile_slot(h, c.nb));
 }
 
 GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
@@ -583,6 +584,7 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   int worst = MQNPM_OK;
+  int parts = m * w.ctas_row;          // detector partials to sum
   if (h->model == MQNPM_MODEL_LS) {
     int rc = forward_ls(h, m, x, it_chunk, 2, 0);
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
@@ -592,6 +594,7 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
   } else {
     GreenCall c = base_call(h, m, false);
     c.pro = PRO_BORN;
+    c.outplane = true;                 // only the detector plane of G(x u_in) is used
     c.pa.x = x;
     c.pa.tab = h->tab;
     c.pa.illum = w.illum;
@@ -601,10 +604,14 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     c.ea.illum = w.illum;
     c.part_epi = w.partd;
     CK(glaunch(h, c, s));
+    parts = m * green_plane_ctas(h->n, h->tile);   // the plane pass 5 writes fewer partials
   }
   CK(cudaGetLastError());
-  if (h->remote) CK(detector_forward(h, det_out, m, ym, w.illum));   // D(slice) - y, partials replaced
-  k_sum_all<<<1, 256, 0, s>>>(w.partd, m * w.ctas_row, w.dscal);
+  if (h->remote) {                     // D(slice) - y; the partials are rewritten per row CTA
+    CK(detector_forward(h, det_out, m, ym, w.illum));
+    parts = m * w.ctas_row;
+  }
+  k_sum_all<<<1, 256, 0, s>>>(w.partd, parts, w.dscal);
   CK(cudaMemcpyAsync(w.h_scal, w.dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
   h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + 1;
   return worst;
@@ -748,6 +755,7 @@ int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, cons
       CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, s));
       GreenCall c = base_call(h, m, false);
       c.pro = PRO_BORN;                 // S G (q u_in)
+      c.outplane = true;
       c.pa.x = q;
       c.pa.tab = h->tab;
       c.pa.illum = w.illum;
