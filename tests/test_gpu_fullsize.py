@@ -151,6 +151,39 @@ def test_ls128_gradient_central_difference():
     h.close()
 
 
+def test_ls128_gradient_16_seeded_directions():
+    """ls128 with the hand-written adjoint: the mini-batch gradient against
+    central differences of the loss along 16 seeded directions, each a
+    Gaussian bump (sigma 4 voxels) centred on a random voxel of the phantom
+    (the voxel-direction gradient check of the autograd configuration), batch
+    8, Krylov tol 1e-6."""
+    w = synth.workload("ls128")
+    h = handle(w, "ls", 1e-6, w.batch)
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    measure(h, w, xt, illum)
+    x0 = 0.5 * xt
+    g, f0, _ = h.grad_batch(x0, illum, 1.0)
+    g = g.clone()
+    n = w.n
+    support = np.argwhere(xt.reshape(n, n, n).cpu().numpy() > 0)
+    rng = np.random.default_rng(16)
+    centres = support[rng.choice(len(support), 16, replace=False)]
+    ax = np.arange(n, dtype=np.float64)
+    for k, (cz, cy, cx) in enumerate(centres):
+        bz, by, bx = (np.exp(-(ax - c) ** 2 / (2 * 4.0 ** 2)) for c in (cz, cy, cx))
+        d = torch.from_numpy((bz[:, None, None] * by[None, :, None] * bx[None, None, :]).astype(np.float32)
+                             .reshape(-1)).to(DEV)
+        eps = 0.01
+        fp, _ = h.loss_batch(x0 + eps * d, illum, 1.0)
+        fm, _ = h.loss_batch(x0 - eps * d, illum, 1.0)
+        fd = (fp - fm) / (2 * eps)
+        an = dot64(g, d)
+        assert abs(fd - an) <= 5e-3 * abs(an), (k, fd, an, abs(fd - an) / abs(an))
+    assert np.isfinite(f0) and f0 > 0
+    h.close()
+
+
 def test_ls128_batched_equals_single_launches():
     """The bench configuration (batch 8, tolerance 1e-4): each slot of the
     batched solve gives the gradient and iteration counts of a solve alone."""
