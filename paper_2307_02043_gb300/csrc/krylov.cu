@@ -24,9 +24,9 @@ struct dc {
   double re, im;
 };
 MQ_D dc dmul(dc a, dc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-MQ_D dc ddiv(dc a, dc b) {
-  const double d = b.re * b.re + b.im * b.im;
-  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+MQ_D dc ddiv(dc a, dc b) {   // one FP64 reciprocal (division is a long sequence on this device)
+  const double r = 1.0 / (b.re * b.re + b.im * b.im);
+  return {(a.re * b.re + a.im * b.im) * r, (a.im * b.re - a.re * b.im) * r};
 }
 MQ_D bool dfinite(dc a) { return isfinite(a.re) && isfinite(a.im); }
 
@@ -37,7 +37,8 @@ MQ_D void sum_partials(const double* part, int b, int nctas, double (&out)[K]) {
   double v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0.0;
-  for (int c = threadIdx.x; c < nctas; c += blockDim.x) {
+#pragma unroll 4
+  for (int c = threadIdx.x; c < nctas; c += blockDim.x) {   // unrolled: loads of 4 CTAs in flight
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] += part[((size_t)b * nctas + c) * K + k];
   }
@@ -112,8 +113,9 @@ __global__ void k_fin_omega(KState* st, const double* part1, const double* part5
       k.active = 0;
       return;
     }
-    k.omega_re = s5[0] / s5[2];
-    k.omega_im = s5[1] / s5[2];
+    const double r = 1.0 / s5[2];
+    k.omega_re = s5[0] * r;
+    k.omega_im = s5[1] * r;
   }
 }
 

@@ -64,35 +64,46 @@ __global__ void k_gram_setup(const double* part, int nctas, double tau, double* 
   __shared__ double A[S * S];
   __shared__ int ok;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  __shared__ double rdiag[S];   // reciprocals of the factor's diagonal
   for (int k = warp; k < NV; k += nwarps) {
-    double v = 0.0;
-    for (int c = lane; c < nctas; c += 32) v += part[(size_t)c * NV + k];
-    v = warp_sum(v);
-    if (lane == 0) tot[k] = v;
+    // eight independent partial sums per lane keep eight loads in flight
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int c = lane;
+    for (; c + 7 * 32 < nctas; c += 8 * 32) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] += part[(size_t)(c + 32 * u) * NV + k];
+    }
+    for (int u = 0; c < nctas; c += 32, ++u) v[u & 7] += part[(size_t)c * NV + k];
+    double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    t = warp_sum(t);
+    if (lane == 0) tot[k] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    const double inv_tau = 1.0 / tau;
     int k = 0;
     for (int a = 0; a < S; ++a)
       for (int b = a; b < S; ++b) {
         scal[OFF_G + a * S + b] = tot[k];
         scal[OFF_G + b * S + a] = tot[k];
-        A[a * S + b] = A[b * S + a] = (a == b ? 1.0 : 0.0) + tot[k] / tau;
+        A[a * S + b] = A[b * S + a] = (a == b ? 1.0 : 0.0) + tot[k] * inv_tau;
         ++k;
       }
     for (int a = 0; a < S; ++a) scal[OFF_UV + a] = tot[NG + a];
-    // lower Cholesky factor in place
+    // lower Cholesky factor in place, one FP64 reciprocal per column (FP64
+    // division is a long instruction sequence on this device)
     ok = 1;
     for (int j = 0; j < S; ++j) {
       double d = A[j * S + j];
       for (int q = 0; q < j; ++q) d -= A[j * S + q] * A[j * S + q];
       if (!(d > 0.0)) { ok = 0; break; }
-      const double l = sqrt(d);
+      const double l = sqrt(d), rl = 1.0 / l;
       A[j * S + j] = l;
+      rdiag[j] = rl;
       for (int i = j + 1; i < S; ++i) {
         double t = A[i * S + j];
         for (int q = 0; q < j; ++q) t -= A[i * S + q] * A[j * S + q];
-        A[i * S + j] = t / l;
+        A[i * S + j] = t * rl;
       }
     }
   }
@@ -105,12 +116,12 @@ __global__ void k_gram_setup(const double* part, int nctas, double tau, double* 
       for (int i = 0; i < S; ++i) {
         double t = b[i];
         for (int q = 0; q < i; ++q) t -= A[i * S + q] * b[q];
-        b[i] = t / A[i * S + i];
+        b[i] = t * rdiag[i];
       }
       for (int i = S - 1; i >= 0; --i) {
         double t = b[i];
         for (int q = i + 1; q < S; ++q) t -= A[q * S + i] * b[q];
-        b[i] = t / A[i * S + i];
+        b[i] = t * rdiag[i];
       }
     }
     for (int i = 0; i < S; ++i) scal[OFF_M + i * S + col] = b[i];
