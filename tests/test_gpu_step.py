@@ -107,6 +107,32 @@ def physics_tv(x, kind):
     return otv.tv(x, kind)
 
 
+def test_non_default_stream_gives_identical_results(ls32):
+    """Every call runs on the caller's current stream (set per call): outer
+    iterations and a gradient on a side stream equal those on the default
+    stream bit for bit (captured iteration graphs, event records and copies all
+    follow the caller's stream)."""
+    import contextlib
+    w, kd, om, ys, subs, so, alpha, _, _ = ls32
+    out = []
+    for side in (False, True):
+        h = handle(w, kd, so, alpha, warm_start=True)
+        ctx = torch.cuda.stream(torch.cuda.Stream()) if side else contextlib.nullcontext()
+        with ctx:
+            h.set_measurements(torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1))
+            x = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+            for _ in range(w.S + 2):
+                h.step(x)
+            g, loss, _ = h.grad_batch(x, [0, 1], 0.5)
+            xc, gc = x.cpu(), g.cpu()
+        torch.cuda.synchronize()
+        out.append((xc, gc, loss))
+        h.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
 def test_strategy2_trajectory_matches_oracle(ls32):
     """Strategy II (s' drawn uniformly, seeded draws passed to both sides) on
     config 1: per-iterate error against the FP64 oracle."""
