@@ -235,6 +235,13 @@ def test_remote_detector_propagation_pins():
     pw = np.exp(1j * (kx * xx + ky * yy))
     kz = math.sqrt(kb * kb - kx * kx - ky * ky)
     assert np.allclose(ph.propagate(pw, H), np.exp(1j * kz * d) * pw, atol=1e-12)
+    # an evanescent grid wave (|k| > k_b, pupil opened past 1) decays by exp(-sqrt(k^2 - k_b^2) d)
+    fe = 6
+    ke = 2 * math.pi * fe / (n * h)
+    assert ke > kb
+    ew = np.exp(1j * ke * xx)
+    He = ph.transfer_function(n, kb, h, d, 3.0)
+    assert np.allclose(ph.propagate(ew, He), math.exp(-math.sqrt(ke * ke - kb * kb) * d) * ew, atol=1e-12)
     H1, H2 = ph.transfer_function(n, kb, h, 3.0, 0.9), ph.transfer_function(n, kb, h, 4.5, 0.9)
     assert np.allclose(ph.propagate(ph.propagate(a, H1), H2), ph.propagate(a, H), atol=1e-12)
     band = ph.propagate(a, ph.transfer_function(n, kb, h, 0.0, 0.9))   # pupil-limited field
