@@ -7,6 +7,8 @@ the ones the oracle runs).
   solved by the active-set BVLS method of scipy.
 * box_qp_enumerate: min_{x in [lo,hi]^N} 1/2 ||x - w||_B^2 by enumerating all
   3^N active sets and keeping the one that satisfies the KKT conditions.
+* admm_quadratic_tv: the same ADMM for min_{x in C} 1/2 x^T Q x + q^T x + c TV(x)
+  with a general dense quadratic (an objective written term by term).
 """
 import itertools
 
@@ -97,3 +99,34 @@ def box_qp_enumerate(w, Bmat, lo, hi):
             if best is None or val < best[0]:
                 best = (val, x)
     return best[1]
+
+
+def admm_quadratic_tv(Q, q, shape, c, lo, hi, kind="iso", rho=1.0, iters=20000):
+    """min_{x in [lo,hi]^N} 1/2 x^T Q x + q^T x + c TV(x) by ADMM with the same
+    splitting as admm_wprox (z1 = grad x, z2 = x), for a general quadratic:
+    no metric, no completed square, so a model whose objective is written as
+    a sum of quadratic terms can be solved as printed."""
+    N = int(np.prod(shape))
+    D = len(shape)
+    K = grad_matrix(shape)
+    x = np.clip(np.linalg.solve(Q, -q), lo, hi)
+    z1 = K @ x
+    z2 = x.copy()
+    m1 = np.zeros_like(z1)
+    m2 = np.zeros_like(z2)
+    Ainv = np.linalg.inv(Q + rho * (K.T @ K) + rho * np.eye(N))
+    for _ in range(iters):
+        x = Ainv @ (-q + rho * K.T @ (z1 - m1) + rho * (z2 - m2))
+        kx = K @ x
+        t = kx + m1
+        if kind == "iso":
+            g = t.reshape(D, N)
+            nrm = np.sqrt(np.sum(g * g, axis=0))
+            shrink = np.maximum(0.0, 1.0 - (c / rho) / np.maximum(nrm, 1e-300))
+            z1 = (g * shrink[None]).reshape(-1)
+        else:
+            z1 = np.sign(t) * np.maximum(np.abs(t) - c / rho, 0.0)
+        z2 = np.clip(x + m2, lo, hi)
+        m1 += kx - z1
+        m2 += x - z2
+    return z2.reshape(shape)

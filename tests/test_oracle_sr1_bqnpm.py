@@ -7,6 +7,8 @@ import pytest
 import synth
 from oracle import bqnpm, physics, sr1
 
+from tests import independent as ind
+
 
 def test_sr1_secant_and_bounds():
     rng = np.random.default_rng(0)
@@ -122,3 +124,68 @@ def test_bias_error_pins():
     assert one.bias_error(x, 0) == 0.0
     same = bqnpm.BQNPM(m, ys, [subs[0], subs[0]], [1.0, 1.0], lam=1e-4, box=w.box)
     assert same.bias_error(x, 1) <= 1e-30
+
+
+class _FixedGradient:
+    """Stand-in for the physics in the k > S pin: every subset's gradient at
+    the current iterate is the prescribed g (the test fixes g = grad F_{s'}(x_{k-1}))."""
+
+    def __init__(self, n, g):
+        self.n = n
+        self.g = g
+
+    def batch_loss_grad(self, x, subset, ys, scale):
+        return 0.0, self.g.copy()
+
+
+def test_bqnpm_step_beyond_S_solves_eq_4_4():
+    """One iteration k > S of Algorithm 4.1 (steps 8-10, Eq. 4.4 -> Eq. 4.5) against an
+    independent ADMM solve of the model it minimises, written term by term:
+
+        argmin_{x in C} (1/S) sum_s [ <g_s, x - x_s> + 1/(2a) ||x - x_s||^2_{B_s} ] + lam TV(x)
+
+    with x_s = x_{k-1} and g_s = grad F_{s'}(x_{k-1}) for every s (strategy I / II reading of
+    Section 4.2), B_{s'} the SR1 update of this iteration and every other B_s = tau_s I + u_s u_s^T
+    left as stored.  No square is completed here, so the a S factor of v_k, the c = a S lam of the
+    proximal mapping and tau* = sum_s tau_s (un-updated terms included) are all exercised."""
+    rng = np.random.default_rng(21)
+    n, S = 3, 3
+    shape, N = (n, n, n), n ** 3
+    a, lam, lo, hi = 0.7, 0.03, 0.0, 0.5
+    x_prev = rng.uniform(0.05, 0.45, shape)
+    g = 0.3 * rng.standard_normal(shape)
+    subs = [np.array([s]) for s in range(S)]
+    opt = bqnpm.BQNPM(_FixedGradient(n, g), None, subs, [0.9, 1.3, 1.1], lam=lam, box=(lo, hi),
+                      kind="iso", step=a, gamma=0.8, dual_iters=4000, newton_tol=1e-13)
+    # state after k = 5: every subset visited; iteration k = 6 takes s' = 2 (strategy I)
+    opt.k = 5
+    for s in range(S):
+        opt.xbar[s] = rng.uniform(0.0, 0.5, shape)
+        opt.gbar[s] = rng.standard_normal(shape)
+    opt.tau = [0.8, 1.7, 1.2]
+    opt.u = [0.25 * rng.standard_normal(shape), 0.25 * rng.standard_normal(shape), None]
+    sp = 2
+    A = rng.standard_normal((N, N))
+    H = A @ A.T / N + 0.5 * np.eye(N)
+    s_vec = (x_prev - opt.xbar[sp]).reshape(-1)
+    m_vec = H @ s_vec
+    opt.gbar[sp] = (g.reshape(-1) - m_vec).reshape(shape)
+    x_new = opt.step(x_prev)
+    assert opt.history[-1]["s"] == sp and opt.history[-1]["sr1"] == "rank1"
+    Bs = []
+    for s in range(S):
+        B = opt.tau[s] * np.eye(N)
+        if opt.u[s] is not None:
+            B = B + np.outer(opt.u[s].reshape(-1), opt.u[s].reshape(-1))
+        Bs.append(B)
+    assert np.allclose(Bs[sp] @ s_vec, m_vec, rtol=1e-10, atol=1e-12)   # the SR1 secant equation
+    assert opt.tau[0] == 0.8 and opt.tau[1] == 1.7                         # B_s, s != s', untouched
+    # the model of Eq. 4.4 as 1/2 x^T Q x + q^T x (+ constants) + lam TV(x)
+    gf, xf = g.reshape(-1), x_prev.reshape(-1)
+    Q = sum(B for B in Bs) / (a * S)
+    q = sum(gf - (B @ xf) / a for B in Bs) / S
+    ref = ind.admm_quadratic_tv(Q, q, shape, lam, lo, hi, "iso", iters=30000)
+    # the TV term and the box are both active at this solution
+    unreg = np.clip(np.linalg.solve(Q, -q), lo, hi).reshape(shape)
+    assert np.max(np.abs(unreg - ref)) > 1e-2
+    assert np.max(np.abs(x_new - ref)) < 2e-6
