@@ -28,9 +28,14 @@ Arrays are indexed [z, y, x] (x fastest in memory).
 from __future__ import annotations
 
 import math
+import os
 from typing import Callable, Sequence, Tuple
 
 import numpy as np
+import scipy.fft as sfft
+
+# Threads of the FFT library routine: every core this process may run on.
+FFT_WORKERS = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
 def kb_default(h: float = 1.0) -> float:
@@ -67,7 +72,7 @@ def green_kernel(n: int, kb: float, h: float = 1.0) -> np.ndarray:
 
 def green_hat(n: int, kb: float, h: float = 1.0) -> np.ndarray:
     """K_hat = DFT_P of the periodic kernel (P^3 complex128)."""
-    return np.fft.fftn(green_kernel(n, kb, h))
+    return sfft.fftn(green_kernel(n, kb, h), workers=FFT_WORKERS)
 
 
 def green_apply(v: np.ndarray, khat: np.ndarray, adjoint: bool = False) -> np.ndarray:
@@ -82,7 +87,7 @@ def green_apply(v: np.ndarray, khat: np.ndarray, adjoint: bool = False) -> np.nd
     pad = np.zeros((P, P, P), dtype=np.complex128)
     pad[:n, :n, :n] = v
     k = np.conj(khat) if adjoint else khat
-    out = np.fft.ifftn(k * np.fft.fftn(pad))
+    out = sfft.ifftn(k * sfft.fftn(pad, workers=FFT_WORKERS), workers=FFT_WORKERS)
     return out[:n, :n, :n]
 
 
@@ -98,7 +103,7 @@ def transfer_function(n: int, kb: float, h: float, distance: float, na: float) -
 
 def propagate(field: np.ndarray, H: np.ndarray, adjoint: bool = False) -> np.ndarray:
     """D f = F^-1 (H F f) on an n x n slice; D^H uses conj(H)."""
-    return np.fft.ifft2((np.conj(H) if adjoint else H) * np.fft.fft2(field))
+    return sfft.ifft2((np.conj(H) if adjoint else H) * sfft.fft2(field, workers=FFT_WORKERS), workers=FFT_WORKERS)
 
 
 def incident_field(n: int, kdir: Sequence[float], kb: float, h: float = 1.0) -> np.ndarray:
