@@ -122,6 +122,10 @@ typedef struct mqnpm_config {
                               framed by guard bands of this many bytes (rounded
                               up to 256) filled with 0xA5, checked by
                               mqnpm_check_guards                              */
+  long long barrier_wait_cycles; /* longest wait of one block of the weighted
+                              proximal mapping at a grid barrier, in SM clock
+                              cycles, before it gives up and the call returns
+                              MQNPM_ERR_TIMEOUT; 0 selects 4e9 (about 2 s)    */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;
@@ -157,6 +161,13 @@ const char* mqnpm_last_error(const mqnpm_handle* h);
 
 /* Replace the stream all later work is ordered on. */
 int mqnpm_set_stream(mqnpm_handle* h, void* stream);
+
+/* Replace barrier_wait_cycles (failure detection: no counterpart in the
+ * paper).  cycles >= 0; 0 selects the default.  A wait that runs out makes
+ * the next mqnpm_wprox or mqnpm_step return MQNPM_ERR_TIMEOUT with its
+ * outputs unspecified; the handle stays usable and the next call starts
+ * clean.  INVALID_ARG for a negative value. */
+int mqnpm_set_wait_limit(mqnpm_handle* h, long long cycles);
 
 /* Bytes of device memory the handle holds. */
 size_t mqnpm_workspace_bytes(const mqnpm_handle* h);
@@ -293,30 +304,32 @@ int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms);
 int mqnpm_profile_begin(mqnpm_handle* h, int max_calls);
 int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches, int* calls);
 
-/* Allocation-free Green's convolution (no counterpart in the paper: the
- * operation is the G v / G^H v of Section 6, as mqnpm_green_apply computes it
- * for one volume, without a handle).  It is for callers that cannot allocate
+/* Allocation-free Green's convolution.  The paper has no counterpart: this is
+ * a library service, computing for one volume and without a handle the same
+ * G v / G^H v as mqnpm_green_apply.  It is for callers that cannot allocate
  * device memory: code running inside another framework's memory pool or on a
  * device whose memory is already handed out, and allocator hooks that must not
  * re-enter the allocator.  It calls no cudaMalloc/cudaFree and no allocating
  * library routine; its scratch is one file-scope device array of
  * mqnpm_noalloc_scratch_bytes() bytes (3,012,352 B, 2.9 MiB), present on every GPU
- * that loads the library, whose address is taken with cudaGetSymbolAddress
- * once per device.
+ * that loads the library until the process exits.
  *   n: grid edge, at most 32, with 2n a compiled transform length
  *      (n in {8, 12, 16, 24, 32}); larger or unsupported n returns
  *      MQNPM_ERR_INVALID_ARG and prints why on stderr.
  *   h, kb: voxel size and background wavenumber (> 0).
  *   v, out: device, n^3 complex64 each ([z][y][x], interleaved re/im), distinct.
  *   adjoint != 0 selects G^H.  stream: cudaStream_t (NULL: legacy stream).
- * Works on the current device.  The first call on a device, and the first after
- * n, h or kb changed, builds the kernel spectrum in the scratch array and
- * synchronises the stream; make such a call before any stream capture.  Every
- * call synchronises the stream before it returns (it reads the device error
- * flag, which must start at zero and is reset when raised).  All calls on one
- * device share the scratch array: calls from several host threads are
- * serialised by a lock, but calls on different streams whose work overlaps in
- * any other way (e.g. a captured graph replayed beside a direct call) race.
+ * Works on the current device.  Set-up: the first call on a device (and the
+ * first in a new context of that device, e.g. after cudaDeviceReset) takes the
+ * array's device address with cudaGetSymbolAddress, with the device current;
+ * that call, and the first after n, h or kb changed, also builds the kernel
+ * spectrum in the array and synchronises the stream, so make it before any
+ * stream capture.  Every call synchronises the stream before it returns (it
+ * reads the device error flag, which must start at zero and is reset when
+ * raised).  All calls on one device share the array, which keeps the last
+ * call's spectrum; calls whose GPU work overlapped would race on it.  This
+ * entry point keeps its own calls apart: each holds a process-wide lock from
+ * its set-up to its final synchronisation.
  * Returns MQNPM_OK, MQNPM_ERR_INVALID_ARG, MQNPM_ERR_CUDA or MQNPM_ERR_TIMEOUT
  * (a bounded wait for a tile load gave up). */
 int mqnpm_green_apply_noalloc(int n, double h, double kb, const float* v, float* out, int adjoint,

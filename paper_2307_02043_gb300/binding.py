@@ -53,6 +53,7 @@ class Config(ctypes.Structure):
         ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
         ("green_hat", ctypes.POINTER(ctypes.c_float)), ("tile", ctypes.c_int),
         ("det_distance", ctypes.c_double), ("det_na", ctypes.c_double), ("guard_bytes", ctypes.c_size_t),
+        ("barrier_wait_cycles", ctypes.c_longlong),
     ]
 
 
@@ -72,6 +73,7 @@ SIGNATURES = {
     "mqnpm_destroy": (None, [ctypes.c_void_p]),
     "mqnpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "mqnpm_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mqnpm_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "mqnpm_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "mqnpm_set_measurements": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mqnpm_green_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -176,7 +178,8 @@ class MQNPM:
                  dual_iters: int = 20, newton_tol: float = 1e-6, newton_maxit: int = 50, max_batch: int = 8,
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
                  direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1,
-                 det_distance: float = 0.0, det_na: float = 0.0, guard_bytes: int = 0):
+                 det_distance: float = 0.0, det_na: float = 0.0, guard_bytes: int = 0,
+                 barrier_wait_cycles: int = 0):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -223,6 +226,7 @@ class MQNPM:
         cfg.det_distance = float(det_distance)
         cfg.det_na = float(det_na)
         cfg.guard_bytes = int(guard_bytes)
+        cfg.barrier_wait_cycles = int(barrier_wait_cycles)
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
             if gh.size != (self.n + 1) ** 3:
@@ -285,6 +289,10 @@ class MQNPM:
                                         int(s_prime), out)
         self._raise(rc, allow_not_converged)
         return {"bias_error": out[0], "step_sq": out[1], "data_term": out[2]}
+
+    def set_wait_limit(self, cycles: int):
+        """Grid-barrier wait limit of the proximal mapping (SM cycles; 0 = default)."""
+        self._raise(self.lib.mqnpm_set_wait_limit(self._h, int(cycles)))
 
     def check_guards(self) -> int:
         """Guard bands (guard_bytes > 0) no longer holding their fill pattern."""

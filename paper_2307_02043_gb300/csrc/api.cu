@@ -179,6 +179,12 @@ int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms) {
 
 size_t mqnpm_workspace_bytes(const mqnpm_handle* h) { return h ? h->bytes : 0; }
 
+int mqnpm_set_wait_limit(mqnpm_handle* h, long long cycles) {
+  if (!h || cycles < 0) return set_error(h, MQNPM_ERR_INVALID_ARG, "set_wait_limit: negative limit");
+  h->barrier_limit = cycles > 0 ? cycles : 4000000000LL;
+  return MQNPM_OK;
+}
+
 int mqnpm_set_stream(mqnpm_handle* h, void* stream) {
   if (!h) return MQNPM_ERR_INVALID_ARG;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -227,7 +233,8 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
       !(cfg->krylov_tol > 0) || cfg->krylov_maxit < 1 || (cfg->model != MQNPM_MODEL_LS && cfg->model != MQNPM_MODEL_BORN) ||
       (cfg->tv != MQNPM_TV_ISO && cfg->tv != MQNPM_TV_ANISO) || (cfg->strategy != 1 && cfg->strategy != 2) ||
       !(cfg->gamma > 0 && cfg->gamma <= 1.0) || cfg->tile < -1 || cfg->tile >= MQ_TILES ||
-      !(cfg->det_na >= 0.0 && std::isfinite(cfg->det_na)) || !std::isfinite(cfg->det_distance)) {
+      !(cfg->det_na >= 0.0 && std::isfinite(cfg->det_na)) || !std::isfinite(cfg->det_distance) ||
+      cfg->barrier_wait_cycles < 0) {
     fprintf(stderr, "mqnpm_create: invalid configuration\n");
     delete h;
     return MQNPM_ERR_INVALID_ARG;
@@ -275,6 +282,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->direct_launches = cfg->direct_launches != 0;
   h->budget = cfg->hbm_budget_bytes;
   h->guard = (cfg->guard_bytes + 255) / 256 * 256;
+  if (cfg->barrier_wait_cycles > 0) h->barrier_limit = cfg->barrier_wait_cycles;
   h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
   h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);
   h->subset_of.assign(cfg->subset_of, cfg->subset_of + cfg->L);

@@ -141,6 +141,7 @@ struct mqnpm_handle {
   double delta1 = 1e-8, delta2 = 1e-12, krylov_tol = 1e-6, newton_tol = 1e-6;
   int krylov_maxit = 500, dual_iters = 20, newton_maxit = 50, max_batch = 1, device = 0;
   int check_every = 1;
+  long long barrier_limit = 4000000000LL;   // grid-barrier wait of the prox kernel, SM cycles
   std::vector<double> kdir, alpha;
   std::vector<int> subset_of, draws;
   std::vector<std::vector<int>> subsets;

@@ -12,8 +12,10 @@
 // kernel spectrum, its FP64 construction buffers and the twiddles for grids
 // up to NA_MAX_N^3.  Every GPU that loads the library keeps this array until
 // the process exits.  In host code the array's name is only a stand-in: its
-// device address comes from cudaGetSymbolAddress, once per device, with that
-// device current.
+// device address comes from cudaGetSymbolAddress, once per device (again only
+// when the device's context has changed), with that device current.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -44,6 +46,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 // Per-device set-up state (host side).
 struct NoallocDevice {
   unsigned char* base = nullptr;   // device address of g_noalloc_scratch
+  unsigned long long ctx = 0;      // unique id of the context the address was taken in
   int n = 0;                       // grid of the spectrum currently held (0: none)
   double h = 0.0, kb = 0.0;
   alignas(64) unsigned char tmap[128];
@@ -51,6 +54,31 @@ struct NoallocDevice {
 constexpr int NA_MAX_DEVICES = 64;
 NoallocDevice g_devices[NA_MAX_DEVICES];
 std::mutex g_mutex;
+
+// Unique id of the calling thread's current context (driver entry points
+// through the runtime's query, so the library does not link libcuda).  False
+// when no context is current or the id cannot be read.  A device reset or a
+// re-created primary context gets a new id, which sends the next call through
+// the set-up again (the module, and with it the scratch array, may have moved).
+bool current_context_id(unsigned long long* id) {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f1 ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f2)
+      return false;
+    get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+    get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -69,10 +97,17 @@ extern "C" int mqnpm_green_apply_noalloc(int n, double h, double kb, const float
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return MQNPM_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
   NoallocDevice& d = g_devices[dev];
-  if (d.base == nullptr) {
+  unsigned long long ctx = 0;
+  if (d.base == nullptr || !current_context_id(&ctx) || ctx != d.ctx) {
+    // set-up of this device (first call, or a new context since the last one):
+    // the device address of the scratch array, taken with the device current
     void* p = nullptr;
+    d.base = nullptr;
+    d.n = 0;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return MQNPM_ERR_CUDA;
+    if (!current_context_id(&ctx)) return MQNPM_ERR_CUDA;
     d.base = static_cast<unsigned char*>(p);
+    d.ctx = ctx;
   }
   float2* T1 = reinterpret_cast<float2*>(d.base + NA_T1);
   float2* T2 = reinterpret_cast<float2*>(d.base + NA_T2);

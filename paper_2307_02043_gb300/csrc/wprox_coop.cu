@@ -1046,7 +1046,7 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.step = (float)(tau / (4.0 * 3.0 * c));
   a.tol = h->newton_tol;
   a.maxit = h->newton_maxit;
-  a.limit = 4000000000LL;   // about 2 s at 2 GHz per wait
+  a.limit = h->barrier_limit;   // per wait (default about 2 s at 2 GHz)
   a.trace = h->wp.trace;
   a.trace_cap = h->wp.trace_cap;
   cudaError_t e = h->tv == MQNPM_TV_ISO ? dispatch<MQNPM_TV_ISO>(h, S_eff, a) : dispatch<MQNPM_TV_ANISO>(h, S_eff, a);

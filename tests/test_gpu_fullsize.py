@@ -14,6 +14,10 @@ Tolerances (written per test):
     1e-6 Krylov tolerance ~1e-5 / 0.16 relative, so 2e-3.
   * batching: slots of one batched launch and separate launches differ only in
     the summation order of the gradient over illuminations: 1e-5.
+  * against the oracle at 128^3: gradient 1e-4 norm-wise and loss 1e-5 with the
+    GPU Krylov solves run to 1e-6 (the complex64 floor) and the oracle's to
+    1e-9; weighted proximal map 1e-5 norm-wise at equal dual iterations (the
+    tolerances of the small-size parity tests).
 """
 import math
 
@@ -22,6 +26,7 @@ import pytest
 
 import synth
 from oracle import physics
+from oracle import wprox as owprox
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -241,3 +246,55 @@ def test_uneven_grid_gradient(n):
     measure(h, w, xt, illum)
     central_difference_check(h, 0.5 * xt, xt, illum, 0.02, 2e-3)
     h.close()
+
+
+# ------------------------------------------------- against the oracle at 128^3
+def test_ls128_gradient_matches_oracle():
+    """ls128 in the bench's launch configuration (batch-8 workspace, the
+    autotuned launch shapes): two illuminations of subset 0, F_s scaling S/L,
+    at x = 0.5 x_true, against the FP64 oracle's adjoint-state gradient at the
+    same (float32-rounded) x.  The measurements are zero, so the data term is
+    1/2 ||S(u - u_in)||^2 and no input comes from the GPU path."""
+    w = synth.workload("ls128")
+    h = handle(w, "ls", 1e-6, w.batch)
+    illum = [int(i) for i in synth.subsets(w)[0][:2]]
+    x0 = (0.5 * synth.phantom(w)).astype(np.float32)
+    h.set_measurements(torch.zeros(w.L * w.n * w.n, dtype=torch.complex64, device=DEV))
+    scale = w.S / w.L
+    g, f, its = h.grad_batch(torch.from_numpy(x0).to(DEV).reshape(-1), illum, scale)
+    g = g.cpu().numpy().astype(np.float64).reshape(w.n, w.n, w.n)
+    h.close()
+    om = physics.Model(w.n, synth.illumination_dirs(w), "ls", tol=1e-9)
+    ys = np.zeros((w.L, w.n * w.n), dtype=np.complex128)
+    fo, go = om.batch_loss_grad(x0.astype(np.float64), illum, ys, scale)
+    assert all(a > 0 and b > 0 for a, b in its)
+    assert abs(f - fo) <= 1e-5 * abs(fo), (f, fo)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
+@pytest.mark.parametrize("kind", ["iso", "aniso"])
+def test_wprox_128_rank8_matches_oracle(kind):
+    """The weighted proximal map at the bench's grid and rank (128^3, eight
+    rank-one terms, 20 dual iterations, warm-started dual field).  The
+    cooperative kernel's grid-stride loops take several trips per phase at this
+    size (304 blocks x 256 threads x 4 voxels per trip), which no small grid
+    reaches."""
+    n, S_eff, J, tau, c = 128, 8, 20, 1.5, 2e-3
+    rng = np.random.default_rng(128 + (kind == "aniso"))
+    v = rng.uniform(-0.02, 0.07, (n, n, n))
+    v[n // 4: n // 2, n // 4: 3 * n // 4, :] += 0.03
+    U = rng.standard_normal((S_eff, n, n, n)) * 0.05
+    P0 = rng.uniform(-0.5, 0.5, (3, n, n, n))
+    h = binding.MQNPM(n, [[0.0, 0.0, 1.0]], [0], [1.0], tv=kind, box=(0.0, 0.05), dual_iters=J,
+                      newton_tol=1e-6, max_batch=1)
+    Pw = torch.from_numpy(P0.astype(np.float32)).to(DEV).reshape(-1)
+    xg = h.wprox(torch.from_numpy(v.astype(np.float32)).to(DEV).reshape(-1), tau,
+                 torch.from_numpy(U.astype(np.float32)).to(DEV).reshape(-1), c, P_warm=Pw)
+    xg = xg.cpu().numpy().astype(np.float64).reshape(n, n, n)
+    Pg = Pw.cpu().numpy().astype(np.float64).reshape(3, n, n, n)
+    h.close()
+    xo, Po, _ = owprox.wprox(v.astype(np.float32).astype(np.float64), tau,
+                             U.astype(np.float32).astype(np.float64), c, 0.0, 0.05, kind, J,
+                             P0=P0.astype(np.float32).astype(np.float64), newton_tol=1e-6)
+    assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo), np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert np.linalg.norm(Pg - Po) <= 1e-4 * np.linalg.norm(Po)

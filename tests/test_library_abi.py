@@ -40,7 +40,7 @@ def test_config_struct_layout_matches_header():
         text = f.read()
     body = text[text.index("typedef struct mqnpm_config"):text.index("} mqnpm_config;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    fields = re.findall(r"(?:int|double|size_t|void\*|const \w+\*)\s+([\w, ]+);", body)
+    fields = re.findall(r"(?:long long|int|double|size_t|void\*|const \w+\*)\s+([\w, ]+);", body)
     names = [f.strip() for group in fields for f in group.split(",")]
     mirror = [f for f, _ in binding.Config._fields_]
     mirror = ["lambda" if f == "lam" else f for f in mirror]
@@ -91,7 +91,7 @@ def _config(**kw):
     ("gamma", 1.5), ("h", 0.0), ("kb", -1.0), ("lam", -1.0), ("box_lo", 1.0), ("step", 0.0),
     ("krylov_tol", 0.0), ("krylov_maxit", 0), ("dual_iters", -1), ("model", 7), ("tv", 5),
     ("strategy", 3), ("tile", -2), ("tile", 16), ("det_na", -0.5), ("det_na", float("inf")),
-    ("det_distance", float("nan"))])
+    ("det_distance", float("nan")), ("barrier_wait_cycles", -1)])
 def test_create_rejects_invalid_configurations(field, value):
     """Host-side validation of mqnpm_create runs before any CUDA call: every
     out-of-range option returns MQNPM_ERR_INVALID_ARG and no handle."""

@@ -72,6 +72,29 @@ def test_noalloc_switches_grid_and_holds_no_new_memory():
     assert torch.cuda.mem_get_info(DEV)[0] == free0
 
 
+def test_noalloc_rebuilds_the_spectrum_for_new_h_and_kb():
+    """Same n, new voxel size and wavenumber (the physical units of a 1.333
+    medium at four voxels per vacuum wavelength): the second call must rebuild
+    the spectrum held in the scratch array.  Checked against the FP64 oracle's
+    G v at that (h, kb), since the handle's apply shares the spectrum
+    construction with this entry point."""
+    from oracle import physics
+
+    n = 16
+    v = volume(n, 21)
+    first = torch.empty_like(v)
+    binding.green_apply_noalloc(n, 1.0, KB, v, first)
+    h2, kb2 = 0.25, 2.0 * math.pi * 1.333
+    out = torch.empty_like(v)
+    for _ in range(2):
+        binding.green_apply_noalloc(n, h2, kb2, v, out)
+        torch.cuda.synchronize()
+        vn = v.cpu().numpy().astype(np.complex128).reshape(n, n, n)
+        ref = physics.green_apply(vn, physics.green_hat(n, kb2, h2))
+        assert relmax(out.cpu().numpy().reshape(n, n, n), ref) < 2e-6
+    assert relmax(first.cpu().numpy(), out.cpu().numpy()) > 1e-2
+
+
 def test_noalloc_rejects_sizes_beyond_scratch():
     lib = binding.load()
     v = torch.zeros(48 ** 3, dtype=torch.complex64, device=DEV)
