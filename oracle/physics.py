@@ -14,6 +14,10 @@ and in the CUDA library alike:
   w_D = h^3 exp(j k_b |D| h) / (4 pi |D| h) for D != 0 and the self term
   w_0 = [exp(j k_b a)(1 - j k_b a) - 1] / k_b^2, a = (3/(4 pi))^(1/3) h, the
   exact integral of the Green's function over the sphere of volume h^3;
+  or, as an option, the truncated kernel (Vico, Greengard and Ferrando 2016):
+  w_D from the transform of g restricted to r <= sqrt(3) n h, sampled on a
+  grid of period 4 n h, which makes G v the continuous convolution of v's
+  band-limited interpolant with g (spectrally accurate for smooth v);
 * LS: u = u_in + G (x * u); Born: u_sc = G (x * u_in);
 * detector: the scattered field u - u_in on the last z-slice (M = n^2), or,
   with a remote detector, that slice carried a distance d further along z by
@@ -70,8 +74,67 @@ def green_kernel(n: int, kb: float, h: float = 1.0) -> np.ndarray:
     return kb ** 2 * w
 
 
-def green_hat(n: int, kb: float, h: float = 1.0) -> np.ndarray:
-    """K_hat = DFT_P of the periodic kernel (P^3 complex128)."""
+def truncated_green_ft(s, kb: float, R: float) -> np.ndarray:
+    """Fourier transform of the truncated Green's function
+    g_R(r) = exp(j kb r) / (4 pi r) for r <= R and 0 beyond, at radial
+    frequencies s >= 0 (the kernel of the truncated-kernel method of Vico,
+    Greengard and Ferrando, J. Comput. Phys. 2016), written from its
+    definition: for s > 0
+        g_R^(s) = (1/s) int_0^R exp(j kb r) sin(s r) dr
+                = (E(j(kb + s)) - E(j(kb - s))) / (2 j s),
+        E(a)    = int_0^R exp(a r) dr = R expm1(a R) / (a R)   (E(0) = R),
+    and g_R^(0) = int_0^R r exp(j kb r) dr = (exp(j kb R)(1 - j kb R) - 1) / kb^2.
+    (Accurate for s R >= 1; every nonzero frequency of the grids below has
+    s R >= 2.7.)"""
+    s = np.asarray(s, dtype=np.float64)
+
+    def E(a):
+        z = a * R
+        zs = np.where(z == 0, 1.0, z)
+        return np.where(z == 0, R, R * np.expm1(zs) / zs)
+
+    ss = np.where(s == 0, 1.0, s)
+    val = (E(1j * (kb + ss)) - E(1j * (kb - ss))) / (2j * ss)
+    g0 = (np.exp(1j * kb * R) * (1.0 - 1j * kb * R) - 1.0) / kb ** 2
+    return np.where(s == 0, g0, val)
+
+
+def truncated_green_kernel(n: int, kb: float, h: float = 1.0) -> np.ndarray:
+    """k_b^2 w_D on the P-periodic grid (P = 2n) for the truncated kernel.
+
+    Voxel sums with this kernel are the continuous convolution of the band-
+    limited interpolant of v with g_R: the transform of g_R is sampled on the
+    frequency grid of a period T = 4 n h (m in [-2n, 2n)^3, s_m = 2 pi m / T),
+    so  w_D = (h^3 / T^3) sum_m g_R^(|s_m|) exp(j s_m . D h)  (an inverse DFT of
+    length 4n per axis).  R = sqrt(3) n h covers every distance between two
+    voxels of the domain, and T >= n h + R keeps the periodic copies of g_R
+    out of the offsets (-n, n)^3 the domain uses, which are laid out on the P
+    grid as in green_kernel (index n unused, 0)."""
+    T = 4 * n
+    R = math.sqrt(3.0) * n * h
+    f = 2.0 * math.pi * np.fft.fftfreq(T, d=h)
+    s = np.sqrt(f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2)
+    w = sfft.ifftn(truncated_green_ft(s, kb, R), workers=FFT_WORKERS)
+    del s
+    P = 2 * n
+    idx = np.arange(P)
+    sel = np.where(idx < n, idx, idx - P) % T
+    wp = w[np.ix_(sel, sel, sel)].copy()
+    unused = idx == n
+    wp[unused, :, :] = 0.0
+    wp[:, unused, :] = 0.0
+    wp[:, :, unused] = 0.0
+    return kb ** 2 * wp
+
+
+def green_hat(n: int, kb: float, h: float = 1.0, kernel: str = "sampled") -> np.ndarray:
+    """K_hat = DFT_P of the periodic kernel (P^3 complex128): the sampled
+    Green's function with the sphere self term ("sampled") or the truncated
+    kernel ("truncated")."""
+    if kernel == "truncated":
+        return sfft.fftn(truncated_green_kernel(n, kb, h), workers=FFT_WORKERS)
+    if kernel != "sampled":
+        raise ValueError("kernel must be 'sampled' or 'truncated'")
     return sfft.fftn(green_kernel(n, kb, h), workers=FFT_WORKERS)
 
 
@@ -157,7 +220,7 @@ class Model:
     def __init__(self, n: int, kdirs: np.ndarray, model: str = "ls",
                  kb: float | None = None, h: float = 1.0,
                  tol: float = 1e-12, maxit: int = 2000,
-                 det_distance: float = 0.0, det_na: float = 0.0):
+                 det_distance: float = 0.0, det_na: float = 0.0, kernel: str = "sampled"):
         self.n = n
         self.h = h
         self.kb = kb_default(h) if kb is None else kb
@@ -165,7 +228,7 @@ class Model:
         self.model = model
         self.tol = tol
         self.maxit = maxit
-        self.khat = green_hat(n, self.kb, h)
+        self.khat = green_hat(n, self.kb, h, kernel)
         # remote detector (det_na > 0): angular-spectrum transfer function
         self.H = transfer_function(n, self.kb, h, det_distance, det_na) if det_na > 0 else None
 
