@@ -319,24 +319,6 @@ def aggregate_ranks(torch, dist, device, ms, ms_e2e, illum, illum_e2e):
     return float(tt[0]), float(tt[1]), float(cnt[0]), float(cnt[1])
 
 
-def oracle_sample(w, x_np, seconds_hint=20.0):
-    """Bounded FP64 oracle sample: seconds per BiCGSTAB iteration of one LS
-    forward solve at the workload size (K_hat set-up excluded)."""
-    from oracle import physics
-    kd = synth.illumination_dirs(w)
-    m = physics.Model(w.n, kd[:1], "ls", kb=w.kb, h=w.h, tol=1e-30, maxit=1)
-    uin = m.u_in(0)
-    A = lambda p: p - m.G(x_np * p)  # noqa: E731
-    physics.bicgstab(A, uin, uin, 1e-30, 1)       # warm caches / first-touch
-    its = 2
-    t0, c0 = time.perf_counter(), time.process_time()
-    physics.bicgstab(A, uin, uin, 1e-30, its)
-    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
-    # bicgstab(maxit=its) = 1 residual apply + 2 applies per iteration
-    t_apply = dt / (1 + 2 * its)
-    return 2 * t_apply, dt, round(cpu / dt, 1)   # cores: CPU time of all threads / wall time
-
-
 def run_reference(args, world, rank):
     """--impl reference: the FP64 oracle on the host cores, bounded samples."""
     if rank != 0:
@@ -573,6 +555,282 @@ def weighted_vs_unweighted_prox(torch, h, x, infos, w):
             "dual_iters": w.dual_iters, "weighted_rank": w.S}
 
 
+def prox_bytes(trace: dict, rank: int, N: int) -> int:
+    """Algorithmic bytes of one weighted proximal mapping from the barrier
+    counts of its phase trace (float32 vectors, N voxels, rank-S metric):
+    Gram set-up (4S + 4) N; per divergence pass (R in, d out, U in)
+    (16 + 4S) N; per Newton evaluation (U, v, d, status in, x out)
+    (13 + 4S) N; per fix-up after a rejected trial (12 + 4S) N; per dual
+    update (x, R, P in; P, R out) 52 N; unweighted x pass (R, v in, x out)
+    20 N.  The last evaluation's fix-up passes no barrier and is not counted."""
+    c = trace.get("counts", {})
+    S = rank
+    b = 0
+    b += c.get("gram", 0) * (4 * S + 4)
+    b += c.get("div_UTd", 0) * (16 + 4 * S)
+    b += c.get("newton_eval", 0) * (13 + 4 * S)
+    b += c.get("x_fixup", 0) * (12 + 4 * S)
+    b += c.get("dual_update", 0) * 52
+    b += c.get("x_plain", 0) * 20
+    if S == 0:   # the final x pass has no barrier after it
+        b += 20
+    return int(b * N)
+
+
+def prox_roofline(trace: dict, rank: int, N: int, ms: float):
+    peak, kind = peaks()
+    by = prox_bytes(trace, rank, N)
+    ach = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": "k_wprox (one cooperative launch per proximal mapping)",
+            "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "peak_kind": kind, "algorithmic_bytes_per_launch": by, "ms_per_launch": round(ms, 3),
+            "rank": rank, "barrier_counts": trace.get("counts", {}),
+            "note": "U rows (4 S N bytes) are re-read by every pass; at 128^3 and S = 8 they fit the 129 MB L2, so "
+                    "DRAM traffic can be below these algorithmic bytes"}
+
+
+def plain_vs_fused(w, kd, y, alpha, so, subs, x, tile, torch, binding, dev):
+    """The same gradient (one whole subset, same x, same measurements, Krylov
+    tolerance and start u_in) on both arms: the fused library call on a handle
+    without warm start, and the plain torch.fft (cuFFT) path with one
+    illumination per launch.  Reports per-illumination and per-Krylov-
+    iteration times and the speedup at equal solver work."""
+    il = [int(i) for i in subs[0]]
+    scale = w.S / w.L
+    hc = binding.MQNPM(w.n, kd, so, alpha, model=w.model, h=w.h, kb=w.kb, tv=w.tv, lam=w.lam, box=w.box,
+                       krylov_tol=w.krylov_tol, krylov_maxit=1000, dual_iters=w.dual_iters, max_batch=len(il),
+                       warm_start=False, tile=tile)
+    hc.set_measurements(y.reshape(-1))
+    hc.grad_batch(x, il, scale, allow_not_converged=True)          # warm-up
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        _, _, its = hc.grad_batch(x, il, scale, allow_not_converged=True)
+    e1.record()
+    torch.cuda.synchronize()
+    f_ms = e0.elapsed_time(e1) / reps
+    hc.close()
+    f_iters = sum(a + b for a, b in its)
+    plain = PlainPath(w, kd, y, torch, dev)
+    plain.grad(x, il[0], w.krylov_tol)                                # warm-up
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    p_iters = 0
+    for l in il:
+        _, it = plain.grad(x, l, w.krylov_tol)
+        p_iters += it
+    p1.record()
+    torch.cuda.synchronize()
+    p_ms = p0.elapsed_time(p1)
+    del plain
+    born = w.model == "born"
+    fused = {"value": round(len(il) / (f_ms / 1e3), 3), "unit": UNIT, "ms_per_illum": round(f_ms / len(il), 3),
+             "krylov_iters": f_iters, "illuminations": len(il),
+             "ms_per_krylov_iter_per_illum": None if born else round(f_ms / max(1, f_iters), 4),
+             "what": "libmqnpm grad_batch, all %d illuminations of subset 0 in one batch, %s" % (
+                 len(il), "first Born" if born else "BiCGSTAB from u_in (no warm start)")}
+    plain_d = {"value": round(len(il) / (p_ms / 1e3), 3), "unit": UNIT, "ms_per_illum": round(p_ms / len(il), 3),
+               "krylov_iters": p_iters, "illuminations": len(il),
+               "ms_per_krylov_iter_per_illum": None if born else round(p_ms / max(1, p_iters), 4),
+               "what": "torch.fft (cuFFT) padded %d^3, one illumination per launch, %s" % (
+                   2 * w.n, "Born (two applies)" if born else "host-driven BiCGSTAB from u_in")}
+    return fused, plain_d, round(fused["value"] / plain_d["value"], 2)
+
+
+def cpu_oracle_timings(w, x_np, alpha_np):
+    """The FP64 oracle as it stands on the host cores (scipy.fft with one
+    worker per available core): one whole illumination-gradient of the workload
+    (forward and adjoint BiCGSTAB from u_in at the workload's tolerance) and
+    one weighted proximal mapping of its size (rank S, J dual iterations)."""
+    from oracle import physics
+    from oracle import wprox as owprox
+    kd = synth.illumination_dirs(w)
+    m = physics.Model(w.n, kd[:1], w.model, kb=w.kb, h=w.h, tol=w.krylov_tol)
+    y0 = np.zeros(w.n * w.n, dtype=np.complex128)
+    c0, t0 = time.process_time(), time.perf_counter()
+    _, _, its = m.loss_grad(x_np, 0, y0)
+    t_grad = time.perf_counter() - t0
+    busy = (time.process_time() - c0) / t_grad
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((w.S, w.n, w.n, w.n)) * 0.05
+    t0 = time.perf_counter()
+    owprox.wprox(x_np, 1.5, U, w.step * w.S * w.lam, w.box[0], w.box[1], w.tv, w.dual_iters,
+                 newton_tol=1e-6)
+    t_prox = time.perf_counter() - t0
+    return t_grad, its, t_prox, busy
+
+
+def cpu_ls32_end_to_end(outer: int = 10):
+    """The small nonlinear configuration end to end on the oracle: 32^3, L = 8,
+    S = 4, 10 outer iterations of Algorithm 4.1 from x0 = 0 (data simulated by
+    the oracle at its own Krylov tolerance 1e-6)."""
+    from oracle import bqnpm, physics
+    w = synth.workload("ls32")
+    kd = synth.illumination_dirs(w)
+    m = physics.Model(w.n, kd, "ls", kb=w.kb, h=w.h, tol=w.krylov_tol)
+    t0 = time.perf_counter()
+    ys = physics.simulate(m, synth.phantom(w), synth.noise_draws(w), w.snr_db)
+    subs = synth.subsets(w)
+    alpha = [m.lipschitz(s, w.S / w.L, synth.power_start(w), 10) for s in subs]
+    t_setup = time.perf_counter() - t0
+    opt = bqnpm.BQNPM(m, ys, subs, alpha, lam=w.lam, box=w.box, kind=w.tv, step=w.step, gamma=w.gamma,
+                      dual_iters=w.dual_iters)
+    t0 = time.perf_counter()
+    opt.run(np.zeros((w.n,) * 3), outer)
+    return t_setup, time.perf_counter() - t0
+
+
+def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=True):
+    """Set-up, timed MQNPM iterations (inputs resident in HBM), the end-to-end
+    repeat through host buffers and the per-kernel figures of one workload."""
+    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile)
+    x = torch.zeros(w.N, dtype=torch.float32, device=dev)
+    # Set-up iterations from x0 = 0: the S initial steps of Algorithm 4.1 and the
+    # reconstruction up to iteration SETUP_ITERS, so that the warm-up and timed
+    # steps sit where the paper's BQNPM-I reached ASPM's best SNR (38 iterations).
+    for _ in range(max(w.S, SETUP_ITERS - args.warmup - args.steps)):
+        h.step(x, allow_not_converged=True)
+    for _ in range(args.warmup):
+        h.step(x, allow_not_converged=True)
+    torch.cuda.synchronize()
+    # the end-to-end run below repeats the same iterations from this state
+    state0, x0 = h.save_state(), x.cpu()
+    # ---- timed region: inputs resident in HBM
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    h.profile_begin(8192)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    illum_done = 0
+    infos = []
+    launches0 = h.launch_count
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = h.step(x, allow_not_converged=True)
+        infos.append(info)
+        illum_done += len(subs[info["subset"]])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = h.launch_count - launches0
+    prox_trace = h.prox_trace()
+    if world > 1:
+        dist.barrier()
+    prof = h.profile_end()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # ---- end-to-end through the public call with host buffers, same iterations
+    h.load_state(state0)
+    del state0
+    xh = torch.empty(w.N, dtype=torch.float32).pin_memory()
+    xh.copy_(x0)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xd = torch.empty_like(x)
+    e2e_illum = 0
+    e2e_infos = []
+    f0.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        info = h.step(xd, allow_not_converged=True)
+        e2e_infos.append(info)
+        e2e_illum += len(subs[info["subset"]])
+        xh.copy_(xd, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    if full and args.log_jsonl and rank == 0:
+        with open(args.log_jsonl, "w") as f:
+            for i in infos:
+                f.write(json.dumps({k: (round(v, 6) if isinstance(v, float) else v) for k, v in i.items()}) + "\n")
+    wprox_ratio = weighted_vs_unweighted_prox(torch, h, x, infos, w)
+    # ---- max over ranks
+    t_max, ms_e2e, illum_total, e2e_total = aggregate_ranks(torch, dist if world > 1 else None, dev, ms, ms_e2e,
+                                                            illum_done, e2e_illum)
+    value = illum_total / (t_max / 1e3)
+    iters_per_s = world * args.steps / (t_max / 1e3)
+    e2e_value = e2e_total / (ms_e2e / 1e3)
+    # ---- roofline of the dominant Green's pass
+    N = w.N
+    n = w.n
+    per_slot = [28 * N, 48 * N, 64 * N, 48 * N, 32 * N]
+    names = ["x_fwd", "y_fwd", "z_conv", "y_inv", "x_inv"]
+    pms = prof["pass_ms"]
+    dom = int(np.argmax(pms))
+    bytes_dom = per_slot[dom] * prof["slot_launches"] + (8 * (n + 1) ** 3 * prof["calls"] if dom == 2 else 0)
+    peak, peak_kind = peaks()
+    achieved = bytes_dom / (pms[dom] / 1e3) / 1e9 if pms[dom] > 0 else 0.0
+    # GB/s only where the bytes per slot do not depend on the fused prologue or
+    # epilogue (the x passes move 20-52 N bytes per slot depending on the kind)
+    passes = {nm: {"ms": round(t, 3), "GB/s": round(per_slot[i] * prof["slot_launches"] / (t / 1e3) / 1e9, 1)
+                   if t > 0 and nm not in ("x_fwd", "x_inv") else None} for i, (nm, t) in enumerate(zip(names, pms))}
+    kit = [i["krylov_iters_max"] for i in infos]
+    kit_per_illum = [i["krylov_iters_total"] / max(1, i["n_illum"]) for i in infos]
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "padded": 2 * n, "L": w.L, "batch": max(len(s) for s in subs),
+                   "S": w.S, "model": "lippmann-schwinger" if w.model == "ls" else "first-born",
+                   "krylov_tol": w.krylov_tol if w.model == "ls" else None, "dual_iters": w.dual_iters,
+                   "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
+                   "krylov_start": "forward solves warm-started from each illumination's last field"
+                   if w.model == "ls" else None,
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "mqnpm_iters_per_s": round(iters_per_s, 3),
+        "roofline": {"bound": "hbm", "kernel": "k_pass3 (" + names[dom] + ")" if dom == 2 else names[dom],
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": pass3_traffic(n, prof["slot_launches"] / max(1, prof["calls"]), h.tile_info()["tile"])
+                     if dom == 2 else None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_slot": per_slot[dom],
+                     "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof["calls"])),
+                     "launches": prof["calls"], "slots_per_launch": round(prof["slot_launches"] / max(1, prof["calls"]), 2)},
+        "roofline_alu": pass3_alu_view(n, prof, pms[2]) if prof["calls"] else None,
+        "roofline_prox": prox_roofline(prox_trace, infos[-1]["rank"], N, infos[-1]["ms_prox"]),
+        "passes": passes,
+        "green_applies": prof["calls"],
+        "green_tile": h.tile_info(),
+        "phase_ms": {k: round(statistics.mean(i["ms_" + k] for i in infos), 3) for k in ("gradient", "metric", "prox")},
+        "newton_iters_max": [i["newton_iters_max"] for i in infos],
+        "prox_trace_us": prox_trace,
+        "krylov_iters_max_per_step": kit,
+        "krylov_iters_per_illum": [round(k, 2) for k in kit_per_illum],
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wprox_vs_unweighted": wprox_ratio,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+                "iterations": "the timed k = %d..%d again, from a checkpoint" % (infos[0]["k"], infos[-1]["k"]),
+                "pass_events": "none (the timed region above records 6 per Green's apply for the pass timings)",
+                "same_krylov_iters": [i["krylov_iters_total"] for i in e2e_infos] ==
+                                     [i["krylov_iters_total"] for i in infos]},
+    }
+    if prof["calls"] == 0:
+        out["roofline"] = out["roofline_prox"]
+        out["roofline_note"] = ("every Green's apply of this model touches one z-plane (first-Born data, adjoint "
+                                "right-hand sides) and the pass timers cover full applies only; the dominant "
+                                "kernel is the weighted proximal mapping")
+    out["config"]["iterations"] = "k = %d..%d from x0 = 0" % (infos[0]["k"], infos[-1]["k"])
+    h.close()
+    if rank == 0 and not args.no_plain:
+        fused, plain_d, sp = plain_vs_fused(w, kd, y, alpha, so, subs, x, args.tile, torch, binding, dev)
+        out["fused_cold"] = fused
+        out["plain_gpu"] = plain_d
+        out["speedup_vs_plain"] = sp
+        out["speedup_vs_plain_note"] = ("same subset, x, tolerance and start u_in on both arms (equal solver "
+                                        "work); the headline value above warm-starts the forward solves")
+        if fused["ms_per_krylov_iter_per_illum"] and plain_d["ms_per_krylov_iter_per_illum"]:
+            out["speedup_per_krylov_iter"] = round(plain_d["ms_per_krylov_iter_per_illum"] /
+                                                   fused["ms_per_krylov_iter_per_illum"], 2)
+    return out, x
+
+
 # ---------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -583,6 +841,7 @@ def main():
     ap.add_argument("--workload", default="ls128")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-born", action="store_true", help="skip the born128 figures of the default line")
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
@@ -628,175 +887,34 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     w = synth.workload(args.workload)
-    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile)
-    x = torch.zeros(w.N, dtype=torch.float32, device=dev)
-    # Set-up iterations from x0 = 0: the S initial steps of Algorithm 4.1 and the
-    # reconstruction up to iteration SETUP_ITERS, so that the warm-up and timed
-    # steps sit where the paper's BQNPM-I reached ASPM's best SNR (38 iterations).
-    for _ in range(max(w.S, SETUP_ITERS - args.warmup - args.steps)):
-        h.step(x, allow_not_converged=True)
-    for _ in range(args.warmup):
-        h.step(x, allow_not_converged=True)
-    torch.cuda.synchronize()
-    # the end-to-end run below repeats the same iterations from this state
-    state0, x0 = h.save_state(), x.cpu()
-    # ---- timed region: inputs resident in HBM
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    h.profile_begin(8192)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    illum_done = 0
-    infos = []
-    launches0 = h.launch_count
-    nvtx = getattr(torch.cuda, "nvtx", None)
-    try:
-        nvtx.range_push("timed")
-    except Exception:
-        nvtx = None
-    e0.record(stream)
-    for _ in range(args.steps):
-        info = h.step(x, allow_not_converged=True)
-        infos.append(info)
-        illum_done += len(subs[info["subset"]])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if nvtx is not None:
-        nvtx.range_pop()
-    launches = h.launch_count - launches0
-    prox_trace = h.prox_trace()
-    if world > 1:
-        dist.barrier()
-    prof = h.profile_end()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    # ---- end-to-end through the public call with host buffers, same iterations
-    h.load_state(state0)
-    del state0
-    xh = torch.empty(w.N, dtype=torch.float32).pin_memory()
-    xh.copy_(x0)
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    xd = torch.empty_like(x)
-    e2e_illum = 0
-    e2e_infos = []
-    f0.record(stream)
-    for _ in range(args.steps):
-        xd.copy_(xh, non_blocking=True)
-        info = h.step(xd, allow_not_converged=True)
-        e2e_infos.append(info)
-        e2e_illum += len(subs[info["subset"]])
-        xh.copy_(xd, non_blocking=True)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = f0.elapsed_time(f1)
-    if args.log_jsonl and rank == 0:
-        with open(args.log_jsonl, "w") as f:
-            for i in infos:
-                f.write(json.dumps({k: (round(v, 6) if isinstance(v, float) else v) for k, v in i.items()}) + "\n")
-    wprox_ratio = weighted_vs_unweighted_prox(torch, h, x, infos, w)
-    # ---- max over ranks
-    t_max, ms_e2e, illum_total, e2e_total = aggregate_ranks(torch, dist if world > 1 else None, dev, ms, ms_e2e,
-                                                            illum_done, e2e_illum)
-    value = illum_total / (t_max / 1e3)
-    iters_per_s = world * args.steps / (t_max / 1e3)
-    e2e_value = e2e_total / (ms_e2e / 1e3)
-    # ---- roofline of the dominant Green's pass
-    N = w.N
-    n = w.n
-    per_slot = [28 * N, 48 * N, 64 * N, 48 * N, 32 * N]
-    names = ["x_fwd", "y_fwd", "z_conv", "y_inv", "x_inv"]
-    pms = prof["pass_ms"]
-    dom = int(np.argmax(pms))
-    bytes_dom = per_slot[dom] * prof["slot_launches"] + (8 * (n + 1) ** 3 * prof["calls"] if dom == 2 else 0)
-    peak, peak_kind = peaks()
-    achieved = bytes_dom / (pms[dom] / 1e3) / 1e9 if pms[dom] > 0 else 0.0
-    # GB/s only where the bytes per slot do not depend on the fused prologue or
-    # epilogue (the x passes move 20-52 N bytes per slot depending on the kind)
-    passes = {nm: {"ms": round(t, 3), "GB/s": round(per_slot[i] * prof["slot_launches"] / (t / 1e3) / 1e9, 1)
-                   if t > 0 and nm not in ("x_fwd", "x_inv") else None} for i, (nm, t) in enumerate(zip(names, pms))}
-    kit = [i["krylov_iters_max"] for i in infos]
-    kit_per_illum = [i["krylov_iters_total"] / max(1, i["n_illum"]) for i in infos]
-    out = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)", "data": "synthetic",
-        "config": {"workload": w.name, "n": n, "padded": 2 * n, "L": w.L, "batch": max(len(s) for s in subs),
-                   "S": w.S, "model": "lippmann-schwinger" if w.model == "ls" else "first-born",
-                   "krylov_tol": w.krylov_tol if w.model == "ls" else None, "dual_iters": w.dual_iters,
-                   "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
-                   "krylov_start": "forward solves warm-started from each illumination's last field",
-                   "parallelism": "replicas" if world > 1 else "single-gpu"},
-        "mqnpm_iters_per_s": round(iters_per_s, 3),
-        "roofline": {"bound": "hbm", "kernel": "k_pass3 (" + names[dom] + ")" if dom == 2 else names[dom],
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4),
-                     "traffic": pass3_traffic(n, prof["slot_launches"] / max(1, prof["calls"]), h.tile_info()["tile"])
-                     if dom == 2 else None,
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_slot": per_slot[dom],
-                     "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof["calls"])),
-                     "launches": prof["calls"], "slots_per_launch": round(prof["slot_launches"] / max(1, prof["calls"]), 2)},
-        "roofline_alu": pass3_alu_view(n, prof, pms[2]) if prof["calls"] else None,
-        "passes": passes,
-        "green_applies": prof["calls"],
-        "green_tile": h.tile_info(),
-        "phase_ms": {k: round(statistics.mean(i["ms_" + k] for i in infos), 3) for k in ("gradient", "metric", "prox")},
-        "newton_iters_max": [i["newton_iters_max"] for i in infos],
-        "prox_trace_us": prox_trace,
-        "krylov_iters_max_per_step": kit,
-        "krylov_iters_per_illum": [round(k, 2) for k in kit_per_illum],
-        "gpu_launches": None,
-        "clocks": clk,
-        "wprox_vs_unweighted": wprox_ratio,
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
-                "iterations": "the timed k = %d..%d again, from a checkpoint" % (infos[0]["k"], infos[-1]["k"]),
-                "pass_events": "none (the timed region above records 6 per Green's apply for the pass timings)",
-                "same_krylov_iters": [i["krylov_iters_total"] for i in e2e_infos] ==
-                                     [i["krylov_iters_total"] for i in infos]},
-    }
-    if prof["calls"] == 0:
-        out["roofline"] = None
-        out["roofline_note"] = ("every Green's apply of this model touches one z-plane (first-Born data, adjoint "
-                                "right-hand sides); the pass timers cover full applies only")
-    out["gpu_launches"] = int(launches)
-    out["config"]["iterations"] = "k = %d..%d from x0 = 0" % (infos[0]["k"], infos[-1]["k"])
-    if rank == 0 and not args.no_plain:
-        plain = PlainPath(w, kd, y, torch, dev)
-        il = [0, 1]
-        for l in il[:1]:
-            plain.grad(x, l, w.krylov_tol)       # warm-up
-        torch.cuda.synchronize()
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record()
-        pits = 0
-        for l in il:
-            _, it = plain.grad(x, l, w.krylov_tol)
-            pits += it
-        p1.record()
-        torch.cuda.synchronize()
-        pms_plain = p0.elapsed_time(p1)
-        out["plain_gpu"] = {"value": round(len(il) / (pms_plain / 1e3), 3), "unit": UNIT,
-                            "ms_per_illum": round(pms_plain / len(il), 2), "krylov_iters": pits,
-                            "what": "torch.fft (cuFFT) padded %d^3, one illumination per launch, %s" % (
-                                2 * n, "Born (two applies)" if w.model == "born" else "BiCGSTAB from u_in")}
-        out["speedup_vs_plain"] = round(value / out["plain_gpu"]["value"], 2)
-        del plain
+    out, x = run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=True)
+    if rank == 0 and world == 1 and args.workload == "ls128" and not args.no_born:
+        # the other 128^3 configuration of the metric, same steps and warm-up
+        wb = synth.workload("born128")
+        ob, _ = run_workload(wb, args, torch, binding, dev, local, world, rank, dist, full=False)
+        keep = ("value", "unit", "ms_per_step", "mqnpm_iters_per_s", "roofline", "roofline_note", "phase_ms",
+                "gpu_launches", "clocks", "e2e", "fused_cold", "plain_gpu", "speedup_vs_plain", "newton_iters_max",
+                "wprox_vs_unweighted", "config")
+        out["born128"] = {k: ob[k] for k in keep if k in ob}
     if rank == 0 and not args.no_cpu:
-        t_it, dt, cores = oracle_sample(w, synth.phantom(w))
-        # GPU-measured mean iterations per illumination-gradient in the timed steps
-        per_illum = statistics.mean(kit_per_illum) if kit_per_illum else LS128_ITERS_PER_ILLUM
-        t_ig = t_it * per_illum + t_it
-        out["cpu_baseline"] = {"value": round(1.0 / t_ig, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": "FP64 oracle, 2 BiCGSTAB iterations of one LS forward solve at n=%d "
-                                         "(%.1f s), scaled by %.1f iterations + 2 Green's applies per "
-                                         "illumination-gradient" % (n, dt, per_illum)}
+        x_np = x.cpu().numpy().astype(np.float64).reshape(w.n, w.n, w.n)
+        t_grad, its, t_prox, busy = cpu_oracle_timings(w, x_np, None)
+        t_setup32, t_run32 = cpu_ls32_end_to_end()
+        from oracle import physics as _ph
+        out["cpu_baseline"] = {
+            "value": round(1.0 / t_grad, 6), "unit": UNIT, "cores": _ph.FFT_WORKERS, "kind": "oracle",
+            "sample": "FP64 oracle (scipy.fft, %d workers): one whole %d^3 illumination-gradient at the last "
+                      "iterate, forward + adjoint BiCGSTAB from u_in at tol %g (%d + %d iterations, %.1f s)"
+                      % (_ph.FFT_WORKERS, w.n, w.krylov_tol, its[0], its[1], t_grad),
+            "busy_threads": round(busy, 1),
+            "wprox_s": round(t_prox, 2),
+            "wprox_sample": "one weighted proximal mapping, %d^3, rank %d, %d dual iterations" % (w.n, w.S,
+                                                                                                 w.dual_iters),
+            "ls32_end_to_end_s": round(t_run32, 2),
+            "ls32_sample": "32^3, L = 8, S = 4: 10 outer iterations of Algorithm 4.1 from x0 = 0 (%.1f s of "
+                           "data simulation and alpha_s before them)" % t_setup32}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -48,6 +48,15 @@ typedef enum mqnpm_status {
 
 enum { MQNPM_MODEL_BORN = 0, MQNPM_MODEL_LS = 1 };
 enum { MQNPM_TV_ISO = 0, MQNPM_TV_ANISO = 1 };
+/* Discretisation of the Green's function (Section 6; the paper defers its
+ * forward model to a supplement, so both are the library's stated readings):
+ * SAMPLED  w_D = h^3 g(|D| h) with the exact integral over the equal-volume
+ *          sphere at D = 0;
+ * TRUNCATED the truncated kernel of Vico, Greengard and Ferrando (2016): the
+ *          transform of g restricted to r <= sqrt(3) n h, sampled with period
+ *          4 n h, which makes G v the continuous convolution of the band-limited
+ *          interpolant of v (spectrally accurate for smooth v). */
+enum { MQNPM_KERNEL_SAMPLED = 0, MQNPM_KERNEL_TRUNCATED = 1 };
 
 /* Largest number of subsets S (rank of the quasi-Newton metric) supported. */
 #define MQNPM_MAX_S 16
@@ -126,6 +135,10 @@ typedef struct mqnpm_config {
                               proximal mapping at a grid barrier, in SM clock
                               cycles, before it gives up and the call returns
                               MQNPM_ERR_TIMEOUT; 0 selects 4e9 (about 2 s)    */
+  int green_kernel;        /* MQNPM_KERNEL_SAMPLED (0) or MQNPM_KERNEL_TRUNCATED;
+                              ignored when green_hat is given. The truncated
+                              kernel's construction at create holds two
+                              (2n+1)^3 FP64 complex buffers for its duration */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;

@@ -24,6 +24,7 @@ STATUS = {
 }
 MODEL = {"born": 0, "ls": 1}
 TV = {"iso": 0, "aniso": 1}
+KERNEL = {"sampled": 0, "truncated": 1}
 MAX_S = 16
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 192)
 
@@ -53,7 +54,7 @@ class Config(ctypes.Structure):
         ("stream", ctypes.c_void_p), ("warm_start", ctypes.c_int), ("direct_launches", ctypes.c_int),
         ("green_hat", ctypes.POINTER(ctypes.c_float)), ("tile", ctypes.c_int),
         ("det_distance", ctypes.c_double), ("det_na", ctypes.c_double), ("guard_bytes", ctypes.c_size_t),
-        ("barrier_wait_cycles", ctypes.c_longlong),
+        ("barrier_wait_cycles", ctypes.c_longlong), ("green_kernel", ctypes.c_int),
     ]
 
 
@@ -179,7 +180,7 @@ class MQNPM:
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
                  direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1,
                  det_distance: float = 0.0, det_na: float = 0.0, guard_bytes: int = 0,
-                 barrier_wait_cycles: int = 0):
+                 barrier_wait_cycles: int = 0, green_kernel: str = "sampled"):
         self.lib = load()
         self.n = int(n)
         self.N = self.n ** 3
@@ -227,6 +228,7 @@ class MQNPM:
         cfg.det_na = float(det_na)
         cfg.guard_bytes = int(guard_bytes)
         cfg.barrier_wait_cycles = int(barrier_wait_cycles)
+        cfg.green_kernel = KERNEL[green_kernel]
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
             if gh.size != (self.n + 1) ** 3:
@@ -439,18 +441,22 @@ class MQNPM:
         self._raise(self.lib.mqnpm_prox_trace(self._h, buf, cap, ctypes.byref(cnt)))
         names = {1: "gram", 2: "x_plain", 3: "div_UTd", 4: "newton_eval", 5: "x_fixup", 6: "dual_update", 99: "tail"}
         out = {"barriers": cnt.value - 1, "total_us": 0.0}
+        counts = {}
         prev = buf[1]
         for e in range(1, cnt.value + 1):
             tag, t = buf[2 * e], buf[2 * e + 1]
             key = names.get(int(tag), str(tag))
             out[key] = out.get(key, 0.0) + (t - prev) / 1e3
             out["total_us"] += (t - prev) / 1e3
+            counts[key] = counts.get(key, 0) + 1
             prev = t
         acc = ["dual_update_block0", "pre_dual_block0", "newton_pass_block0", "newton_decide_block0",
                "div_pass_block0", "barrier_wait_block0"]
         for k, nm in enumerate(acc):
             out[nm] = buf[2000 + k] / 1e3
-        return {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
+        out = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
+        out["counts"] = counts
+        return out
 
     def profile_begin(self, max_calls: int = 4096):
         self._raise(self.lib.mqnpm_profile_begin(self._h, int(max_calls)))

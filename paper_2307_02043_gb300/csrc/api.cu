@@ -234,7 +234,8 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
       (cfg->tv != MQNPM_TV_ISO && cfg->tv != MQNPM_TV_ANISO) || (cfg->strategy != 1 && cfg->strategy != 2) ||
       !(cfg->gamma > 0 && cfg->gamma <= 1.0) || cfg->tile < -1 || cfg->tile >= MQ_TILES ||
       !(cfg->det_na >= 0.0 && std::isfinite(cfg->det_na)) || !std::isfinite(cfg->det_distance) ||
-      cfg->barrier_wait_cycles < 0) {
+      cfg->barrier_wait_cycles < 0 ||
+      (cfg->green_kernel != MQNPM_KERNEL_SAMPLED && cfg->green_kernel != MQNPM_KERNEL_TRUNCATED)) {
     fprintf(stderr, "mqnpm_create: invalid configuration\n");
     delete h;
     return MQNPM_ERR_INVALID_ARG;
@@ -283,6 +284,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->budget = cfg->hbm_budget_bytes;
   h->guard = (cfg->guard_bytes + 255) / 256 * 256;
   if (cfg->barrier_wait_cycles > 0) h->barrier_limit = cfg->barrier_wait_cycles;
+  h->green_kernel = cfg->green_kernel;
   h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
   h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);
   h->subset_of.assign(cfg->subset_of, cfg->subset_of + cfg->L);
@@ -445,7 +447,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   }
   if ((e = cudaMemcpyAsync(h->tw, tw.data(), P * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = (cfg->green_hat ? upload_khat(cfg->green_hat, n, h->khat, s) : build_khat(n, h->h, h->kb, h->khat, s))) !=
+      (e = (cfg->green_hat ? upload_khat(cfg->green_hat, n, h->khat, s) : build_khat(n, h->h, h->kb, h->khat, s, h->green_kernel))) !=
           cudaSuccess) {
     set_cuda_error(h, e, "create tables");
     return fail(MQNPM_ERR_CUDA);

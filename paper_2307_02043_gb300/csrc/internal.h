@@ -87,7 +87,7 @@ MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
 #undef MQ_DECL
 
 // K_hat octant in FP64 by separable even (cosine) sums, rounded to complex64.
-cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s);
+cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s, int kernel);
 cudaError_t upload_khat(const float* host, int n, float2* khat_out, cudaStream_t s);
 cudaError_t build_khat_scratch(int n, double h, double kb, float2* khat_out, double2* a, double2* b, double* dcos,
                                cudaStream_t s);
@@ -142,6 +142,7 @@ struct mqnpm_handle {
   int krylov_maxit = 500, dual_iters = 20, newton_maxit = 50, max_batch = 1, device = 0;
   int check_every = 1;
   long long barrier_limit = 4000000000LL;   // grid-barrier wait of the prox kernel, SM cycles
+  int green_kernel = 0;                      // MQNPM_KERNEL_SAMPLED or MQNPM_KERNEL_TRUNCATED
   std::vector<double> kdir, alpha;
   std::vector<int> subset_of, draws;
   std::vector<std::vector<int>> subsets;
