@@ -248,6 +248,23 @@ int mqnpm_wprox(mqnpm_handle* h, const float* v, double tau_star, const float* U
  * info (host) may be NULL. */
 int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info);
 
+/* mqnpm_step in two halves, for callers that form the subset gradient
+ * themselves, e.g. with its illuminations split over several GPUs and the
+ * partial sums added by an all-reduce (Eq. 4.1: grad F_s = (S/L) sum over the
+ * illuminations of S_s).
+ * mqnpm_step_subset: the subset iteration k+1 will use (Algorithm 4.1 step 3:
+ *   s = k for k <= S, else strategy I or II) in *subset (0-based, may be NULL)
+ *   and its illuminations in illum (host, room for L ints, may be NULL);
+ *   *count receives their number.  No device work, no state change.
+ *   STATE if strategy II has run out of draws.
+ * mqnpm_step_with_gradient: iteration k+1 with the caller's g = grad F_s(x)
+ *   (device N floats, distinct from x) and loss = F_s(x): the SR1 update
+ *   (Algorithm 4.2), quasi-Newton point and weighted proximal mapping exactly
+ *   as in mqnpm_step, x updated in place.  info as mqnpm_step, with the
+ *   Krylov counts 0.  NONFINITE for a non-finite loss. */
+int mqnpm_step_subset(const mqnpm_handle* h, int* subset, int* illum, int* count);
+int mqnpm_step_with_gradient(mqnpm_handle* h, float* x, const float* g, double loss, mqnpm_step_info* info);
+
 /* alpha estimate for a subset: `iters` power steps on
  * scale * sum_{l in illum} Re(J_l^H J_l) with J_l the Born Jacobian at x = 0,
  * from the device start vector `start` (N floats); result in *alpha_out (host). */

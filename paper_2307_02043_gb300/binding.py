@@ -90,6 +90,10 @@ SIGNATURES = {
     "mqnpm_wprox": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "mqnpm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
+    "mqnpm_step_subset": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "mqnpm_step_with_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                                ctypes.POINTER(StepInfo)]),
     "mqnpm_lipschitz": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mqnpm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
@@ -408,6 +412,23 @@ class MQNPM:
         self._stream()
         rc = self.lib.mqnpm_step(self._h, _ptr(x), ctypes.byref(info))
         self._raise(rc, allow_not_converged)
+        return {f: getattr(info, f) for f, _ in StepInfo._fields_}
+
+    def step_subset(self):
+        """(subset, illuminations) that the next iteration uses."""
+        sub = ctypes.c_int()
+        cnt = ctypes.c_int()
+        il = (ctypes.c_int * self.L)()
+        self._raise(self.lib.mqnpm_step_subset(self._h, ctypes.byref(sub), il, ctypes.byref(cnt)))
+        return sub.value, [il[i] for i in range(cnt.value)]
+
+    def step_with_gradient(self, x: torch.Tensor, g: torch.Tensor, loss: float) -> dict:
+        """The next iteration with the caller's subset gradient g = grad F_s(x) and loss F_s(x)."""
+        _check_cuda(x, torch.float32, self.N, "x", self.device)
+        _check_cuda(g, torch.float32, self.N, "g", self.device)
+        info = StepInfo()
+        self._stream()
+        self._raise(self.lib.mqnpm_step_with_gradient(self._h, _ptr(x), _ptr(g), float(loss), ctypes.byref(info)))
         return {f: getattr(info, f) for f, _ in StepInfo._fields_}
 
     def lipschitz(self, illum: Sequence[int], scale: float, start: torch.Tensor, iters: int = 20) -> float:

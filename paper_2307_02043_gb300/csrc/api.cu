@@ -591,33 +591,34 @@ int mqnpm_lipschitz(mqnpm_handle* h, const int* illum, int nb, double scale, con
   return lipschitz_impl(h, illum, nb, scale, start, iters, alpha_out);
 }
 
-int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
-  if (!h || !x) return set_error(h, MQNPM_ERR_INVALID_ARG, "step: bad arguments");
-  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "step: measurements not set");
-  CK(cudaSetDevice(h->device));
-  cudaStream_t s = h->stream;
-  const size_t N = h->N;
+}  // extern "C"
+
+namespace {
+
+// Subset of iteration k (Algorithm 4.1): s = k for k <= S, then s' by
+// strategy I (cyclic) or II (the caller's draws).
+int select_subset(mqnpm_handle* h, int k, int* sel) {
   const int S = h->S;
-  const int k = h->k + 1;
-  int sel;
-  if (k <= S) sel = k - 1;
-  else if (h->strategy == 1) sel = (k - 1) % S;
+  if (k <= S) *sel = k - 1;
+  else if (h->strategy == 1) *sel = (k - 1) % S;
   else {
     const int idx = k - S - 1;
     if (idx >= (int)h->draws.size()) return set_error(h, MQNPM_ERR_STATE, "step: strategy II draws exhausted");
-    sel = h->draws[idx];
+    *sel = h->draws[idx];
   }
+  return MQNPM_OK;
+}
+
+// Iteration k after its gradient: h->g holds grad F_{sel}(x) and loss its
+// data term.  SR1 metric update (Algorithm 4.2), quasi-Newton point and the
+// weighted proximal mapping (Eq. 4.5), then the bookkeeping of the step.
+int finish_step(mqnpm_handle* h, float* x, int k, int sel, double loss, const std::vector<int>& its, int grad_rc,
+                mqnpm_step_info* info) {
+  cudaStream_t s = h->stream;
+  const size_t N = h->N;
+  const int S = h->S;
+  int rc = MQNPM_OK;
   const std::vector<int>& sub = h->subsets[sel];
-  double loss = 0.0;
-  std::vector<int> its(2 * sub.size());
-  if (!h->step_ev[0]) {
-    for (auto& ev : h->step_ev) CK(cudaEventCreate(&ev));
-  }
-  CK(cudaEventRecord(h->step_ev[0], s));
-  int rc = grad_batch_impl(h, x, sub.data(), (int)sub.size(), (double)S / h->L, h->g, &loss, its.data(), true, nullptr);
-  CK(cudaEventRecord(h->step_ev[1], s));
-  if (rc != MQNPM_OK && rc != MQNPM_ERR_NOT_CONVERGED) return rc;
-  const int grad_rc = rc;
   float* xb = h->xbar + (size_t)sel * N;
   float* gb = h->gbar + (size_t)sel * N;
   int branch = -1;
@@ -736,6 +737,68 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
     info->ms_prox = t23;
   }
   return grad_rc;
+}
+
+
+int step_events(mqnpm_handle* h) {
+  if (!h->step_ev[0]) {
+    for (auto& ev : h->step_ev) CK(cudaEventCreate(&ev));
+  }
+  return MQNPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info) {
+  if (!h || !x) return set_error(h, MQNPM_ERR_INVALID_ARG, "step: bad arguments");
+  if (!h->have_meas) return set_error(h, MQNPM_ERR_STATE, "step: measurements not set");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const int S = h->S;
+  const int k = h->k + 1;
+  int sel = 0;
+  int rc = select_subset(h, k, &sel);
+  if (rc != MQNPM_OK) return rc;
+  const std::vector<int>& sub = h->subsets[sel];
+  double loss = 0.0;
+  std::vector<int> its(2 * sub.size());
+  if ((rc = step_events(h)) != MQNPM_OK) return rc;
+  CK(cudaEventRecord(h->step_ev[0], s));
+  rc = grad_batch_impl(h, x, sub.data(), (int)sub.size(), (double)S / h->L, h->g, &loss, its.data(), true, nullptr);
+  CK(cudaEventRecord(h->step_ev[1], s));
+  if (rc != MQNPM_OK && rc != MQNPM_ERR_NOT_CONVERGED) return rc;
+  return finish_step(h, x, k, sel, loss, its, rc, info);
+}
+
+int mqnpm_step_subset(const mqnpm_handle* h, int* subset, int* illum, int* count) {
+  if (!h || !count) return MQNPM_ERR_INVALID_ARG;
+  int sel = 0;
+  const int rc = select_subset(const_cast<mqnpm_handle*>(h), h->k + 1, &sel);
+  if (rc != MQNPM_OK) return rc;
+  const std::vector<int>& sub = h->subsets[sel];
+  if (subset) *subset = sel;
+  if (illum) std::memcpy(illum, sub.data(), sub.size() * sizeof(int));
+  *count = (int)sub.size();
+  return MQNPM_OK;
+}
+
+int mqnpm_step_with_gradient(mqnpm_handle* h, float* x, const float* g, double loss, mqnpm_step_info* info) {
+  if (!h || !x || !g || g == x) return set_error(h, MQNPM_ERR_INVALID_ARG, "step_with_gradient: bad arguments");
+  if (!std::isfinite(loss)) return set_error(h, MQNPM_ERR_NONFINITE, "step_with_gradient: non-finite loss");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const int k = h->k + 1;
+  int sel = 0;
+  int rc = select_subset(h, k, &sel);
+  if (rc != MQNPM_OK) return rc;
+  if ((rc = step_events(h)) != MQNPM_OK) return rc;
+  h->fields_valid = false;
+  CK(cudaEventRecord(h->step_ev[0], s));
+  CK(cudaMemcpyAsync(h->g, g, h->N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  CK(cudaEventRecord(h->step_ev[1], s));
+  return finish_step(h, x, k, sel, loss, std::vector<int>(), MQNPM_OK, info);
 }
 
 // ---- checkpoint: header, then xbar, gbar, U (S x N floats each), P (3N floats)

@@ -287,3 +287,36 @@ def test_failures_are_reported():
         h.grad_batch(f32(bad).reshape(-1), [0], 1.0)
     assert e.value.code == 5
     h.close()
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_step_halves_and_sharded_step_equal_step(ls32, warm):
+    """mqnpm_step_subset + the caller's gradient + mqnpm_step_with_gradient (the
+    path of the illumination-sharded step, here with one rank: no collective)
+    give exactly what mqnpm_step gives, iterate for iterate, bit for bit."""
+    from paper_2307_02043_gb300.sharded import ShardedStep
+
+    w, kd, om, ys, subs, so, alpha, opt, xs = ls32
+    ya = torch.from_numpy(ys.astype(np.complex64)).to(DEV).reshape(-1)
+    h1 = handle(w, kd, so, alpha, warm_start=warm)
+    h2 = handle(w, kd, so, alpha, warm_start=warm)
+    h1.set_measurements(ya)
+    h2.set_measurements(ya)
+    x1 = torch.zeros(w.N, dtype=torch.float32, device=DEV)
+    x2 = torch.zeros_like(x1)
+    sharded = ShardedStep(h2)
+    assert (sharded.rank, sharded.world) == (0, 1)
+    for k in range(1, w.outer_iters + 1):
+        sub, il = h2.step_subset()
+        assert il == [int(i) for i in subs[sub]]
+        i1 = h1.step(x1)
+        i2 = sharded.step(x2)
+        assert i1["subset"] == i2["subset"] == sub and i1["k"] == i2["k"] == k
+        assert i1["loss"] == i2["loss"] and i1["tau_star"] == i2["tau_star"] and i1["rank"] == i2["rank"]
+        assert torch.equal(x1, x2), k
+    with pytest.raises(binding.MQNPMError):
+        h2.step_with_gradient(x2, x2, 0.0)              # g must not alias x
+    with pytest.raises(binding.MQNPMError):
+        h2.step_with_gradient(x2, torch.zeros_like(x2), float("nan"))
+    h1.close()
+    h2.close()
