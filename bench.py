@@ -688,22 +688,31 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     repeat through host buffers and the per-kernel figures of one workload."""
     h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile)
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
+    shard = bool(getattr(args, "shard", False))
+    if shard:
+        # the subset's illuminations split over the ranks, one all-reduce of the
+        # gradient, the rest of the iteration replicated (Eq. 4.1)
+        from paper_2307_02043_gb300.sharded import ShardedStep
+        sharded_step = ShardedStep(h, rank, world)
+        step = sharded_step.step
+    else:
+        step = lambda xx: h.step(xx, allow_not_converged=True)  # noqa: E731
     # Set-up iterations from x0 = 0: the S initial steps of Algorithm 4.1 and the
     # reconstruction up to iteration SETUP_ITERS, so that the warm-up and timed
     # steps sit where the paper's BQNPM-I reached ASPM's best SNR (38 iterations).
     for _ in range(max(w.S, SETUP_ITERS - args.warmup - args.steps)):
-        h.step(x, allow_not_converged=True)
+        step(x)
     for _ in range(args.warmup):
-        h.step(x, allow_not_converged=True)
+        step(x)
     torch.cuda.synchronize()
     # the end-to-end run below repeats the same iterations from this state
     state0, x0 = h.save_state(), x.cpu()
-    # ---- timed region: inputs resident in HBM
+    # ---- timed region: inputs resident in HBM, no pass timers (so that every
+    # BiCGSTAB solve runs as one graph launch with its loop on the device)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
-    h.profile_begin(8192)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -712,7 +721,7 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     launches0 = h.launch_count
     e0.record(stream)
     for _ in range(args.steps):
-        info = h.step(x, allow_not_converged=True)
+        info = step(x)
         infos.append(info)
         illum_done += len(subs[info["subset"]])
     e1.record(stream)
@@ -721,12 +730,10 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     prox_trace = h.prox_trace()
     if world > 1:
         dist.barrier()
-    prof = h.profile_end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     # ---- end-to-end through the public call with host buffers, same iterations
     h.load_state(state0)
-    del state0
     xh = torch.empty(w.N, dtype=torch.float32).pin_memory()
     xh.copy_(x0)
     torch.cuda.synchronize()
@@ -737,13 +744,24 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     f0.record(stream)
     for _ in range(args.steps):
         xd.copy_(xh, non_blocking=True)
-        info = h.step(xd, allow_not_converged=True)
+        info = step(xd)
         e2e_infos.append(info)
         e2e_illum += len(subs[info["subset"]])
         xh.copy_(xd, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
+    # ---- the same iterations once more with the pass timers (six events per
+    # Green's apply; the BiCGSTAB iterations then replay one graph each with a
+    # host check in between) for the per-pass times and the roofline
+    h.load_state(state0)
+    del state0
+    xp = x0.to(dev)
+    h.profile_begin(8192)
+    prof_infos = [step(xp) for _ in range(args.steps)]
+    prof = h.profile_end()
+    prof_same = [i["krylov_iters_total"] for i in prof_infos] == [i["krylov_iters_total"] for i in infos]
+    del xp
     if full and args.log_jsonl and rank == 0:
         with open(args.log_jsonl, "w") as f:
             for i in infos:
@@ -752,8 +770,10 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     # ---- max over ranks
     t_max, ms_e2e, illum_total, e2e_total = aggregate_ranks(torch, dist if world > 1 else None, dev, ms, ms_e2e,
                                                             illum_done, e2e_illum)
+    if shard:   # every rank stepped the same reconstruction: count its illuminations once
+        illum_total, e2e_total = float(illum_done), float(e2e_illum)
     value = illum_total / (t_max / 1e3)
-    iters_per_s = world * args.steps / (t_max / 1e3)
+    iters_per_s = (1 if shard else world) * args.steps / (t_max / 1e3)
     e2e_value = e2e_total / (ms_e2e / 1e3)
     # ---- roofline of the dominant Green's pass
     N = w.N
@@ -774,14 +794,16 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)", "data": "synthetic",
+        "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)",
+        "data": "synthetic",
         "config": {"workload": w.name, "n": n, "padded": 2 * n, "L": w.L, "batch": max(len(s) for s in subs),
                    "S": w.S, "model": "lippmann-schwinger" if w.model == "ls" else "first-born",
                    "krylov_tol": w.krylov_tol if w.model == "ls" else None, "dual_iters": w.dual_iters,
                    "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
                    "krylov_start": "forward solves warm-started from each illumination's last field"
                    if w.model == "ls" else None,
-                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+                   "parallelism": ("illumination-sharded x%d (one all-reduce per step)" % world) if shard
+                   else ("replicas" if world > 1 else "single-gpu")},
         "mqnpm_iters_per_s": round(iters_per_s, 3),
         "roofline": {"bound": "hbm", "kernel": "k_pass3 (" + names[dom] + ")" if dom == 2 else names[dom],
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -795,6 +817,8 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
         "roofline_alu": pass3_alu_view(n, prof, pms[2]) if prof["calls"] else None,
         "roofline_prox": prox_roofline(prox_trace, infos[-1]["rank"], N, infos[-1]["ms_prox"]),
         "passes": passes,
+        "passes_note": "pass times from a repeat of the timed iterations with CUDA events around every pass "
+                       "(same Krylov counts: %s)" % prof_same,
         "green_applies": prof["calls"],
         "green_tile": h.tile_info(),
         "phase_ms": {k: round(statistics.mean(i["ms_" + k] for i in infos), 3) for k in ("gradient", "metric", "prox")},
@@ -807,7 +831,7 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
         "wprox_vs_unweighted": wprox_ratio,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
                 "iterations": "the timed k = %d..%d again, from a checkpoint" % (infos[0]["k"], infos[-1]["k"]),
-                "pass_events": "none (the timed region above records 6 per Green's apply for the pass timings)",
+                "pass_events": "none, like the timed region",
                 "same_krylov_iters": [i["krylov_iters_total"] for i in e2e_infos] ==
                                      [i["krylov_iters_total"] for i in infos]},
     }
@@ -842,6 +866,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-born", action="store_true", help="skip the born128 figures of the default line")
+    ap.add_argument("--shard", action="store_true",
+                    help="one reconstruction with each subset's illuminations split over the ranks and the gradient "
+                         "summed by an all-reduce (strong scaling) instead of one replica per rank")
     ap.add_argument("--green-only", action="store_true",
                     help="small case for profiler captures: batched Green's applies of the workload grid")
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")

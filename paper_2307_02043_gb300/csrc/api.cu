@@ -209,6 +209,7 @@ void mqnpm_destroy(mqnpm_handle* h) {
     if (ev) cudaEventDestroy(ev);
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_nactive) cudaFreeHost(h->w.h_nactive);
+  if (h->w.h_loops) cudaFreeHost(h->w.h_loops);
   if (h->w.h_illum) cudaFreeHost(h->w.h_illum);
   if (h->w.h_warm) cudaFreeHost(h->w.h_warm);
   if (h->w.h_scal) cudaFreeHost(h->w.h_scal);
@@ -380,6 +381,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   if (h->warm_start && h->model == MQNPM_MODEL_LS) AL(h->ufield, (size_t)h->L * N);
   h->have_field.assign(h->L, 0);
   AL(w.nactive, 1);
+  AL(w.loops, 1);
   AL(w.dscal, 64);
   WproxWork& wp = h->wp;
   AL(wp.R, 3 * N); AL(wp.Pd, 3 * N); AL(wp.d, N); AL(wp.x, N);
@@ -422,6 +424,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
     }
   }
   if ((e = cudaMallocHost(&w.h_nactive, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
+  if ((e = cudaMallocHost(&w.h_loops, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_illum, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_warm, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_scal, 64 * sizeof(double))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }

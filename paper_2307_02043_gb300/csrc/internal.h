@@ -56,6 +56,7 @@ struct Profiler {
 struct KrylovGraph {
   int nb = 0;
   bool adjoint = false, prof = false;
+  bool loop = false;             // the whole solve: a conditional WHILE node around the iteration
   const float* x = nullptr;
   const float2* xs = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -105,6 +106,8 @@ struct Workspace {
   int* illum = nullptr;                  // [max_batch]
   int* nactive = nullptr;                // device counter
   int* h_nactive = nullptr;              // pinned host mirror
+  int* loops = nullptr;                  // device: iterations run by the device-side Krylov loop
+  int* h_loops = nullptr;                // pinned host mirror
   int* h_illum = nullptr;                // pinned staging of slot illuminations
   int* warm = nullptr;                   // [max_batch]: slot starts from a stored field
   int* h_warm = nullptr;                 // pinned staging of warm
@@ -186,6 +189,7 @@ struct mqnpm_handle {
   cudaStream_t capture_stream = nullptr;   // stream the iteration graphs are captured on
   std::vector<KrylovGraph> graphs;         // captured iterations (a few batch shapes)
   long long launches = 0;        // kernels launched by this handle since creation
+  long long pending_loop_kernels = 0;   // kernels per pass of the last device-side Krylov loop (not yet counted)
   cudaEvent_t step_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // phase timing of mqnpm_step
 };
 

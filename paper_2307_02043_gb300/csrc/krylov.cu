@@ -194,6 +194,16 @@ __global__ void k_fin_rho(KState* st, const double* partu, int nctas, int maxit,
   }
 }
 
+// End of one pass through the device-side Krylov loop: keep looping while a
+// slot is active.  k_fin_rho retires every slot at krylov_maxit iterations, so
+// the loop ends by itself; `loops` counts the passes and caps them at `cap`
+// as well (a bound that does not rely on the slot bookkeeping).
+__global__ void k_loop_cond(cudaGraphConditionalHandle cond, const int* nactive, int* loops, int cap) {
+  const int done = *loops + 1;
+  *loops = done;
+  cudaGraphSetConditional(cond, (*nactive > 0 && done < cap) ? 1u : 0u);
+}
+
 MQ_D float2 incident_at(const float2* tab, int l, int n, size_t i) {
   const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
   const float2* t = tab + (size_t)l * 3 * n;
@@ -388,6 +398,50 @@ int iteration_body(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adj
   return MQNPM_OK;
 }
 
+// The whole solve as one graph: a conditional WHILE node whose body is one
+// BiCGSTAB iteration followed by k_loop_cond, so the iterations of all slots
+// run without a host round trip; the caller reads the slot states once at the
+// end.  Event records are not allowed in a conditional body, so this form is
+// used only when the pass timers are off.
+int loop_graph(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint, cudaGraphExec_t* exec_out,
+               long long* kernels_out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNode_t node = nullptr;
+  cudaGraphNodeParams params = {};
+  params.type = cudaGraphNodeTypeConditional;
+  params.conditional.handle = cond;
+  params.conditional.type = cudaGraphCondTypeWhile;
+  params.conditional.size = 1;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &params);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return set_cuda_error(h, e, "conditional node of the Krylov loop");
+  }
+  cudaGraph_t body = params.conditional.phGraph_out[0];
+  cudaStream_t cs = h->capture_stream;
+  const long long before = h->launches;
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  int rc = MQNPM_OK;
+  if (e == cudaSuccess) {
+    rc = iteration_body(h, nb, x, xs, adjoint, cs, nullptr, nullptr);
+    k_loop_cond<<<1, 1, 0, cs>>>(cond, h->w.nactive, h->w.loops, h->krylov_maxit + 1);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = ee;
+  }
+  *kernels_out = h->launches - before + 1;
+  h->launches = before;
+  if (rc == MQNPM_OK && e == cudaSuccess) e = cudaGraphInstantiate(exec_out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (rc != MQNPM_OK) return rc;
+  if (e != cudaSuccess) return set_cuda_error(h, e, "capture of the device-side Krylov loop");
+  return MQNPM_OK;
+}
+
 void destroy_graph(KrylovGraph& g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   for (cudaEvent_t& e : g.ev)
@@ -399,9 +453,10 @@ void destroy_graph(KrylovGraph& g) {
 // private stream at first use (the caller's stream may be the legacy default
 // stream, which cannot be captured).  The graph ends with the copy of the
 // active-slot count to the host.
-int iteration_graph(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint, KrylovGraph** out) {
+int iteration_graph(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint, bool loop,
+                    KrylovGraph** out) {
   for (KrylovGraph& g : h->graphs)
-    if (g.nb == nb && g.adjoint == adjoint && g.x == x && g.xs == xs && g.prof == h->prof.on) {
+    if (g.nb == nb && g.adjoint == adjoint && g.x == x && g.xs == xs && g.prof == h->prof.on && g.loop == loop) {
       *out = &g;
       return MQNPM_OK;
     }
@@ -416,6 +471,17 @@ int iteration_graph(mqnpm_handle* h, int nb, const float* x, float2* xs, bool ad
   g.x = x;
   g.xs = xs;
   g.prof = h->prof.on;
+  g.loop = loop;
+  if (loop) {
+    const int rc = loop_graph(h, nb, x, xs, adjoint, &g.exec, &g.kernels);
+    if (rc != MQNPM_OK) {
+      destroy_graph(g);
+      return rc;
+    }
+    h->graphs.push_back(g);
+    *out = &h->graphs.back();
+    return MQNPM_OK;
+  }
   if (g.prof)
     for (cudaEvent_t& e : g.ev) CK(cudaEventCreate(&e));
   cudaStream_t cs = h->capture_stream;
@@ -445,9 +511,20 @@ int iteration_graph(mqnpm_handle* h, int nb, const float* x, float2* xs, bool ad
 int krylov_iterate(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
+  if (!h->direct_launches && !h->prof.on) {
+    // the whole loop on the device: one graph launch, no host round trip
+    KrylovGraph* g = nullptr;
+    const int rc = iteration_graph(h, nb, x, xs, adjoint, true, &g);
+    if (rc != MQNPM_OK) return rc;
+    CK(cudaMemsetAsync(w.loops, 0, sizeof(int), s));
+    CK(cudaGraphLaunch(g->exec, s));
+    CK(cudaMemcpyAsync(w.h_loops, w.loops, sizeof(int), cudaMemcpyDeviceToHost, s));
+    h->pending_loop_kernels = g->kernels;   // counted once the stream has been synchronised
+    return MQNPM_OK;
+  }
   if (!h->direct_launches) {
     KrylovGraph* g = nullptr;
-    const int rc = iteration_graph(h, nb, x, xs, adjoint, &g);
+    const int rc = iteration_graph(h, nb, x, xs, adjoint, false, &g);
     if (rc != MQNPM_OK) return rc;
     for (int it = 0; it < h->krylov_maxit; ++it) {
       CK(cudaGraphLaunch(g->exec, s));
@@ -485,6 +562,10 @@ int collect_states(mqnpm_handle* h, int nb, int* iters_out, int stride, int offs
   cudaError_t e = cudaMemcpyAsync(ks.data(), h->w.st, nb * sizeof(KState), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return set_cuda_error(h, e, "collect_states");
+  if (h->pending_loop_kernels) {   // kernels of the device-side loop: per pass times passes
+    h->launches += h->pending_loop_kernels * (long long)*h->w.h_loops;
+    h->pending_loop_kernels = 0;
+  }
   int code = MQNPM_OK;
   for (int b = 0; b < nb; ++b) {
     if (iters_out) iters_out[b * stride + offset] = ks[b].iters;

@@ -445,3 +445,27 @@ def test_graph_replay_equals_direct_launches(model):
     (ga, la, ia, ka, ca, sa), (gb, lb, ib, kb, cb, sb) = outs
     assert np.array_equal(ga, gb) and la == lb and ia == ib
     assert ka == kb and ca == cb and sa == sb
+
+
+def test_device_side_krylov_loop_equals_direct_launches():
+    """Without pass timers a whole BiCGSTAB solve is one graph launch: a
+    conditional WHILE node around the iteration, ended on the device when no
+    slot is active.  It gives the gradients, losses and iteration counts of
+    direct launches bit for bit, and launches exactly one more kernel (the
+    loop condition) per pass through the loop."""
+    n = 16
+    w, kd, xt, om, ys, subs, so = problem(n, "ls", L=6, batch=3)
+    outs = []
+    for direct in (False, True):
+        h = make_handle(n, kd, so, [1.0] * w.S, model="ls", krylov_tol=1e-6, max_batch=2, direct_launches=direct)
+        h.set_measurements(c64(ys).reshape(-1))
+        x = f32(0.7 * xt).reshape(-1)
+        h.grad_batch(x, [0, 1, 2], 1.0)                 # builds the graphs
+        k0 = h.launch_count
+        g, loss, its = h.grad_batch(x, [0, 1, 2], 1.0)
+        outs.append((g.cpu().numpy(), loss, its, h.launch_count - k0))
+        h.close()
+    (ga, la, ia, ka), (gb, lb, ib, kb) = outs
+    assert np.array_equal(ga, gb) and la == lb and ia == ib
+    passes = sum(max(1, max(ia[b][j] for b in chunk)) for chunk in ([0, 1], [2]) for j in (0, 1))
+    assert ka == kb + passes, (ka, kb, passes)
