@@ -433,19 +433,10 @@ def grad_only(args, torch, binding):
     h.close()
 
 
-def serve_uneven(args, torch, binding):
-    """Uneven request mix (16 reconstructions, grids 64^3-160^3, L in {24, 48, 60},
-    mini-batch 4-8): requests are admitted while their workspace fits the HBM
-    budget (the library's own budget check at create), served round-robin one
-    MQNPM iteration at a time, and retired after `outer_iters` iterations, which
-    admits queued requests.  Prints throughput and per-iteration latency
-    percentiles as one JSON line."""
-    dev = torch.device("cuda", 0)
-    reqs = synth.uneven_requests()
-    budget = int(args.hbm_budget_gb * 2 ** 30)
-    # measurements and alpha_s of every request (set-up, not timed)
+def prepare_uneven(torch, binding, dev):
+    """Measurements and alpha_s of every request of the uneven mix (set-up, not timed)."""
     prepared = []
-    for w in reqs:
+    for w in synth.uneven_requests():
         subs = synth.subsets(w)
         kd = synth.illumination_dirs(w)
         so = subset_of(w)
@@ -463,70 +454,150 @@ def serve_uneven(args, torch, binding):
         del xt
         prepared.append((w, kd, so, alpha, y, mb))
     torch.cuda.synchronize()
-    queue = list(range(len(reqs)))
-    active = {}        # request index -> (handle, x, iterations done)
-    used = 0
-    lat_ms, illum_done, admitted_order, peak_used = [], 0, [], 0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    return prepared
+
+
+def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_slots=16):
+    """One pass of the request loop over the uneven mix.  Requests are admitted
+    in order while their workspace fits the HBM budget (the library's own
+    budget check at create refuses the rest, which wait for a retirement) and
+    retired after `outer_iters` iterations.  shared = False: the active
+    requests step one after another, each on its own workspace of one
+    mini-batch.  shared = True: the active requests of one grid form a group
+    whose subset gradients run as one batch of slots (shared launches, up to
+    max_group_slots slots per chunk); each round steps every group once.
+    Per-iteration latency: the time from the start of the call that advances a
+    request to its end."""
+    queue = list(range(len(prepared)))
+    active = {}        # request index -> [handle, x, iterations done]
+    used = [0]
+    peak = [0]
+    tiles = {}
+    groups = {}        # n -> (Group, member ids)
+    lat_ms, illum_done = [], 0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def admit():
-        nonlocal used, peak_used
         while queue:
             i = queue[0]
             w, kd, so, alpha, y, mb = prepared[i]
-            if budget - used <= 0:                   # a zero budget would mean "no limit"
+            if budget - used[0] <= 0:                 # a zero budget would mean "no limit"
                 return
             try:
                 h = binding.MQNPM(w.n, kd, so, alpha, tv=w.tv, lam=w.lam, box=w.box, krylov_tol=w.krylov_tol,
                                   krylov_maxit=1000, dual_iters=w.dual_iters, gamma=w.gamma, step=w.step,
-                                  max_batch=mb, warm_start=True, hbm_budget_bytes=budget - used)
+                                  max_batch=1 if shared else mb, warm_start=True, hbm_budget_bytes=budget - used[0],
+                                  tile=tiles.get(w.n, -1))
             except binding.MQNPMError as err:
-                if err.code == 2 and active:     # over budget: wait for a retirement
+                if err.code == 2 and active:          # over budget: wait for a retirement
                     return
                 raise
             h.set_measurements(y.reshape(-1))
-            tiles[str(w.n)] = h.tile_info()["tile"]
-            used += h.workspace_bytes
-            peak_used = max(peak_used, used)
-            active[i] = (h, torch.zeros(w.N, dtype=torch.float32, device=dev), 0)
-            admitted_order.append(i)
+            tiles[w.n] = h.tile_info()["tile"]
+            used[0] += h.workspace_bytes
+            peak[0] = max(peak[0], used[0])
+            active[i] = [h, torch.zeros(w.N, dtype=torch.float32, device=dev), 0]
             queue.pop(0)
 
-    tiles = {}
+    def retire(i):
+        h = active[i][0]
+        used[0] -= h.workspace_bytes
+        n = prepared[i][0].n
+        if n in groups:                               # membership changes: the group is rebuilt
+            g, _ = groups.pop(n)
+            used[0] -= g.workspace_bytes
+            g.close()
+        h.close()
+        del active[i]
+
+    def group_for(n, ids):
+        cur = groups.get(n)
+        if cur is not None and cur[1] == ids:
+            return cur[0]
+        if cur is not None:
+            used[0] -= cur[0].workspace_bytes
+            cur[0].close()
+            del groups[n]
+        slots = min(max_group_slots, sum(prepared[i][5] for i in ids))
+        while True:
+            try:
+                g = binding.Group([active[i][0] for i in ids], max_slots=slots,
+                                  hbm_budget_bytes=max(1, budget - used[0]))
+                break
+            except binding.MQNPMError as err:
+                if err.code != 2 or slots == 1:
+                    raise
+                slots = max(1, slots // 2)
+        used[0] += g.workspace_bytes
+        peak[0] = max(peak[0], used[0])
+        groups[n] = (g, ids)
+        return g
+
     admit()
     admitted_first = len(active)
-    t0.record()
+    ev[2].record()
     while active:
-        for i in list(active):
-            h, x, done = active[i]
-            e0.record()
-            info = h.step(x, allow_not_converged=True)
-            e1.record()
-            e1.synchronize()
-            lat_ms.append(e0.elapsed_time(e1))
-            illum_done += info["n_illum"]
-            done += 1
-            if done >= prepared[i][0].outer_iters:
-                used -= h.workspace_bytes
-                h.close()
-                del active[i]
-                admit()
-            else:
-                active[i] = (h, x, done)
-    t1.record()
+        if shared:
+            by_n = {}
+            for i in sorted(active):
+                by_n.setdefault(prepared[i][0].n, []).append(i)
+            for n, ids in sorted(by_n.items()):
+                g = group_for(n, ids)
+                ev[0].record()
+                infos = g.step([active[i][1] for i in ids], allow_not_converged=True)
+                ev[1].record()
+                ev[1].synchronize()
+                t = ev[0].elapsed_time(ev[1])
+                for i, info in zip(ids, infos):
+                    lat_ms.append(t)
+                    illum_done += info["n_illum"]
+                    active[i][2] += 1
+            for i in [i for i in list(active) if active[i][2] >= prepared[i][0].outer_iters]:
+                retire(i)
+            admit()
+        else:
+            for i in list(active):
+                h, x, done = active[i]
+                ev[0].record()
+                info = h.step(x, allow_not_converged=True)
+                ev[1].record()
+                ev[1].synchronize()
+                lat_ms.append(ev[0].elapsed_time(ev[1]))
+                illum_done += info["n_illum"]
+                active[i][2] += 1
+                if active[i][2] >= prepared[i][0].outer_iters:
+                    retire(i)
+                    admit()
+    ev[3].record()
     torch.cuda.synchronize()
-    total_ms = t0.elapsed_time(t1)
+    total_ms = ev[2].elapsed_time(ev[3])
     lat = np.array(lat_ms)
-    print(json.dumps({
-        "workload": "uneven16", "requests": len(reqs), "grids": sorted({w.n for w in reqs}),
-        "hbm_budget_gb": args.hbm_budget_gb, "peak_workspace_gb": round(peak_used / 2 ** 30, 2),
-        "admitted_at_start": admitted_first, "admission_order": admitted_order, "iterations": int(lat.size),
-        "illum_gradients_per_s": round(illum_done / (total_ms / 1e3), 2),
-        "iteration_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
-                                 "p99": round(float(np.percentile(lat, 99)), 3),
-                                 "max": round(float(lat.max()), 3)},
-        "total_ms": round(total_ms, 1), "green_tile_per_grid": tiles}), flush=True)
+    return {"mode": "shared launches per grid" if shared else "one request after another",
+            "peak_workspace_gb": round(peak[0] / 2 ** 30, 2), "admitted_at_start": admitted_first,
+            "iterations": int(lat.size), "illum_gradients_per_s": round(illum_done / (total_ms / 1e3), 2),
+            "iteration_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                     "p99": round(float(np.percentile(lat, 99)), 3),
+                                     "max": round(float(lat.max()), 3)},
+            "total_ms": round(total_ms, 1), "green_tile_per_grid": {str(k): v for k, v in tiles.items()}}
+
+
+def serve_uneven(args, torch, binding):
+    """Uneven request mix (16 reconstructions, grids 64^3-160^3, L in {24, 48, 60},
+    mini-batch 4-8): the request loop with shared launches per grid (the
+    served figures) and, for comparison, one request after another.  Prints
+    both as one JSON line."""
+    dev = torch.device("cuda", 0)
+    prepared = prepare_uneven(torch, binding, dev)
+    budget = int(args.hbm_budget_gb * 2 ** 30)
+    shared = serve_uneven_run(prepared, budget, True, torch, binding, dev)
+    serial = serve_uneven_run(prepared, budget, False, torch, binding, dev)
+    print(json.dumps({"workload": "uneven16", "requests": len(prepared),
+                      "grids": sorted({p[0].n for p in prepared}), "hbm_budget_gb": args.hbm_budget_gb,
+                      "illum_gradients_per_s": shared["illum_gradients_per_s"],
+                      "iteration_latency_ms": shared["iteration_latency_ms"],
+                      "shared": shared, "serial": serial,
+                      "speedup_shared_vs_serial": round(shared["illum_gradients_per_s"] /
+                                                        serial["illum_gradients_per_s"], 3)}), flush=True)
 
 
 def weighted_vs_unweighted_prox(torch, h, x, infos, w):

@@ -265,6 +265,35 @@ int mqnpm_step(mqnpm_handle* h, float* x, mqnpm_step_info* info);
 int mqnpm_step_subset(const mqnpm_handle* h, int* subset, int* illum, int* count);
 int mqnpm_step_with_gradient(mqnpm_handle* h, float* x, const float* g, double loss, mqnpm_step_info* info);
 
+/* Shared launches for several reconstructions of one grid (the request loop of
+ * the serving configuration; no counterpart in the paper beyond Algorithm 4.1
+ * run for each member).  A group holds count member handles with equal n, h,
+ * kb, green_kernel, tile, device, krylov_tol, krylov_maxit and
+ * direct_launches, the LS model and the slice detector (else INVALID_ARG or
+ * UNSUPPORTED); members keep their own L, subsets, measurements, metric
+ * state, TV, box and warm-start fields, and stay usable on their own.  The
+ * group allocates a shared Krylov workspace of max_slots slots (1..
+ * MQNPM_MAX_BATCH, within hbm_budget_bytes when non-zero), concatenated
+ * incident-field tables and measurements, and copies member 0's Green's
+ * spectrum.  The group must be destroyed before its members.
+ * mqnpm_group_step: iteration k+1 of Algorithm 4.1 for every member.  x:
+ *   host array of count device pointers (each member's N-float iterate,
+ *   in/out, distinct); info: host array of count, or NULL.  All subset
+ *   gradients run as one batch of slots in chunks of max_slots (each Green's
+ *   pass and BiCGSTAB iteration one launch over the slots of all members,
+ *   each slot reading its own volume's contrast); then each member's SR1
+ *   update, quasi-Newton point and weighted proximal mapping.  Runs on the
+ *   group's stream, which becomes every member's stream.  NOT_CONVERGED as
+ *   mqnpm_step (outputs written); STATE if a member has no measurements. */
+typedef struct mqnpm_group mqnpm_group;
+int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, size_t hbm_budget_bytes,
+                       mqnpm_group** out);
+void mqnpm_group_destroy(mqnpm_group* g);
+int mqnpm_group_step(mqnpm_group* g, float* const* x, mqnpm_step_info* info);
+int mqnpm_group_set_stream(mqnpm_group* g, void* stream);
+size_t mqnpm_group_workspace_bytes(const mqnpm_group* g);
+const char* mqnpm_group_last_error(const mqnpm_group* g);
+
 /* alpha estimate for a subset: `iters` power steps on
  * scale * sum_{l in illum} Re(J_l^H J_l) with J_l the Born Jacobian at x = 0,
  * from the device start vector `start` (N floats); result in *alpha_out (host). */

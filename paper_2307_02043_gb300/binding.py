@@ -113,6 +113,13 @@ SIGNATURES = {
     "mqnpm_green_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mqnpm_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+    "mqnpm_group_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "mqnpm_group_destroy": (None, [ctypes.c_void_p]),
+    "mqnpm_group_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(StepInfo)]),
+    "mqnpm_group_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mqnpm_group_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "mqnpm_group_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
 
@@ -490,3 +497,52 @@ class MQNPM:
         self._stream()
         self._raise(self.lib.mqnpm_profile_end(self._h, ms, ctypes.byref(slots), ctypes.byref(calls)))
         return {"pass_ms": list(ms), "slot_launches": slots.value, "calls": calls.value}
+
+
+class Group:
+    """Several reconstructions of one grid whose subset gradients run in shared
+    launches (a libmqnpm group of member handles)."""
+
+    def __init__(self, members: Sequence[MQNPM], max_slots: int, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        self.members = list(members)
+        if not self.members:
+            raise ValueError("a group needs at least one member")
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        g = ctypes.c_void_p()
+        rc = self.lib.mqnpm_group_create(arr, len(self.members), int(max_slots), int(hbm_budget_bytes),
+                                         ctypes.byref(g))
+        if rc != OK:
+            raise MQNPMError(rc, "mqnpm_group_create failed")
+        self._g = g
+        self.device = self.members[0].device
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self.lib.mqnpm_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.lib.mqnpm_group_workspace_bytes(self._g))
+
+    def step(self, xs: Sequence[torch.Tensor], allow_not_converged=False) -> list:
+        if len(xs) != len(self.members):
+            raise ValueError("one iterate per member")
+        for m, x in zip(self.members, xs):
+            _check_cuda(x, torch.float32, m.N, "x", self.device)
+        ptrs = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        infos = (StepInfo * len(xs))()
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.mqnpm_group_set_stream(self._g, ctypes.c_void_p(s))
+        rc = self.lib.mqnpm_group_step(self._g, ptrs, infos)
+        if rc != OK and not (allow_not_converged and rc == 4):
+            msg = self.lib.mqnpm_group_last_error(self._g).decode()
+            raise (NotConverged if rc == 4 else MQNPMError)(rc, msg)
+        return [{f: getattr(i, f) for f, _ in StepInfo._fields_} for i in infos]

@@ -38,7 +38,8 @@ def _units():
     units = []
     for P in P_VALUES:
         units.append(("green_inst.cu", ["-DMQ_P=%d" % P], "green_P%d.o" % P))
-    for name in ("green.cu", "krylov.cu", "wprox_coop.cu", "woodbury.cu", "api.cu", "noalloc.cu", "tune.cu", "detector.cu"):
+    for name in ("green.cu", "krylov.cu", "wprox_coop.cu", "woodbury.cu", "api.cu", "noalloc.cu", "tune.cu", "detector.cu",
+                 "group.cu"):
         units.append((name, [], name.replace(".cu", ".o")))
     units.append(("wprox_coop.cu", ["-DMQ_WP_HIGH"], "wprox_high.o"))   # ranks 9-16 of the prox kernel
     return units

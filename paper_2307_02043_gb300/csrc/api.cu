@@ -211,7 +211,10 @@ void mqnpm_destroy(mqnpm_handle* h) {
   if (h->w.h_nactive) cudaFreeHost(h->w.h_nactive);
   if (h->w.h_loops) cudaFreeHost(h->w.h_loops);
   if (h->w.h_illum) cudaFreeHost(h->w.h_illum);
-  if (h->w.h_warm) cudaFreeHost(h->w.h_warm);
+  if (h->w.h_xslot) cudaFreeHost(h->w.h_xslot);
+  if (h->w.h_fwarm) cudaFreeHost(h->w.h_fwarm);
+  if (h->w.h_fstore) cudaFreeHost(h->w.h_fstore);
+  if (h->w.h_segs) cudaFreeHost(h->w.h_segs);
   if (h->w.h_scal) cudaFreeHost(h->w.h_scal);
   cudaSetDevice(dev);
   delete h;
@@ -377,7 +380,10 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   AL(w.st, B);
   AL(w.gerr, 1);
   AL(w.illum, B);
-  AL(w.warm, B);
+  AL(w.xslot, B);
+  AL(w.fwarm, B);
+  AL(w.fstore, B);
+  AL(w.segs, B);
   if (h->warm_start && h->model == MQNPM_MODEL_LS) AL(h->ufield, (size_t)h->L * N);
   h->have_field.assign(h->L, 0);
   AL(w.nactive, 1);
@@ -426,7 +432,13 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   if ((e = cudaMallocHost(&w.h_nactive, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_loops, sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
   if ((e = cudaMallocHost(&w.h_illum, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
-  if ((e = cudaMallocHost(&w.h_warm, B * sizeof(int))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
+  if ((e = cudaMallocHost(&w.h_xslot, B * sizeof(const float*))) != cudaSuccess ||
+      (e = cudaMallocHost(&w.h_fwarm, B * sizeof(float2*))) != cudaSuccess ||
+      (e = cudaMallocHost(&w.h_fstore, B * sizeof(float2*))) != cudaSuccess ||
+      (e = cudaMallocHost(&w.h_segs, B * sizeof(GradSeg))) != cudaSuccess) {
+    set_cuda_error(h, e, "cudaMallocHost");
+    return fail(MQNPM_ERR_CUDA);
+  }
   if ((e = cudaMallocHost(&w.h_scal, 64 * sizeof(double))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
 
   // ---- tables: twiddles W_P^j and incident-field axis factors, built in FP64
@@ -596,8 +608,6 @@ int mqnpm_lipschitz(mqnpm_handle* h, const int* illum, int nb, double scale, con
 
 }  // extern "C"
 
-namespace {
-
 // Subset of iteration k (Algorithm 4.1): s = k for k <= S, then s' by
 // strategy I (cyclic) or II (the caller's draws).
 int select_subset(mqnpm_handle* h, int k, int* sel) {
@@ -749,8 +759,6 @@ int step_events(mqnpm_handle* h) {
   }
   return MQNPM_OK;
 }
-
-}  // namespace
 
 extern "C" {
 

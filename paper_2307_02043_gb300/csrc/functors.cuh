@@ -31,15 +31,19 @@ struct Pro<PRO_PLAIN> {
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const { return a.q[g.vox(b, x, y, z)]; }
 };
 
+// Contrast of slot b: the shared one, or the slot's own (several volumes in one launch).
+MQ_D const float* slot_contrast(const ProArgs& a, int b) { return a.xs ? a.xs[b] : a.x; }
+
 template <>
 struct Pro<PRO_CONTRAST> {
   static constexpr int NPART = 0;
   ProArgs a;
   Geo g;
-  MQ_D void begin(int) {}
+  const float* xb;
+  MQ_D void begin(int b) { xb = slot_contrast(a, b); }
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
-    return cscale(a.q[g.vox(b, x, y, z)], a.x[g.vox0(x, y, z)]);
+    return cscale(a.q[g.vox(b, x, y, z)], xb[g.vox0(x, y, z)]);
   }
 };
 
@@ -48,10 +52,11 @@ struct Pro<PRO_BORN> {
   static constexpr int NPART = 0;
   ProArgs a;
   Geo g;
-  MQ_D void begin(int) {}
+  const float* xb;
+  MQ_D void begin(int b) { xb = slot_contrast(a, b); }
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
-    return cscale(incident(a.tab, a.illum[b], g.n, x, y, z), a.x[g.vox0(x, y, z)]);
+    return cscale(incident(a.tab, a.illum[b], g.n, x, y, z), xb[g.vox0(x, y, z)]);
   }
 };
 
@@ -63,7 +68,9 @@ struct Pro<PRO_BICG_P> {
   const KState* st;
   float2 beta, omega;   // slot scalars, rounded once per thread by begin()
   bool first;
+  const float* xb;
   MQ_D void begin(int b) {
+    xb = slot_contrast(a, b);
     first = st[b].iters == 0;
     beta = make_float2((float)st[b].beta_re, (float)st[b].beta_im);
     omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
@@ -77,7 +84,7 @@ struct Pro<PRO_BICG_P> {
       pn = caxpy(beta, pv, pn);                                 // r + beta (p - omega v)
     }
     a.w[i] = pn;
-    return cscale(pn, a.x[g.vox0(x, y, z)]);
+    return cscale(pn, xb[g.vox0(x, y, z)]);
   }
 };
 
@@ -88,14 +95,18 @@ struct Pro<PRO_BICG_S> {
   Geo g;
   const KState* st;
   float2 alpha;         // slot scalar, rounded once per thread by begin()
-  MQ_D void begin(int b) { alpha = make_float2((float)st[b].alpha_re, (float)st[b].alpha_im); }
+  const float* xb;
+  MQ_D void begin(int b) {
+    xb = slot_contrast(a, b);
+    alpha = make_float2((float)st[b].alpha_re, (float)st[b].alpha_im);
+  }
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt& parts) const {
     const size_t i = g.vox(b, x, y, z);
     const float2 s = caxpy(make_float2(-alpha.x, -alpha.y), a.v[i], a.r[i]);   // r - alpha v
     a.w[i] = s;
     parts.v[0] += cabs2(s);
-    return cscale(s, a.x[g.vox0(x, y, z)]);
+    return cscale(s, xb[g.vox0(x, y, z)]);
   }
 };
 

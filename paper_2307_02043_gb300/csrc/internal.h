@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "kstate.h"
+#include "mqnpm.h"
 
 // One Green's apply over a batch: pass 1 (prologue) ... pass 5 (epilogue).
 struct GreenCall {
@@ -109,8 +110,14 @@ struct Workspace {
   int* loops = nullptr;                  // device: iterations run by the device-side Krylov loop
   int* h_loops = nullptr;                // pinned host mirror
   int* h_illum = nullptr;                // pinned staging of slot illuminations
-  int* warm = nullptr;                   // [max_batch]: slot starts from a stored field
-  int* h_warm = nullptr;                 // pinned staging of warm
+  const float** xslot = nullptr;         // [max_batch] contrast of each slot (shared launches)
+  float2** fwarm = nullptr;              // [max_batch] field a warm start reads (NULL: u_in)
+  float2** fstore = nullptr;             // [max_batch] where the converged field is kept (NULL: nowhere)
+  GradSeg* segs = nullptr;               // [max_batch] gradient segments of the chunk
+  const float** h_xslot = nullptr;       // pinned staging of the four tables above
+  float2** h_fwarm = nullptr;
+  float2** h_fstore = nullptr;
+  GradSeg* h_segs = nullptr;
   double* h_scal = nullptr;              // pinned scalar staging (64 doubles)
   double* dscal = nullptr;               // device scalar scratch (64 doubles)
   int ctas_row = 0, ctas_upd = 0, ctas_vec = 0;
@@ -197,6 +204,19 @@ struct mqnpm_handle {
 cudaEvent_t* profile_slot(mqnpm_handle* h, int nb);
 
 // krylov.cu
+// Per-slot tables of one chunk of solves (see stage_chunk).
+struct ChunkTables {
+  int m = 0;
+  std::vector<int> illum;           // illumination of each slot (index into tab and ymeas)
+  std::vector<const float*> x;      // contrast of each slot (empty: the call's shared x)
+  std::vector<float2*> warm, store; // start field / field store of each slot (empty: none)
+  std::vector<GradSeg> segs;        // runs of slots summed into one gradient each
+};
+int stage_chunk(mqnpm_handle* h, const ChunkTables& t);
+int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2* det_out, const float2* ym,
+                  bool warm, bool store, const std::vector<GradSeg>& segs);
+int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, int nseg);
+int check_tile_waits(mqnpm_handle* h);
 int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale,
                     float* grad, double* loss, int* iters, bool want_grad, float2* y_out);
 int loss_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, double* loss,
@@ -229,6 +249,13 @@ cudaError_t detector_tables(mqnpm_handle* h, double distance, double na);
 cudaError_t detector_forward(mqnpm_handle* h, float2* det, int m, const float2* ym, const int* illum);
 // out <- D^H r (m slices)
 cudaError_t detector_adjoint(mqnpm_handle* h, const float2* r, float2* out, int m);
+
+// api.cu: the outer loop around a subset gradient (shared by mqnpm_step,
+// mqnpm_step_with_gradient and the group step)
+int select_subset(mqnpm_handle* h, int k, int* sel);
+int finish_step(mqnpm_handle* h, float* x, int k, int sel, double loss, const std::vector<int>& its, int grad_rc,
+                mqnpm_step_info* info);
+int step_events(mqnpm_handle* h);
 
 // tune.cu: pick the launch shapes of the Green's passes by timing
 int autotune_tile(mqnpm_handle* h);

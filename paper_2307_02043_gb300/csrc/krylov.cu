@@ -218,21 +218,21 @@ __global__ void k_init_uin(float2* u, const float2* tab, const int* illum, int n
 }
 
 // Start fields of a warm-started forward solve: the field stored for the
-// slot's illumination where there is one, else u_in.
-__global__ void k_init_u_warm(float2* u, const float2* __restrict__ ufield, const int* warm, const float2* tab,
-                              const int* illum, int n, size_t N) {
+// slot's illumination where there is one (fwarm[b]), else u_in.
+__global__ void k_init_u_warm(float2* u, float2* const* fwarm, const float2* tab, const int* illum, int n, size_t N) {
   const int b = blockIdx.y;
   const int l = illum[b];
-  const bool w = warm[b] != 0;
-  const float2* src = ufield + (size_t)l * N;
+  const float2* src = fwarm[b];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
-    u[(size_t)b * N + i] = w ? src[i] : incident_at(tab, l, n, i);
+    u[(size_t)b * N + i] = src ? src[i] : incident_at(tab, l, n, i);
 }
 
-// Keep each slot's converged field for its illumination's next solve.
-__global__ void k_store_field(float2* __restrict__ ufield, const float2* __restrict__ u, const int* illum, size_t N) {
+// Keep each slot's converged field for its illumination's next solve
+// (fstore[b]; slots without a destination keep nothing).
+__global__ void k_store_field(float2* const* fstore, const float2* __restrict__ u, size_t N) {
   const int b = blockIdx.y;
-  float2* dst = ufield + (size_t)illum[b] * N;
+  float2* dst = fstore[b];
+  if (dst == nullptr) return;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = u[(size_t)b * N + i];
 }
@@ -271,6 +271,24 @@ __global__ void k_grad(const float2* __restrict__ u, const float2* __restrict__ 
     }
     const float g = scale * acc;
     grad[i] = accumulate ? grad[i] + g : g;
+  }
+}
+
+// Gradient assembly per segment of consecutive slots (blockIdx.y = segment):
+// seg.grad[i] (+)= seg.scale * sum_{b in [b0, b1)} Re(conj(u_b[i]) z_b[i]),
+// u_b = u_in(l_b) when u == NULL (Born).
+__global__ void k_grad_seg(const float2* __restrict__ u, const float2* __restrict__ zsol, const float2* tab,
+                           const int* illum, int n, size_t N, const GradSeg* segs) {
+  const GradSeg sg = segs[blockIdx.y];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = sg.b0; b < sg.b1; ++b) {
+      const float2 uu = u ? u[(size_t)b * N + i] : incident_at(tab, illum[b], n, i);
+      const float2 zz = zsol[(size_t)b * N + i];
+      acc = fmaf(uu.x, zz.x, fmaf(uu.y, zz.y, acc));
+    }
+    const float g = sg.scale * acc;
+    sg.grad[i] = sg.accumulate ? sg.grad[i] + g : g;
   }
 }
 
@@ -374,6 +392,7 @@ int iteration_body(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adj
   c.st = w.st;
   c.pro = PRO_BICG_P;
   c.pa.x = x;
+  c.pa.xs = x ? nullptr : w.xslot;   // x == NULL: each slot's own contrast (shared launches)
   c.pa.w = w.p;
   c.pa.r = w.r;
   c.pa.v = w.v;
@@ -578,17 +597,20 @@ int collect_states(mqnpm_handle* h, int nb, int* iters_out, int stride, int offs
 
 }  // namespace
 
-// Forward LS solve for nb slots: u = (I - G X)^{-1} u_in.
-static int forward_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int stride, int offset) {
+// Forward LS solve for nb slots: u = (I - G X)^{-1} u_in.  The staged tables
+// of the chunk give each slot its start field (fwarm) and the place its
+// converged field is kept (fstore); warm selects the warm-start form of the
+// first residual.  x == NULL: each slot's own contrast (xslot).
+static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool store, int* iters, int stride,
+                      int offset) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   GreenCall c = base_call(h, nb, false);
-  if (h->ufield) {
+  c.pa.xs = x ? nullptr : w.xslot;
+  if (warm) {
     // warm start: u_0 = the stored field (or u_in), r_0 = u_in - u_0 + G(x u_0)
-    for (int b = 0; b < nb; ++b) w.h_warm[b] = h->have_field[w.h_illum[b]] ? 1 : 0;
-    CK(cudaMemcpyAsync(w.warm, w.h_warm, nb * sizeof(int), cudaMemcpyHostToDevice, s));
-    k_init_u_warm<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->ufield, w.warm, h->tab, w.illum, h->n, N);
+    k_init_u_warm<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, w.fwarm, h->tab, w.illum, h->n, N);
     c.pro = PRO_CONTRAST;
     c.pa.x = x;
     c.pa.q = w.u;
@@ -612,15 +634,12 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   h->launches += 2;   // init, fin_init
   int rc = krylov_iterate(h, nb, x, w.u, false);
   if (rc != MQNPM_OK) return rc;
-  if (h->ufield) {
-    k_store_field<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(h->ufield, w.u, w.illum, N);
+  if (store) {
+    k_store_field<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.fstore, w.u, N);
     CK(cudaGetLastError());
     h->launches += 1;
   }
-  rc = collect_states(h, nb, iters, stride, offset);
-  if (h->ufield)
-    for (int b = 0; b < nb; ++b) h->have_field[w.h_illum[b]] = (rc == MQNPM_ERR_NONFINITE) ? 0 : 1;
-  return rc;
+  return collect_states(h, nb, iters, stride, offset);
 }
 
 // Adjoint solve for nb slots: z = (I - G^H X)^{-1} G^H S^T r_det.
@@ -649,27 +668,71 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   return collect_states(h, nb, iters, stride, offset);
 }
 
-namespace {
 
-// Stage the illuminations of one chunk (pinned staging, then the device copy).
-int chunk_illum(mqnpm_handle* h, const int* illum, int c0, int m) {
+// Stage the per-slot tables of one chunk (pinned staging, then the device
+// copies): illuminations, contrasts (shared launches only), warm-start and
+// store fields, gradient segments.  Waits for the previous chunk's copies.
+int stage_chunk(mqnpm_handle* h, const ChunkTables& t) {
   Workspace& w = h->w;
+  const int m = t.m;
+  if (m < 1 || m > h->max_batch || (int)t.segs.size() < 1 || (int)t.segs.size() > m)
+    return set_error(h, MQNPM_ERR_INVALID_ARG, "stage_chunk: bad chunk");
   CK(cudaStreamSynchronize(h->stream));
-  for (int b = 0; b < m; ++b) w.h_illum[b] = illum[c0 + b];
-  CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  for (int b = 0; b < m; ++b) {
+    w.h_illum[b] = t.illum[b];
+    w.h_xslot[b] = t.x.empty() ? nullptr : t.x[b];
+    w.h_fwarm[b] = t.warm.empty() ? nullptr : t.warm[b];
+    w.h_fstore[b] = t.store.empty() ? nullptr : t.store[b];
+  }
+  for (size_t q = 0; q < t.segs.size(); ++q) w.h_segs[q] = t.segs[q];
+  cudaStream_t s = h->stream;
+  CK(cudaMemcpyAsync(w.illum, w.h_illum, m * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.xslot, w.h_xslot, m * sizeof(const float*), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.fwarm, w.h_fwarm, m * sizeof(float2*), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.fstore, w.h_fstore, m * sizeof(float2*), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.segs, w.h_segs, t.segs.size() * sizeof(GradSeg), cudaMemcpyHostToDevice, s));
   return MQNPM_OK;
 }
 
-// Forward fields and detector residuals of one chunk (slots [0, m)); the
-// residual norm lands in w.h_scal[0] after the next synchronisation.
-int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2* det_out, const float2* ym) {
+namespace {
+
+// The tables of chunk [c0, c0 + m) of one handle's illumination list: every
+// slot reads the handle's contrast, the handle's stored fields (warm start)
+// and adds into one gradient.
+ChunkTables handle_chunk(mqnpm_handle* h, const int* illum, int c0, int m, double scale, float* grad) {
+  ChunkTables t;
+  t.m = m;
+  t.illum.assign(illum + c0, illum + c0 + m);
+  if (h->ufield) {
+    t.warm.resize(m);
+    t.store.resize(m);
+    for (int b = 0; b < m; ++b) {
+      const int l = t.illum[b];
+      t.store[b] = h->ufield + (size_t)l * h->N;
+      t.warm[b] = h->have_field[l] ? t.store[b] : nullptr;
+    }
+  }
+  t.segs.push_back(GradSeg{0, m, c0 > 0 ? 1 : 0, (float)scale, grad});
+  return t;
+}
+
+}  // namespace
+
+// Forward fields and detector residuals of one staged chunk (slots [0, m));
+// the residual norm of segment q lands in w.h_scal[q] after the next
+// synchronisation (nseg > 1 only for LS without a remote detector).
+int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2* det_out, const float2* ym,
+                  bool warm, bool store, const std::vector<GradSeg>& segs) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   int worst = MQNPM_OK;
   int parts = m * w.ctas_row;          // detector partials to sum
+  const int nseg = (int)segs.size();
+  if (nseg > 1 && (h->model != MQNPM_MODEL_LS || h->remote))
+    return set_error(h, MQNPM_ERR_UNSUPPORTED, "per-segment losses need the LS model and the slice detector");
   if (h->model == MQNPM_MODEL_LS) {
-    int rc = forward_ls(h, m, x, it_chunk, 2, 0);
+    int rc = forward_ls(h, m, x, warm, store, it_chunk, 2, 0);
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
     if (rc != MQNPM_OK) worst = rc;
     k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, h->remote ? nullptr : ym, det_out,
@@ -679,6 +742,7 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     c.pro = PRO_BORN;
     c.outplane = true;                 // only the detector plane of G(x u_in) is used
     c.pa.x = x;
+    c.pa.xs = x ? nullptr : w.xslot;
     c.pa.tab = h->tab;
     c.pa.illum = w.illum;
     c.epi = EPI_DETECT;
@@ -694,15 +758,22 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     CK(detector_forward(h, det_out, m, ym, w.illum));
     parts = m * w.ctas_row;
   }
-  k_sum_all<<<1, 256, 0, s>>>(w.partd, parts, w.dscal);
-  CK(cudaMemcpyAsync(w.h_scal, w.dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
-  h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + 1;
+  if (nseg == 1) {
+    k_sum_all<<<1, 256, 0, s>>>(w.partd, parts, w.dscal);
+  } else {   // LS: partials [slot][ctas_row], one sum per segment of slots
+    for (int q = 0; q < nseg; ++q)
+      k_sum_all<<<1, 256, 0, s>>>(w.partd + (size_t)segs[q].b0 * w.ctas_row, (segs[q].b1 - segs[q].b0) * w.ctas_row,
+                                  w.dscal + q);
+  }
+  CK(cudaMemcpyAsync(w.h_scal, w.dscal, nseg * sizeof(double), cudaMemcpyDeviceToHost, s));
+  h->launches += (h->model == MQNPM_MODEL_LS ? 1 : 0) + nseg;
   return worst;
 }
 
-// Adjoint solves and gradient assembly of one chunk from the fields and
-// residuals in the workspace; accumulate adds to grad.
-int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, double scale, float* grad, bool accumulate) {
+
+// Adjoint solves and gradient assembly of one staged chunk from the fields
+// and residuals in the workspace (into the staged gradient segments).
+int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, int nseg) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
   const size_t N = h->N;
@@ -711,7 +782,7 @@ int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, double 
     int rc = adjoint_ls(h, m, x, it_chunk, 2, 1);
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
     if (rc != MQNPM_OK) worst = rc;
-    k_grad<<<w.ctas_vec, 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, accumulate);
+    k_grad_seg<<<dim3(w.ctas_vec, nseg), 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, h->n, N, w.segs);
   } else {
     GreenCall c = base_call(h, m, true);
     c.pro = PRO_LIFT;
@@ -724,7 +795,7 @@ int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, double 
     c.epi = EPI_PLAIN;
     c.ea.out = w.zs;
     CK(glaunch(h, c, s));
-    k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, grad, accumulate);
+    k_grad_seg<<<dim3(w.ctas_vec, nseg), 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, h->n, N, w.segs);
   }
   CK(cudaGetLastError());
   h->launches += 1;
@@ -738,7 +809,6 @@ int check_tile_waits(mqnpm_handle* h) {
   return MQNPM_OK;
 }
 
-}  // namespace
 
 int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, double scale, float* grad,
                     double* loss, int* iters, bool want_grad, float2* y_out) {
@@ -750,16 +820,19 @@ int grad_batch_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, d
   h->last_iters.assign(2 * nb, 0);
   for (int c0 = 0; c0 < nb; c0 += h->max_batch) {
     const int m = std::min(h->max_batch, nb - c0);
-    int rc = chunk_illum(h, illum, c0, m);
+    const ChunkTables t = handle_chunk(h, illum, c0, m, scale, grad);
+    int rc = stage_chunk(h, t);
     if (rc != MQNPM_OK) return rc;
     int* it_chunk = h->last_iters.data() + 2 * c0;
     float2* det_out = y_out ? y_out + (size_t)c0 * M : w.rdet;
     const float2* ym = y_out ? nullptr : h->ymeas;
-    rc = chunk_forward(h, x, m, it_chunk, det_out, ym);
+    rc = chunk_forward(h, x, m, it_chunk, det_out, ym, h->ufield != nullptr, h->ufield != nullptr, t.segs);
+    if (h->ufield)
+      for (int b = 0; b < m; ++b) h->have_field[t.illum[b]] = (rc == MQNPM_ERR_NONFINITE) ? 0 : 1;
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
     if (rc != MQNPM_OK) worst = rc;
     if (!y_out && want_grad) {
-      rc = chunk_adjoint(h, x, m, it_chunk, scale, grad, c0 > 0);
+      rc = chunk_adjoint(h, x, m, it_chunk, 1);
       if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
       if (rc != MQNPM_OK) worst = rc;
     }
@@ -797,7 +870,9 @@ int grad_fields_impl(mqnpm_handle* h, const float* x, const int* illum, int nb, 
   if (!match) return grad_batch_impl(h, x, illum, nb, scale, grad, nullptr, nullptr, true, nullptr);
   h->fields_valid = false;   // the adjoint solve reuses the Krylov workspace
   std::vector<int> it(2 * nb, 0);
-  int rc = chunk_adjoint(h, x, nb, it.data(), scale, grad, false);
+  int rc = stage_chunk(h, handle_chunk(h, illum, 0, nb, scale, grad));
+  if (rc != MQNPM_OK) return rc;
+  rc = chunk_adjoint(h, x, nb, it.data(), 1);
   if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
   CK(cudaStreamSynchronize(h->stream));
   const int rt = check_tile_waits(h);

@@ -45,7 +45,8 @@ enum EpiKind {
 };
 
 struct ProArgs {
-  const float* x;        // contrast (N)
+  const float* x;        // contrast (N), shared by every slot
+  const float* const* xs;  // or per slot: contrast of slot b's volume (when non-null)
   const float2* q;       // input vector [b][N]
   float2* w;             // vector written by the prologue [b][N]
   const float2* r;       // [b][N]
@@ -63,4 +64,13 @@ struct EpiArgs {
   const float2* ymeas;   // [L][n*n]
   const int* illum;
   const float2* tab;     // incident-field axis tables [l][3][n]
+};
+
+// One run of consecutive slots whose gradients add into one output (the
+// illuminations of one volume): grad (+)= scale * sum_{b0 <= b < b1} Re(conj(u_b) z_b).
+struct GradSeg {
+  int b0, b1;
+  int accumulate;        // add to grad (1) or overwrite it (0)
+  float scale;
+  float* grad;
 };
