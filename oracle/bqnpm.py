@@ -50,8 +50,7 @@ class BQNPM:
         self.draws = draws
         self.newton_tol = newton_tol
         self.newton_maxit = newton_maxit
-        n = model.n
-        self.shape = (n, n, n)
+        self.shape = tuple(model.shape)
         self.k = 0
         self.xbar: List[Optional[np.ndarray]] = [None] * self.S
         self.gbar: List[Optional[np.ndarray]] = [None] * self.S

@@ -19,7 +19,7 @@ and in the CUDA library alike:
   grid of period 4 n h, which makes G v the continuous convolution of v's
   band-limited interpolant with g (spectrally accurate for smooth v);
 * LS: u = u_in + G (x * u); Born: u_sc = G (x * u_in);
-* detector: the scattered field u - u_in on the last z-slice (M = n^2), or,
+* detector: the scattered field u - u_in on the last z-slice (M = nx ny), or,
   with a remote detector, that slice carried a distance d further along z by
   the angular spectrum with a pupil of numerical aperture na (relative to the
   medium): D = F^-1 diag(H) F with H = exp(j k_z d) 1[kx^2 + ky^2 <= (na k_b)^2],
@@ -53,24 +53,36 @@ def self_term(kb: float, h: float = 1.0) -> complex:
     return (np.exp(1j * kb * a) * (1.0 - 1j * kb * a) - 1.0) / kb ** 2
 
 
-def green_kernel(n: int, kb: float, h: float = 1.0) -> np.ndarray:
-    """k_b^2 w_D laid out on the periodic grid of edge P = 2n.
+def grid_shape(n) -> Tuple[int, int, int]:
+    """(nz, ny, nx) of a grid given as one edge n or as a (nz, ny, nx) triple."""
+    if np.ndim(n) == 0:
+        return (int(n),) * 3
+    nz, ny, nx = (int(v) for v in n)
+    return nz, ny, nx
 
-    Index i along an axis carries the offset i (i < n) or i - P (i > n); the
-    index i = n (offset -n, never reached by two voxels of the domain) is 0.
-    """
-    P = 2 * n
-    idx = np.arange(P)
-    off = np.where(idx < n, idx, idx - P).astype(np.float64)
-    dz, dy, dx = np.meshgrid(off, off, off, indexing="ij")
+
+def _wrapped_offsets(nd: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Offsets along one axis of the periodic grid of length P = 2 nd: index i
+    carries i (i < nd) or i - P (i > nd); index nd (offset -nd, never reached
+    by two voxels of the domain) is marked unused."""
+    idx = np.arange(2 * nd)
+    return np.where(idx < nd, idx, idx - 2 * nd), idx == nd
+
+
+def green_kernel(n, kb: float, h: float = 1.0) -> np.ndarray:
+    """k_b^2 w_D laid out on the periodic grid of edges P_d = 2 n_d (n: one
+    edge or (nz, ny, nx)); every offset of the domain appears once, the unused
+    index n_d of each axis is 0."""
+    nz, ny, nx = grid_shape(n)
+    (oz, uz), (oy, uy), (ox, ux) = (_wrapped_offsets(v) for v in (nz, ny, nx))
+    dz, dy, dx = np.meshgrid(oz.astype(np.float64), oy.astype(np.float64), ox.astype(np.float64), indexing="ij")
     r = h * np.sqrt(dx ** 2 + dy ** 2 + dz ** 2)
     with np.errstate(divide="ignore", invalid="ignore"):
         w = h ** 3 * np.exp(1j * kb * r) / (4.0 * math.pi * r)
     w[0, 0, 0] = self_term(kb, h)
-    unused = idx == n
-    w[unused, :, :] = 0.0
-    w[:, unused, :] = 0.0
-    w[:, :, unused] = 0.0
+    w[uz, :, :] = 0.0
+    w[:, uy, :] = 0.0
+    w[:, :, ux] = 0.0
     return kb ** 2 * w
 
 
@@ -99,36 +111,49 @@ def truncated_green_ft(s, kb: float, R: float) -> np.ndarray:
     return np.where(s == 0, g0, val)
 
 
-def truncated_green_kernel(n: int, kb: float, h: float = 1.0) -> np.ndarray:
-    """k_b^2 w_D on the P-periodic grid (P = 2n) for the truncated kernel.
+def truncated_periods(n, h: float = 1.0) -> Tuple[float, Tuple[int, int, int]]:
+    """Truncation radius R (the diagonal of the domain, h sqrt(nz^2 + ny^2 + nx^2),
+    which covers every distance between two voxels) and the sample counts T_d
+    of the period T_d h along each axis: 4 n_d, raised to the next even count
+    >= n_d + R/h where the domain is elongated, so that T_d h >= n_d h + R."""
+    shape = grid_shape(n)
+    R = h * math.sqrt(sum(v * v for v in shape))
+    T = tuple(max(4 * v, 2 * math.ceil((v + R / h) / 2.0)) for v in shape)
+    return R, T
+
+
+def truncated_green_kernel(n, kb: float, h: float = 1.0) -> np.ndarray:
+    """k_b^2 w_D on the periodic grid of edges P_d = 2 n_d for the truncated kernel.
 
     Voxel sums with this kernel are the continuous convolution of the band-
     limited interpolant of v with g_R: the transform of g_R is sampled on the
-    frequency grid of a period T = 4 n h (m in [-2n, 2n)^3, s_m = 2 pi m / T),
-    so  w_D = (h^3 / T^3) sum_m g_R^(|s_m|) exp(j s_m . D h)  (an inverse DFT of
-    length 4n per axis).  R = sqrt(3) n h covers every distance between two
-    voxels of the domain, and T >= n h + R keeps the periodic copies of g_R
-    out of the offsets (-n, n)^3 the domain uses, which are laid out on the P
-    grid as in green_kernel (index n unused, 0)."""
-    T = 4 * n
-    R = math.sqrt(3.0) * n * h
-    f = 2.0 * math.pi * np.fft.fftfreq(T, d=h)
-    s = np.sqrt(f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2)
+    frequency grid of periods T_d h (s_m = 2 pi m_d / (T_d h), m_d in
+    [-T_d/2, T_d/2)), so  w_D = (h^3 / prod_d T_d h) sum_m g_R^(|s_m|)
+    exp(j s_m . D h)  (an inverse DFT of length T_d per axis).  R covers every
+    distance between two voxels of the domain and T_d h >= n_d h + R keeps the
+    periodic copies of g_R out of the offsets the domain uses, which are laid
+    out on the P grid as in green_kernel (index n_d unused, 0).  A cubic grid
+    has T = 4n and R = sqrt(3) n h."""
+    shape = grid_shape(n)
+    R, T = truncated_periods(shape, h)
+    fz, fy, fx = (2.0 * math.pi * np.fft.fftfreq(t, d=h) for t in T)
+    s = np.sqrt(fz[:, None, None] ** 2 + fy[None, :, None] ** 2 + fx[None, None, :] ** 2)
     w = sfft.ifftn(truncated_green_ft(s, kb, R), workers=FFT_WORKERS)
     del s
-    P = 2 * n
-    idx = np.arange(P)
-    sel = np.where(idx < n, idx, idx - P) % T
-    wp = w[np.ix_(sel, sel, sel)].copy()
-    unused = idx == n
-    wp[unused, :, :] = 0.0
-    wp[:, unused, :] = 0.0
-    wp[:, :, unused] = 0.0
+    sel, unused = [], []
+    for v, t in zip(shape, T):
+        off, un = _wrapped_offsets(v)
+        sel.append(off % t)
+        unused.append(un)
+    wp = w[np.ix_(*sel)].copy()
+    wp[unused[0], :, :] = 0.0
+    wp[:, unused[1], :] = 0.0
+    wp[:, :, unused[2]] = 0.0
     return kb ** 2 * wp
 
 
-def green_hat(n: int, kb: float, h: float = 1.0, kernel: str = "sampled") -> np.ndarray:
-    """K_hat = DFT_P of the periodic kernel (P^3 complex128): the sampled
+def green_hat(n, kb: float, h: float = 1.0, kernel: str = "sampled") -> np.ndarray:
+    """K_hat = DFT_P of the periodic kernel (2nz x 2ny x 2nx complex128): the sampled
     Green's function with the sphere self term ("sampled") or the truncated
     kernel ("truncated")."""
     if kernel == "truncated":
@@ -141,38 +166,39 @@ def green_hat(n: int, kb: float, h: float = 1.0, kernel: str = "sampled") -> np.
 def green_apply(v: np.ndarray, khat: np.ndarray, adjoint: bool = False) -> np.ndarray:
     """G v (or G^H v) by zero padding to P = 2n and circular convolution.
 
-    Because the periodic kernel holds every offset in (-n, n)^3 exactly once,
+    Because the periodic kernel holds every offset of the domain exactly once,
     the circular convolution restricted to the domain equals the aperiodic sum.
     G is complex symmetric, so G^H uses conj(K_hat).
     """
-    n = v.shape[0]
-    P = 2 * n
-    pad = np.zeros((P, P, P), dtype=np.complex128)
-    pad[:n, :n, :n] = v
+    nz, ny, nx = v.shape
+    pad = np.zeros((2 * nz, 2 * ny, 2 * nx), dtype=np.complex128)
+    pad[:nz, :ny, :nx] = v
     k = np.conj(khat) if adjoint else khat
     out = sfft.ifftn(k * sfft.fftn(pad, workers=FFT_WORKERS), workers=FFT_WORKERS)
-    return out[:n, :n, :n]
+    return out[:nz, :ny, :nx]
 
 
-def transfer_function(n: int, kb: float, h: float, distance: float, na: float) -> np.ndarray:
+def transfer_function(n, kb: float, h: float, distance: float, na: float) -> np.ndarray:
     """H[ky, kx] of the angular-spectrum propagation over `distance` with the
     pupil kx^2 + ky^2 <= (na kb)^2 (remote-detector reading of Section 6)."""
-    f = 2.0 * math.pi * np.fft.fftfreq(n, d=h)
-    KY, KX = np.meshgrid(f, f, indexing="ij")
+    _, ny, nx = grid_shape(n)
+    KY, KX = np.meshgrid(2.0 * math.pi * np.fft.fftfreq(ny, d=h), 2.0 * math.pi * np.fft.fftfreq(nx, d=h),
+                         indexing="ij")
     k2 = KX * KX + KY * KY
     kz = np.sqrt((kb * kb - k2).astype(np.complex128))   # principal root: Im >= 0
     return np.where(k2 <= (na * kb) ** 2, np.exp(1j * kz * distance), 0.0)
 
 
 def propagate(field: np.ndarray, H: np.ndarray, adjoint: bool = False) -> np.ndarray:
-    """D f = F^-1 (H F f) on an n x n slice; D^H uses conj(H)."""
+    """D f = F^-1 (H F f) on an ny x nx slice; D^H uses conj(H)."""
     return sfft.ifft2((np.conj(H) if adjoint else H) * sfft.fft2(field, workers=FFT_WORKERS), workers=FFT_WORKERS)
 
 
-def incident_field(n: int, kdir: Sequence[float], kb: float, h: float = 1.0) -> np.ndarray:
-    """u_in(r) = exp(j kb <kdir, r>), r = (idx - n/2) h, shape (n, n, n) [z, y, x]."""
-    c = (np.arange(n) - n / 2.0) * h
-    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+def incident_field(n, kdir: Sequence[float], kb: float, h: float = 1.0) -> np.ndarray:
+    """u_in(r) = exp(j kb <kdir, r>), r_d = (idx_d - n_d/2) h, shape (nz, ny, nx) [z, y, x]."""
+    nz, ny, nx = grid_shape(n)
+    Z, Y, X = np.meshgrid((np.arange(nz) - nz / 2.0) * h, (np.arange(ny) - ny / 2.0) * h,
+                          (np.arange(nx) - nx / 2.0) * h, indexing="ij")
     return np.exp(1j * kb * (kdir[0] * X + kdir[1] * Y + kdir[2] * Z))
 
 
@@ -217,11 +243,12 @@ def bicgstab(apply_a: Callable[[np.ndarray], np.ndarray], b: np.ndarray,
 class Model:
     """One configuration of the forward model (grid, wavenumber, directions)."""
 
-    def __init__(self, n: int, kdirs: np.ndarray, model: str = "ls",
+    def __init__(self, n, kdirs: np.ndarray, model: str = "ls",
                  kb: float | None = None, h: float = 1.0,
                  tol: float = 1e-12, maxit: int = 2000,
                  det_distance: float = 0.0, det_na: float = 0.0, kernel: str = "sampled"):
-        self.n = n
+        self.shape = grid_shape(n)          # (nz, ny, nx)
+        self.n = n if np.ndim(n) == 0 else self.shape
         self.h = h
         self.kb = kb_default(h) if kb is None else kb
         self.kdirs = np.asarray(kdirs, dtype=np.float64)
@@ -240,7 +267,7 @@ class Model:
         return green_apply(v, self.khat, adjoint=True)
 
     def u_in(self, l: int) -> np.ndarray:
-        return incident_field(self.n, self.kdirs[l], self.kb, self.h)
+        return incident_field(self.shape, self.kdirs[l], self.kb, self.h)
 
     def total_field(self, x: np.ndarray, l: int) -> Tuple[np.ndarray, int]:
         """u solving u = u_in + G(x u) (LS) or u = u_in (Born)."""
@@ -261,10 +288,10 @@ class Model:
     def lift(self, r: np.ndarray) -> np.ndarray:
         """S^T (after D^H for a remote detector): embed a detector vector into
         the last z-slice of a zero volume."""
-        r2 = r.reshape(self.n, self.n)
+        r2 = r.reshape(self.shape[1], self.shape[2])
         if self.H is not None:
             r2 = propagate(r2, self.H, adjoint=True)
-        out = np.zeros((self.n,) * 3, dtype=np.complex128)
+        out = np.zeros(self.shape, dtype=np.complex128)
         out[-1] = r2
         return out
 
@@ -333,7 +360,7 @@ def simulate(model: Model, x_true: np.ndarray, noise: np.ndarray, snr_db: float)
     paper's noisy complex measurements).
     """
     L = model.kdirs.shape[0]
-    M = model.n * model.n
+    M = model.shape[1] * model.shape[2]
     ys = np.zeros((L, M), dtype=np.complex128)
     for l in range(L):
         clean = model.forward(x_true, l)

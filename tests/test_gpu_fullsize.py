@@ -298,3 +298,50 @@ def test_wprox_128_rank8_matches_oracle(kind):
                              P0=P0.astype(np.float32).astype(np.float64), newton_tol=1e-6)
     assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo), np.linalg.norm(xg - xo) / np.linalg.norm(xo)
     assert np.linalg.norm(Pg - Po) <= 1e-4 * np.linalg.norm(Po)
+
+
+def test_ls192_gradient_matches_oracle():
+    """ls192 (P = 384, the largest transform) in the bench's launch
+    configuration (batch-16 workspace): one illumination's gradient and loss
+    against the FP64 oracle at the same x, measurements zero (no input from
+    the GPU path)."""
+    w = synth.workload("ls192")
+    h = handle(w, "ls", 1e-6, w.batch)
+    x0 = (0.5 * synth.phantom(w)).astype(np.float32)
+    h.set_measurements(torch.zeros(w.L * w.n * w.n, dtype=torch.complex64, device=DEV))
+    illum = [int(synth.subsets(w)[0][0])]
+    g, f, its = h.grad_batch(torch.from_numpy(x0).to(DEV).reshape(-1), illum, 1.0)
+    g = g.cpu().numpy().astype(np.float64).reshape(w.n, w.n, w.n)
+    h.close()
+    om = physics.Model(w.n, synth.illumination_dirs(w), "ls", tol=1e-9)
+    fo, go = om.batch_loss_grad(x0.astype(np.float64), illum, np.zeros((w.L, w.n * w.n), np.complex128), 1.0)
+    assert its[0][0] > 0 and its[0][1] > 0
+    assert abs(f - fo) <= 1e-5 * abs(fo), (f, fo)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
+def test_ls192_recomputed_fields_equal_stored_fields():
+    """The recompute path of the autograd split at the large configuration: a
+    15-illumination subset on a 4-slot workspace cannot keep its forward
+    fields between the loss and the gradient call, so the gradient call
+    recomputes them chunk by chunk; it equals the gradient of a 16-slot
+    workspace that holds the whole subset (summation regrouped: 1e-5)."""
+    w = synth.workload("ls192")
+    xt = phantom(w)
+    illum = [int(i) for i in synth.subsets(w)[0]]
+    big = handle(w, "ls", w.krylov_tol, 16)
+    measure(big, w, xt, illum)
+    x0 = 0.5 * xt
+    gb, fb, _ = big.grad_batch(x0, illum, w.S / w.L)
+    gb = gb.clone()
+    y = torch.zeros((w.L, w.n * w.n), dtype=torch.complex64, device=DEV)
+    y[torch.tensor(illum, device=DEV)] = big.forward(xt, illum)[0]
+    big.close()
+    small = handle(w, "ls", w.krylov_tol, 4)
+    small.set_measurements(y.reshape(-1))
+    fs, _ = small.loss_batch(x0, illum, w.S / w.L)
+    gs, reused = small.grad_fields(x0, illum, w.S / w.L)
+    assert not reused
+    assert abs(fs - fb) <= 1e-6 * abs(fb)
+    assert float((gs.double() - gb.double()).norm() / gb.double().norm()) < 1e-5
+    small.close()

@@ -78,7 +78,8 @@ def test_group_rejects_mismatched_members():
     with pytest.raises(binding.MQNPMError) as err:
         binding.Group([a, b], max_slots=4)
     assert err.value.code == 1                       # different grids
-    c = binding.MQNPM(16, synth.illumination_dirs(w), [0, 1, 0, 1], [1.0, 1.0], model="born", max_batch=1)
+    c = binding.MQNPM(16, synth.illumination_dirs(w), [0, 1, 0, 1], [1.0, 1.0], model="born", max_batch=1,
+                      krylov_tol=1e-6, tile=0)
     with pytest.raises(binding.MQNPMError) as err:
         binding.Group([a, c], max_slots=4)
     assert err.value.code == 7                       # first-Born members are not grouped

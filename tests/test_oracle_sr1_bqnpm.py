@@ -132,6 +132,7 @@ class _FixedGradient:
 
     def __init__(self, n, g):
         self.n = n
+        self.shape = (n, n, n)
         self.g = g
 
     def batch_loss_grad(self, x, subset, ys, scale):
