@@ -51,14 +51,27 @@ class Workload:
     voxel_m: float = 0.0        # physical units: voxel edge (m); 0 = the lambda/4 voxel convention
     wavelength_m: float = 0.0   # vacuum wavelength (m)
     eta_m: float = 0.0          # refractive index of the medium
+    grid: Tuple[int, ...] = ()  # (nz, ny, nx) of a box-shaped grid; () = the cube of edge n
 
     @property
     def S(self) -> int:
         return int(math.ceil(self.L / self.batch))
 
     @property
+    def dims(self) -> Tuple[int, int, int]:
+        """(nz, ny, nx) of the grid."""
+        return tuple(self.grid) if self.grid else (self.n, self.n, self.n)
+
+    @property
     def N(self) -> int:
-        return self.n ** 3
+        nz, ny, nx = self.dims
+        return nz * ny * nx
+
+    @property
+    def M(self) -> int:
+        """Detector values: the last z-slice, ny x nx."""
+        _, ny, nx = self.dims
+        return ny * nx
 
     @property
     def P(self) -> int:
@@ -149,7 +162,7 @@ def _random_rotation(rng: np.random.Generator) -> np.ndarray:
 
 
 def phantom(w: Workload) -> np.ndarray:
-    """Ground-truth contrast x_true, float64 array of shape (n, n, n) = (z, y, x).
+    """Ground-truth contrast x_true, float64 array of shape (nz, ny, nx) = (z, y, x).
 
     Objects are spheres or randomly rotated ellipsoids with contrast drawn
     uniformly in [0, contrast_max]; overlaps take the maximum.  Every object's
@@ -158,10 +171,11 @@ def phantom(w: Workload) -> np.ndarray:
     background is tapered to zero inside the same margin.
     """
     rng = _rng(w, 0)
-    n = w.n
-    c = np.arange(n, dtype=np.float64)
-    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
-    x = np.zeros((n, n, n), dtype=np.float64)
+    nz, ny, nx = w.dims
+    ext = np.array([nx, ny, nz], dtype=np.float64)           # extents in (x, y, z) order
+    Z, Y, X = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    x = np.zeros((nz, ny, nx), dtype=np.float64)
     lo_s, hi_s = w.size_range
     for _ in range(w.n_objects):
         if w.shape == "sphere":
@@ -170,19 +184,19 @@ def phantom(w: Workload) -> np.ndarray:
         else:
             axes = rng.uniform(lo_s, hi_s, size=3)
             rot = _random_rotation(rng)
-        room = ((n - 1) - 2 * w.margin) / 2.0
+        room = float(((ext - 1) - 2 * w.margin).min()) / 2.0
         if room <= 0:
             raise ValueError("grid too small for the margin")
         if axes.max() > room:                             # tiny grids: shrink to fit
             axes = axes * (room / axes.max())
         rmax = float(axes.max())
         lo_c = w.margin + rmax
-        hi_c = (n - 1) - w.margin - rmax
+        hi_c = (ext - 1) - w.margin - rmax
         centre = rng.uniform(lo_c, hi_c, size=3)          # (cx, cy, cz)
         value = rng.uniform(0.0, w.contrast_max)
         # only the bounding box of the bounding sphere can be inside
         lo = np.maximum(np.floor(centre - rmax).astype(int), 0)
-        hi = np.minimum(np.ceil(centre + rmax).astype(int) + 1, n)
+        hi = np.minimum(np.ceil(centre + rmax).astype(int) + 1, ext.astype(int))
         box = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         d = np.stack([X[box] - centre[0], Y[box] - centre[1], Z[box] - centre[2]], axis=-1)
         local = d @ rot                                   # coordinates in the body frame
@@ -190,12 +204,16 @@ def phantom(w: Workload) -> np.ndarray:
         x[box] = np.where(inside, np.maximum(x[box], value), x[box])
     amp, sigma = w.background
     if amp > 0.0:
-        mid = (n - 1) / 2.0
-        g = amp * np.exp(-((X - mid) ** 2 + (Y - mid) ** 2 + (Z - mid) ** 2) / (2.0 * sigma ** 2))
-        inner = np.ones(n, dtype=bool)
-        inner[: w.margin] = False
-        inner[n - w.margin:] = False
-        mask = inner[:, None, None] & inner[None, :, None] & inner[None, None, :]
+        mx, my, mz = (ext - 1) / 2.0
+        g = amp * np.exp(-((X - mx) ** 2 + (Y - my) ** 2 + (Z - mz) ** 2) / (2.0 * sigma ** 2))
+
+        def inner(m):
+            v = np.ones(m, dtype=bool)
+            v[: w.margin] = False
+            v[m - w.margin:] = False
+            return v
+
+        mask = inner(nz)[:, None, None] & inner(ny)[None, :, None] & inner(nx)[None, None, :]
         x = np.maximum(x, np.where(mask, g, 0.0))
     return x
 
@@ -219,9 +237,9 @@ def subsets(w: Workload) -> List[np.ndarray]:
 
 
 def noise_draws(w: Workload) -> np.ndarray:
-    """Unit-variance circular complex Gaussian draws, shape (L, n*n)."""
+    """Unit-variance circular complex Gaussian draws, shape (L, ny*nx)."""
     rng = _rng(w, 1)
-    M = w.n * w.n
+    M = w.M
     re = rng.standard_normal((w.L, M))
     im = rng.standard_normal((w.L, M))
     return (re + 1j * im) / math.sqrt(2.0)
@@ -233,8 +251,8 @@ def strategy2_draws(w: Workload, count: int) -> np.ndarray:
 
 
 def power_start(w: Workload) -> np.ndarray:
-    """Start vector of the power iteration that estimates alpha_s, shape (n,n,n)."""
-    return _rng(w, 3).standard_normal((w.n, w.n, w.n))
+    """Start vector of the power iteration that estimates alpha_s, shape (nz, ny, nx)."""
+    return _rng(w, 3).standard_normal(w.dims)
 
 
 def uneven_requests(seed: int = 4000, count: int = 16) -> List[Workload]:

@@ -71,7 +71,8 @@ def _config(**kw):
     so = np.ascontiguousarray(np.arange(L) % max(S, 1), dtype=np.int32)
     al = np.ascontiguousarray(np.ones(S), dtype=np.float64)
     cfg = binding.Config()
-    cfg.n, cfg.h, cfg.kb, cfg.model, cfg.L = 16, 1.0, 1.5707963, 1, L
+    cfg.nx = cfg.ny = cfg.nz = 16
+    cfg.h, cfg.kb, cfg.model, cfg.L = 1.0, 1.5707963, 1, L
     cfg.kdir = kd.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     cfg.S = S
     cfg.subset_of = so.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
@@ -87,7 +88,7 @@ def _config(**kw):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("n", 3), ("L", 0), ("S", 0), ("S", 17), ("max_batch", 0), ("max_batch", 65), ("gamma", 0.0),
+    ("nx", 3), ("nz", 2), ("L", 0), ("S", 0), ("S", 17), ("max_batch", 0), ("max_batch", 65), ("gamma", 0.0),
     ("gamma", 1.5), ("h", 0.0), ("kb", -1.0), ("lam", -1.0), ("box_lo", 1.0), ("step", 0.0),
     ("krylov_tol", 0.0), ("krylov_maxit", 0), ("dual_iters", -1), ("model", 7), ("tv", 5),
     ("strategy", 3), ("tile", -2), ("tile", 16), ("det_na", -0.5), ("det_na", float("inf")),
@@ -129,7 +130,7 @@ def test_create_rejects_a_nonfinite_spectrum_and_unsupported_grids():
     cfg.green_hat = gh.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     out = ctypes.c_void_p()
     assert lib.mqnpm_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
-    cfg2, keep2 = _config(n=20)                 # P = 40: no compiled transform plan
+    cfg2, keep2 = _config(ny=20)                # P = 40: no compiled transform plan
     assert lib.mqnpm_create(ctypes.byref(cfg2), ctypes.byref(out)) == 7   # MQNPM_ERR_UNSUPPORTED
     assert not out.value
     del keep, keep2
