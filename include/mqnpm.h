@@ -10,8 +10,9 @@
  *     F_s = (S/L) sum_{l in S_s} f_l  over S non-overlapping subsets.
  *
  * Conventions shared by every call
- *   - A volume is n*n*n voxels, indexed [z][y][x] with x fastest; N = n^3.
- *     Detector vectors hold the last z-slice, [y][x], M = n^2 values.
+ *   - A volume is nx*ny*nz voxels, indexed [z][y][x] with x fastest;
+ *     N = nx ny nz.  Detector vectors hold the last z-slice, [y][x],
+ *     M = nx ny values.
  *   - Real vectors are float32; complex vectors are interleaved (re, im)
  *     float32 pairs (the memory layout of torch.complex64).
  *   - Every pointer argument documented as "device" is a CUDA device pointer on
@@ -53,8 +54,10 @@ enum { MQNPM_TV_ISO = 0, MQNPM_TV_ANISO = 1 };
  * SAMPLED  w_D = h^3 g(|D| h) with the exact integral over the equal-volume
  *          sphere at D = 0;
  * TRUNCATED the truncated kernel of Vico, Greengard and Ferrando (2016): the
- *          transform of g restricted to r <= sqrt(3) n h, sampled with period
- *          4 n h, which makes G v the continuous convolution of the band-limited
+ *          transform of g restricted to r <= h sqrt(nx^2 + ny^2 + nz^2) (the
+ *          domain's diagonal), sampled with periods T_d h along each axis,
+ *          T_d = 4 n_d (raised to the next even count >= n_d + R/h for an
+ *          elongated domain), which makes G v the continuous convolution of the band-limited
  *          interpolant of v (spectrally accurate for smooth v). */
 enum { MQNPM_KERNEL_SAMPLED = 0, MQNPM_KERNEL_TRUNCATED = 1 };
 
@@ -66,8 +69,10 @@ enum { MQNPM_KERNEL_SAMPLED = 0, MQNPM_KERNEL_TRUNCATED = 1 };
 
 typedef struct mqnpm_config {
   /* --- forward model (Section 6; discretisation is the library's stated reading) */
-  int n;                   /* grid edge; transform length P = 2n must be one of
-                              16,24,32,48,64,96,128,192,256,320,384                 */
+  int nx, ny, nz;          /* grid edges (x fastest); each transform length 2 n_d
+                              must be one of 16,24,32,48,64,96,128,192,256,320,384
+                              (else UNSUPPORTED), nx a multiple of 4 for the
+                              proximal mapping                                      */
   double h;                /* voxel size (length unit)                              */
   double kb;               /* background wavenumber 2*pi/lambda_b (per unit length) */
   int model;               /* MQNPM_MODEL_LS (Lippmann-Schwinger) or _BORN          */
@@ -109,14 +114,15 @@ typedef struct mqnpm_config {
   int direct_launches;     /* 0: a BiCGSTAB iteration (14 kernels) is captured
                               once per batch shape as a CUDA graph and replayed;
                               1: its kernels are launched one by one          */
-  const float* green_hat;  /* host, (n+1)^3 complex64 [fz][fy][fx] or NULL: the
-                              first octant of DFT_P of the P-periodic Green's
+  const float* green_hat;  /* host, (nz+1)(ny+1)(nx+1) complex64 [fz][fy][fx] or
+                              NULL: the first octant of the DFT of the periodic
+                              (periods 2 nx, 2 ny, 2 nz) Green's
                               kernel (even in every axis; any discretisation of
                               G, e.g. a truncated kernel), used instead of the
                               library's own (Section 6 reading)              */
   int tile;                /* launch shapes of the Green's passes: -1 picks the
                               fastest of 0..15 by timing at create (cached per
-                              device, n and batch slots); 0..15 fixes them: bits
+                              device, grid and batch slots); 0..15 fixes them: bits
                               0, 1, 2 select the alternative shape (lines or
                               columns per CTA, threads per line or column) of
                               the x, y and z passes, bit 3 two exchange buffers
@@ -160,10 +166,11 @@ typedef struct mqnpm_step_info {
 } mqnpm_step_info;
 
 /* Create a handle: validates cfg, builds the Green's kernel spectrum (or
- * scales cfg->green_hat by 1/P^3 and rounds it once) and the incident-field
- * tables, and allocates the workspace for max_batch illuminations.  Host
- * arrays in cfg are copied.  Errors: INVALID_ARG (also a non-finite
- * green_hat value), UNSUPPORTED (n), BUDGET, CUDA.  On error *out is NULL. */
+ * scales cfg->green_hat by 1/(8 nx ny nz) and rounds it once) and the
+ * incident-field tables, and allocates the workspace for max_batch
+ * illuminations.  Host arrays in cfg are copied.  Errors: INVALID_ARG (also
+ * a non-finite green_hat value), UNSUPPORTED (grid), BUDGET, CUDA.  On error
+ * *out is NULL. */
 int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out);
 
 /* Release the workspace.  NULL is accepted. */
@@ -267,7 +274,7 @@ int mqnpm_step_with_gradient(mqnpm_handle* h, float* x, const float* g, double l
 
 /* Shared launches for several reconstructions of one grid (the request loop of
  * the serving configuration; no counterpart in the paper beyond Algorithm 4.1
- * run for each member).  A group holds count member handles with equal n, h,
+ * run for each member).  A group holds count member handles with equal grid, h,
  * kb, green_kernel, tile, device, krylov_tol, krylov_maxit and
  * direct_launches, the LS model and the slice detector (else INVALID_ARG or
  * UNSUPPORTED); members keep their own L, subsets, measurements, metric
@@ -315,7 +322,7 @@ int mqnpm_diagnostics(mqnpm_handle* h, const float* x_prev, const float* x_cur, 
  * u_s, dual field and, with warm_start, the stored forward fields).  With
  * buf == NULL, *size receives the byte count; else buf (host, *size bytes)
  * receives the state.  load restores it exactly; it rejects a state written
- * by a handle of another n, S, L or warm_start. */
+ * by a handle of another grid, S, L or warm_start. */
 int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size);
 int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size);
 
@@ -370,7 +377,7 @@ int mqnpm_profile_end(mqnpm_handle* h, double* pass_ms, long long* slot_launches
  * device whose memory is already handed out, and allocator hooks that must not
  * re-enter the allocator.  It calls no cudaMalloc/cudaFree and no allocating
  * library routine; its scratch is one file-scope device array of
- * mqnpm_noalloc_scratch_bytes() bytes (3,012,352 B, 2.9 MiB), present on every GPU
+ * mqnpm_noalloc_scratch_bytes() bytes (3,013,376 B, 2.9 MiB), present on every GPU
  * that loads the library until the process exits.
  *   n: grid edge, at most 32, with 2n a compiled transform length
  *      (n in {8, 12, 16, 24, 32}); larger or unsupported n returns

@@ -26,7 +26,7 @@ MODEL = {"born": 0, "ls": 1}
 TV = {"iso": 0, "aniso": 1}
 KERNEL = {"sampled": 0, "truncated": 1}
 MAX_S = 16
-SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 192)
+SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 192)   # every edge of a grid takes one of these
 
 
 class MQNPMError(RuntimeError):
@@ -41,7 +41,7 @@ class NotConverged(MQNPMError):
 
 class Config(ctypes.Structure):
     _fields_ = [
-        ("n", ctypes.c_int), ("h", ctypes.c_double), ("kb", ctypes.c_double), ("model", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double), ("kb", ctypes.c_double), ("model", ctypes.c_int),
         ("L", ctypes.c_int), ("kdir", ctypes.POINTER(ctypes.c_double)),
         ("S", ctypes.c_int), ("subset_of", ctypes.POINTER(ctypes.c_int)),
         ("alpha", ctypes.POINTER(ctypes.c_double)), ("step", ctypes.c_double), ("strategy", ctypes.c_int),
@@ -181,9 +181,10 @@ def green_apply_noalloc(n: int, h: float, kb: float, v: torch.Tensor, out: torch
 
 
 class MQNPM:
-    """One reconstruction problem on one GPU (a handle of libmqnpm)."""
+    """One reconstruction problem on one GPU (a handle of libmqnpm).  n is the
+    grid edge of a cubic grid or the (nz, ny, nx) edges of a box."""
 
-    def __init__(self, n: int, kdir, subset_of, alpha, *, model: str = "ls", h: float = 1.0,
+    def __init__(self, n, kdir, subset_of, alpha, *, model: str = "ls", h: float = 1.0,
                  kb: float = math.pi / 2, tv: str = "iso", lam: float = 1e-3, box=(0.0, 1.0),
                  step: float = 1.0, strategy: int = 1, draws: Optional[Sequence[int]] = None,
                  gamma: float = 0.8, tau_max: float = 0.0, krylov_tol: float = 1e-6, krylov_maxit: int = 500,
@@ -193,9 +194,17 @@ class MQNPM:
                  det_distance: float = 0.0, det_na: float = 0.0, guard_bytes: int = 0,
                  barrier_wait_cycles: int = 0, green_kernel: str = "sampled"):
         self.lib = load()
-        self.n = int(n)
-        self.N = self.n ** 3
-        self.M = self.n ** 2
+        if np.ndim(n) == 0:
+            self.shape = (int(n),) * 3
+            self.n = int(n)
+        else:
+            self.shape = tuple(int(v) for v in n)
+            if len(self.shape) != 3:
+                raise ValueError("n must be an edge or (nz, ny, nx)")
+            self.n = self.shape
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self.M = nx * ny
         self.device = int(device)
         kd = np.ascontiguousarray(np.asarray(kdir, dtype=np.float64).reshape(-1, 3))
         so = np.ascontiguousarray(np.asarray(subset_of, dtype=np.int32))
@@ -205,7 +214,7 @@ class MQNPM:
         self.S = al.shape[0]
         self._keep = (kd, so, al, dr)
         cfg = Config()
-        cfg.n = self.n
+        cfg.nz, cfg.ny, cfg.nx = self.shape
         cfg.h = h
         cfg.kb = kb
         cfg.model = MODEL[model]
@@ -242,8 +251,8 @@ class MQNPM:
         cfg.green_kernel = KERNEL[green_kernel]
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
-            if gh.size != (self.n + 1) ** 3:
-                raise ValueError("green_hat must hold (n+1)^3 complex values")
+            if gh.size != (nx + 1) * (ny + 1) * (nz + 1):
+                raise ValueError("green_hat must hold (nz+1)(ny+1)(nx+1) complex values")
             self._keep = self._keep + (gh,)
             cfg.green_hat = gh.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         cfg.device = self.device

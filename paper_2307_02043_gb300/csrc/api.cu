@@ -171,7 +171,7 @@ int mqnpm_debug_poke_guard(mqnpm_handle* h, int band) {
 int mqnpm_tile_info(const mqnpm_handle* h, int* tile, int* shape, double* ms) {
   if (!h || !tile || !shape) return MQNPM_ERR_INVALID_ARG;
   *tile = h->tile;
-  green_shape(h->n, h->tile, shape);
+  green_shape(h->nx, h->ny, h->nz, h->tile, shape);
   if (ms)
     for (int i = 0; i < MQ_TILES; ++i) ms[i] = h->tune_ms[i];
   return MQNPM_OK;
@@ -230,7 +230,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
     return code;
   };
   // ---- validation
-  if (cfg->n < 4 || cfg->L < 1 || cfg->S < 1 || cfg->S > MQNPM_MAX_S || cfg->S > cfg->L || !cfg->kdir ||
+  if (cfg->nx < 4 || cfg->ny < 4 || cfg->nz < 4 || cfg->L < 1 || cfg->S < 1 || cfg->S > MQNPM_MAX_S || cfg->S > cfg->L || !cfg->kdir ||
       !cfg->subset_of || !cfg->alpha || !(cfg->h > 0) || !(cfg->kb > 0) || cfg->max_batch < 1 ||
       cfg->max_batch > MQNPM_MAX_BATCH ||
       !(cfg->box_lo <= cfg->box_hi) || !(cfg->lambda >= 0) || !(cfg->step > 0) || cfg->dual_iters < 0 ||
@@ -244,12 +244,12 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
     delete h;
     return MQNPM_ERR_INVALID_ARG;
   }
-  if (!green_supported(cfg->n)) {
+  if (!green_supported(cfg->nx) || !green_supported(cfg->ny) || !green_supported(cfg->nz)) {
     delete h;
     return MQNPM_ERR_UNSUPPORTED;
   }
   if (cfg->green_hat) {
-    const size_t m = (size_t)cfg->n + 1, cnt = 2 * m * m * m;
+    const size_t cnt = 2 * ((size_t)cfg->nx + 1) * ((size_t)cfg->ny + 1) * ((size_t)cfg->nz + 1);
     for (size_t i = 0; i < cnt; ++i)
       if (!std::isfinite(cfg->green_hat[i])) {
         fprintf(stderr, "mqnpm_create: green_hat holds a non-finite value\n");
@@ -257,10 +257,11 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
         return MQNPM_ERR_INVALID_ARG;
       }
   }
-  h->n = cfg->n;
-  h->P = 2 * cfg->n;
-  h->N = (size_t)cfg->n * cfg->n * cfg->n;
-  h->M = cfg->n * cfg->n;
+  h->nx = cfg->nx;
+  h->ny = cfg->ny;
+  h->nz = cfg->nz;
+  h->N = (size_t)cfg->nx * cfg->ny * cfg->nz;
+  h->M = cfg->nx * cfg->ny;
   h->model = cfg->model;
   h->L = cfg->L;
   h->S = cfg->S;
@@ -313,18 +314,29 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (nsm <= 0) nsm = 1;
   const size_t N = h->N, M = h->M, B = h->max_batch;
-  const int n = h->n, P = h->P;
-  h->tile = cfg->tile < 0 ? 0 : cfg->tile;
+  const int nx = h->nx, ny = h->ny, nz = h->nz;
+  const int Px = 2 * nx, Py = 2 * ny, Pz = 2 * nz;
+  h->tile = cfg->tile;
+  if (h->tile < 0) {   // autotuned below; start from the first tile that fits
+    for (int t = 0; t < MQ_TILES && h->tile < 0; ++t)
+      if (green_tile_fits(nx, ny, nz, t, h->device)) h->tile = t;
+    if (h->tile < 0) {
+      h->err = "no launch shape of the Green's passes fits the device's shared memory at this grid";
+      delete h;
+      return MQNPM_ERR_UNSUPPORTED;
+    }
+  }
   std::fill(h->tune_ms, h->tune_ms + MQ_TILES, -1.0);
-  if (!green_tile_fits(n, h->tile, h->device)) {
-    char msg[120];
-    snprintf(msg, sizeof msg, "tile %d needs more shared memory per block than the device has at n = %d", h->tile, n);
+  if (!green_tile_fits(nx, ny, nz, h->tile, h->device)) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "tile %d needs more shared memory per block than the device has at the %d x %d x %d grid",
+             h->tile, nx, ny, nz);
     h->err = msg;
     *out = nullptr;
     delete h;
     return MQNPM_ERR_INVALID_ARG;
   }
-  h->w.ctas_row = green_row_ctas_max(n);   // partials sized for every tile variant
+  h->w.ctas_row = green_row_ctas_max(nx, ny, nz);   // partials sized for every tile variant
   h->w.ctas_vec = (int)std::min<long long>(ceil_div_ll((long long)N, 256LL * 8), 8LL * nsm);
   h->w.ctas_upd = (int)std::min<long long>(ceil_div_ll((long long)N, 256LL * 8), 4LL * nsm);
   if (h->w.ctas_vec < 1) h->w.ctas_vec = 1;
@@ -334,13 +346,14 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   const int wp_blocks = wprox_blocks_per_sm() * nsm;   // blocks of the cooperative prox kernel, at most
 
   // ---- budget (every device allocation of the handle)
-  const size_t m1 = (size_t)(n + 1);
+  const size_t nkhat = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const size_t ntab = (size_t)h->L * (nx + ny + nz);
   size_t need = 0;
-  need += m1 * m1 * m1 * 8 + (size_t)P * 8 + (size_t)h->L * 3 * n * 8 + (size_t)h->L * M * 8;
+  need += nkhat * 8 + (size_t)(Px + Py + Pz) * 8 + ntab * 8 + (size_t)h->L * M * 8;
   need += 8 * B * N * 8;                                   // u zs r rhat p v s t
-  need += B * ((size_t)n * n * P + (size_t)n * P * P) * 8; // T1, T2
+  need += B * ((size_t)nz * ny * Px + (size_t)nz * Py * Px) * 8;   // T1, T2
   need += B * M * 8;                                       // rdet
-  if (cfg->det_na > 0) need += 3 * B * M * 8 + M * 8 + (size_t)n * 8;   // remote detector
+  if (cfg->det_na > 0) need += 3 * B * M * 8 + M * 8 + (size_t)(nx + ny) * 8;   // remote detector
   need += B * (size_t)h->w.ctas_row * (1 + 3 + 1) * 8 + std::max(B * (size_t)h->w.ctas_upd, (size_t)h->w.ctas_vec) * 3 * 8;
   need += 8 * N * 4 + (size_t)(h->wp.ctas_vec * wprox_part_len() + 600) * 8 + wprox_part_count(wp_blocks) * 8;   // wprox
   need += (3 * (size_t)h->S + 2) * N * 4 + 3 * N * 4;                               // step state
@@ -358,20 +371,22 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   int rc = MQNPM_OK;
 #define AL(ptr, cnt) \
   if ((rc = dalloc(h, &(ptr), (cnt))) != MQNPM_OK) return fail(rc)
-  AL(h->khat, m1 * m1 * m1);
-  AL(h->tw, (size_t)P);
-  AL(h->tab, (size_t)h->L * 3 * n);
+  AL(h->khat, nkhat);
+  AL(h->twx, (size_t)Px);
+  AL(h->twy, (size_t)Py);
+  AL(h->twz, (size_t)Pz);
+  AL(h->tab, ntab);
   AL(h->ymeas, (size_t)h->L * M);
   Workspace& w = h->w;
   AL(w.u, B * N); AL(w.zs, B * N); AL(w.r, B * N); AL(w.rhat, B * N);
   AL(w.p, B * N); AL(w.v, B * N); AL(w.s, B * N); AL(w.t, B * N);
-  AL(w.T1, B * (size_t)n * n * P);
-  AL(w.T2, B * (size_t)n * P * P);
+  AL(w.T1, B * (size_t)nz * ny * Px);
+  AL(w.T2, B * (size_t)nz * Py * Px);
   AL(w.rdet, B * M);
   h->remote = cfg->det_na > 0;
   if (h->remote) {
     AL(w.dtmp1, B * M); AL(w.dtmp2, B * M); AL(w.rlift, B * M);
-    AL(h->Hdet, M); AL(h->twn, (size_t)n);
+    AL(h->Hdet, M); AL(h->twn, (size_t)(nx + ny));
   }
   AL(w.part1, B * (size_t)w.ctas_row * 1);
   AL(w.part5, B * (size_t)w.ctas_row * 3);
@@ -441,29 +456,39 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   }
   if ((e = cudaMallocHost(&w.h_scal, 64 * sizeof(double))) != cudaSuccess) { set_cuda_error(h, e, "cudaMallocHost"); return fail(MQNPM_ERR_CUDA); }
 
-  // ---- tables: twiddles W_P^j and incident-field axis factors, built in FP64
-  std::vector<float2> tw(P);
-  for (int j = 0; j < P; ++j) {
-    const double a = 2.0 * M_PI * (double)j / (double)P;
-    tw[j] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
-  }
-  std::vector<float2> tab((size_t)h->L * 3 * n);
-  for (int l = 0; l < h->L; ++l)
+  // ---- tables: twiddles W_P^j per axis and incident-field axis factors
+  // [l][nx + ny + nz] (x, then y, then z), built in FP64
+  auto twiddles = [](int P) {
+    std::vector<float2> tw(P);
+    for (int j = 0; j < P; ++j) {
+      const double a = 2.0 * M_PI * (double)j / (double)P;
+      tw[j] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+    }
+    return tw;
+  };
+  const std::vector<float2> twx = twiddles(Px), twy = twiddles(Py), twz = twiddles(Pz);
+  std::vector<float2> tab(ntab);
+  const int ext[3] = {nx, ny, nz};
+  for (int l = 0; l < h->L; ++l) {
+    size_t o = (size_t)l * (nx + ny + nz);
     for (int ax = 0; ax < 3; ++ax)
-      for (int i = 0; i < n; ++i) {
-        const double ph = h->kb * h->kdir[3 * l + ax] * ((double)i - n / 2.0) * h->h;
-        tab[((size_t)l * 3 + ax) * n + i] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+      for (int i = 0; i < ext[ax]; ++i, ++o) {
+        const double ph = h->kb * h->kdir[3 * l + ax] * ((double)i - ext[ax] / 2.0) * h->h;
+        tab[o] = make_float2((float)std::cos(ph), (float)std::sin(ph));
       }
+  }
   cudaStream_t s = h->stream;
-  if ((e = make_t2_tensor_map(w.T2, n, (int)B, h->tile, w.t2map)) != cudaSuccess ||
+  if ((e = make_t2_tensor_map(w.T2, nx, ny, nz, (int)B, h->tile, w.t2map)) != cudaSuccess ||
       (e = cudaMemsetAsync(w.gerr, 0, sizeof(int), s)) != cudaSuccess) {
     set_cuda_error(h, e, "tensor map of the transform buffer");
     return fail(MQNPM_ERR_CUDA);
   }
-  if ((e = cudaMemcpyAsync(h->tw, tw.data(), P * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+  if ((e = cudaMemcpyAsync(h->twx, twx.data(), Px * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->twy, twy.data(), Py * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->twz, twz.data(), Pz * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = (cfg->green_hat ? upload_khat(cfg->green_hat, n, h->khat, s) : build_khat(n, h->h, h->kb, h->khat, s, h->green_kernel))) !=
-          cudaSuccess) {
+      (e = (cfg->green_hat ? upload_khat(cfg->green_hat, nx, ny, nz, h->khat, s)
+                           : build_khat(nx, ny, nz, h->h, h->kb, h->khat, s, h->green_kernel))) != cudaSuccess) {
     set_cuda_error(h, e, "create tables");
     return fail(MQNPM_ERR_CUDA);
   }
@@ -475,7 +500,7 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->has_u.assign(h->S, 0);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { set_cuda_error(h, e, "create sync"); return fail(MQNPM_ERR_CUDA); }
   if (cfg->tile < 0 && (rc = autotune_tile(h)) != MQNPM_OK) return fail(rc);
-  w.ctas_row = green_row_ctas(n, h->tile);
+  w.ctas_row = green_row_ctas(nx, ny, nz, h->tile);
   *out = h;
   return MQNPM_OK;
 }
@@ -493,7 +518,9 @@ int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int a
   if (!h || !v || !out || nb < 1 || nb > h->max_batch) return set_error(h, MQNPM_ERR_INVALID_ARG, "green_apply: bad arguments");
   CK(cudaSetDevice(h->device));
   GreenCall c;
-  c.n = h->n;
+  c.nx = h->nx;
+  c.ny = h->ny;
+  c.nz = h->nz;
   c.nb = nb;
   c.adjoint = adjoint != 0;
   c.pro = PRO_PLAIN;
@@ -503,7 +530,9 @@ int mqnpm_green_apply(mqnpm_handle* h, const float* v, float* out, int nb, int a
   c.T1 = h->w.T1;
   c.T2 = h->w.T2;
   c.khat = h->khat;
-  c.tw = h->tw;
+  c.twx = h->twx;
+  c.twy = h->twy;
+  c.twz = h->twz;
   c.part_pro = h->w.part1;
   c.part_epi = h->w.part5;
   c.ev = profile_slot(h, nb);
@@ -815,7 +844,7 @@ int mqnpm_step_with_gradient(mqnpm_handle* h, float* x, const float* g, double l
 // ---- checkpoint: header, then xbar, gbar, U (S x N floats each), P (3N floats)
 struct StateHeader {
   unsigned magic;
-  int n, S, k, have_P, warm, L;
+  int nx, ny, nz, S, k, have_P, warm, L;
   int has_u[MQNPM_MAX_S];
   double tau[MQNPM_MAX_S];
 };
@@ -834,7 +863,9 @@ int mqnpm_save_state(mqnpm_handle* h, void* buf, size_t* size) {
   CK(cudaSetDevice(h->device));
   StateHeader hd{};
   hd.magic = 0x4d514e51u;
-  hd.n = h->n;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.nz = h->nz;
   hd.S = h->S;
   hd.k = h->k;
   hd.warm = warm ? 1 : 0;
@@ -872,7 +903,7 @@ int mqnpm_load_state(mqnpm_handle* h, const void* buf, size_t size) {
   if (size < sizeof(StateHeader) || size < need) return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: buffer too small");
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof hd);
-  if (hd.magic != 0x4d514e51u || hd.n != h->n || hd.S != h->S || hd.L != h->L || hd.warm != (warm ? 1 : 0))
+  if (hd.magic != 0x4d514e51u || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.S != h->S || hd.L != h->L || hd.warm != (warm ? 1 : 0))
     return set_error(h, MQNPM_ERR_INVALID_ARG, "load_state: state does not match this handle");
   CK(cudaSetDevice(h->device));
   const char* p = static_cast<const char*>(buf) + sizeof hd;

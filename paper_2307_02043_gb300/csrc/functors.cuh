@@ -5,17 +5,18 @@
 #include "green_passes.cuh"
 
 struct Geo {
-  int n;
+  int nx, ny, nz;
   MQ_D size_t vox(int b, int x, int y, int z) const {
-    return (((size_t)b * n + z) * n + y) * n + x;
+    return (((size_t)b * nz + z) * ny + y) * nx + x;
   }
-  MQ_D size_t vox0(int x, int y, int z) const { return ((size_t)z * n + y) * n + x; }
+  MQ_D size_t vox0(int x, int y, int z) const { return ((size_t)z * ny + y) * nx + x; }
 };
 
-// u_in(l, x, y, z) = ex[x] * ey[y] * ez[z] from FP64-built axis tables.
-MQ_D float2 incident(const float2* tab, int l, int n, int x, int y, int z) {
-  const float2* t = tab + (size_t)l * 3 * n;
-  return cmul(cmul(t[x], t[n + y]), t[2 * n + z]);
+// u_in(l, x, y, z) = ex[x] * ey[y] * ez[z] from FP64-built axis tables
+// [l][nx + ny + nz].
+MQ_D float2 incident(const float2* tab, int l, const Geo& g, int x, int y, int z) {
+  const float2* t = tab + (size_t)l * (g.nx + g.ny + g.nz);
+  return cmul(cmul(t[x], t[g.nx + y]), t[g.nx + g.ny + z]);
 }
 
 template <int KIND>
@@ -56,7 +57,7 @@ struct Pro<PRO_BORN> {
   MQ_D void begin(int b) { xb = slot_contrast(a, b); }
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
-    return cscale(incident(a.tab, a.illum[b], g.n, x, y, z), xb[g.vox0(x, y, z)]);
+    return cscale(incident(a.tab, a.illum[b], g, x, y, z), xb[g.vox0(x, y, z)]);
   }
 };
 
@@ -118,8 +119,8 @@ struct Pro<PRO_LIFT> {
   MQ_D void begin(int) {}
   template <class Pt>
   MQ_D float2 load(int b, int x, int y, int z, Pt&) const {
-    if (z != g.n - 1) return make_float2(0.f, 0.f);
-    return a.rdet[((size_t)b * g.n + y) * g.n + x];
+    if (z != g.nz - 1) return make_float2(0.f, 0.f);
+    return a.rdet[((size_t)b * g.ny + y) * g.nx + x];
   }
 };
 
@@ -192,7 +193,7 @@ struct Epi<EPI_INIT_WARM> {
   template <class Pt>
   MQ_D void store(int b, int x, int y, int z, float2 gv, Pt& parts) const {
     const size_t i = g.vox(b, x, y, z);
-    const float2 r = cadd(csub(incident(a.tab, a.illum[b], g.n, x, y, z), a.a[i]), gv);
+    const float2 r = cadd(csub(incident(a.tab, a.illum[b], g, x, y, z), a.a[i]), gv);
     a.out[i] = r;
     a.out2[i] = r;
     parts.v[0] += cabs2(r);
@@ -206,9 +207,9 @@ struct Epi<EPI_DETECT> {
   Geo g;
   template <class Pt>
   MQ_D void store(int b, int x, int y, int z, float2 gv, Pt& parts) const {
-    if (z != g.n - 1) return;
-    const size_t M = (size_t)g.n * g.n;
-    const size_t j = (size_t)y * g.n + x;
+    if (z != g.nz - 1) return;
+    const size_t M = (size_t)g.nx * g.ny;
+    const size_t j = (size_t)y * g.nx + x;
     const float2 r = a.ymeas ? csub(gv, a.ymeas[(size_t)a.illum[b] * M + j]) : gv;
     a.out2[b * M + j] = r;
     parts.v[0] += cabs2(r);

@@ -3,12 +3,13 @@
 //
 // Discretisation (our reading of the forward model of Section 6): with voxel h
 // and background wavenumber kb,
-//   (G v)_i = kb^2 sum_j w_{i-j} v_j,  offsets D in (-n, n)^3,
+//   (G v)_i = kb^2 sum_j w_{i-j} v_j,  offsets D in (-nx, nx) x (-ny, ny) x (-nz, nz),
 //   w_D = h^3 exp(j kb |D| h) / (4 pi |D| h) for D != 0,
-//   w_0 = [exp(j kb a)(1 - j kb a) - 1] / kb^2, a = (3/(4 pi))^(1/3) h.
-// On the periodic grid of edge P = 2n the kernel is even in every axis, so its
-// DFT is a product of three 1D cosine sums over the first octant of offsets:
-//   Kf(f) = k(0) + 2 sum_{d=1}^{n-1} k(d) cos(2 pi f d / P),  f = 0..n.
+//   w_0 = [exp(j kb a)(1 - j kb a) - 1] / kb^2, a = (3/(4 pi))^(1/3) h
+// (or the truncated kernel below).  On the periodic grid of edges P_d = 2 n_d
+// the kernel is even in every axis, so its DFT is a product of three 1D cosine
+// sums over the first octant of offsets:
+//   Kf(f) = k(0) + 2 sum_{d=1}^{n-1} k(d) cos(2 pi f d / P),  f = 0..n, per axis.
 // These sums run in FP64 on the device; the result, scaled by 1/P^3 (the
 // normalisation of the inverse transform), is rounded to complex64.
 #include <algorithm>
@@ -35,66 +36,140 @@ bool green_supported(int n) {
   }
 }
 
-void green_shape(int n, int tile, int* shape, size_t* smem) {
-  for (int i = 0; i < 6; ++i) shape[i] = 0;
-  size_t m = 0;
+namespace {
+
+// The shape fields and shared memory of one length's passes.
+bool shape_of(int n, int tile, int* shape, size_t* srow, size_t* scol, size_t* sz) {
   switch (2 * n) {
-#define MQ_CASE(P) case P: green_shape_P##P(tile, n, shape, &m); break;
+#define MQ_CASE(P) case P: green_shape_P##P(tile, shape, srow, scol, sz); return true;
     MQ_DISPATCH(MQ_CASE)
 #undef MQ_CASE
     default:
-      break;
+      return false;
   }
-  if (smem) *smem = m;
 }
 
-bool green_tile_fits(int n, int tile, int device) {
+}  // namespace
+
+void green_shape(int nx, int ny, int nz, int tile, int* shape, size_t* smem) {
+  for (int i = 0; i < 6; ++i) shape[i] = 0;
+  if (smem) *smem = 0;
+  int sx[6], sy[6], sz[6];
+  size_t rx, cx, zx, ry, cy, zy, rz, cz, zz;
+  if (!shape_of(nx, tile, sx, &rx, &cx, &zx) || !shape_of(ny, tile, sy, &ry, &cy, &zy) ||
+      !shape_of(nz, tile, sz, &rz, &cz, &zz))
+    return;
+  shape[0] = sx[0];   // x passes: length Px
+  shape[1] = sx[1];
+  shape[2] = sy[2];   // y passes: length Py
+  shape[3] = sy[3];
+  shape[4] = sz[4];   // z pass: length Pz
+  shape[5] = sz[5];
+  if (smem) *smem = std::max(rx, std::max(cy, zz));
+}
+
+bool green_tile_fits(int nx, int ny, int nz, int tile, int device) {
   int shape[6], optin = 0;
   size_t smem = 0;
-  green_shape(n, tile, shape, &smem);
+  green_shape(nx, ny, nz, tile, shape, &smem);
   if (shape[0] <= 0 || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return false;
   return smem <= (size_t)optin;
 }
 
-int green_row_ctas(int n, int tile) {
+int green_row_ctas(int nx, int ny, int nz, int tile) {
   int shape[6];
-  green_shape(n, tile, shape);
-  return shape[0] > 0 ? (n * n + shape[0] - 1) / shape[0] : 0;
+  green_shape(nx, ny, nz, tile, shape);
+  return shape[0] > 0 ? (ny * nz + shape[0] - 1) / shape[0] : 0;
 }
 
-int green_plane_ctas(int n, int tile) {
+int green_plane_ctas(int nx, int ny, int tile) {
   int shape[6];
-  green_shape(n, tile, shape);
-  return shape[0] > 0 ? (n + shape[0] - 1) / shape[0] : 0;
+  green_shape(nx, ny, nx, tile, shape);   // the x-pass shape depends on nx only
+  return shape[0] > 0 ? (ny + shape[0] - 1) / shape[0] : 0;
 }
 
-int green_row_ctas_max(int n) { return std::max(green_row_ctas(n, 0), green_row_ctas(n, 1)); }
+int green_row_ctas_max(int nx, int ny, int nz) {
+  return std::max(green_row_ctas(nx, ny, nz, 0), green_row_ctas(nx, ny, nz, 1));
+}
 
-int green_col_width(int n, int tile) {   // columns per CTA of pass 3 (the tensor-map box)
+int green_col_width(int nx, int ny, int nz, int tile) {   // columns per CTA of pass 3 (the tensor-map box)
   int shape[6];
-  green_shape(n, tile, shape);
+  green_shape(nx, ny, nz, tile, shape);
   return shape[4];
 }
 
-cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
-  switch (2 * c.n) {
-#define MQ_CASE(P) case P: return green_launch_P##P(c, s);
+namespace {
+
+cudaError_t pass1_any(const GreenCall& c, cudaStream_t s) {
+  switch (2 * c.nx) {
+#define MQ_CASE(P) case P: return green_pass1_P##P(c, s);
     MQ_DISPATCH(MQ_CASE)
 #undef MQ_CASE
-    default:
-      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t pass5_any(const GreenCall& c, cudaStream_t s) {
+  switch (2 * c.nx) {
+#define MQ_CASE(P) case P: return green_pass5_P##P(c, s);
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t passy_any(const GreenCall& c, bool inv, cudaStream_t s) {
+  switch (2 * c.ny) {
+#define MQ_CASE(P) case P: return green_passy_P##P(c, inv, s);
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t pass3_any(const GreenCall& c, cudaStream_t s) {
+  switch (2 * c.nz) {
+#define MQ_CASE(P) case P: return green_pass3_P##P(c, s);
+    MQ_DISPATCH(MQ_CASE)
+#undef MQ_CASE
+    default: return cudaErrorInvalidValue;
   }
 }
 
+}  // namespace
+
+// The five passes of one apply, each from the translation unit of its axis's
+// transform length, with the optional pass events around them.
+cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
+  if (c.tile < 0 || c.tile >= MQ_TILES || !green_supported(c.nx) || !green_supported(c.ny) ||
+      !green_supported(c.nz))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  // inside a stream capture the records must be external to become event-record
+  // nodes of the graph; outside one they are plain records
+  unsigned rec_flags = cudaEventRecordDefault;
+  if (c.ev) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+  }
+  auto rec = [&](int k) { return c.ev ? cudaEventRecordWithFlags(c.ev[k], s, rec_flags) : cudaSuccess; };
+  if ((e = rec(0)) != cudaSuccess || (e = pass1_any(c, s)) != cudaSuccess || (e = rec(1)) != cudaSuccess ||
+      (e = passy_any(c, false, s)) != cudaSuccess || (e = rec(2)) != cudaSuccess ||
+      (e = pass3_any(c, s)) != cudaSuccess || (e = rec(3)) != cudaSuccess ||
+      (e = passy_any(c, true, s)) != cudaSuccess || (e = rec(4)) != cudaSuccess ||
+      (e = pass5_any(c, s)) != cudaSuccess || (e = rec(5)) != cudaSuccess)
+    return e;
+  if (c.launches) *c.launches += 5;
+  return e;
+}
+
 // ---------------------------------------------------------- T2 tensor map
-// T2 viewed as a 3D tensor of 8-byte elements: x = kx (P), y = ky (P),
-// z = slot * n + z (max_batch * n).  Pass 3 loads boxes of C x 1 x n: one
+// T2 viewed as a 3D tensor of 8-byte elements: x = kx (Px), y = ky (Py),
+// z = slot * nz + z (max_batch * nz).  Pass 3 loads boxes of C x 1 x nz: one
 // column set of one slot.  The encoder comes from the driver through the
 // runtime's entry-point query, so the library does not link libcuda.
-cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, int tile, void* map_out) {
-  const int P = 2 * n;
-  const int C = green_col_width(n, tile);
+cudaError_t make_t2_tensor_map(void* T2, int nx, int ny, int nz, int max_batch, int tile, void* map_out) {
+  const int Px = 2 * nx, Py = 2 * ny;
+  const int C = green_col_width(nx, ny, nz, tile);
   if (C <= 0) return cudaErrorInvalidValue;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -105,9 +180,9 @@ cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, int tile, void* m
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)max_batch * n};
-  const cuuint64_t strides[2] = {(cuuint64_t)P * 8, (cuuint64_t)P * P * 8};
-  const cuuint32_t box[3] = {(cuuint32_t)C, 1u, (cuuint32_t)n};
+  const cuuint64_t dims[3] = {(cuuint64_t)Px, (cuuint64_t)Py, (cuuint64_t)max_batch * nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)Px * 8, (cuuint64_t)Px * Py * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)C, 1u, (cuuint32_t)nz};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = encode(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, T2, dims, strides, box,
                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -116,12 +191,12 @@ cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, int tile, void* m
 }
 
 // ------------------------------------------------------------ K_hat build
-// k[dz][dy][dx] for offsets in [0, n)^3 (FP64 complex as double2).
-__global__ void k_kernel_octant(double2* k, int n, double h, double kb) {
-  const long long N = (long long)n * n * n;
+// k[dz][dy][dx] for offsets in [0, nz) x [0, ny) x [0, nx) (FP64 complex as double2).
+__global__ void k_kernel_octant(double2* k, int nx, int ny, int nz, double h, double kb) {
+  const long long N = (long long)nx * ny * nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    const int dx = (int)(i % n), dy = (int)((i / n) % n), dz = (int)(i / ((long long)n * n));
+    const int dx = (int)(i % nx), dy = (int)((i / nx) % ny), dz = (int)(i / ((long long)nx * ny));
     double re, im;
     if (dx == 0 && dy == 0 && dz == 0) {
       const double a = cbrt(3.0 / (4.0 * 3.14159265358979323846)) * h;
@@ -171,27 +246,6 @@ __global__ void k_round_khat(const double2* __restrict__ in, float2* __restrict_
     out[i] = make_float2((float)(in[i].x * scale), (float)(in[i].y * scale));
 }
 
-// The same construction with caller-provided device scratch: a, b hold
-// (n+1)^3 double2 each, dcos holds P doubles.  No device allocation.
-cudaError_t build_khat_scratch(int n, double h, double kb, float2* khat_out, double2* a, double2* b, double* dcos,
-                               cudaStream_t s) {
-  const int P = 2 * n;
-  const long long m = n + 1;
-  std::vector<double> cosv(P);
-  for (int j = 0; j < P; ++j) cosv[j] = std::cos(2.0 * M_PI * (double)j / (double)P);
-  cudaError_t e = cudaMemcpyAsync(dcos, cosv.data(), P * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  const int th = 256, gr = 1024;
-  k_kernel_octant<<<gr, th, 0, s>>>(a, n, h, kb);
-  k_cos_pass<<<gr, th, 0, s>>>(a, b, n, n, n, dcos, P);
-  k_cos_pass<<<gr, th, 0, s>>>(b, a, (int)m, n, n, dcos, P);
-  k_cos_pass<<<gr, th, 0, s>>>(a, b, (int)m, (int)m, n, dcos, P);
-  k_round_khat<<<gr, th, 0, s>>>(b, khat_out, m * m * m, 1.0 / ((double)P * P * P));
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host cosine table goes out of scope
-  return e;
-}
-
 // ------------------------------------------------ truncated Green's kernel
 // Transform of g_R(r) = exp(j kb r)/(4 pi r) 1[r <= R] at radial frequency s
 // (Vico, Greengard and Ferrando, J. Comput. Phys. 2016).  With q = kb:
@@ -229,15 +283,17 @@ __device__ double2 truncated_ft(double s, double q, double R) {
   return make_double2((1.0 - cp) * a - b * 0.5 * t * sh * sh, -sp * a + b * sinc_d(t));
 }
 
-// spec[mz][my][mx] = g_R^(ds |m|) for m in [0, M)^3 (M = 2n + 1: the folded
-// frequencies of the period T = 4n, the transform being radial).
-__global__ void k_truncated_spectrum(double2* spec, int M, double ds, double kb, double R) {
-  const long long total = (long long)M * M * M;
+// spec[mz][my][mx] = g_R^(|s_m|), s_m = (m_x dsx, m_y dsy, m_z dsz), m_d < M_d:
+// the folded frequencies of the periods T_d (M_d = T_d/2 + 1; the transform is
+// radial, so even in every axis).
+__global__ void k_truncated_spectrum(double2* spec, int Mx, int My, int Mz, double dsx, double dsy, double dsz,
+                                     double kb, double R) {
+  const long long total = (long long)Mx * My * Mz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int mx = (int)(i % M), my = (int)((i / M) % M), mz = (int)(i / ((long long)M * M));
-    const double s = ds * sqrt((double)mx * mx + (double)my * my + (double)mz * mz);
-    spec[i] = truncated_ft(s, kb, R);
+    const int mx = (int)(i % Mx), my = (int)((i / Mx) % My), mz = (int)(i / ((long long)Mx * My));
+    const double sx = dsx * mx, sy = dsy * my, sz = dsz * mz;
+    spec[i] = truncated_ft(sqrt(sx * sx + sy * sy + sz * sz), kb, R);
   }
 }
 
@@ -274,53 +330,110 @@ __global__ void k_scale_d2(double2* a, long long count, double sc) {
     a[i] = make_double2(a[i].x * sc, a[i].y * sc);
 }
 
-// Real-space octant kb^2 w_D, D in [0, n)^3, of the truncated kernel into `a`
-// ([dz][dy][dx]), from its transform sampled on the frequency grid of period
-// T = 4n h and R = sqrt(3) n h: w_D = (1/T^3) sum_m g_R^(|s_m|) e^{j s_m . D h}
-// (three even passes), times kb^2.  b: scratch; both hold (2n+1)^3 double2.
-cudaError_t truncated_octant(int n, double h, double kb, double2* a, double2* b, double* dcosT, cudaStream_t s) {
-  const int T = 4 * n, M = 2 * n + 1;
-  const double R = std::sqrt(3.0) * n * h;
-  std::vector<double> cosv(T);
-  for (int j = 0; j < T; ++j) cosv[j] = std::cos(2.0 * M_PI * (double)j / (double)T);
-  cudaError_t e = cudaMemcpyAsync(dcosT, cosv.data(), T * sizeof(double), cudaMemcpyHostToDevice, s);
+namespace {
+
+// Truncation radius (the domain's diagonal, which covers every distance
+// between two voxels) and the sample count T_d of each axis's period T_d h:
+// 4 n_d, raised to the next even count >= n_d + R/h for an elongated domain,
+// so that the periodic copies of g_R miss every offset the domain uses.
+void truncated_periods(int nx, int ny, int nz, double h, double* R, int* T) {
+  const double diag = std::sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+  *R = h * diag;
+  const int n[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) T[d] = std::max(4 * n[d], 2 * (int)std::ceil((n[d] + diag) / 2.0));
+}
+
+std::vector<double> cos_tables(const int* len, int count) {
+  std::vector<double> v;
+  for (int q = 0; q < count; ++q)
+    for (int j = 0; j < len[q]; ++j) v.push_back(std::cos(2.0 * M_PI * (double)j / (double)len[q]));
+  return v;
+}
+
+// Real-space octant kb^2 w_D, D in [0, nz) x [0, ny) x [0, nx), of the
+// truncated kernel into `a` ([dz][dy][dx]), from its transform sampled on the
+// frequency grid of periods T_d h: w_D = (1 / prod T_d) sum_m g_R^(|s_m|) e^{j s_m . D h}
+// (three even passes), times kb^2.  a, b: scratch of prod M_d double2 each;
+// dcosT: Tx + Ty + Tz doubles.
+cudaError_t truncated_octant(int nx, int ny, int nz, double h, double kb, double2* a, double2* b, double* dcosT,
+                             cudaStream_t s) {
+  double R;
+  int T[3];
+  truncated_periods(nx, ny, nz, h, &R, T);
+  const int Mx = T[0] / 2 + 1, My = T[1] / 2 + 1, Mz = T[2] / 2 + 1;
+  const std::vector<double> cosv = cos_tables(T, 3);
+  cudaError_t e = cudaMemcpyAsync(dcosT, cosv.data(), cosv.size() * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
+  const double* cx = dcosT;
+  const double* cy = dcosT + T[0];
+  const double* cz = dcosT + T[0] + T[1];
   const int th = 256, gr = 2048;
-  k_truncated_spectrum<<<gr, th, 0, s>>>(b, M, 2.0 * M_PI / (T * h), kb, R);   // b: [mz][my][mx]
-  k_even_idft_pass<<<gr, th, 0, s>>>(b, a, M, M, M, n, dcosT, T);             // a: [dx][mz][my]
-  k_even_idft_pass<<<gr, th, 0, s>>>(a, b, n, M, M, n, dcosT, T);             // b: [dy][dx][mz]
-  k_even_idft_pass<<<gr, th, 0, s>>>(b, a, n, n, M, n, dcosT, T);             // a: [dz][dy][dx]
-  k_scale_d2<<<gr, th, 0, s>>>(a, (long long)n * n * n, kb * kb / ((double)T * T * T));
+  k_truncated_spectrum<<<gr, th, 0, s>>>(b, Mx, My, Mz, 2.0 * M_PI / (T[0] * h), 2.0 * M_PI / (T[1] * h),
+                                         2.0 * M_PI / (T[2] * h), kb, R);   // b: [mz][my][mx]
+  k_even_idft_pass<<<gr, th, 0, s>>>(b, a, Mz, My, Mx, nx, cx, T[0]);       // a: [dx][mz][my]
+  k_even_idft_pass<<<gr, th, 0, s>>>(a, b, nx, Mz, My, ny, cy, T[1]);       // b: [dy][dx][mz]
+  k_even_idft_pass<<<gr, th, 0, s>>>(b, a, ny, nx, Mz, nz, cz, T[2]);       // a: [dz][dy][dx]
+  k_scale_d2<<<gr, th, 0, s>>>(a, (long long)nx * ny * nz, kb * kb / ((double)T[0] * T[1] * T[2]));
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host cosine table goes out of scope
   return e;
 }
 
-cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s, int kernel) {
-  const int P = 2 * n;
-  const long long m = n + 1;
-  std::vector<double> cosv(P);
-  for (int j = 0; j < P; ++j) cosv[j] = std::cos(2.0 * M_PI * (double)j / (double)P);
+// Scratch of the construction: double2 entries of each of a and b, and
+// doubles of the cosine tables.
+void khat_scratch_sizes(int nx, int ny, int nz, int kernel, size_t* big, size_t* ncos) {
+  *big = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  *ncos = 2 * ((size_t)nx + ny + nz);
+  if (kernel == MQNPM_KERNEL_TRUNCATED) {
+    double R;
+    int T[3];
+    truncated_periods(nx, ny, nz, 1.0, &R, T);
+    *big = std::max(*big, (size_t)(T[0] / 2 + 1) * (T[1] / 2 + 1) * (T[2] / 2 + 1));
+    *ncos = std::max(*ncos, (size_t)T[0] + T[1] + T[2]);
+  }
+}
+
+// K_hat octant [fz][fy][fx] = DFT of the P-periodic kernel / (Px Py Pz), rounded once.
+cudaError_t khat_core(int nx, int ny, int nz, double h, double kb, int kernel, float2* khat_out, double2* a,
+                      double2* b, double* dcos, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (kernel == MQNPM_KERNEL_TRUNCATED) e = truncated_octant(nx, ny, nz, h, kb, a, b, dcos, s);
+  if (e != cudaSuccess) return e;
+  const int P[3] = {2 * nx, 2 * ny, 2 * nz};
+  const std::vector<double> cosv = cos_tables(P, 3);
+  e = cudaMemcpyAsync(dcos, cosv.data(), cosv.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int th = 256, gr = 1024;
+  if (kernel != MQNPM_KERNEL_TRUNCATED) k_kernel_octant<<<gr, th, 0, s>>>(a, nx, ny, nz, h, kb);   // a: [dz][dy][dx]
+  k_cos_pass<<<gr, th, 0, s>>>(a, b, nz, ny, nx, dcos, P[0]);                        // b: [fx][dz][dy]
+  k_cos_pass<<<gr, th, 0, s>>>(b, a, nx + 1, nz, ny, dcos + P[0], P[1]);             // a: [fy][fx][dz]
+  k_cos_pass<<<gr, th, 0, s>>>(a, b, ny + 1, nx + 1, nz, dcos + P[0] + P[1], P[2]);  // b: [fz][fy][fx]
+  k_round_khat<<<gr, th, 0, s>>>(b, khat_out, (long long)(nx + 1) * (ny + 1) * (nz + 1),
+                                 1.0 / ((double)P[0] * P[1] * P[2]));
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host cosine table goes out of scope
+  return e;
+}
+
+}  // namespace
+
+// The sampled kernel on a cubic grid with caller-provided device scratch: a,
+// b hold (n+1)^3 double2 each, dcos holds 6n doubles.  No device allocation.
+cudaError_t build_khat_scratch(int n, double h, double kb, float2* khat_out, double2* a, double2* b, double* dcos,
+                               cudaStream_t s) {
+  return khat_core(n, n, n, h, kb, MQNPM_KERNEL_SAMPLED, khat_out, a, b, dcos, s);
+}
+
+cudaError_t build_khat(int nx, int ny, int nz, double h, double kb, float2* khat_out, cudaStream_t s, int kernel) {
+  size_t big = 0, ncos = 0;
+  khat_scratch_sizes(nx, ny, nz, kernel, &big, &ncos);
   double2 *a = nullptr, *b = nullptr;
   double* dcos = nullptr;
-  const long long M = 2 * n + 1;
-  const size_t big = kernel == MQNPM_KERNEL_TRUNCATED ? (size_t)M * M * M : (size_t)m * m * m;
   cudaError_t e;
   if ((e = cudaMallocAsync(&a, big * sizeof(double2), s)) != cudaSuccess) return e;
   if ((e = cudaMallocAsync(&b, big * sizeof(double2), s)) != cudaSuccess) { cudaFreeAsync(a, s); return e; }
-  if ((e = cudaMallocAsync(&dcos, 4 * (size_t)n * sizeof(double), s)) != cudaSuccess) { cudaFreeAsync(a, s); cudaFreeAsync(b, s); return e; }
-  if (kernel == MQNPM_KERNEL_TRUNCATED) e = truncated_octant(n, h, kb, a, b, dcos, s);   // a: [dz][dy][dx]
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dcos, cosv.data(), P * sizeof(double), cudaMemcpyHostToDevice, s);
-  const int th = 256, gr = 1024;
-  if (e == cudaSuccess) {
-    if (kernel != MQNPM_KERNEL_TRUNCATED) k_kernel_octant<<<gr, th, 0, s>>>(a, n, h, kb);   // a: [dz][dy][dx]
-    k_cos_pass<<<gr, th, 0, s>>>(a, b, n, n, n, dcos, P);             // b: [fx][dz][dy]
-    k_cos_pass<<<gr, th, 0, s>>>(b, a, (int)m, n, n, dcos, P);        // a: [fy][fx][dz]
-    k_cos_pass<<<gr, th, 0, s>>>(a, b, (int)m, (int)m, n, dcos, P);   // b: [fz][fy][fx]
-    k_round_khat<<<gr, th, 0, s>>>(b, khat_out, m * m * m, 1.0 / ((double)P * P * P));
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host cosine table goes out of scope
-  }
+  if ((e = cudaMallocAsync(&dcos, ncos * sizeof(double), s)) != cudaSuccess) { cudaFreeAsync(a, s); cudaFreeAsync(b, s); return e; }
+  e = khat_core(nx, ny, nz, h, kb, kernel, khat_out, a, b, dcos, s);
   cudaFreeAsync(a, s);
   cudaFreeAsync(b, s);
   cudaFreeAsync(dcos, s);
@@ -328,12 +441,11 @@ cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_
 }
 
 // A caller-provided spectrum: the first octant [fz][fy][fx] of the
-// unnormalised DFT_P, complex64 on the host.  Scaled by 1/P^3 in FP64 and
-// rounded once, like the library's own construction.
-cudaError_t upload_khat(const float* host, int n, float2* khat_out, cudaStream_t s) {
-  const int P = 2 * n;
-  const size_t big = (size_t)(n + 1) * (n + 1) * (n + 1);
-  const double scale = 1.0 / ((double)P * P * P);
+// unnormalised DFT_P, complex64 on the host.  Scaled by 1/(Px Py Pz) in FP64
+// and rounded once, like the library's own construction.
+cudaError_t upload_khat(const float* host, int nx, int ny, int nz, float2* khat_out, cudaStream_t s) {
+  const size_t big = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const double scale = 1.0 / (8.0 * (double)nx * ny * nz);
   std::vector<float2> v(big);
   for (size_t i = 0; i < big; ++i) {
     const double re = host[2 * i], im = host[2 * i + 1];

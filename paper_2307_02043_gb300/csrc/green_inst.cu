@@ -1,5 +1,7 @@
 // Instantiation of the Green's-apply passes for one transform length P.
-// Compiled once per supported P with -DMQ_P=<P>.
+// Compiled once per supported P with -DMQ_P=<P>.  Each entry point runs the
+// passes along an axis whose transform length is P: the x passes (1 and 5)
+// when Px = P, the y passes (2 and 4) when Py = P, the z pass (3) when Pz = P.
 #include "functors.cuh"
 #include "internal.h"
 
@@ -18,20 +20,22 @@ cudaError_t set_smem(K kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+Geo geo(const GreenCall& c) { return Geo{c.nx, c.ny, c.nz}; }
+
 template <int RV, int KIND>
 cudaError_t launch1(const GreenCall& c, cudaStream_t s) {
   using RS = RowShape<P, RV>;
   Pro<KIND> pro;
   pro.a = c.pa;
-  pro.g = Geo{c.n};
+  pro.g = geo(c);
   if constexpr (KIND == PRO_BICG_P || KIND == PRO_BICG_S) pro.st = c.st;
   auto kern = k_pass1<P, RV, Pro<KIND>>;
   cudaError_t e = set_smem(kern, RS::SMEM);
   if (e != cudaSuccess) return e;
-  // a plane input needs only the rows of its plane (z = n - 1)
-  const int line0 = c.plane ? (c.n - 1) * c.n : 0, nlines = c.plane ? c.n : c.n * c.n;
+  // a plane input needs only the rows of its plane (z = nz - 1)
+  const int line0 = c.plane ? (c.nz - 1) * c.ny : 0, nlines = c.plane ? c.ny : c.ny * c.nz;
   dim3 grid(ceil_div(nlines, RS::LPB), c.nb);
-  kern<<<grid, RS::THREADS, RS::SMEM, s>>>(pro, c.T1, c.n, c.tw, c.st, c.part_pro, line0, nlines);
+  kern<<<grid, RS::THREADS, RS::SMEM, s>>>(pro, c.T1, c.ny, c.ny * c.nz, c.twx, c.st, c.part_pro, line0, nlines);
   return cudaGetLastError();
 }
 
@@ -40,13 +44,13 @@ cudaError_t launch5(const GreenCall& c, cudaStream_t s) {
   using RS = RowShape<P, RV>;
   Epi<KIND> epi;
   epi.a = c.ea;
-  epi.g = Geo{c.n};
+  epi.g = geo(c);
   auto kern = k_pass5<P, RV, Epi<KIND>>;
   cudaError_t e = set_smem(kern, RS::SMEM);
   if (e != cudaSuccess) return e;
-  const int line0 = c.outplane ? (c.n - 1) * c.n : 0, nlines = c.outplane ? c.n : c.n * c.n;
+  const int line0 = c.outplane ? (c.nz - 1) * c.ny : 0, nlines = c.outplane ? c.ny : c.ny * c.nz;
   dim3 grid(ceil_div(nlines, RS::LPB), c.nb);
-  kern<<<grid, RS::THREADS, RS::SMEM, s>>>(epi, c.T1, c.n, c.tw, c.st, c.part_epi, line0, nlines);
+  kern<<<grid, RS::THREADS, RS::SMEM, s>>>(epi, c.T1, c.ny, c.ny * c.nz, c.twx, c.st, c.part_epi, line0, nlines);
   return cudaGetLastError();
 }
 
@@ -79,13 +83,14 @@ cudaError_t pass5(const GreenCall& c, cudaStream_t s) {
 template <int CV, bool INV>
 cudaError_t pass_y(const GreenCall& c, const float2* in, float2* out, cudaStream_t s) {
   using CS = ColShape<P, CV>;
+  const int px = 2 * c.nx;   // the last column tile may be ragged (kx >= Px masked)
   auto kern = k_pass_y<P, CV, INV>;
   cudaError_t e = set_smem(kern, CS::SMEM);
   if (e != cudaSuccess) return e;
   // forward y pass of a plane input, inverse y pass of a plane output: that plane only
   const bool plane = INV ? c.outplane : c.plane;
-  dim3 grid(P / CS::C, plane ? 1 : c.n, c.nb);
-  kern<<<grid, CS::THREADS, CS::SMEM, s>>>(in, out, c.n, c.tw, c.st, plane ? c.n - 1 : 0);
+  dim3 grid(ceil_div(px, CS::C), plane ? 1 : c.nz, c.nb);
+  kern<<<grid, CS::THREADS, CS::SMEM, s>>>(in, out, c.nz, px, c.twy, c.st, plane ? c.nz - 1 : 0);
   return cudaGetLastError();
 }
 
@@ -95,84 +100,69 @@ cudaError_t pass3(const GreenCall& c, cudaStream_t s) {
   using CS = ColShape<P, CV>;
   const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);
   if (tm == nullptr || c.err == nullptr) return cudaErrorInvalidValue;
+  const int px = 2 * c.nx, py = 2 * c.ny;   // the last column tile may be ragged (kx >= Px masked)
   auto kern = k_pass3<P, CV, DB, CONJ, IO>;
-  const int smem = (int)Pass3Smem<P, CV, DB, IO>::bytes(c.n);
+  const int smem = (int)Pass3Smem<P, CV, DB, IO>::bytes(c.nz);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(P / CS::C, P);
-  kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.n, c.nb, c.tw, c.st, c.err);
+  dim3 grid(ceil_div(px, CS::C), py);
+  kern<<<grid, CS::THREADS, smem, s>>>(*tm, c.T2, c.khat, c.nx, c.ny, c.nb, c.twz, c.st, c.err);
   return cudaGetLastError();
 }
 
-template <int YV, int ZV, bool DB>
-cudaError_t columns(const GreenCall& c, cudaStream_t s, unsigned rec_flags) {
-  cudaError_t e;
-  if ((e = pass_y<YV, false>(c, c.T1, c.T2, s)) != cudaSuccess) return e;
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[2], s, rec_flags)) != cudaSuccess) return e;
+template <int ZV, bool DB>
+cudaError_t pass3_io(const GreenCall& c, cudaStream_t s) {
   if (c.plane) {   // the plane input serves the adjoint lift only
     if (!c.adjoint || c.outplane) return cudaErrorInvalidValue;
-    e = pass3<ZV, DB, true, IO_IN>(c, s);
-  } else if (c.outplane) {   // the plane output serves the first-Born data only
-    if (c.adjoint) return cudaErrorInvalidValue;
-    e = pass3<ZV, DB, false, IO_OUT>(c, s);
-  } else {
-    e = c.adjoint ? pass3<ZV, DB, true>(c, s) : pass3<ZV, DB, false>(c, s);
+    return pass3<ZV, DB, true, IO_IN>(c, s);
   }
-  if (e != cudaSuccess) return e;
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[3], s, rec_flags)) != cudaSuccess) return e;
-  return pass_y<YV, true>(c, c.T2, c.T1, s);
+  if (c.outplane) {   // the plane output serves the first-Born data only
+    if (c.adjoint) return cudaErrorInvalidValue;
+    return pass3<ZV, DB, false, IO_OUT>(c, s);
+  }
+  return c.adjoint ? pass3<ZV, DB, true>(c, s) : pass3<ZV, DB, false>(c, s);
 }
 }  // namespace
 
-void MQ_CAT(green_shape_P, MQ_P)(int tile, int n, int* shape, size_t* smem) {
+void MQ_CAT(green_shape_P, MQ_P)(int tile, int* shape, size_t* smem_row, size_t* smem_col, size_t* smem_z) {
   shape[0] = (tile & 1) ? RowShape<P, 1>::LPB : RowShape<P, 0>::LPB;
   shape[1] = (tile & 1) ? RowShape<P, 1>::T : RowShape<P, 0>::T;
   shape[2] = (tile & 2) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
   shape[3] = (tile & 2) ? ColShape<P, 1>::T : ColShape<P, 0>::T;
   shape[4] = (tile & 4) ? ColShape<P, 1>::C : ColShape<P, 0>::C;
   shape[5] = (tile & 4) ? ColShape<P, 1>::T : ColShape<P, 0>::T;
-  size_t m = 0;   // the largest dynamic shared memory of the tile's five passes
-  switch ((tile >> 2) & 3) {
-    case 0: m = Pass3Smem<P, 0, false>::bytes(n); break;
-    case 1: m = Pass3Smem<P, 1, false>::bytes(n); break;
-    case 2: m = Pass3Smem<P, 0, true>::bytes(n); break;
-    default: m = Pass3Smem<P, 1, true>::bytes(n); break;
+  switch ((tile >> 2) & 3) {   // the z pass at this length: nz = P/2
+    case 0: *smem_z = Pass3Smem<P, 0, false>::bytes(P / 2); break;
+    case 1: *smem_z = Pass3Smem<P, 1, false>::bytes(P / 2); break;
+    case 2: *smem_z = Pass3Smem<P, 0, true>::bytes(P / 2); break;
+    default: *smem_z = Pass3Smem<P, 1, true>::bytes(P / 2); break;
   }
-  const size_t ys = (tile & 2) ? ColShape<P, 1>::SMEM : ColShape<P, 0>::SMEM;
-  const size_t rs = (tile & 1) ? RowShape<P, 1>::SMEM : RowShape<P, 0>::SMEM;
-  *smem = m > ys ? (m > rs ? m : rs) : (ys > rs ? ys : rs);
+  *smem_col = (tile & 2) ? ColShape<P, 1>::SMEM : ColShape<P, 0>::SMEM;
+  *smem_row = (tile & 1) ? RowShape<P, 1>::SMEM : RowShape<P, 0>::SMEM;
 }
 
-cudaError_t MQ_CAT(green_launch_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
-  if (2 * c.n != P || c.tile < 0 || c.tile >= MQ_TILES) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  // inside a stream capture the records must be external to become event-record
-  // nodes of the graph; outside one they are plain records
-  unsigned rec_flags = cudaEventRecordDefault;
-  if (c.ev) {
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
-    if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+cudaError_t MQ_CAT(green_pass1_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
+  if (2 * c.nx != P) return cudaErrorInvalidValue;
+  return (c.tile & 1) ? pass1<1>(c, s) : pass1<0>(c, s);
+}
+
+cudaError_t MQ_CAT(green_pass5_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
+  if (2 * c.nx != P) return cudaErrorInvalidValue;
+  return (c.tile & 1) ? pass5<1>(c, s) : pass5<0>(c, s);
+}
+
+cudaError_t MQ_CAT(green_passy_P, MQ_P)(const GreenCall& c, bool inv, cudaStream_t s) {
+  if (2 * c.ny != P) return cudaErrorInvalidValue;
+  if (inv) return (c.tile & 2) ? pass_y<1, true>(c, c.T2, c.T1, s) : pass_y<0, true>(c, c.T2, c.T1, s);
+  return (c.tile & 2) ? pass_y<1, false>(c, c.T1, c.T2, s) : pass_y<0, false>(c, c.T1, c.T2, s);
+}
+
+cudaError_t MQ_CAT(green_pass3_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
+  if (2 * c.nz != P) return cudaErrorInvalidValue;
+  switch ((c.tile >> 2) & 3) {   // bit 2: z-pass shape, bit 3: its two exchange buffers
+    case 0: return pass3_io<0, false>(c, s);
+    case 1: return pass3_io<1, false>(c, s);
+    case 2: return pass3_io<0, true>(c, s);
+    default: return pass3_io<1, true>(c, s);
   }
-  const bool row_alt = (c.tile & 1) != 0;
-  const int col = (c.tile >> 1) & 7;   // bit 1: y-pass shape, bit 2: z-pass shape, bit 3: its two buffers
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[0], s, rec_flags)) != cudaSuccess) return e;
-  if ((e = row_alt ? pass1<1>(c, s) : pass1<0>(c, s)) != cudaSuccess) return e;
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[1], s, rec_flags)) != cudaSuccess) return e;
-  switch (col) {
-    case 0: e = columns<0, 0, false>(c, s, rec_flags); break;
-    case 1: e = columns<1, 0, false>(c, s, rec_flags); break;
-    case 2: e = columns<0, 1, false>(c, s, rec_flags); break;
-    case 3: e = columns<1, 1, false>(c, s, rec_flags); break;
-    case 4: e = columns<0, 0, true>(c, s, rec_flags); break;
-    case 5: e = columns<1, 0, true>(c, s, rec_flags); break;
-    case 6: e = columns<0, 1, true>(c, s, rec_flags); break;
-    default: e = columns<1, 1, true>(c, s, rec_flags); break;
-  }
-  if (e != cudaSuccess) return e;
-  if (c.ev && (e = cudaEventRecordWithFlags(c.ev[4], s, rec_flags)) != cudaSuccess) return e;
-  if ((e = row_alt ? pass5<1>(c, s) : pass5<0>(c, s)) != cudaSuccess) return e;
-  if (c.ev) e = cudaEventRecordWithFlags(c.ev[5], s, rec_flags);
-  if (c.launches) *c.launches += 5;
-  return e;
 }

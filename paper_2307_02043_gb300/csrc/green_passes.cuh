@@ -1,17 +1,19 @@
 // The five passes of the pruned, zero-padded Green's convolution
-// (G v)|_domain = crop_n( IFFT_P( K_hat * FFT_P( pad_P(v) ) ) ),  P = 2n,
-// batched over the illuminations of a mini-batch (grid dimension "b").
+// (G v)|_domain = crop( IFFT_P( K_hat * FFT_P( pad_P(v) ) ) ),  P_d = 2 n_d,
+// batched over the illuminations of a mini-batch (grid dimension "b").  Each
+// pass is compiled for the transform length of its own axis (the template
+// argument P): Px for passes 1 and 5, Py for passes 2 and 4, Pz for pass 3.
 //
 // Layout (complex64, x fastest everywhere):
-//   volume   v [b][z][y][x]              n^3
-//   T1 / T4    [b][z][y][kx]             n*n*P     (after / before the x pass)
-//   T2 / T3    [b][z][ky][kx]            n*P*P     (after / before the y pass)
-//   K_hat octant [fz][fy][fx]            (n+1)^3   (K_hat is even in each axis)
-// Pass 1 (x, rows)    : n*n lines, n nonzero inputs -> P outputs   + fused prologue
-// Pass 2 (y, columns) : n*P columns, n nonzero inputs -> P outputs
-// Pass 3 (z, columns) : P*P columns, forward, * K_hat, inverse, n outputs kept
-// Pass 4 (y, columns) : n*P columns, P inputs -> n outputs kept
-// Pass 5 (x, rows)    : n*n lines, P inputs -> n outputs kept      + fused epilogue
+//   volume   v [b][z][y][x]              nz*ny*nx
+//   T1 / T4    [b][z][y][kx]             nz*ny*Px   (after / before the x pass)
+//   T2 / T3    [b][z][ky][kx]            nz*Py*Px   (after / before the y pass)
+//   K_hat octant [fz][fy][fx]            (nz+1)(ny+1)(nx+1) (K_hat is even in each axis)
+// Pass 1 (x, rows)    : ny*nz lines, nx nonzero inputs -> Px outputs   + fused prologue
+// Pass 2 (y, columns) : nz*Px columns, ny nonzero inputs -> Py outputs
+// Pass 3 (z, columns) : Py*Px columns, forward, * K_hat, inverse, nz outputs kept
+// Pass 4 (y, columns) : nz*Px columns, Py inputs -> ny outputs kept
+// Pass 5 (x, rows)    : ny*nz lines, Px inputs -> nx outputs kept      + fused epilogue
 // Zero rows of the padding are never read and cropped outputs never written.
 // The 1/P^3 of the inverse transform is folded into K_hat.
 #pragma once
@@ -119,7 +121,7 @@ MQ_D void load_twiddle_table(float2* tw, const float2* __restrict__ twg) {
 // ------------------------------------------------------- pass 1: x forward
 template <int P, int RV, class Pro>
 __global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
-k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
+k_pass1(Pro pro, float2* __restrict__ T1, int ny, int nyz, const float2* __restrict__ twg,
         const KState* __restrict__ st, double* __restrict__ partials, int line0, int nlines) {
   using PL = Plan<P>;
   using SH = RowShape<P, RV>;
@@ -135,7 +137,7 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
   const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
   const int line = line0 + blockIdx.x * SH::LPB + l;   // rows [line0, line0 + nlines) of [z][y]
   const bool valid = line < line0 + nlines;
-  const int z = line / n, y = line - (line / n) * n;
+  const int z = line / ny, y = line - (line / ny) * ny;
   float2* exl = ex + l * SH::PER_LINE;
   Parts<Pro::NPART> parts;
   parts.zero();
@@ -164,7 +166,7 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
     for (int n2 = 0; n2 < R2; ++n2) a[n2] = exl[n2 * SH::PITCH + k1];
     dft<R2, false>(a);
     if (valid) {
-      float2* o = T1 + ((size_t)b * n * n + line) * P;
+      float2* o = T1 + ((size_t)b * nyz + line) * P;
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = a[k2];
     }
@@ -175,7 +177,7 @@ k_pass1(Pro pro, float2* __restrict__ T1, int n, const float2* __restrict__ twg,
 // ------------------------------------------------------- pass 5: x inverse
 template <int P, int RV, class Epi>
 __global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
-k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict__ twg,
+k_pass5(Epi epi, const float2* __restrict__ T4, int ny, int nyz, const float2* __restrict__ twg,
         const KState* __restrict__ st, double* __restrict__ partials, int line0, int nlines) {
   using PL = Plan<P>;
   using SH = RowShape<P, RV>;
@@ -190,9 +192,9 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
   const int l = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
   const int line = line0 + blockIdx.x * SH::LPB + l;   // rows [line0, line0 + nlines) of [z][y]
   const bool valid = line < line0 + nlines;
-  const int z = line / n, y = line - (line / n) * n;
+  const int z = line / ny, y = line - (line / ny) * ny;
   float2* exl = ex + l * SH::PER_LINE;
-  const float2* src = T4 + ((size_t)b * n * n + (valid ? line : line0)) * P;
+  const float2* src = T4 + ((size_t)b * nyz + (valid ? line : line0)) * P;
   Parts<Epi::NPART> parts;
   parts.zero();
   __syncthreads();
@@ -225,11 +227,12 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int n, const float2* __restrict_
 }
 
 // ------------------------------------------------- passes 2 and 4: y columns
-// INV = false: T1 [b][z][y < n][kx] -> T2 [b][z][ky < P][kx]
-// INV = true : T3 [b][z][ky < P][kx] -> T4 [b][z][y < n][kx]
+// P = Py; rows of px = Px values (the x pass's output pitch).
+// INV = false: T1 [b][z][y < ny][kx] -> T2 [b][z][ky < P][kx]
+// INV = true : T3 [b][z][ky < P][kx] -> T4 [b][z][y < ny][kx]
 template <int P, int CV, bool INV>
 __global__ void __launch_bounds__(ColShape<P, CV>::THREADS)
-k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
+k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int nz, int px,
          const float2* __restrict__ twg, const KState* __restrict__ st, int z0) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
@@ -243,10 +246,11 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
   load_twiddle_table<P>(tw, twg);
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
   const int kx = blockIdx.x * C + c;
+  const bool kv = kx < px;         // the last column tile may reach past Px
   const int z = z0 + blockIdx.y;   // planes [z0, z0 + gridDim.y)
-  const int len_in = INV ? P : n, len_out = INV ? n : P;
-  const float2* src = in + ((size_t)b * n + z) * len_in * P + kx;
-  float2* dst = out + ((size_t)b * n + z) * len_out * P + kx;
+  constexpr int len_in = INV ? P : P / 2, len_out = INV ? P / 2 : P;
+  const float2* src = in + ((size_t)b * nz + z) * len_in * px + kx;
+  float2* dst = out + ((size_t)b * nz + z) * len_out * px + kx;
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < I1; ++i) {
@@ -256,7 +260,7 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       a[n1] = make_float2(0.f, 0.f);
-      if (INV || n1 < R1 / 2) a[n1] = src[(size_t)(R2 * n1 + n2) * P];
+      if ((INV || n1 < R1 / 2) && kv) a[n1] = src[(size_t)(R2 * n1 + n2) * px];
     }
     dft<R1, INV, INV ? R1 : R1 / 2>(a);
 #pragma unroll
@@ -274,8 +278,10 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int n,
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) a[n2] = ex[(n2 * R1 + k1) * C + c];
     dft<R2, INV>(a);
+    if (kv) {
 #pragma unroll
-    for (int k2 = 0; k2 < (INV ? R2 / 2 : R2); ++k2) dst[(size_t)(k1 + R1 * k2) * P] = a[k2];
+      for (int k2 = 0; k2 < (INV ? R2 / 2 : R2); ++k2) dst[(size_t)(k1 + R1 * k2) * px] = a[k2];
+    }
   }
 }
 
@@ -338,8 +344,8 @@ struct Pass3Occ {
 
 template <int P, int CV, bool DB, bool CONJ, int IO = IO_FULL>
 __global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB, IO>::MIN_BLOCKS)
-k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int n,
-        int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
+k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int nx,
+        int ny, int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
   using SM = Pass3Smem<P, CV, DB, IO>;
@@ -355,12 +361,16 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   float2* ex = reinterpret_cast<float2*>(sm + SM::ex_off());
   float2* ex2 = DB ? reinterpret_cast<float2*>(sm + SM::ex2_off()) : ex;   // inverse-stage exchange
   float2* in = reinterpret_cast<float2*>(sm + SM::in_off());
+  constexpr int n = P / 2;   // nz: the z extent of the domain
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::bar_off(n));
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
   const int kx0 = blockIdx.x * C, kx = kx0 + c;
   const int ky = blockIdx.y;
-  const size_t zs = (size_t)P * P;
-  const int m1 = n + 1;
+  const int px = 2 * nx, py = 2 * ny;
+  const bool kv = kx < px;   // the last column tile may reach past Px: those columns are
+                             // zero-filled by the tile load and never stored
+  const size_t zs = (size_t)px * py;
+  const int mx = nx + 1, mxy = (nx + 1) * (ny + 1);   // K_hat octant strides
   const uint32_t tile_bytes = (uint32_t)SM::in_bytes(n);
   unsigned long long act = 0ull;   // active slots as a bit mask (nb <= 64)
   for (int q = 0; q < nb; ++q)
@@ -378,11 +388,11 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   // at compile-time offsets from one base
   load_twiddle_table<P>(tw, twg);
   {
-    const int fx = kx <= n ? kx : P - kx;
-    const int fy = ky <= n ? ky : P - ky;
-    const float2* kcol = khat + (size_t)fy * m1 + fx;
+    const int fx = !kv ? 0 : kx <= nx ? kx : px - kx;
+    const int fy = ky <= ny ? ky : py - ky;
+    const float2* kcol = khat + (size_t)fy * mx + fx;
     for (int fz = t; fz < KH; fz += T) {
-      float2 v = kcol[(size_t)fz * m1 * m1];
+      float2 v = kcol[(size_t)fz * mxy];
       if (CONJ) v.y = -v.y;
       kh[fz * C + c] = v;
     }
@@ -397,7 +407,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       __syncthreads();
       const unsigned long long rest = act & ~((2ull << b) - 1ull);
       next = rest ? __ffsll((long long)rest) - 1 : nb;
-      vplane = T2[((size_t)b * n + (n - 1)) * zs + (size_t)ky * P + kx];
+      vplane = kv ? T2[((size_t)b * n + (n - 1)) * zs + (size_t)ky * px + kx] : make_float2(0.f, 0.f);
     } else {
       if (!mbar_wait_bounded(bar, phase, 1 << 22)) {
         if (threadIdx.x == 0) atomicExch(err, 1);
@@ -490,10 +500,10 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       float2* red = reinterpret_cast<float2*>(sm + SM::red_off(n));
       red[t * C + c] = opart;
       __syncthreads();
-      if (t == 0) {
+      if (t == 0 && kv) {
         float2 x = red[c];
         for (int q = 1; q < T; ++q) x = cadd(x, red[q * C + c]);
-        T2[((size_t)b * n + (n - 1)) * zs + (size_t)ky * P + kx] = x;
+        T2[((size_t)b * n + (n - 1)) * zs + (size_t)ky * px + kx] = x;
       }
       if (next >= nb) break;
       b = next;
@@ -511,7 +521,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
       __syncthreads();
     }
     // inverse stage B (j1-threads): outputs z = j1 + R2 j2 for j2 < R1/2
-    float2* colb = T2 + (size_t)b * n * zs + (size_t)ky * P + kx;
+    float2* colb = T2 + (size_t)b * n * zs + (size_t)ky * px + kx;
 #pragma unroll
     for (int i = 0; i < I1; ++i) {
       const int j1 = t + T * i;
@@ -521,11 +531,13 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) a[k1] = exr[k1 * R2 * C];
       dft<R1, true>(a);
-      float2* col = colb + (size_t)j1 * zs;
+      if (kv) {
+        float2* col = colb + (size_t)j1 * zs;
 #pragma unroll
-      for (int j2 = 0; j2 < R1 / 2; ++j2) {
-        *col = a[j2];
-        col += (size_t)R2 * zs;
+        for (int j2 = 0; j2 < R1 / 2; ++j2) {
+          *col = a[j2];
+          col += (size_t)R2 * zs;
+        }
       }
     }
     // one buffer: ex is free again for the next slot's first stage only after

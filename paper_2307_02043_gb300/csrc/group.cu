@@ -62,7 +62,7 @@ int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, s
     if (!m) return MQNPM_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
       if (members[j] == m) return MQNPM_ERR_INVALID_ARG;   // a member once
-    if (m->n != m0->n || m->h != m0->h || m->kb != m0->kb || m->device != m0->device || m->tile != m0->tile ||
+    if (m->nx != m0->nx || m->ny != m0->ny || m->nz != m0->nz || m->h != m0->h || m->kb != m0->kb || m->device != m0->device || m->tile != m0->tile ||
         m->green_kernel != m0->green_kernel || m->krylov_tol != m0->krylov_tol ||
         m->krylov_maxit != m0->krylov_maxit || m->direct_launches != m0->direct_launches)
       return MQNPM_ERR_INVALID_ARG;
@@ -81,7 +81,9 @@ int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, s
   const double alpha = 1.0;
   mqnpm_config c;
   std::memset(&c, 0, sizeof c);
-  c.n = m0->n;
+  c.nx = m0->nx;
+  c.ny = m0->ny;
+  c.nz = m0->nz;
   c.h = m0->h;
   c.kb = m0->kb;
   c.model = MQNPM_MODEL_LS;
@@ -113,8 +115,8 @@ int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, s
     return rc;
   }
   // the members' spectrum (it may come from a caller's green_hat)
-  const size_t m1 = (size_t)m0->n + 1;
-  cudaError_t e = cudaMemcpyAsync(g->engine->khat, m0->khat, m1 * m1 * m1 * sizeof(float2), cudaMemcpyDeviceToDevice,
+  const size_t nk = (size_t)(m0->nx + 1) * (m0->ny + 1) * (m0->nz + 1);
+  cudaError_t e = cudaMemcpyAsync(g->engine->khat, m0->khat, nk * sizeof(float2), cudaMemcpyDeviceToDevice,
                                   g->engine->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->engine->stream);
   if (e != cudaSuccess) {

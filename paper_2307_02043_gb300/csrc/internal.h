@@ -11,17 +11,19 @@
 
 // One Green's apply over a batch: pass 1 (prologue) ... pass 5 (epilogue).
 struct GreenCall {
-  int n = 0;
+  int nx = 0, ny = 0, nz = 0;  // grid; transform lengths Px = 2 nx, Py = 2 ny, Pz = 2 nz
   int nb = 0;                  // batch slots
   int pro = PRO_PLAIN;
   int epi = EPI_PLAIN;
   bool adjoint = false;        // use conj(K_hat): G^H
   ProArgs pa{};
   EpiArgs ea{};
-  float2* T1 = nullptr;        // [nb][n][n][P]
-  float2* T2 = nullptr;        // [nb][n][P][P]
-  const float2* khat = nullptr;  // octant (n+1)^3, scaled by 1/P^3
-  const float2* tw = nullptr;    // W_P^j, j < P
+  float2* T1 = nullptr;        // [nb][nz][ny][Px]
+  float2* T2 = nullptr;        // [nb][nz][Py][Px]
+  const float2* khat = nullptr;  // octant (nz+1)(ny+1)(nx+1), scaled by 1/(Px Py Pz)
+  const float2* twx = nullptr;   // W_P^j, j < P, for P = Px, Py, Pz
+  const float2* twy = nullptr;
+  const float2* twz = nullptr;
   const KState* st = nullptr;    // slot activity (nullptr: all active)
   double* part_pro = nullptr;    // [nb][ctas1][NPART]
   double* part_epi = nullptr;    // [nb][ctas5][NPART]
@@ -37,9 +39,10 @@ struct GreenCall {
 
 constexpr int MQ_TILES = 16;     // launch-shape variants of the Green's passes
 
-// Tensor map of the pass-3 buffer T2 = [max_batch * n][P][P] complex64, box C x 1 x n
-// with C the column width of the tile's column shape.
-cudaError_t make_t2_tensor_map(void* T2, int n, int max_batch, int tile, void* map_out /* CUtensorMap, 64 B aligned */);
+// Tensor map of the pass-3 buffer T2 = [max_batch * nz][Py][Px] complex64, box C x 1 x nz
+// with C the column width of the tile's z-pass shape.
+cudaError_t make_t2_tensor_map(void* T2, int nx, int ny, int nz, int max_batch, int tile,
+                               void* map_out /* CUtensorMap, 64 B aligned */);
 
 // Per-pass timing (opt-in tracing): events recorded around every Green's apply.
 struct Profiler {
@@ -67,30 +70,36 @@ struct KrylovGraph {
 
 // Number of CTAs pass 1 / pass 5 use per slot (partials layout) for a tile
 // variant; green_row_ctas_max covers every variant.
-int green_row_ctas(int n, int tile);
-int green_row_ctas_max(int n);
-int green_plane_ctas(int n, int tile);     // CTAs per slot of pass 1/5 over one z-plane
-// shape[6] = lines per CTA and threads per line of passes 1/5, columns per
-// CTA and threads per column of passes 2/4, then of pass 3 (zeros if n is
-// unsupported); smem = the largest dynamic shared memory of the tile's passes.
-void green_shape(int n, int tile, int* shape, size_t* smem = nullptr);
-// Whether a tile's passes fit the device's shared memory per block.
-bool green_tile_fits(int n, int tile, int device);
-int green_col_width(int n, int tile);
-bool green_supported(int n);
+int green_row_ctas(int nx, int ny, int nz, int tile);
+int green_row_ctas_max(int nx, int ny, int nz);
+int green_plane_ctas(int nx, int ny, int tile);   // CTAs per slot of pass 1/5 over one z-plane
+// shape[6] = lines per CTA and threads per line of passes 1/5 (length Px),
+// columns per CTA and threads per column of passes 2/4 (Py), then of pass 3
+// (Pz) (zeros if a length is unsupported); smem = the largest dynamic shared
+// memory of the tile's passes.
+void green_shape(int nx, int ny, int nz, int tile, int* shape, size_t* smem = nullptr);
+// Whether a tile's passes fit the device's shared memory per block (the
+// column passes cover kx < Px with a ragged last tile where needed).
+bool green_tile_fits(int nx, int ny, int nz, int tile, int device);
+int green_col_width(int nx, int ny, int nz, int tile);   // columns per CTA of pass 3 (the tensor-map box)
+bool green_supported(int n);                             // 2n is a compiled transform length
 cudaError_t green_launch(const GreenCall& c, cudaStream_t s);
 
-// Per-P entry points (one translation unit each).
-#define MQ_DECL(P)                                                   \
-  cudaError_t green_launch_P##P(const GreenCall& c, cudaStream_t s); \
-  void green_shape_P##P(int tile, int n, int* shape, size_t* smem);
+// Per-P entry points (one translation unit each): the passes along an axis
+// whose transform length is P.
+#define MQ_DECL(P)                                                                         \
+  cudaError_t green_pass1_P##P(const GreenCall& c, cudaStream_t s);                        \
+  cudaError_t green_pass5_P##P(const GreenCall& c, cudaStream_t s);                        \
+  cudaError_t green_passy_P##P(const GreenCall& c, bool inv, cudaStream_t s);              \
+  cudaError_t green_pass3_P##P(const GreenCall& c, cudaStream_t s);                        \
+  void green_shape_P##P(int tile, int* shape, size_t* smem_row, size_t* smem_col, size_t* smem_z);
 MQ_DECL(16) MQ_DECL(24) MQ_DECL(32) MQ_DECL(48) MQ_DECL(64) MQ_DECL(96) MQ_DECL(128)
 MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
 #undef MQ_DECL
 
 // K_hat octant in FP64 by separable even (cosine) sums, rounded to complex64.
-cudaError_t build_khat(int n, double h, double kb, float2* khat_out, cudaStream_t s, int kernel);
-cudaError_t upload_khat(const float* host, int n, float2* khat_out, cudaStream_t s);
+cudaError_t build_khat(int nx, int ny, int nz, double h, double kb, float2* khat_out, cudaStream_t s, int kernel);
+cudaError_t upload_khat(const float* host, int nx, int ny, int nz, float2* khat_out, cudaStream_t s);
 cudaError_t build_khat_scratch(int n, double h, double kb, float2* khat_out, double2* a, double2* b, double* dcos,
                                cudaStream_t s);
 
@@ -144,8 +153,9 @@ struct WproxWork {
 };
 
 struct mqnpm_handle {
-  // problem
-  int n = 0, P = 0, M = 0, model = 1, L = 0, S = 0, tv = 0, strategy = 1;
+  // problem: an nx x ny x nz grid (transform lengths 2 nx, 2 ny, 2 nz), M = nx ny detector values
+  int nx = 0, ny = 0, nz = 0, M = 0, model = 1, L = 0, S = 0, tv = 0, strategy = 1;
+  int3 dims() const { return make_int3(nx, ny, nz); }
   size_t N = 0;
   double h = 1.0, kb = 0.0, lambda = 0.0, lo = 0.0, hi = 0.0, a = 1.0, gamma = 0.8, tau_max = 0.0;
   double delta1 = 1e-8, delta2 = 1e-12, krylov_tol = 1e-6, newton_tol = 1e-6;
@@ -165,9 +175,10 @@ struct mqnpm_handle {
   unsigned char** guard_ptr = nullptr;            // device table of the bands (check kernel)
   int* guard_bad = nullptr;                       // device flags, one per band
   // device tables
-  float2 *khat = nullptr, *tw = nullptr, *tab = nullptr, *ymeas = nullptr;
+  float2 *khat = nullptr, *tab = nullptr, *ymeas = nullptr;
+  float2 *twx = nullptr, *twy = nullptr, *twz = nullptr;   // W_P^j per axis (P = 2 nx, 2 ny, 2 nz)
   bool remote = false;                    // detector behind an angular-spectrum propagation
-  float2 *twn = nullptr, *Hdet = nullptr;  // W_n^j (n) and H / n^2 ([ky][kx], M)
+  float2 *twn = nullptr, *Hdet = nullptr;  // W_nx^j (nx), then W_ny^j (ny); H / (nx ny) ([ky][kx], M)
   bool have_meas = false;
   Workspace w;
   WproxWork wp;

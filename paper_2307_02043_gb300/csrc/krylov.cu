@@ -204,13 +204,15 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle cond, const int* nactive,
   cudaGraphSetConditional(cond, (*nactive > 0 && done < cap) ? 1u : 0u);
 }
 
-MQ_D float2 incident_at(const float2* tab, int l, int n, size_t i) {
-  const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((size_t)n * n));
-  const float2* t = tab + (size_t)l * 3 * n;
-  return cmul(cmul(t[x], t[n + y]), t[2 * n + z]);
+// u_in of illumination l at voxel i of an nx x ny x nz grid (d = (nx, ny, nz));
+// axis tables [l][nx + ny + nz].
+MQ_D float2 incident_at(const float2* tab, int l, int3 d, size_t i) {
+  const int x = (int)(i % d.x), y = (int)((i / d.x) % d.y), z = (int)(i / ((size_t)d.x * d.y));
+  const float2* t = tab + (size_t)l * (d.x + d.y + d.z);
+  return cmul(cmul(t[x], t[d.x + y]), t[d.x + d.y + z]);
 }
 
-__global__ void k_init_uin(float2* u, const float2* tab, const int* illum, int n, size_t N) {
+__global__ void k_init_uin(float2* u, const float2* tab, const int* illum, int3 n, size_t N) {
   const int b = blockIdx.y;
   const int l = illum[b];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
@@ -219,7 +221,7 @@ __global__ void k_init_uin(float2* u, const float2* tab, const int* illum, int n
 
 // Start fields of a warm-started forward solve: the field stored for the
 // slot's illumination where there is one (fwarm[b]), else u_in.
-__global__ void k_init_u_warm(float2* u, float2* const* fwarm, const float2* tab, const int* illum, int n, size_t N) {
+__global__ void k_init_u_warm(float2* u, float2* const* fwarm, const float2* tab, const int* illum, int3 n, size_t N) {
   const int b = blockIdx.y;
   const int l = illum[b];
   const float2* src = fwarm[b];
@@ -239,11 +241,11 @@ __global__ void k_store_field(float2* const* fstore, const float2* __restrict__ 
 
 // Detector of the LS field: usc = (u - u_in) on z = n-1; r_det = usc - y (or usc if y == NULL).
 __global__ void k_detect_ls(const float2* u, const float2* tab, const int* illum, const float2* ymeas,
-                            float2* out, int n, size_t N, double* part) {
+                            float2* out, int3 n, size_t N, double* part) {
   const int b = blockIdx.y;
   const int l = illum[b];
-  const size_t M = (size_t)n * n;
-  const size_t base = (size_t)(n - 1) * M;
+  const size_t M = (size_t)n.x * n.y;
+  const size_t base = (size_t)(n.z - 1) * M;
   float acc = 0.f;
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < M; j += (size_t)gridDim.x * blockDim.x) {
     const size_t i = base + j;
@@ -261,7 +263,7 @@ __global__ void k_detect_ls(const float2* u, const float2* tab, const int* illum
 
 // grad[i] (+)= scale * sum_b Re(conj(u_b[i]) z_b[i]); u_b = u_in(l_b) when u == NULL (Born).
 __global__ void k_grad(const float2* __restrict__ u, const float2* __restrict__ zsol, const float2* tab,
-                       const int* illum, int nb, int n, size_t N, float scale, float* grad, int accumulate) {
+                       const int* illum, int nb, int3 n, size_t N, float scale, float* grad, int accumulate) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
     for (int b = 0; b < nb; ++b) {
@@ -278,7 +280,7 @@ __global__ void k_grad(const float2* __restrict__ u, const float2* __restrict__ 
 // seg.grad[i] (+)= seg.scale * sum_{b in [b0, b1)} Re(conj(u_b[i]) z_b[i]),
 // u_b = u_in(l_b) when u == NULL (Born).
 __global__ void k_grad_seg(const float2* __restrict__ u, const float2* __restrict__ zsol, const float2* tab,
-                           const int* illum, int n, size_t N, const GradSeg* segs) {
+                           const int* illum, int3 n, size_t N, const GradSeg* segs) {
   const GradSeg sg = segs[blockIdx.y];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
@@ -369,13 +371,17 @@ cudaError_t glaunch(mqnpm_handle* h, GreenCall c, cudaStream_t s) {
 
 GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
   GreenCall c;
-  c.n = h->n;
+  c.nx = h->nx;
+  c.ny = h->ny;
+  c.nz = h->nz;
   c.nb = nb;
   c.adjoint = adjoint;
   c.T1 = h->w.T1;
   c.T2 = h->w.T2;
   c.khat = h->khat;
-  c.tw = h->tw;
+  c.twx = h->twx;
+  c.twy = h->twy;
+  c.twz = h->twz;
   c.st = nullptr;
   c.part_pro = h->w.part1;
   c.part_epi = h->w.part5;
@@ -610,7 +616,7 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool s
   c.pa.xs = x ? nullptr : w.xslot;
   if (warm) {
     // warm start: u_0 = the stored field (or u_in), r_0 = u_in - u_0 + G(x u_0)
-    k_init_u_warm<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, w.fwarm, h->tab, w.illum, h->n, N);
+    k_init_u_warm<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, w.fwarm, h->tab, w.illum, h->dims(), N);
     c.pro = PRO_CONTRAST;
     c.pa.x = x;
     c.pa.q = w.u;
@@ -619,7 +625,7 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool s
     c.ea.tab = h->tab;
     c.ea.illum = w.illum;
   } else {
-    k_init_uin<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->tab, w.illum, h->n, N);
+    k_init_uin<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, h->tab, w.illum, h->dims(), N);
     c.pro = PRO_BORN;                    // r_0 = u_in - A u_in = G(x u_in)
     c.pa.x = x;
     c.pa.tab = h->tab;
@@ -736,7 +742,7 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
     if (rc != MQNPM_OK) worst = rc;
     k_detect_ls<<<dim3(w.ctas_row, m), 256, 0, s>>>(w.u, h->tab, w.illum, h->remote ? nullptr : ym, det_out,
-                                                     h->n, N, w.partd);
+                                                     h->dims(), N, w.partd);
   } else {
     GreenCall c = base_call(h, m, false);
     c.pro = PRO_BORN;
@@ -751,7 +757,7 @@ int chunk_forward(mqnpm_handle* h, const float* x, int m, int* it_chunk, float2*
     c.ea.illum = w.illum;
     c.part_epi = w.partd;
     CK(glaunch(h, c, s));
-    parts = m * green_plane_ctas(h->n, h->tile);   // the plane pass 5 writes fewer partials
+    parts = m * green_plane_ctas(h->nx, h->ny, h->tile);   // the plane pass 5 writes fewer partials
   }
   CK(cudaGetLastError());
   if (h->remote) {                     // D(slice) - y; the partials are rewritten per row CTA
@@ -782,7 +788,7 @@ int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, int nse
     int rc = adjoint_ls(h, m, x, it_chunk, 2, 1);
     if (rc == MQNPM_ERR_CUDA || rc == MQNPM_ERR_NONFINITE) return rc;
     if (rc != MQNPM_OK) worst = rc;
-    k_grad_seg<<<dim3(w.ctas_vec, nseg), 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, h->n, N, w.segs);
+    k_grad_seg<<<dim3(w.ctas_vec, nseg), 256, 0, s>>>(w.u, w.zs, h->tab, w.illum, h->dims(), N, w.segs);
   } else {
     GreenCall c = base_call(h, m, true);
     c.pro = PRO_LIFT;
@@ -795,7 +801,7 @@ int chunk_adjoint(mqnpm_handle* h, const float* x, int m, int* it_chunk, int nse
     c.epi = EPI_PLAIN;
     c.ea.out = w.zs;
     CK(glaunch(h, c, s));
-    k_grad_seg<<<dim3(w.ctas_vec, nseg), 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, h->n, N, w.segs);
+    k_grad_seg<<<dim3(w.ctas_vec, nseg), 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, h->dims(), N, w.segs);
   }
   CK(cudaGetLastError());
   h->launches += 1;
@@ -935,7 +941,7 @@ int lipschitz_impl(mqnpm_handle* h, const int* illum, int nb, double scale, cons
       c2.epi = EPI_PLAIN;
       c2.ea.out = w.zs;
       CK(glaunch(h, c2, s));
-      k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->n, N, (float)scale, a, c0 > 0);
+      k_grad<<<w.ctas_vec, 256, 0, s>>>(nullptr, w.zs, h->tab, w.illum, m, h->dims(), N, (float)scale, a, c0 > 0);
       CK(cudaGetLastError());
     }
     CK(vec_reduce(h, 0, q, nullptr, a, nullptr, d3));   // <q,q>, <q,a>, <a,a>

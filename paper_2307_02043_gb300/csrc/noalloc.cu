@@ -37,7 +37,7 @@ constexpr size_t NA_KH = na_align(NA_T2 + (size_t)NA_MAX_N * NA_MAX_P * NA_MAX_P
 constexpr size_t NA_KA = na_align(NA_KH + NA_M1 * NA_M1 * NA_M1 * sizeof(float2));
 constexpr size_t NA_KB = na_align(NA_KA + NA_M1 * NA_M1 * NA_M1 * sizeof(double2));
 constexpr size_t NA_COS = na_align(NA_KB + NA_M1 * NA_M1 * NA_M1 * sizeof(double2));
-constexpr size_t NA_TW = na_align(NA_COS + NA_MAX_P * sizeof(double));
+constexpr size_t NA_TW = na_align(NA_COS + 3 * NA_MAX_P * sizeof(double));   // one cosine table per axis
 constexpr size_t NA_ERR = na_align(NA_TW + NA_MAX_P * sizeof(float2));
 constexpr size_t NA_BYTES = na_align(NA_ERR + sizeof(int));
 
@@ -128,14 +128,14 @@ extern "C" int mqnpm_green_apply_noalloc(int n, double h, double kb, const float
         build_khat_scratch(n, h, kb, khat, reinterpret_cast<double2*>(d.base + NA_KA),
                            reinterpret_cast<double2*>(d.base + NA_KB), reinterpret_cast<double*>(d.base + NA_COS),
                            s) != cudaSuccess ||
-        make_t2_tensor_map(T2, n, 1, 0, d.tmap) != cudaSuccess)
+        make_t2_tensor_map(T2, n, n, n, 1, 0, d.tmap) != cudaSuccess)
       return MQNPM_ERR_CUDA;
     d.n = n;
     d.h = h;
     d.kb = kb;
   }
   GreenCall c;
-  c.n = n;
+  c.nx = c.ny = c.nz = n;
   c.nb = 1;
   c.adjoint = adjoint != 0;
   c.pro = PRO_PLAIN;
@@ -145,7 +145,7 @@ extern "C" int mqnpm_green_apply_noalloc(int n, double h, double kb, const float
   c.T1 = T1;
   c.T2 = T2;
   c.khat = khat;
-  c.tw = tw;
+  c.twx = c.twy = c.twz = tw;
   c.tmap = d.tmap;
   c.err = err;
   if (green_launch(c, s) != cudaSuccess) return MQNPM_ERR_CUDA;

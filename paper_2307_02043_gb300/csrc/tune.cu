@@ -8,8 +8,9 @@
 // input: the passes do the same work for any values), round-robin over two
 // rounds after one warm-up round so that clock ramp-up does not favour a late
 // candidate, and keeps the tile with the smallest best time.  The choice is
-// cached per (device, n, slots) for the life of the process, so handles of the
-// same shape are not re-timed.
+// cached per (device, grid, slots) for the life of the process, so handles of
+// the same shape are not re-timed.  Tiles whose shared memory does not fit
+// are skipped.
 #include <array>
 #include <map>
 #include <mutex>
@@ -20,7 +21,7 @@
 
 namespace {
 std::mutex g_mu;
-std::map<std::tuple<int, int, int>, std::array<double, MQ_TILES>> g_cache;
+std::map<std::tuple<int, int, int, int, int>, std::array<double, MQ_TILES>> g_cache;
 
 // Fastest timed tile; tiles whose shared memory does not fit carry -1.
 int pick(const std::array<double, MQ_TILES>& ms) {
@@ -34,7 +35,7 @@ int pick(const std::array<double, MQ_TILES>& ms) {
 int autotune_tile(mqnpm_handle* h) {
   Workspace& w = h->w;
   const int nb = h->max_batch < 8 ? h->max_batch : 8;
-  const auto key = std::make_tuple(h->device, h->n, nb);
+  const auto key = std::make_tuple(h->device, h->nx, h->ny, h->nz, nb);
   std::array<double, MQ_TILES> ms{};
   bool cached = false;
   {
@@ -51,7 +52,9 @@ int autotune_tile(mqnpm_handle* h) {
     if ((e = cudaMemsetAsync(w.u, 0, (size_t)nb * h->N * sizeof(float2), s)) != cudaSuccess)
       return set_cuda_error(h, e, "autotune: input");
     GreenCall c;
-    c.n = h->n;
+    c.nx = h->nx;
+    c.ny = h->ny;
+    c.nz = h->nz;
     c.nb = nb;
     c.pro = PRO_PLAIN;
     c.pa.q = w.u;
@@ -60,14 +63,18 @@ int autotune_tile(mqnpm_handle* h) {
     c.T1 = w.T1;
     c.T2 = w.T2;
     c.khat = h->khat;
-    c.tw = h->tw;
+    c.twx = h->twx;
+    c.twy = h->twy;
+    c.twz = h->twz;
     c.part_pro = w.part1;
     c.part_epi = w.part5;
     c.launches = &h->launches;
     c.err = w.gerr;
     alignas(64) unsigned char maps[MQ_TILES][128];
+    bool fits[MQ_TILES];
+    for (int t = 0; t < MQ_TILES; ++t) fits[t] = green_tile_fits(h->nx, h->ny, h->nz, t, h->device);
     for (int t = 0; t < MQ_TILES; ++t)
-      if ((e = make_t2_tensor_map(w.T2, h->n, h->max_batch, t, maps[t])) != cudaSuccess)
+      if (fits[t] && (e = make_t2_tensor_map(w.T2, h->nx, h->ny, h->nz, h->max_batch, t, maps[t])) != cudaSuccess)
         return set_cuda_error(h, e, "autotune: tensor map");
     cudaEvent_t ev[2];
     if ((e = cudaEventCreate(&ev[0])) != cudaSuccess) return set_cuda_error(h, e, "autotune: event");
@@ -76,8 +83,6 @@ int autotune_tile(mqnpm_handle* h) {
       return set_cuda_error(h, e, "autotune: event");
     }
     ms.fill(1e30);
-    bool fits[MQ_TILES];
-    for (int t = 0; t < MQ_TILES; ++t) fits[t] = green_tile_fits(h->n, t, h->device);
     for (int round = 0; round < 3 && e == cudaSuccess; ++round)
       for (int t = 0; t < MQ_TILES && e == cudaSuccess; ++t) {
         if (!fits[t]) continue;
@@ -105,7 +110,7 @@ int autotune_tile(mqnpm_handle* h) {
   }
   for (int t = 0; t < MQ_TILES; ++t) h->tune_ms[t] = ms[t];
   h->tile = pick(ms);
-  if ((e = make_t2_tensor_map(w.T2, h->n, h->max_batch, h->tile, w.t2map)) != cudaSuccess)
+  if ((e = make_t2_tensor_map(w.T2, h->nx, h->ny, h->nz, h->max_batch, h->tile, w.t2map)) != cudaSuccess)
     return set_cuda_error(h, e, "autotune: tensor map");
   return MQNPM_OK;
 }

@@ -12,7 +12,7 @@
 //   X  (U = 0) x = clip(v - (c/tau) d(R))
 //   D  P_j = Proj(R_j + tau/(4 D c) grad x),  R_{j+1} = P_j + mom_j (P_j - P_{j-1})
 // Every streaming loop handles four consecutive voxels per thread with 16-byte
-// loads (the grid edge n is a multiple of 4), so each thread keeps its whole
+// loads (the grid's x edge nx is a multiple of 4), so each thread keeps its whole
 // working set of loads in flight.
 #include <algorithm>
 #include <cmath>
@@ -62,7 +62,7 @@ struct WpArgs {
   int* err;
   double* stat;           // [0] last newton count, [1] max, [2] total, [3] evaluations
   unsigned char* status;  // per voxel: 1 if the last evaluated z was strictly inside the box
-  int n, N, J;
+  int nx, ny, nz, N, J;
   double tau, c;
   double inv_tau, c_tau, c_tau2;   // 1/tau, c/tau, c/tau^2 (FP64 divisions are slow on the device)
   float cdt;                       // (float) c/tau
@@ -243,18 +243,18 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
   return true;
 }
 
-// Coordinates of the first of four voxels i4 = 4 k4 (n is a multiple of 4).
-MQ_D void coords4(int k4, int n, int& x0, int& y, int& z) {
+// Coordinates of the first of four voxels i4 = 4 k4 (nx is a multiple of 4).
+MQ_D void coords4(int k4, int nx, int ny, int& x0, int& y, int& z) {
   const int i4 = 4 * k4;
-  const int r = i4 / n;
-  x0 = i4 - r * n;
-  z = r / n;
-  y = r - z * n;
+  const int r = i4 / nx;
+  x0 = i4 - r * nx;
+  z = r / ny;
+  y = r - z * ny;
 }
 
-// d(R) = sum_d q_d(i - e_d)[i_d >= 1] - q_d(i)[i_d <= n-2] at four voxels.
-MQ_D F4 div4(const float* __restrict__ R, int N, int n, int k4, int x0, int y, int z) {
-  const int n4 = n / 4, nn4 = n * n / 4;
+// d(R) = sum_d q_d(i - e_d)[i_d >= 1] - q_d(i)[i_d <= n_d - 2] at four voxels.
+MQ_D F4 div4(const float* __restrict__ R, int N, int nx, int ny, int nz, int k4, int x0, int y, int z) {
+  const int n4 = nx / 4, nn4 = nx * ny / 4;
   const float* qx = R;
   const float* qy = R + N;
   const float* qz = R + 2 * (size_t)N;
@@ -266,11 +266,11 @@ MQ_D F4 div4(const float* __restrict__ R, int N, int n, int k4, int x0, int y, i
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     float s = (m == 0) ? axm : ax.v[m - 1];
-    if (x0 + m < n - 1) s -= ax.v[m];
+    if (x0 + m < nx - 1) s -= ax.v[m];
     s += aym.v[m];
-    if (y < n - 1) s -= ay.v[m];
+    if (y < ny - 1) s -= ay.v[m];
     s += azm.v[m];
-    if (z < n - 1) s -= az.v[m];
+    if (z < nz - 1) s -= az.v[m];
     d.v[m] = s;
   }
   return d;
@@ -525,7 +525,7 @@ __device__ __noinline__ void pass_gram(Shared<S>* sh) {
 template <int S>
 __device__ __noinline__ void pass_div(Shared<S>* sh, const float* src) {
   const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
-  const int n = a.n, N = a.N, N4 = a.N / 4;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, N = a.N, N4 = a.N / 4;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const float* __restrict__ rs = src;
   float* __restrict__ dout = a.d;
@@ -534,11 +534,11 @@ __device__ __noinline__ void pass_div(Shared<S>* sh, const float* src) {
   for (int s = 0; s < S; ++s) acc[s] = 0.f;
   for (int k4 = tid; k4 < N4; k4 += stride) {
     int x0, y, z;
-    coords4(k4, n, x0, y, z);
+    coords4(k4, nx, ny, x0, y, z);
     F4 u[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) u[s] = F4::ldg(a.U.u[s], k4);   // U is read-only in the kernel
-    const F4 dv = div4(rs, N, n, k4, x0, y, z);
+    const F4 dv = div4(rs, N, nx, ny, nz, k4, x0, y, z);
     dv.store(dout, k4);
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] += dot4(u[s], dv);
@@ -552,13 +552,13 @@ __device__ __noinline__ void pass_div(Shared<S>* sh, const float* src) {
 // ---- phase X (U = 0): x = clip(v - (c/tau) d(src)).
 __device__ __noinline__ void pass_x(const WpArgs* pa, const float* src, float* xw) {
   const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
-  const int n = a.n, N = a.N, N4 = a.N / 4;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, N = a.N, N4 = a.N / 4;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const float cdt = a.cdt;
   for (int k4 = tid; k4 < N4; k4 += stride) {
     int x0, y, z;
-    coords4(k4, n, x0, y, z);
-    const F4 dv = div4(src, N, n, k4, x0, y, z);
+    coords4(k4, nx, ny, x0, y, z);
+    const F4 dv = div4(src, N, nx, ny, nz, k4, x0, y, z);
     const F4 v4 = F4::load(a.v, k4);
     F4 xo;
 #pragma unroll
@@ -707,9 +707,9 @@ __device__ __noinline__ void pass_fixup(Shared<S>* sh, float* xw) {
 template <int TV>
 __device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
   const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
-  const int n = a.n, N = a.N, N4 = a.N / 4;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, N = a.N, N4 = a.N / 4;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const int n4 = n / 4, nn4 = n * n / 4;
+  const int n4 = nx / 4, nn4 = nx * ny / 4;
   const float* __restrict__ xs = a.x;
   float* __restrict__ Rx = a.R;
   float* __restrict__ Ry = a.R + N;
@@ -730,11 +730,11 @@ __device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
       const int k4 = kb + q * stride;
       ok[q] = k4 < N4;
       const int kk = ok[q] ? k4 : kb;
-      coords4(kk, n, x0[q], y[q], z[q]);
+      coords4(kk, nx, ny, x0[q], y[q], z[q]);
       x4[q] = F4::load(xs, kk);
-      xnext[q] = (x0[q] + 4 < n) ? xs[4 * kk + 4] : 0.f;
-      xy[q] = (y[q] < n - 1) ? F4::load(xs, kk + n4) : x4[q];
-      xz[q] = (z[q] < n - 1) ? F4::load(xs, kk + nn4) : x4[q];
+      xnext[q] = (x0[q] + 4 < nx) ? xs[4 * kk + 4] : 0.f;
+      xy[q] = (y[q] < ny - 1) ? F4::load(xs, kk + n4) : x4[q];
+      xz[q] = (z[q] < nz - 1) ? F4::load(xs, kk + nn4) : x4[q];
       rx[q] = F4::load(Rx, kk);
       ry[q] = F4::load(Ry, kk);
       rz[q] = F4::load(Rz, kk);
@@ -747,7 +747,7 @@ __device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const float xn = (m < 3) ? x4[q].v[m + 1] : xnext[q];
-        const float gx = (x0[q] + m < n - 1) ? xn - x4[q].v[m] : 0.f;
+        const float gx = (x0[q] + m < nx - 1) ? xn - x4[q].v[m] : 0.f;
         float px = rx[q].v[m] + step * gx;
         float py = ry[q].v[m] + step * (xy[q].v[m] - x4[q].v[m]);
         float pz = rz[q].v[m] + step * (xz[q].v[m] - x4[q].v[m]);
@@ -994,7 +994,7 @@ cudaError_t wprox_dispatch_high(mqnpm_handle* h, int S, int tv, void* args) {
 int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int S_eff, double c, float* P_warm,
                bool warm, float* x_out) {
   if (S_eff < 0 || S_eff > MQNPM_MAX_S) return set_error(h, MQNPM_ERR_INVALID_ARG, "wprox: S_eff out of range");
-  if (h->n % 4 != 0) return set_error(h, MQNPM_ERR_UNSUPPORTED, "wprox: grid edge must be a multiple of 4");
+  if (h->nx % 4 != 0) return set_error(h, MQNPM_ERR_UNSUPPORTED, "wprox: the x edge of the grid must be a multiple of 4");
   cudaStream_t s = h->stream;
   const size_t N = h->N;
   const int J = h->dual_iters;
@@ -1032,7 +1032,9 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.err = h->wp.err;
   a.stat = h->wp.stat;
   a.status = h->wp.status;
-  a.n = h->n;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
   a.N = (int)N;
   a.J = J;
   a.tau = tau;
