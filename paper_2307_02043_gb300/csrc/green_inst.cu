@@ -84,7 +84,7 @@ template <int CV, bool INV>
 cudaError_t pass_y(const GreenCall& c, const float2* in, float2* out, cudaStream_t s) {
   using CS = ColShape<P, CV>;
   const int px = 2 * c.nx;   // the last column tile may be ragged (kx >= Px masked)
-  auto kern = k_pass_y<P, CV, INV>;
+  auto kern = px == P ? k_pass_y<P, CV, INV, true> : k_pass_y<P, CV, INV, false>;
   cudaError_t e = set_smem(kern, CS::SMEM);
   if (e != cudaSuccess) return e;
   // forward y pass of a plane input, inverse y pass of a plane output: that plane only
@@ -101,7 +101,7 @@ cudaError_t pass3(const GreenCall& c, cudaStream_t s) {
   const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tmap);
   if (tm == nullptr || c.err == nullptr) return cudaErrorInvalidValue;
   const int px = 2 * c.nx, py = 2 * c.ny;   // the last column tile may be ragged (kx >= Px masked)
-  auto kern = k_pass3<P, CV, DB, CONJ, IO>;
+  auto kern = (px == P && py == P) ? k_pass3<P, CV, DB, CONJ, IO, true> : k_pass3<P, CV, DB, CONJ, IO, false>;
   const int smem = (int)Pass3Smem<P, CV, DB, IO>::bytes(c.nz);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;

@@ -79,6 +79,17 @@ struct ColShape : ColBase<P> {
   static constexpr int SMEM = (P + P * C) * 8;
 };
 
+// Co-resident CTAs per SM the x-forward pass is compiled for where its CTA
+// has 256 threads and the length is at most 256: five, i.e. at most 48
+// registers per thread, the occupancy this HBM-bound pass needs to keep its
+// loads in flight (spill-free by ptxas; the other shapes and the x-inverse
+// pass with its BiCGSTAB epilogues would spill under the cap and are left
+// unbounded).
+template <int P, int THREADS>
+struct StreamOcc {
+  static constexpr int MINB = (P <= 256 && THREADS == 256) ? 5 : 1;
+};
+
 // Per-thread FP32 partial sums, reduced per CTA into FP64 partials.
 template <int K>
 struct Parts {
@@ -120,7 +131,7 @@ MQ_D void load_twiddle_table(float2* tw, const float2* __restrict__ twg) {
 
 // ------------------------------------------------------- pass 1: x forward
 template <int P, int RV, class Pro>
-__global__ void __launch_bounds__(RowShape<P, RV>::THREADS)
+__global__ void __launch_bounds__(RowShape<P, RV>::THREADS, StreamOcc<P, RowShape<P, RV>::THREADS>::MINB)
 k_pass1(Pro pro, float2* __restrict__ T1, int ny, int nyz, const float2* __restrict__ twg,
         const KState* __restrict__ st, double* __restrict__ partials, int line0, int nlines) {
   using PL = Plan<P>;
@@ -227,12 +238,14 @@ k_pass5(Epi epi, const float2* __restrict__ T4, int ny, int nyz, const float2* _
 }
 
 // ------------------------------------------------- passes 2 and 4: y columns
-// P = Py; rows of px = Px values (the x pass's output pitch).
+// P = Py; rows of px = Px values (the x pass's output pitch).  SQ: Px = Py,
+// so the row pitch is the compile-time P and the column loads and stores take
+// immediate offsets from one base (the cube's case).
 // INV = false: T1 [b][z][y < ny][kx] -> T2 [b][z][ky < P][kx]
 // INV = true : T3 [b][z][ky < P][kx] -> T4 [b][z][y < ny][kx]
-template <int P, int CV, bool INV>
+template <int P, int CV, bool INV, bool SQ>
 __global__ void __launch_bounds__(ColShape<P, CV>::THREADS)
-k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int nz, int px,
+k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int nz, int px_arg,
          const float2* __restrict__ twg, const KState* __restrict__ st, int z0) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
@@ -244,9 +257,10 @@ k_pass_y(const float2* __restrict__ in, float2* __restrict__ out, int nz, int px
   const int b = blockIdx.z;
   if (!slot_active(st, b)) return;
   load_twiddle_table<P>(tw, twg);
+  const int px = SQ ? P : px_arg;
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
   const int kx = blockIdx.x * C + c;
-  const bool kv = kx < px;         // the last column tile may reach past Px
+  const bool kv = SQ || kx < px;   // the last column tile may reach past Px
   const int z = z0 + blockIdx.y;   // planes [z0, z0 + gridDim.y)
   constexpr int len_in = INV ? P : P / 2, len_out = INV ? P / 2 : P;
   const float2* src = in + ((size_t)b * nz + z) * len_in * px + kx;
@@ -342,10 +356,12 @@ struct Pass3Occ {
                                     : (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
-template <int P, int CV, bool DB, bool CONJ, int IO = IO_FULL>
+// SQ: a cubic grid (Px = Py = Pz = P), whose strides and K_hat folds are
+// compile-time constants; otherwise nx, ny (and so Px, Py) come at run time.
+template <int P, int CV, bool DB, bool CONJ, int IO = IO_FULL, bool SQ = true>
 __global__ void __launch_bounds__(ColShape<P, CV>::THREADS, Pass3Occ<P, CV, DB, IO>::MIN_BLOCKS)
-k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int nx,
-        int ny, int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
+k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const float2* __restrict__ khat, int nx_arg,
+        int ny_arg, int nb, const float2* __restrict__ twg, const KState* __restrict__ st, int* __restrict__ err) {
   using PL = Plan<P>;
   using SH = ColShape<P, CV>;
   using SM = Pass3Smem<P, CV, DB, IO>;
@@ -364,11 +380,12 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   constexpr int n = P / 2;   // nz: the z extent of the domain
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::bar_off(n));
   const int t = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
+  const int nx = SQ ? P / 2 : nx_arg, ny = SQ ? P / 2 : ny_arg;
   const int kx0 = blockIdx.x * C, kx = kx0 + c;
   const int ky = blockIdx.y;
   const int px = 2 * nx, py = 2 * ny;
-  const bool kv = kx < px;   // the last column tile may reach past Px: those columns are
-                             // zero-filled by the tile load and never stored
+  const bool kv = SQ || kx < px;   // the last column tile may reach past Px: those columns
+                                   // are zero-filled by the tile load and never stored
   const size_t zs = (size_t)px * py;
   const int mx = nx + 1, mxy = (nx + 1) * (ny + 1);   // K_hat octant strides
   const uint32_t tile_bytes = (uint32_t)SM::in_bytes(n);
