@@ -189,7 +189,7 @@ def subset_of(w):
     return so
 
 
-def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, l2_persist=True):
+def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1):
     """Synthetic measurements and alpha_s, produced with the library itself."""
     kd = synth.illumination_dirs(w)
     so = subset_of(w)
@@ -211,7 +211,7 @@ def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, l2_persist=True)
     start = torch.from_numpy(synth.power_start(w).astype(np.float32)).to(dev).reshape(-1)
     alpha = [setup.lipschitz(list(s), w.S / w.L, start, iters=10) for s in subs]
     setup.close()
-    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, l2_persist=l2_persist, **common)
+    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, **common)
     h.set_measurements(y.reshape(-1))
     return h, y, alpha, kd, so, subs
 
@@ -359,7 +359,7 @@ def prox_only(args, torch, binding):
     w = synth.workload(args.workload)
     dev = torch.device("cuda", 0)
     h = binding.MQNPM(w.n, synth.illumination_dirs(w), subset_of(w), [1.0] * w.S, tv=w.tv, lam=w.lam,
-                      box=w.box, dual_iters=w.dual_iters, max_batch=1, l2_persist=not args.no_l2_persist)
+                      box=w.box, dual_iters=w.dual_iters, max_batch=1)
     g = torch.Generator(device=dev).manual_seed(0)
     x_true = torch.from_numpy(synth.phantom(w).astype(np.float32)).to(dev).reshape(-1)
     v = x_true + 0.01 * torch.randn(w.N, device=dev, generator=g)
@@ -757,8 +757,7 @@ def cpu_ls32_end_to_end(outer: int = 10):
 def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=True):
     """Set-up, timed MQNPM iterations (inputs resident in HBM), the end-to-end
     repeat through host buffers and the per-kernel figures of one workload."""
-    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile,
-                                             l2_persist=not getattr(args, "no_l2_persist", False))
+    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile)
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
     shard = bool(getattr(args, "shard", False))
     if shard:
@@ -938,8 +937,6 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-born", action="store_true", help="skip the born128 figures of the default line")
-    ap.add_argument("--no-l2-persist", action="store_true",
-                    help="no L2 access-policy window for the metric rows during the proximal mapping")
     ap.add_argument("--shard", action="store_true",
                     help="one reconstruction with each subset's illuminations split over the ranks and the gradient "
                          "summed by an all-reduce (strong scaling) instead of one replica per rank")

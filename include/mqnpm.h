@@ -145,14 +145,6 @@ typedef struct mqnpm_config {
                               ignored when green_hat is given. The truncated
                               kernel's construction at create holds two
                               (2n+1)^3 FP64 complex buffers for its duration */
-  int l2_persist;          /* 1: during each weighted proximal mapping the rows
-                              of U (re-read by every dual iteration) are kept
-                              in L2 as persisting lines (an access-policy
-                              window on the prox launch; create raises the
-                              context's persisting-L2 limit to the S x N floats
-                              of U, capped by the device, and never lowers it;
-                              the lines are reset to normal after each prox);
-                              0: no L2 policy                                 */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;

@@ -290,7 +290,6 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->guard = (cfg->guard_bytes + 255) / 256 * 256;
   if (cfg->barrier_wait_cycles > 0) h->barrier_limit = cfg->barrier_wait_cycles;
   h->green_kernel = cfg->green_kernel;
-  const int want_l2 = cfg->l2_persist;
   h->kdir.assign(cfg->kdir, cfg->kdir + 3 * cfg->L);
   h->alpha.assign(cfg->alpha, cfg->alpha + cfg->S);
   h->subset_of.assign(cfg->subset_of, cfg->subset_of + cfg->L);
@@ -501,23 +500,6 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   h->has_u.assign(h->S, 0);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { set_cuda_error(h, e, "create sync"); return fail(MQNPM_ERR_CUDA); }
   if (cfg->tile < 0 && (rc = autotune_tile(h)) != MQNPM_OK) return fail(rc);
-  if (want_l2) {
-    // L2 set-aside for the metric rows U during the prox: the context's
-    // persisting-L2 limit is raised to S x N floats (capped by the device), never lowered
-    int max_persist = 0, max_window = 0;
-    size_t cur = 0;
-    if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h->device) == cudaSuccess &&
-        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, h->device) == cudaSuccess &&
-        max_persist > 0 && max_window > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
-      const size_t want = std::min((size_t)max_persist, (size_t)h->S * N * sizeof(float));
-      if (cur < want && (e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want)) != cudaSuccess) {
-        set_cuda_error(h, e, "persisting L2 limit");
-        return fail(MQNPM_ERR_CUDA);
-      }
-      h->l2_persist_bytes = std::max(cur, want);
-      h->l2_window_max = (size_t)max_window;
-    }
-  }
   w.ctas_row = green_row_ctas(nx, ny, nz, h->tile);
   *out = h;
   return MQNPM_OK;

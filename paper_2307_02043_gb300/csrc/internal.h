@@ -163,8 +163,6 @@ struct mqnpm_handle {
   int check_every = 1;
   long long barrier_limit = 4000000000LL;   // grid-barrier wait of the prox kernel, SM cycles
   int green_kernel = 0;                      // MQNPM_KERNEL_SAMPLED or MQNPM_KERNEL_TRUNCATED
-  size_t l2_persist_bytes = 0;               // L2 set-aside for U during the prox (0: no window)
-  size_t l2_window_max = 0;                  // largest access-policy window of the device
   std::vector<double> kdir, alpha;
   std::vector<int> subset_of, draws;
   std::vector<std::vector<int>> subsets;

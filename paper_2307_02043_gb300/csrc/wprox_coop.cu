@@ -72,9 +72,6 @@ struct WpArgs {
   long long limit;
   long long* trace;       // optional: (phase tag, ns) after every barrier, recorded by block 0
   int trace_cap;
-  const float* l2_window_base;   // host-side launch policy: rows of U kept in L2 (0 bytes: none)
-  size_t l2_window_bytes;
-  float l2_hit_ratio;
 };
 
 MQ_D float clampf(float a, float lo, float hi) { return fminf(fmaxf(a, lo), hi); }
@@ -938,29 +935,8 @@ cudaError_t launch_wprox(mqnpm_handle* h, WpArgs& a) {
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   const int blocks = h->wp.nsm * std::min(per_sm, WP_BPS);
   if (blocks > WP_GS * WP_MAXG) return cudaErrorInvalidConfiguration;
-  // cooperative launch; with a window, the metric rows U (re-read by every
-  // phase of every dual iteration) are held in the L2 set-aside as persisting
-  // lines, the other vectors stream through the rest of the L2
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(WP_THREADS);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = h->stream;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (a.l2_window_bytes > 0) {
-    attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[1].val.accessPolicyWindow.base_ptr = const_cast<float*>(a.l2_window_base);
-    attr[1].val.accessPolicyWindow.num_bytes = a.l2_window_bytes;
-    attr[1].val.accessPolicyWindow.hitRatio = a.l2_hit_ratio;
-    attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    cfg.numAttrs = 2;
-  }
-  return cudaLaunchKernelEx(&cfg, k_wprox<S, TV>, a);
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((void*)k_wprox<S, TV>, dim3(blocks), dim3(WP_THREADS), args, 0, h->stream);
 }
 
 #ifdef MQ_WP_HIGH
@@ -1075,22 +1051,6 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.limit = h->barrier_limit;   // per wait (default about 2 s at 2 GHz)
   a.trace = h->wp.trace;
   a.trace_cap = h->wp.trace_cap;
-  a.l2_window_base = nullptr;
-  a.l2_window_bytes = 0;
-  a.l2_hit_ratio = 0.f;
-  if (h->l2_persist_bytes > 0 && S_eff > 0) {
-    // the window spans the rows of U in use (contiguous in a step, any order)
-    const float* lo = U.u[0];
-    const float* hi = U.u[0];
-    for (int q = 1; q < S_eff; ++q) {
-      lo = std::min(lo, U.u[q]);
-      hi = std::max(hi, U.u[q]);
-    }
-    const size_t span = (size_t)(hi - lo) * sizeof(float) + N * sizeof(float);
-    a.l2_window_base = lo;
-    a.l2_window_bytes = std::min(span, h->l2_window_max);
-    a.l2_hit_ratio = (float)std::min(1.0, (double)h->l2_persist_bytes / (double)a.l2_window_bytes);
-  }
   cudaError_t e = h->tv == MQNPM_TV_ISO ? dispatch<MQNPM_TV_ISO>(h, S_eff, a) : dispatch<MQNPM_TV_ANISO>(h, S_eff, a);
   if (e != cudaSuccess) return set_cuda_error(h, e, "wprox launch");
   h->launches += 1;
@@ -1101,7 +1061,6 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   CK(cudaStreamSynchronize(s));
   h->last_newton_max = (int)stat[1];
   h->last_newton_total = (int)stat[2];
-  if (a.l2_window_bytes > 0) CK(cudaCtxResetPersistingL2Cache());   // U's lines back to normal for the other kernels
   if (errflag) return set_error(h, MQNPM_ERR_TIMEOUT, "wprox: grid barrier wait gave up");
   if (P_warm) CK(cudaMemcpyAsync(P_warm, h->wp.Pd, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   return MQNPM_OK;
