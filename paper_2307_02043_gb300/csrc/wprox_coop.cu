@@ -80,6 +80,17 @@ MQ_D void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Arrival at a grid barrier: one atomic with release semantics (the block's
+// writes, made visible to thread 0 by the __syncthreads before it, are
+// published with it) and acquire semantics (the arrivals before it are
+// visible to the block after its next __syncthreads).  Replaces a full fence
+// followed by a relaxed atomic.
+MQ_D unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 MQ_D long long globaltimer() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -152,12 +163,10 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
   const unsigned target = ep.all + 1;
   if constexpr (NV == 0) {
     if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned old = atomicAdd(a.count, 1u);
+      const unsigned old = atom_add_acq_rel(a.count, 1u);
       s_role = (old == (ep.flat + 1) * gridDim.x - 1) ? 2 : 0;
       s_ok = 1;
       if (s_role == 2) {
-        __threadfence();
         st_release_u32(a.gen, target);
       } else if (!wait_generation(a, target)) {
         s_ok = 0;
@@ -173,14 +182,12 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
     const int ngroups = ((int)gridDim.x + WP_GS - 1) / WP_GS;
     double* gpart = a.part + (size_t)gridDim.x * NVMAX;
     if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned old = atomicAdd(a.gcount + g, 1u);
+      const unsigned old = atom_add_acq_rel(a.gcount + g, 1u);
       s_role = (old == (ep.hier + 1) * (unsigned)gsize - 1) ? 1 : 0;
       s_ok = 1;
     }
     __syncthreads();
     if (s_role == 1) {
-      __threadfence();
       if (threadIdx.x < NV) {
         double vals[WP_GS];
 #pragma unroll
@@ -193,13 +200,11 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
       }
       __syncthreads();
       if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned old = atomicAdd(a.count_groups, 1u);
+        const unsigned old = atom_add_acq_rel(a.count_groups, 1u);
         if (old == (ep.hier + 1) * (unsigned)ngroups - 1) s_role = 2;
       }
       __syncthreads();
       if (s_role == 2) {
-        __threadfence();
         if (threadIdx.x < NV) {
           // all group sums of a chunk are loaded before any is added (one
           // round trip for up to 24 groups: 384 blocks)
@@ -215,10 +220,7 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
           a.tot[threadIdx.x] = acc;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-          __threadfence();
-          st_release_u32(a.gen, target);
-        }
+        if (threadIdx.x == 0) st_release_u32(a.gen, target);
       }
     }
     if (s_role != 2 && threadIdx.x == 0 && !wait_generation(a, target)) s_ok = 0;
