@@ -790,6 +790,9 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     illum_done = 0
     infos = []
     launches0 = h.launch_count
+    nvtx = getattr(torch.cuda, "nvtx", None)   # a "timed" range for profiler captures
+    if full and nvtx is not None:
+        nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         info = step(x)
@@ -797,6 +800,8 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
         illum_done += len(subs[info["subset"]])
     e1.record(stream)
     torch.cuda.synchronize()
+    if full and nvtx is not None:
+        nvtx.range_pop()
     launches = h.launch_count - launches0
     prox_trace = h.prox_trace()
     if world > 1:
