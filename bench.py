@@ -189,7 +189,7 @@ def subset_of(w):
     return so
 
 
-def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1):
+def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False):
     """Synthetic measurements and alpha_s, produced with the library itself."""
     kd = synth.illumination_dirs(w)
     so = subset_of(w)
@@ -211,7 +211,7 @@ def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1):
     start = torch.from_numpy(synth.power_start(w).astype(np.float32)).to(dev).reshape(-1)
     alpha = [setup.lipschitz(list(s), w.S / w.L, start, iters=10) for s in subs]
     setup.close()
-    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, **common)
+    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, direct_launches=direct, **common)
     h.set_measurements(y.reshape(-1))
     return h, y, alpha, kd, so, subs
 
@@ -757,7 +757,8 @@ def cpu_ls32_end_to_end(outer: int = 10):
 def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=True):
     """Set-up, timed MQNPM iterations (inputs resident in HBM), the end-to-end
     repeat through host buffers and the per-kernel figures of one workload."""
-    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile)
+    h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile,
+                                             direct=getattr(args, "direct_launches", False))
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
     shard = bool(getattr(args, "shard", False))
     if shard:
@@ -942,6 +943,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-born", action="store_true", help="skip the born128 figures of the default line")
+    ap.add_argument("--direct-launches", action="store_true",
+                    help="launch every kernel directly instead of through the captured BiCGSTAB graphs (for launch "
+                         "lists of profilers that do not descend into conditional graph nodes)")
     ap.add_argument("--shard", action="store_true",
                     help="one reconstruction with each subset's illuminations split over the ranks and the gradient "
                          "summed by an all-reduce (strong scaling) instead of one replica per rank")
