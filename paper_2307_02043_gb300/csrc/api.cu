@@ -407,7 +407,6 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   WproxWork& wp = h->wp;
   AL(wp.R, 3 * N); AL(wp.Pd, 3 * N); AL(wp.d, N); AL(wp.x, N);
   AL(wp.part, wprox_part_count(wp_blocks));
-  AL(wp.tot, (size_t)wprox_part_len());
   AL(wp.stat, 4);
   AL(wp.gram, (size_t)wp.ctas_vec * wprox_part_len());
   AL(wp.scal, (size_t)woodbury_scal_count());

@@ -139,11 +139,10 @@ struct WproxWork {
   float* mom = nullptr;         // momentum table of the dual iterations (dual_iters)
   int mom_len = 0;
   double* part = nullptr;       // per-block and per-group partials of the cooperative kernel
-  double* tot = nullptr;        // [44] reduced totals
   double* stat = nullptr;       // [4] Newton statistics of the last call
   double* gram = nullptr;       // partials of the Woodbury Gram pass [ctas_vec][44]
   double* scal = nullptr;       // Woodbury scalars (G, M, U^T g)
-  unsigned* barrier = nullptr;  // arrival counters and released generation (wprox_barrier_words())
+  unsigned* barrier = nullptr;  // monotonic arrival counters of the grid barriers (wprox_barrier_words())
   int* err = nullptr;           // device error flag
   unsigned char* status = nullptr;  // per-voxel inner/clipped status of the Newton evaluations
   long long* trace = nullptr;   // phase trace of the last call: (tag, ns) per barrier

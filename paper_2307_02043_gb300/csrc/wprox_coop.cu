@@ -1,8 +1,8 @@
 // The whole weighted proximal mapping (Eq. 4.5) as one cooperative kernel.
 //
-// Phases, separated by grid-wide barriers (deterministic reductions: the last
-// block to arrive sums the per-block partials in a fixed order and releases
-// the others; every wait is bounded):
+// Phases, separated by grid-wide barriers (deterministic reductions: group
+// sums of the per-block partials, then every block adds the group sums in a
+// fixed order; every wait is bounded):
 //   G  (U != 0, once)  G = U^T U, U^T v; every block forms M = (I + G/tau)^{-1}.
 //   per dual iteration j = 1..J, then once more on P_J:
 //   A  d = d(R) and U^T d              -> gamma = (c/tau^2) M U^T d   (Woodbury)
@@ -53,10 +53,8 @@ struct WpArgs {
   float* x;
   float* xout;
   const float* mom;
-  double* part;           // [gridDim.x][NVMAX] block partials, then [WP_MAXG][NVMAX] group sums
-  double* tot;            // [NVMAX]
+  double* part;           // [gridDim.x][NVMAX] block partials, then 2 x [WP_MAXG][NVMAX] group sums
   unsigned* count;        // arrivals at barriers without sums (monotonic)
-  unsigned* gen;          // released barrier generation
   unsigned* count_groups; // group sums finished (monotonic)
   unsigned* gcount;       // [WP_MAXG] arrivals per group (monotonic)
   int* err;
@@ -75,10 +73,6 @@ struct WpArgs {
 };
 
 MQ_D float clampf(float a, float lo, float hi) { return fminf(fmaxf(a, lo), hi); }
-
-MQ_D void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Arrival at a grid barrier: one atomic with release semantics (the block's
 // writes, made visible to thread 0 by the __syncthreads before it, are
@@ -135,9 +129,11 @@ struct Epochs {
   unsigned hier = 0;   // barriers with sums
 };
 
-MQ_D bool wait_generation(const WpArgs& a, unsigned target) {
+// Thread 0 of a block polls a monotonic arrival counter until it reaches
+// target (bounded; gives up when another block reported an error).
+MQ_D bool wait_count(const WpArgs& a, const unsigned* ctr, unsigned target) {
   const long long t0 = clock64();
-  while (ld_acquire_u32(a.gen) < target) {
+  while (ld_acquire_u32(ctr) < target) {
     if (*((volatile int*)a.err) != 0) return false;
     if (clock64() - t0 > a.limit) {
       atomicExch(a.err, 1);
@@ -149,28 +145,25 @@ MQ_D bool wait_generation(const WpArgs& a, unsigned target) {
 }
 
 // Grid-wide barrier with an optional sum of NV doubles per block (blk[],
-// shared).  NV = 0: one arrival counter, the last block releases.  NV > 0:
-// each block stores its partials (block-major); the last block of each group
-// of WP_GS blocks sums the group's partials in block order, and the last group
-// to finish sums the group sums in group order and releases the others, so the
-// totals are deterministic.  The totals land in sh_tot (shared) for every
-// thread.
+// shared).  Every wait polls the arrival counter it waits for, so a barrier
+// ends as soon as the last arrival reaches memory (no separate release word).
+// NV = 0: one arrival counter.  NV > 0: each block stores its partials
+// (block-major); the last block of each group of WP_GS blocks sums the
+// group's partials in block order into a group sum (double-buffered by the
+// barrier's parity) and counts the group as done; every block waits for all
+// groups and sums the group sums itself in group order, so every block holds
+// bit-identical totals in sh_tot.  Release-acquire: each block's arrival is an
+// acquire-release atomic after __syncthreads, and each wait an acquire load,
+// so whatever a block wrote before the barrier is visible to every block after it.
 template <int NV>
 MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs& ep, int tag) {
-  __shared__ int s_role, s_ok;   // role: 0 waits, 1 group reducer, 2 releases
+  __shared__ int s_role, s_ok;   // role: 1 = group reducer
   const long long t_in = tracer(a) ? globaltimer() : 0;
   __syncthreads();
-  const unsigned target = ep.all + 1;
   if constexpr (NV == 0) {
     if (threadIdx.x == 0) {
-      const unsigned old = atom_add_acq_rel(a.count, 1u);
-      s_role = (old == (ep.flat + 1) * gridDim.x - 1) ? 2 : 0;
-      s_ok = 1;
-      if (s_role == 2) {
-        st_release_u32(a.gen, target);
-      } else if (!wait_generation(a, target)) {
-        s_ok = 0;
-      }
+      atom_add_acq_rel(a.count, 1u);
+      s_ok = wait_count(a, a.count, (ep.flat + 1) * gridDim.x) ? 1 : 0;
     }
     __syncthreads();
     ep.flat += 1;
@@ -180,7 +173,8 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
     const int g = blockIdx.x / WP_GS, g0 = g * WP_GS;
     const int gsize = min(WP_GS, (int)gridDim.x - g0);
     const int ngroups = ((int)gridDim.x + WP_GS - 1) / WP_GS;
-    double* gpart = a.part + (size_t)gridDim.x * NVMAX;
+    // a block can be one barrier ahead of another still reading group sums, never two
+    double* gpart = a.part + (size_t)gridDim.x * NVMAX + (size_t)(ep.hier & 1u) * WP_MAXG * NVMAX;
     if (threadIdx.x == 0) {
       const unsigned old = atom_add_acq_rel(a.gcount + g, 1u);
       s_role = (old == (ep.hier + 1) * (unsigned)gsize - 1) ? 1 : 0;
@@ -199,31 +193,24 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
         gpart[(size_t)g * NVMAX + threadIdx.x] = acc;
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned old = atom_add_acq_rel(a.count_groups, 1u);
-        if (old == (ep.hier + 1) * (unsigned)ngroups - 1) s_role = 2;
-      }
-      __syncthreads();
-      if (s_role == 2) {
-        if (threadIdx.x < NV) {
-          // all group sums of a chunk are loaded before any is added (one
-          // round trip for up to 24 groups: 384 blocks)
-          double acc = 0.0;
-          for (int q0 = 0; q0 < ngroups; q0 += 24) {
-            double vals[24];
-#pragma unroll
-            for (int q = 0; q < 24; ++q)
-              vals[q] = (q0 + q < ngroups) ? __ldcg(gpart + (size_t)(q0 + q) * NVMAX + threadIdx.x) : 0.0;
-#pragma unroll
-            for (int q = 0; q < 24; ++q) acc += vals[q];
-          }
-          a.tot[threadIdx.x] = acc;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) st_release_u32(a.gen, target);
-      }
+      if (threadIdx.x == 0) atom_add_acq_rel(a.count_groups, 1u);
     }
-    if (s_role != 2 && threadIdx.x == 0 && !wait_generation(a, target)) s_ok = 0;
+    if (threadIdx.x == 0 && !wait_count(a, a.count_groups, (ep.hier + 1) * (unsigned)ngroups)) s_ok = 0;
+    __syncthreads();
+    if (s_ok && threadIdx.x < NV) {
+      // all group sums of a chunk are loaded before any is added (one round
+      // trip for up to 24 groups: 384 blocks)
+      double acc = 0.0;
+      for (int q0 = 0; q0 < ngroups; q0 += 24) {
+        double vals[24];
+#pragma unroll
+        for (int q = 0; q < 24; ++q)
+          vals[q] = (q0 + q < ngroups) ? __ldcg(gpart + (size_t)(q0 + q) * NVMAX + threadIdx.x) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 24; ++q) acc += vals[q];
+      }
+      sh_tot[threadIdx.x] = acc;
+    }
     __syncthreads();
     ep.hier += 1;
   }
@@ -237,12 +224,7 @@ MQ_D bool grid_reduce(const double* blk, double* sh_tot, const WpArgs& a, Epochs
     tr_acc()[5] += t - t_in;
     tr_acc()[TR_SLOTS] = t;
   }
-  if (!s_ok) return false;
-  if constexpr (NV > 0) {
-    if (threadIdx.x < NV) sh_tot[threadIdx.x] = __ldcg(a.tot + threadIdx.x);
-    __syncthreads();
-  }
-  return true;
+  return s_ok != 0;
 }
 
 // Coordinates of the first of four voxels i4 = 4 k4 (nx is a multiple of 4).
@@ -1026,11 +1008,9 @@ int wprox_impl(mqnpm_handle* h, const float* v, double tau, const UPtrs& U, int 
   a.xout = x_out;
   a.mom = h->wp.mom;
   a.part = h->wp.part;
-  a.tot = h->wp.tot;
   a.count = h->wp.barrier;
-  a.gen = h->wp.barrier + 1;
-  a.count_groups = h->wp.barrier + 2;
-  a.gcount = h->wp.barrier + 3;
+  a.count_groups = h->wp.barrier + 1;
+  a.gcount = h->wp.barrier + 2;
   a.err = h->wp.err;
   a.stat = h->wp.stat;
   a.status = h->wp.status;
@@ -1083,6 +1063,6 @@ std::vector<float> wprox_momentum(int J) {
 
 int wprox_part_len() { return NVMAX; }
 int wprox_blocks_per_sm() { return WP_BPS; }
-size_t wprox_part_count(int max_blocks) { return (size_t)(max_blocks + WP_MAXG) * NVMAX; }
-int wprox_barrier_words() { return 3 + WP_MAXG; }
+size_t wprox_part_count(int max_blocks) { return (size_t)(max_blocks + 2 * WP_MAXG) * NVMAX; }
+int wprox_barrier_words() { return 2 + WP_MAXG; }
 #endif
