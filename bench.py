@@ -475,6 +475,7 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
     tiles = {}
     groups = {}        # n -> (Group, member ids)
     lat_ms, illum_done = [], 0
+    builds = [0, 0.0]  # group (re)builds, host seconds spent in them
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def admit():
@@ -519,6 +520,7 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
             cur[0].close()
             del groups[n]
         slots = min(max_group_slots, sum(prepared[i][5] for i in ids))
+        t_build = time.perf_counter()
         while True:
             try:
                 g = binding.Group([active[i][0] for i in ids], max_slots=slots,
@@ -531,6 +533,8 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
         used[0] += g.workspace_bytes
         peak[0] = max(peak[0], used[0])
         groups[n] = (g, ids)
+        builds[0] += 1
+        builds[1] += time.perf_counter() - t_build
         return g
 
     admit()
@@ -578,7 +582,9 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
             "iteration_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                                      "p99": round(float(np.percentile(lat, 99)), 3),
                                      "max": round(float(lat.max()), 3)},
-            "total_ms": round(total_ms, 1), "green_tile_per_grid": {str(k): v for k, v in tiles.items()}}
+            "total_ms": round(total_ms, 1), "green_tile_per_grid": {str(k): v for k, v in tiles.items()},
+            "group_builds": builds[0], "group_build_ms": round(1e3 * builds[1], 1),
+            "slowest_iterations_ms": [round(float(v), 1) for v in sorted(lat_ms)[-8:]]}
 
 
 def serve_uneven(args, torch, binding):
