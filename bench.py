@@ -465,7 +465,9 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
     requests step one after another, each on its own workspace of one
     mini-batch.  shared = True: the active requests of one grid form a group
     whose subset gradients run as one batch of slots (shared launches, up to
-    max_group_slots slots per chunk); each round steps every group once.
+    max_group_slots slots per chunk); a request is admitted only while its
+    grid's group, rebuilt with one slot per illumination of its members'
+    mini-batches, still fits the budget; each round steps every group once.
     Per-iteration latency: the time from the start of the call that advances a
     request to its end."""
     queue = list(range(len(prepared)))
@@ -476,7 +478,37 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
     groups = {}        # n -> (Group, member ids)
     lat_ms, illum_done = [], 0
     builds = [0, 0.0]  # group (re)builds, host seconds spent in them
+    per_grid = {}      # n -> [step ms, illumination-gradients, Krylov iterations]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def build_group(n, ids, allow_fewer):
+        """(Re)build grid n's group for the members ids with one slot per
+        illumination of their mini-batches (up to max_group_slots).  Without
+        allow_fewer a group that does not fit the budget is not built (None);
+        with it the slot count is halved until it fits."""
+        cur = groups.pop(n, None)
+        if cur is not None:
+            used[0] -= cur[0].workspace_bytes
+            cur[0].close()
+        slots = min(max_group_slots, sum(prepared[i][5] for i in ids))
+        t_build = time.perf_counter()
+        while True:
+            try:
+                g = binding.Group([active[i][0] for i in ids], max_slots=slots,
+                                  hbm_budget_bytes=max(1, budget - used[0]))
+                break
+            except binding.MQNPMError as err:
+                if err.code == 2 and not allow_fewer:
+                    return None
+                if err.code != 2 or slots == 1:
+                    raise
+                slots = max(1, slots // 2)
+        used[0] += g.workspace_bytes
+        peak[0] = max(peak[0], used[0])
+        groups[n] = (g, ids)
+        builds[0] += 1
+        builds[1] += time.perf_counter() - t_build
+        return g
 
     def admit():
         while queue:
@@ -496,46 +528,36 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
             h.set_measurements(y.reshape(-1))
             tiles[w.n] = h.tile_info()["tile"]
             used[0] += h.workspace_bytes
-            peak[0] = max(peak[0], used[0])
             active[i] = [h, torch.zeros(w.N, dtype=torch.float32, device=dev), 0]
+            if shared:
+                # a request is admitted with its share of its grid's shared slots
+                ids = sorted(j for j in active if prepared[j][0].n == w.n)
+                if build_group(w.n, ids, allow_fewer=len(active) == 1) is None:
+                    used[0] -= h.workspace_bytes
+                    h.close()
+                    del active[i]
+                    return                            # wait for a retirement
+            peak[0] = max(peak[0], used[0])
             queue.pop(0)
 
     def retire(i):
         h = active[i][0]
         used[0] -= h.workspace_bytes
         n = prepared[i][0].n
-        if n in groups:                               # membership changes: the group is rebuilt
+        h.close()
+        del active[i]
+        # the grid's group keeps its reservation until it is rebuilt for the
+        # remaining members (and is freed with the grid's last member)
+        if n in groups and not any(prepared[j][0].n == n for j in active):
             g, _ = groups.pop(n)
             used[0] -= g.workspace_bytes
             g.close()
-        h.close()
-        del active[i]
 
     def group_for(n, ids):
         cur = groups.get(n)
         if cur is not None and cur[1] == ids:
             return cur[0]
-        if cur is not None:
-            used[0] -= cur[0].workspace_bytes
-            cur[0].close()
-            del groups[n]
-        slots = min(max_group_slots, sum(prepared[i][5] for i in ids))
-        t_build = time.perf_counter()
-        while True:
-            try:
-                g = binding.Group([active[i][0] for i in ids], max_slots=slots,
-                                  hbm_budget_bytes=max(1, budget - used[0]))
-                break
-            except binding.MQNPMError as err:
-                if err.code != 2 or slots == 1:
-                    raise
-                slots = max(1, slots // 2)
-        used[0] += g.workspace_bytes
-        peak[0] = max(peak[0], used[0])
-        groups[n] = (g, ids)
-        builds[0] += 1
-        builds[1] += time.perf_counter() - t_build
-        return g
+        return build_group(n, ids, allow_fewer=True)
 
     admit()
     admitted_first = len(active)
@@ -552,9 +574,13 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
                 ev[1].record()
                 ev[1].synchronize()
                 t = ev[0].elapsed_time(ev[1])
+                pg = per_grid.setdefault(n, [0.0, 0, 0])
+                pg[0] += t
                 for i, info in zip(ids, infos):
                     lat_ms.append(t)
                     illum_done += info["n_illum"]
+                    pg[1] += info["n_illum"]
+                    pg[2] += info["krylov_iters_total"]
                     active[i][2] += 1
             for i in [i for i in list(active) if active[i][2] >= prepared[i][0].outer_iters]:
                 retire(i)
@@ -568,6 +594,10 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
                 ev[1].synchronize()
                 lat_ms.append(ev[0].elapsed_time(ev[1]))
                 illum_done += info["n_illum"]
+                pg = per_grid.setdefault(prepared[i][0].n, [0.0, 0, 0])
+                pg[0] += lat_ms[-1]
+                pg[1] += info["n_illum"]
+                pg[2] += info["krylov_iters_total"]
                 active[i][2] += 1
                 if active[i][2] >= prepared[i][0].outer_iters:
                     retire(i)
@@ -584,7 +614,9 @@ def serve_uneven_run(prepared, budget, shared, torch, binding, dev, max_group_sl
                                      "max": round(float(lat.max()), 3)},
             "total_ms": round(total_ms, 1), "green_tile_per_grid": {str(k): v for k, v in tiles.items()},
             "group_builds": builds[0], "group_build_ms": round(1e3 * builds[1], 1),
-            "slowest_iterations_ms": [round(float(v), 1) for v in sorted(lat_ms)[-8:]]}
+            "slowest_iterations_ms": [round(float(v), 1) for v in sorted(lat_ms)[-8:]],
+            "per_grid": {str(k): {"step_ms": round(v[0], 1), "illum_gradients": v[1], "krylov_iters": v[2]}
+                         for k, v in sorted(per_grid.items())}}
 
 
 def serve_uneven(args, torch, binding):

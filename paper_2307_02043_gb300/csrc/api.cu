@@ -220,7 +220,11 @@ void mqnpm_destroy(mqnpm_handle* h) {
   delete h;
 }
 
-int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
+}  // extern "C"
+
+// mqnpm_create with an optional device copy source for the Green's spectrum
+// (a group's engine takes its members' spectrum instead of building it again).
+int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle** out) {
   if (!out) return MQNPM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!cfg) return MQNPM_ERR_INVALID_ARG;
@@ -486,8 +490,10 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
       (e = cudaMemcpyAsync(h->twy, twy.data(), Py * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->twz, twz.data(), Pz * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = (cfg->green_hat ? upload_khat(cfg->green_hat, nx, ny, nz, h->khat, s)
-                           : build_khat(nx, ny, nz, h->h, h->kb, h->khat, s, h->green_kernel))) != cudaSuccess) {
+      (e = (khat_src ? cudaMemcpyAsync(h->khat, khat_src, (size_t)(nx + 1) * (ny + 1) * (nz + 1) * sizeof(float2),
+                                       cudaMemcpyDeviceToDevice, s)
+            : cfg->green_hat ? upload_khat(cfg->green_hat, nx, ny, nz, h->khat, s)
+                             : build_khat(nx, ny, nz, h->h, h->kb, h->khat, s, h->green_kernel))) != cudaSuccess) {
     set_cuda_error(h, e, "create tables");
     return fail(MQNPM_ERR_CUDA);
   }
@@ -503,6 +509,10 @@ int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) {
   *out = h;
   return MQNPM_OK;
 }
+
+extern "C" {
+
+int mqnpm_create(const mqnpm_config* cfg, mqnpm_handle** out) { return create_handle(cfg, nullptr, out); }
 
 int mqnpm_set_measurements(mqnpm_handle* h, const float* y) {
   if (!h || !y) return MQNPM_ERR_INVALID_ARG;

@@ -12,7 +12,8 @@
 //
 // The group owns an internal handle ("engine") that holds the shared Krylov
 // workspace of max_slots slots, the concatenated incident-field tables and
-// measurements, and a copy of member 0's Green's spectrum.
+// measurements, and a copy of member 0's Green's spectrum (copied at create,
+// not built again).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -109,19 +110,11 @@ int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, s
   c.direct_launches = m0->direct_launches ? 1 : 0;
   c.tile = m0->tile;
   c.green_kernel = m0->green_kernel;
-  int rc = mqnpm_create(&c, &g->engine);
+  // the engine takes the members' spectrum (it may come from a caller's green_hat)
+  int rc = create_handle(&c, m0->khat, &g->engine);
   if (rc != MQNPM_OK) {
     delete g;
     return rc;
-  }
-  // the members' spectrum (it may come from a caller's green_hat)
-  const size_t nk = (size_t)(m0->nx + 1) * (m0->ny + 1) * (m0->nz + 1);
-  cudaError_t e = cudaMemcpyAsync(g->engine->khat, m0->khat, nk * sizeof(float2), cudaMemcpyDeviceToDevice,
-                                  g->engine->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(g->engine->stream);
-  if (e != cudaSuccess) {
-    mqnpm_group_destroy(g);
-    return MQNPM_ERR_CUDA;
   }
   *out = g;
   return MQNPM_OK;

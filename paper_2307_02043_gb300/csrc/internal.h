@@ -210,6 +210,10 @@ struct mqnpm_handle {
   cudaEvent_t step_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // phase timing of mqnpm_step
 };
 
+// mqnpm_create with the Green's spectrum copied from khat_src (device, the
+// folded octant of the same grid) when it is not null (api.cu).
+int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle** out);
+
 // Record the next profiling group for a Green's apply of nb slots (nullptr when off/full).
 cudaEvent_t* profile_slot(mqnpm_handle* h, int nb);
 
