@@ -121,12 +121,15 @@ typedef struct mqnpm_config {
                               G, e.g. a truncated kernel), used instead of the
                               library's own (Section 6 reading)              */
   int tile;                /* launch shapes of the Green's passes: -1 picks the
-                              fastest of 0..15 by timing at create (cached per
-                              device, grid and batch slots); 0..15 fixes them: bits
+                              fastest of 0..31 by timing at create (cached per
+                              device, grid and batch slots); 0..31 fixes them: bits
                               0, 1, 2 select the alternative shape (lines or
                               columns per CTA, threads per line or column) of
                               the x, y and z passes, bit 3 two exchange buffers
-                              in the z pass (0 = the built-in defaults)       */
+                              in the z pass, bit 4 the fused x/y passes (pairs
+                              of CTAs per z-plane in a thread-block cluster;
+                              nx = ny = 64 or 128 with bits 0 and 1 clear; same
+                              results bit for bit) (0 = the built-in defaults) */
   double det_distance;     /* remote detector (det_na > 0): distance from the last
                               z-slice to the detector plane, units of h        */
   double det_na;           /* 0: the detector is the last z-slice; > 0: that
@@ -359,9 +362,9 @@ long long mqnpm_launch_count(const mqnpm_handle* h);
 int mqnpm_check_guards(mqnpm_handle* h, int* corrupted);
 int mqnpm_debug_poke_guard(mqnpm_handle* h, int band);
 
-/* Launch shapes the handle uses: *tile (0..15); shape (6 ints) receives the
+/* Launch shapes the handle uses: *tile (0..31); shape (6 ints) receives the
  * lines per CTA and threads per line of the x passes, then the columns per CTA
- * and threads per column of the y passes and of the z pass; ms (16 doubles,
+ * and threads per column of the y passes and of the z pass; ms (32 doubles,
  * may be NULL) receives the autotuner's time of one Green's apply per tile,
  * -1 where none was taken (a fixed tile, or one whose shared memory does not
  * fit).  Returns MQNPM_OK or INVALID_ARG. */

@@ -327,12 +327,13 @@ class MQNPM:
         """Launch shapes of the Green's passes and the autotuner's timings (ms per apply)."""
         tile = ctypes.c_int()
         shape = (ctypes.c_int * 6)()
-        ms = (ctypes.c_double * 16)()
+        ms = (ctypes.c_double * 32)()
         self._raise(self.lib.mqnpm_tile_info(self._h, ctypes.byref(tile), shape, ms))
         return {"tile": tile.value, "x": {"lines_per_cta": shape[0], "threads_per_line": shape[1]},
                 "y": {"columns_per_cta": shape[2], "threads_per_column": shape[3]},
                 "z": {"columns_per_cta": shape[4], "threads_per_column": shape[5],
                       "exchange_buffers": 2 if tile.value & 8 else 1},
+                "fused_xy": bool(tile.value & 16),
                 "tuned_ms": [round(m, 4) if m >= 0 else None for m in ms]}
 
     # -- calls -------------------------------------------------------------

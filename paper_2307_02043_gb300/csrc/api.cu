@@ -333,8 +333,8 @@ int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle*
   std::fill(h->tune_ms, h->tune_ms + MQ_TILES, -1.0);
   if (!green_tile_fits(nx, ny, nz, h->tile, h->device)) {
     char msg[160];
-    snprintf(msg, sizeof msg, "tile %d needs more shared memory per block than the device has at the %d x %d x %d grid",
-             h->tile, nx, ny, nz);
+    snprintf(msg, sizeof msg, "tile %d does not run at the %d x %d x %d grid on this device (shared memory per block, "
+             "or fused x/y passes without square 64 or 128 planes)", h->tile, nx, ny, nz);
     h->err = msg;
     *out = nullptr;
     delete h;

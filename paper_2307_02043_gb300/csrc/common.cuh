@@ -23,7 +23,16 @@ MQ_HD float2 cmul(float2 a, float2 b) {
 MQ_HD float2 cmulc(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
 }
-MQ_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// A rounded product that the compiler never contracts into a following add
+// (the first butterflies of the prologue's transform): every kernel that
+// scales by the contrast then rounds the same way.
+MQ_HD float2 cscale(float2 a, float s) {
+#ifdef __CUDA_ARCH__
+  return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s));
+#else
+  return make_float2(a.x * s, a.y * s);
+#endif
+}
 MQ_HD float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 // a + s * b (s complex)
 MQ_HD float2 caxpy(float2 s, float2 b, float2 a) {

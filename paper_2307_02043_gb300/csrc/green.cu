@@ -36,12 +36,22 @@ bool green_supported(int n) {
   }
 }
 
+bool green_fused_supported(int nx, int ny) { return nx == ny && (2 * nx == 128 || 2 * nx == 256); }
+
 namespace {
+
+size_t fused_smem(int n) {
+  switch (2 * n) {
+    case 128: return green_fused_smem_P128();
+    case 256: return green_fused_smem_P256();
+    default: return 0;
+  }
+}
 
 // The shape fields and shared memory of one length's passes.
 bool shape_of(int n, int tile, int* shape, size_t* srow, size_t* scol, size_t* sz) {
   switch (2 * n) {
-#define MQ_CASE(P) case P: green_shape_P##P(tile, shape, srow, scol, sz); return true;
+#define MQ_CASE(P) case P: green_shape_P##P(tile & 15, shape, srow, scol, sz); return true;
     MQ_DISPATCH(MQ_CASE)
 #undef MQ_CASE
     default:
@@ -54,6 +64,9 @@ bool shape_of(int n, int tile, int* shape, size_t* srow, size_t* scol, size_t* s
 void green_shape(int nx, int ny, int nz, int tile, int* shape, size_t* smem) {
   for (int i = 0; i < 6; ++i) shape[i] = 0;
   if (smem) *smem = 0;
+  // the fused x/y passes exist for square planes of the default row shape;
+  // their plane-input and plane-output applies use the unfused passes
+  if ((tile & MQ_TILE_FUSED) && (!green_fused_supported(nx, ny) || (tile & 3) != 0)) return;
   int sx[6], sy[6], sz[6];
   size_t rx, cx, zx, ry, cy, zy, rz, cz, zz;
   if (!shape_of(nx, tile, sx, &rx, &cx, &zx) || !shape_of(ny, tile, sy, &ry, &cy, &zy) ||
@@ -66,6 +79,7 @@ void green_shape(int nx, int ny, int nz, int tile, int* shape, size_t* smem) {
   shape[4] = sz[4];   // z pass: length Pz
   shape[5] = sz[5];
   if (smem) *smem = std::max(rx, std::max(cy, zz));
+  if (smem && (tile & MQ_TILE_FUSED)) *smem = std::max(*smem, fused_smem(nx));
 }
 
 bool green_tile_fits(int nx, int ny, int nz, int tile, int device) {
@@ -125,6 +139,13 @@ cudaError_t passy_any(const GreenCall& c, bool inv, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
 }
+cudaError_t fused_any(const GreenCall& c, bool inv, cudaStream_t s) {
+  switch (2 * c.nx) {
+    case 128: return green_fused_P128(c, inv, s);
+    case 256: return green_fused_P256(c, inv, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 cudaError_t pass3_any(const GreenCall& c, cudaStream_t s) {
   switch (2 * c.nz) {
 #define MQ_CASE(P) case P: return green_pass3_P##P(c, s);
@@ -152,13 +173,28 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
     if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
   }
   auto rec = [&](int k) { return c.ev ? cudaEventRecordWithFlags(c.ev[k], s, rec_flags) : cudaSuccess; };
-  if ((e = rec(0)) != cudaSuccess || (e = pass1_any(c, s)) != cudaSuccess || (e = rec(1)) != cudaSuccess ||
-      (e = passy_any(c, false, s)) != cudaSuccess || (e = rec(2)) != cudaSuccess ||
-      (e = pass3_any(c, s)) != cudaSuccess || (e = rec(3)) != cudaSuccess ||
-      (e = passy_any(c, true, s)) != cudaSuccess || (e = rec(4)) != cudaSuccess ||
-      (e = pass5_any(c, s)) != cudaSuccess || (e = rec(5)) != cudaSuccess)
+  // fused x/y passes (tile bit 4) for full applies; a plane input or output
+  // takes the unfused passes on that side.  Their time counts as the x pass's
+  // (events 1 and 2, 3 and 4 coincide).
+  const bool fuse = (c.tile & MQ_TILE_FUSED) && green_fused_supported(c.nx, c.ny);
+  const bool ffwd = fuse && !c.plane, finv = fuse && !c.outplane;
+  if ((e = rec(0)) != cudaSuccess) return e;
+  if (ffwd) {
+    if ((e = fused_any(c, false, s)) != cudaSuccess || (e = rec(1)) != cudaSuccess || (e = rec(2)) != cudaSuccess)
+      return e;
+  } else if ((e = pass1_any(c, s)) != cudaSuccess || (e = rec(1)) != cudaSuccess ||
+             (e = passy_any(c, false, s)) != cudaSuccess || (e = rec(2)) != cudaSuccess) {
     return e;
-  if (c.launches) *c.launches += 5;
+  }
+  if ((e = pass3_any(c, s)) != cudaSuccess || (e = rec(3)) != cudaSuccess) return e;
+  if (finv) {
+    if ((e = rec(4)) != cudaSuccess || (e = fused_any(c, true, s)) != cudaSuccess || (e = rec(5)) != cudaSuccess)
+      return e;
+  } else if ((e = passy_any(c, true, s)) != cudaSuccess || (e = rec(4)) != cudaSuccess ||
+             (e = pass5_any(c, s)) != cudaSuccess || (e = rec(5)) != cudaSuccess) {
+    return e;
+  }
+  if (c.launches) *c.launches += 1 + (ffwd ? 1 : 2) + (finv ? 1 : 2);
   return e;
 }
 

@@ -2,7 +2,10 @@
 // Compiled once per supported P with -DMQ_P=<P>.  Each entry point runs the
 // passes along an axis whose transform length is P: the x passes (1 and 5)
 // when Px = P, the y passes (2 and 4) when Py = P, the z pass (3) when Pz = P.
+#include <algorithm>
+
 #include "functors.cuh"
+#include "green_fused.cuh"
 #include "internal.h"
 
 #ifndef MQ_P
@@ -110,6 +113,90 @@ cudaError_t pass3(const GreenCall& c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Fused x/y passes: persistent pairs of CTAs over the (slot, z-plane) tasks,
+// as many pairs as fit on the device at once.
+template <class K>
+int fused_pairs(K kernel, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(FusedShape<P>::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)kernel, &cfg) != cudaSuccess) return 0;
+  return n;
+}
+
+template <int KIND>
+cudaError_t launch12(const GreenCall& c, cudaStream_t s) {
+  using FS = FusedShape<P>;
+  Pro<KIND> pro;
+  pro.a = c.pa;
+  pro.g = geo(c);
+  if constexpr (KIND == PRO_BICG_P || KIND == PRO_BICG_S) pro.st = c.st;
+  auto kern = k_pass12<P, Pro<KIND>>;
+  static int pairs = 0;   // per instantiation: the device's co-resident pairs
+  if (pairs == 0) {
+    cudaError_t e = set_smem(kern, (int)FS::SMEM);
+    if (e != cudaSuccess) return e;
+    pairs = fused_pairs(kern, FS::SMEM);
+    if (pairs <= 0) return cudaErrorLaunchOutOfResources;
+  }
+  const int n = std::min(pairs, c.nb * c.nz);
+  const int nctas = ceil_div(c.ny * c.nz, RowShape<P, 0>::LPB);   // pass 1's partial layout
+  kern<<<2 * n, FS::THREADS, FS::SMEM, s>>>(pro, c.T2, c.nz, c.nb, c.twx, c.st, c.part_pro, nctas);
+  return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch45(const GreenCall& c, cudaStream_t s) {
+  using FS = FusedShape<P>;
+  Epi<KIND> epi;
+  epi.a = c.ea;
+  epi.g = geo(c);
+  auto kern = k_pass45<P, Epi<KIND>>;
+  static int pairs = 0;
+  if (pairs == 0) {
+    cudaError_t e = set_smem(kern, (int)FS::SMEM);
+    if (e != cudaSuccess) return e;
+    pairs = fused_pairs(kern, FS::SMEM);
+    if (pairs <= 0) return cudaErrorLaunchOutOfResources;
+  }
+  const int n = std::min(pairs, c.nb * c.nz);
+  const int nctas = ceil_div(c.ny * c.nz, RowShape<P, 0>::LPB);   // pass 5's partial layout
+  kern<<<2 * n, FS::THREADS, FS::SMEM, s>>>(epi, c.T2, c.nz, c.nb, c.twx, c.st, c.part_epi, nctas);
+  return cudaGetLastError();
+}
+
+cudaError_t fused(const GreenCall& c, bool inv, cudaStream_t s) {
+  if constexpr (FusedShape<P>::OK && (P == 128 || P == 256)) {
+    if (!inv) {
+      switch (c.pro) {
+        case PRO_PLAIN: return launch12<PRO_PLAIN>(c, s);
+        case PRO_CONTRAST: return launch12<PRO_CONTRAST>(c, s);
+        case PRO_BORN: return launch12<PRO_BORN>(c, s);
+        case PRO_BICG_P: return launch12<PRO_BICG_P>(c, s);
+        case PRO_BICG_S: return launch12<PRO_BICG_S>(c, s);
+        case PRO_LIFT: return launch12<PRO_LIFT>(c, s);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    switch (c.epi) {
+      case EPI_PLAIN: return launch45<EPI_PLAIN>(c, s);
+      case EPI_V: return launch45<EPI_V>(c, s);
+      case EPI_T: return launch45<EPI_T>(c, s);
+      case EPI_INIT: return launch45<EPI_INIT>(c, s);
+      case EPI_INIT_WARM: return launch45<EPI_INIT_WARM>(c, s);
+      case EPI_DETECT: return launch45<EPI_DETECT>(c, s);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    (void)c;
+    (void)inv;
+    (void)s;
+    return cudaErrorNotSupported;
+  }
+}
+
 template <int ZV, bool DB>
 cudaError_t pass3_io(const GreenCall& c, cudaStream_t s) {
   if (c.plane) {   // the plane input serves the adjoint lift only
@@ -165,4 +252,15 @@ cudaError_t MQ_CAT(green_pass3_P, MQ_P)(const GreenCall& c, cudaStream_t s) {
     case 2: return pass3_io<0, true>(c, s);
     default: return pass3_io<1, true>(c, s);
   }
+}
+
+// Fused x/y passes of a square plane of edge P/2 (tile bit 4; P = 128, 256).
+cudaError_t MQ_CAT(green_fused_P, MQ_P)(const GreenCall& c, bool inv, cudaStream_t s) {
+  if (2 * c.nx != P || 2 * c.ny != P) return cudaErrorInvalidValue;
+  return fused(c, inv, s);
+}
+
+size_t MQ_CAT(green_fused_smem_P, MQ_P)() {
+  if constexpr (FusedShape<P>::OK && (P == 128 || P == 256)) return FusedShape<P>::SMEM;
+  return 0;
 }

@@ -34,10 +34,12 @@ struct GreenCall {
   bool plane = false;            // input nonzero on the last z-plane only (the lift S^T r; G^H only)
   bool outplane = false;         // only the last z-plane of the output is needed (first-Born data; G only)
   int tile = 0;                  // launch shapes: alternative shape of bit 0 the x passes, bit 1 the
-                                 // y passes, bit 2 the z pass; bit 3 two z-pass exchange buffers
+                                 // y passes, bit 2 the z pass; bit 3 two z-pass exchange buffers;
+                                 // bit 4 the fused x/y passes (square planes, P = 128 or 256)
 };
 
-constexpr int MQ_TILES = 16;     // launch-shape variants of the Green's passes
+constexpr int MQ_TILES = 32;     // launch-shape variants of the Green's passes
+constexpr int MQ_TILE_FUSED = 16;   // tile bit: passes 1+2 and 4+5 as fused cluster kernels
 
 // Tensor map of the pass-3 buffer T2 = [max_batch * nz][Py][Px] complex64, box C x 1 x nz
 // with C the column width of the tile's z-pass shape.
@@ -83,6 +85,7 @@ void green_shape(int nx, int ny, int nz, int tile, int* shape, size_t* smem = nu
 bool green_tile_fits(int nx, int ny, int nz, int tile, int device);
 int green_col_width(int nx, int ny, int nz, int tile);   // columns per CTA of pass 3 (the tensor-map box)
 bool green_supported(int n);                             // 2n is a compiled transform length
+bool green_fused_supported(int nx, int ny);              // fused x/y passes exist for this plane
 cudaError_t green_launch(const GreenCall& c, cudaStream_t s);
 
 // Per-P entry points (one translation unit each): the passes along an axis
@@ -92,7 +95,9 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s);
   cudaError_t green_pass5_P##P(const GreenCall& c, cudaStream_t s);                        \
   cudaError_t green_passy_P##P(const GreenCall& c, bool inv, cudaStream_t s);              \
   cudaError_t green_pass3_P##P(const GreenCall& c, cudaStream_t s);                        \
-  void green_shape_P##P(int tile, int* shape, size_t* smem_row, size_t* smem_col, size_t* smem_z);
+  void green_shape_P##P(int tile, int* shape, size_t* smem_row, size_t* smem_col, size_t* smem_z); \
+  cudaError_t green_fused_P##P(const GreenCall& c, bool inv, cudaStream_t s);              \
+  size_t green_fused_smem_P##P();
 MQ_DECL(16) MQ_DECL(24) MQ_DECL(32) MQ_DECL(48) MQ_DECL(64) MQ_DECL(96) MQ_DECL(128)
 MQ_DECL(192) MQ_DECL(256) MQ_DECL(320) MQ_DECL(384)
 #undef MQ_DECL

@@ -2,8 +2,9 @@
 //
 // Each transform length has two shapes for the x passes, two for the y
 // passes and two for the z pass (lines or columns per CTA and threads per
-// line or column), and two exchange schemes of the z pass (one or two
-// shared-memory buffers): sixteen tiles.  The tuner times a plain apply of
+// line or column), two exchange schemes of the z pass (one or two
+// shared-memory buffers), and on square planes of edge 64 or 128 the fused
+// x/y passes: up to twenty tiles that run.  The tuner times a plain apply of
 // min(max_batch, 8) slots for each tile on the handle's own buffers (zero
 // input: the passes do the same work for any values), round-robin over two
 // rounds after one warm-up round so that clock ramp-up does not favour a late
@@ -88,8 +89,22 @@ int autotune_tile(mqnpm_handle* h) {
         if (!fits[t]) continue;
         c.tile = t;
         c.tmap = maps[t];
-        if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess || (e = green_launch(c, s)) != cudaSuccess ||
-            (e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[1])) != cudaSuccess)
+        if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) break;
+        if ((e = green_launch(c, s)) != cudaSuccess) {
+          // a fused-pass tile that cannot be launched here (no co-resident CTA
+          // pair, a launch configuration the device refuses) drops out; any
+          // other failure ends the tuning
+          if ((t & MQ_TILE_FUSED) && round == 0 &&
+              (e == cudaErrorLaunchOutOfResources || e == cudaErrorInvalidConfiguration ||
+               e == cudaErrorNotSupported || e == cudaErrorInvalidValue)) {
+            (void)cudaGetLastError();
+            fits[t] = false;
+            e = cudaSuccess;
+            continue;
+          }
+          break;
+        }
+        if ((e = cudaEventRecord(ev[1], s)) != cudaSuccess || (e = cudaEventSynchronize(ev[1])) != cudaSuccess)
           break;
         float t_ms = 0.f;
         if ((e = cudaEventElapsedTime(&t_ms, ev[0], ev[1])) != cudaSuccess) break;

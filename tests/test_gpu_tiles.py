@@ -1,9 +1,9 @@
 """Launch-shape variants of the Green's apply and the autotuner that picks one.
 
 Every tile runs the same arithmetic per line and per column (only the number
-of lines or columns per CTA and the pass-3 exchange scheme change), so a plain
-Green's apply must be bit-identical across the eight tiles at every transform
-length; reductions inside the Krylov solves regroup with the row shape, so
+of lines or columns per CTA, the pass-3 exchange scheme, or the fusion of the
+x and y passes into one cluster kernel change), so a plain Green's apply must
+be bit-identical across the tiles at every transform length; reductions inside the Krylov solves regroup with the row shape, so
 gradients agree to rounding and against the oracle.
 """
 import math
@@ -22,7 +22,7 @@ from paper_2307_02043_gb300 import binding  # noqa: E402
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 KB = math.pi / 2
-TILES = range(16)
+TILES = range(32)
 
 
 def cone(L, deg=30.0):
@@ -51,15 +51,19 @@ def test_every_tile_gives_the_same_apply(n, adjoint):
             skipped.append(t)
             continue
         info = h.tile_info()
-        assert info["tile"] == t and info["tuned_ms"] == [None] * 16
+        assert info["tile"] == t and info["tuned_ms"] == [None] * 32
         out = h.green_apply(v, adjoint=adjoint).cpu()
         h.close()
         if ref is None:
             ref = out
         else:
             assert torch.equal(out, ref), (n, t)
-    # only the two-buffer z pass with the alternative shape can outgrow shared memory (P = 320)
-    assert all(t & 12 == 12 for t in skipped), skipped
+    # only the two-buffer z pass with the alternative shape can outgrow shared memory (P = 320);
+    # the fused x/y passes (bit 4) run on square planes of edge 64 or 128 with bits 0, 1 clear
+    fused_ok = n in (64, 128)
+    assert all(t & 12 == 12 or (t & 16 and (t & 3 or not fused_ok)) for t in skipped), skipped
+    if fused_ok:
+        assert not any(t in skipped for t in (16, 20, 24, 28)), skipped
     if n <= 32:
         vh = v.cpu().numpy().reshape(nb, n, n, n)
         kh = physics.green_hat(n, KB)
@@ -102,8 +106,11 @@ def test_autotuner_picks_the_fastest_and_caches():
     h1 = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=nb)
     a = h1.tile_info()
     ms = a["tuned_ms"]
-    assert all(m is not None and m > 0 for m in ms), ms
-    assert a["tile"] == int(np.argmin(ms))
+    # every unfused tile fits at n = 64; the fused x/y passes run with bits 0 and 1 clear
+    timed = [t for t, m in enumerate(ms) if m is not None]
+    assert timed == list(range(16)) + [16, 20, 24, 28], timed
+    assert all(ms[t] > 0 for t in timed), ms
+    assert a["tile"] == min(timed, key=lambda t: ms[t])
     h2 = binding.MQNPM(n, cone(2), [0, 0], [1.0], max_batch=nb)
     assert h2.tile_info() == a          # same (device, n, slots): cached, not re-timed
     h1.close()
@@ -111,7 +118,7 @@ def test_autotuner_picks_the_fastest_and_caches():
 
 
 def test_invalid_tile_is_rejected():
-    for t in (-2, 16):
+    for t in (-2, 16, 32):   # 16: the fused x/y passes need square planes of edge 64 or 128
         with pytest.raises(binding.MQNPMError):
             binding.MQNPM(16, cone(2), [0, 0], [1.0], tile=t)
 
@@ -146,3 +153,41 @@ def test_gradient_agrees_across_tiles_and_with_oracle(model):
         grads.append(g)
     for g in grads[1:]:
         assert np.linalg.norm(g - grads[0]) <= 1e-5 * np.linalg.norm(grads[0]), model
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (48, 64, 64), (128, 128, 128)])
+@pytest.mark.parametrize("model", ["ls", "born"])
+def test_fused_xy_passes_equal_the_unfused_ones_bit_for_bit(shape, model):
+    """Tile bit 4 replaces passes 1+2 and 4+5 by cluster kernels that keep a
+    z-plane in shared memory and run the same register DFTs, and form the
+    prologue and epilogue partial sums per group of the unfused row pass's
+    lines in its order.  Plain applies, Krylov solves (iteration counts,
+    losses) and gradients equal the unfused tile 0's bit for bit."""
+    nz, ny, nx = shape
+    L, nb = 4, 4 if nx == 64 else 2
+    kd = cone(L)
+    so = [0] * L
+    rng = np.random.default_rng(900 + nz)
+    x = (0.02 * rng.random(nz * ny * nx)).astype(np.float32)
+    xd = torch.from_numpy(x).to(DEV)
+    M = ny * nx
+    y = c64(rng.standard_normal((L, M)) + 1j * rng.standard_normal((L, M))).reshape(-1)
+    v = c64(rng.standard_normal((nb, nz, ny, nx)) + 1j * rng.standard_normal((nb, nz, ny, nx))).reshape(-1)
+    out = []
+    for t in (0, 16):
+        h = binding.MQNPM(shape, kd, so, [1.0], model=model, krylov_tol=1e-6, max_batch=nb, tile=t)
+        assert h.tile_info()["fused_xy"] == bool(t & 16)
+        h.set_measurements(y)
+        a_f = h.green_apply(v, adjoint=False).cpu()
+        a_a = h.green_apply(v, adjoint=True).cpu()
+        g, loss, its = h.grad_batch(xd, list(range(nb)), 0.5)
+        out.append((a_f, a_a, g.cpu(), loss, list(its)))
+        h.close()
+    (f0, b0, g0, l0, i0), (f1, b1, g1, l1, i1) = out
+
+    def rel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+    d = {"apply": rel(f1, f0), "adjoint": rel(b1, b0), "grad": rel(g1, g0), "loss": abs(l1 - l0) / abs(l0)}
+    print(shape, model, d, i0, i1)
+    assert i0 == i1 and l0 == l1, (d, i0, i1)
+    assert torch.equal(f0, f1) and torch.equal(b0, b1) and torch.equal(g0, g1), d
