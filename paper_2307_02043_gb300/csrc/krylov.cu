@@ -45,11 +45,24 @@ MQ_D void sum_partials(const double* part, int b, int nctas, double (&out)[K]) {
   block_sum<K>(v, scratch, out);
 }
 
+// ||b||^2 of each slot's right-hand side from an apply's partials, kept in
+// the slot state for a k_fin_init whose start is not 0 (bnorm2_fwd < 0).
+__global__ void k_set_bnorm(KState* st, const double* part, int nctas) {
+  const int b = blockIdx.x;
+  double s[1];
+  sum_partials<1>(part, b, nctas, s);
+  if (threadIdx.x == 0) st[b].bnorm2 = s[0];
+}
+
+// Slot state of a solve whose first residual r_0 has its partials in part.
+// bnorm2_fwd > 0: ||b||^2 for every slot; == 0: ||r_0||^2 (a start at 0);
+// < 0: the value k_set_bnorm left in the slot state.
 __global__ void k_fin_init(KState* st, const double* part, int nctas, double tol2, double bnorm2_fwd) {
   const int b = blockIdx.x;
   double s[1];
   sum_partials<1>(part, b, nctas, s);
   if (threadIdx.x == 0) {
+    const double bkept = st[b].bnorm2;
     KState k;
     memset(&k, 0, sizeof(k));
     k.rho_re = s[0];
@@ -57,7 +70,7 @@ __global__ void k_fin_init(KState* st, const double* part, int nctas, double tol
     k.omega_re = 1.0;
     k.beta_re = 0.0;   // the first iteration takes p_1 = r_0 (iters == 0)
     k.rnorm2 = s[0];
-    k.bnorm2 = bnorm2_fwd > 0.0 ? bnorm2_fwd : s[0];
+    k.bnorm2 = bnorm2_fwd > 0.0 ? bnorm2_fwd : bnorm2_fwd < 0.0 ? bkept : s[0];
     k.tol2 = tol2;
     k.iters = 0;
     if (!isfinite(s[0])) {
@@ -648,12 +661,14 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool s
   return collect_states(h, nb, iters, stride, offset);
 }
 
-// Adjoint solve for nb slots: z = (I - G^H X)^{-1} G^H S^T r_det.
+// Adjoint solve for nb slots: z = (I - G^H X)^{-1} b, b = G^H S^T r_det,
+// started at z_0 = b (the first term of z's Neumann series, as u_in starts a
+// cold forward solve): r_0 = b - (I - G^H X) b = G^H (x b), one more apply
+// that saves about one BiCGSTAB iteration (two applies) at the step's
+// contrasts.  The stopping rule keeps ||r|| <= tol ||b||.
 static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int stride, int offset) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
-  const size_t N = h->N;
-  CK(cudaMemsetAsync(w.zs, 0, nb * N * sizeof(float2), s));
   GreenCall c = base_call(h, nb, true);
   c.pro = PRO_LIFT;
   c.plane = true;                      // S^T r: nonzero on the detector plane only
@@ -662,13 +677,23 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
     CK(detector_adjoint(h, w.rdet, w.rlift, nb));
     c.pa.rdet = w.rlift;
   }
-  c.epi = EPI_INIT;                    // r_0 = b = G^H S^T r_det (start z_0 = 0)
-  c.ea.out = w.r;
+  c.epi = EPI_INIT;                    // z_0 = b = G^H S^T r_det, and ||b||^2
+  c.ea.out = w.zs;
   c.ea.out2 = w.rhat;
   CK(glaunch(h, c, s));
-  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, 0.0);
+  k_set_bnorm<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row);
+  GreenCall c0 = base_call(h, nb, true);
+  c0.pro = PRO_CONTRAST;               // r_0 = G^H (x z_0)
+  c0.pa.x = x;
+  c0.pa.xs = x ? nullptr : w.xslot;
+  c0.pa.q = w.zs;
+  c0.epi = EPI_INIT;
+  c0.ea.out = w.r;
+  c0.ea.out2 = w.rhat;
+  CK(glaunch(h, c0, s));
+  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, -1.0);
   CK(cudaGetLastError());
-  h->launches += 1;
+  h->launches += 2;
   int rc = krylov_iterate(h, nb, x, w.zs, true);
   if (rc != MQNPM_OK) return rc;
   return collect_states(h, nb, iters, stride, offset);
