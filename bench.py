@@ -182,6 +182,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ problem set-up
+# Start of the LS adjoint solves per workload (mqnpm_config.adjoint_start):
+# at b = G^H S^T r by default; at 0 where the extra apply of the b start
+# saves no BiCGSTAB iteration (measured on GB300: ls192, contrast up to 0.05,
+# 153.7 illum-gradients/s from 0 against 146.6 from b at the same counts).
+ADJOINT_START = {"ls192": "zero"}
+
+
+def adjoint_start(w, args=None):
+    forced = getattr(args, "adjoint_start", None) if args is not None else None
+    return forced or ADJOINT_START.get(w.name, "b")
+
+
 def subset_of(w):
     so = np.zeros(w.L, dtype=np.int32)
     for s, idx in enumerate(synth.subsets(w)):
@@ -189,7 +201,7 @@ def subset_of(w):
     return so
 
 
-def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False):
+def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False, adj="b"):
     """Synthetic measurements and alpha_s, produced with the library itself."""
     kd = synth.illumination_dirs(w)
     so = subset_of(w)
@@ -211,7 +223,8 @@ def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False):
     start = torch.from_numpy(synth.power_start(w).astype(np.float32)).to(dev).reshape(-1)
     alpha = [setup.lipschitz(list(s), w.S / w.L, start, iters=10) for s in subs]
     setup.close()
-    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, direct_launches=direct, **common)
+    h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, direct_launches=direct, adjoint_start=adj,
+                      **common)
     h.set_measurements(y.reshape(-1))
     return h, y, alpha, kd, so, subs
 
@@ -222,8 +235,9 @@ class PlainPath:
     FFTs, pointwise multiply, inverse, crop; host-driven BiCGSTAB.  This is the
     baseline the fused path is compared with (same model, same tolerance)."""
 
-    def __init__(self, w, kd, y, torch, dev):
+    def __init__(self, w, kd, y, torch, dev, adj="b"):
         self.t = torch
+        self.adj = adj
         self.w = w
         self.n = w.n
         self.P = 2 * w.n
@@ -302,7 +316,8 @@ class PlainPath:
         lift = t.zeros_like(ui)
         lift[-1] = r
         b = self.G(lift, adj=True)
-        z, ita = self.bicgstab(lambda q: q - self.G(x3 * q, adj=True), b, b, tol)   # started at b, as the library's
+        z0 = b if self.adj == "b" else t.zeros_like(b)   # the library's start
+        z, ita = self.bicgstab(lambda q: q - self.G(x3 * q, adj=True), b, z0, tol)
         return (u.conj() * z).real.reshape(-1), itf + ita
 
 
@@ -698,10 +713,10 @@ def prox_roofline(trace: dict, rank: int, N: int, ms: float):
                     "DRAM traffic can be below these algorithmic bytes"}
 
 
-def plain_vs_fused(w, kd, y, alpha, so, subs, x, tile, torch, binding, dev):
+def plain_vs_fused(w, kd, y, alpha, so, subs, x, tile, torch, binding, dev, adj="b"):
     """The same gradient (one whole subset, same x, same measurements, Krylov
-    tolerance and solver starts: forward at u_in, adjoint at b = G^H S^T r) on
-    both arms: the fused library call on a handle
+    tolerance and solver starts: forward at u_in, adjoint at b = G^H S^T r or
+    at 0 as the workload's) on both arms: the fused library call on a handle
     without warm start, and the plain torch.fft (cuFFT) path with one
     illumination per launch.  Reports per-illumination and per-Krylov-
     iteration times and the speedup at equal solver work."""
@@ -709,7 +724,7 @@ def plain_vs_fused(w, kd, y, alpha, so, subs, x, tile, torch, binding, dev):
     scale = w.S / w.L
     hc = binding.MQNPM(w.n, kd, so, alpha, model=w.model, h=w.h, kb=w.kb, tv=w.tv, lam=w.lam, box=w.box,
                        krylov_tol=w.krylov_tol, krylov_maxit=1000, dual_iters=w.dual_iters, max_batch=len(il),
-                       warm_start=False, tile=tile)
+                       warm_start=False, tile=tile, adjoint_start=adj)
     hc.set_measurements(y.reshape(-1))
     hc.grad_batch(x, il, scale, allow_not_converged=True)          # warm-up
     reps = 3
@@ -723,7 +738,7 @@ def plain_vs_fused(w, kd, y, alpha, so, subs, x, tile, torch, binding, dev):
     f_ms = e0.elapsed_time(e1) / reps
     hc.close()
     f_iters = sum(a + b for a, b in its)
-    plain = PlainPath(w, kd, y, torch, dev)
+    plain = PlainPath(w, kd, y, torch, dev, adj)
     plain.grad(x, il[0], w.krylov_tol)                                # warm-up
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -798,7 +813,8 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     """Set-up, timed MQNPM iterations (inputs resident in HBM), the end-to-end
     repeat through host buffers and the per-kernel figures of one workload."""
     h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile,
-                                             direct=getattr(args, "direct_launches", False))
+                                             direct=getattr(args, "direct_launches", False),
+                                             adj=adjoint_start(w, args))
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
     shard = bool(getattr(args, "shard", False))
     if shard:
@@ -917,7 +933,8 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
                    "S": w.S, "model": "lippmann-schwinger" if w.model == "ls" else "first-born",
                    "krylov_tol": w.krylov_tol if w.model == "ls" else None, "dual_iters": w.dual_iters,
                    "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
-                   "krylov_start": "forward solves warm-started from each illumination's last field"
+                   "krylov_start": "forward solves warm-started from each illumination's last field; adjoint "
+                                   "solves from %s" % ("b = G^H S^T r" if adjoint_start(w, args) == "b" else "0")
                    if w.model == "ls" else None,
                    "parallelism": ("illumination-sharded x%d (one all-reduce per step)" % world) if shard
                    else ("replicas" if world > 1 else "single-gpu")},
@@ -960,7 +977,8 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     out["config"]["iterations"] = "k = %d..%d from x0 = 0" % (infos[0]["k"], infos[-1]["k"])
     h.close()
     if rank == 0 and not args.no_plain:
-        fused, plain_d, sp = plain_vs_fused(w, kd, y, alpha, so, subs, x, args.tile, torch, binding, dev)
+        fused, plain_d, sp = plain_vs_fused(w, kd, y, alpha, so, subs, x, args.tile, torch, binding, dev,
+                                            adjoint_start(w, args))
         out["fused_cold"] = fused
         out["plain_gpu"] = plain_d
         out["speedup_vs_plain"] = sp
@@ -995,6 +1013,8 @@ def main():
     ap.add_argument("--batch", type=int, default=2, help="slots per apply in --green-only mode")
     ap.add_argument("--log-jsonl", default=None,
                     help="write one JSON line per timed MQNPM iteration (step info) to this file")
+    ap.add_argument("--adjoint-start", choices=["b", "zero"], default=None,
+                    help="start of the LS adjoint solves (default: the workload's, b unless listed in ADJOINT_START)")
     ap.add_argument("--tile", type=int, default=-1,
                     help="launch-shape tile of the Green's passes (-1: autotuned when a handle is created)")
     ap.add_argument("--serve-uneven", action="store_true",

@@ -148,6 +148,11 @@ typedef struct mqnpm_config {
                               ignored when green_hat is given. The truncated
                               kernel's construction at create holds two
                               (2n+1)^3 FP64 complex buffers for its duration */
+  int adjoint_start;       /* LS adjoint solves (I - G^H X) z = b, b = G^H S^T r:
+                              0 starts at z_0 = b (one more Green's apply for
+                              r_0 = G^H(x b); at contrasts up to about 0.04 it
+                              saves one BiCGSTAB iteration, two applies);
+                              1 starts at z_0 = 0 (r_0 = b)                    */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;

@@ -243,7 +243,8 @@ int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle*
       !(cfg->gamma > 0 && cfg->gamma <= 1.0) || cfg->tile < -1 || cfg->tile >= MQ_TILES ||
       !(cfg->det_na >= 0.0 && std::isfinite(cfg->det_na)) || !std::isfinite(cfg->det_distance) ||
       cfg->barrier_wait_cycles < 0 ||
-      (cfg->green_kernel != MQNPM_KERNEL_SAMPLED && cfg->green_kernel != MQNPM_KERNEL_TRUNCATED)) {
+      (cfg->green_kernel != MQNPM_KERNEL_SAMPLED && cfg->green_kernel != MQNPM_KERNEL_TRUNCATED) ||
+      (cfg->adjoint_start != 0 && cfg->adjoint_start != 1)) {
     fprintf(stderr, "mqnpm_create: invalid configuration\n");
     delete h;
     return MQNPM_ERR_INVALID_ARG;
@@ -289,6 +290,7 @@ int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle*
   h->device = cfg->device;
   h->stream = static_cast<cudaStream_t>(cfg->stream);
   h->warm_start = cfg->warm_start != 0;
+  h->adjoint_from_b = cfg->adjoint_start == 0;
   h->direct_launches = cfg->direct_launches != 0;
   h->budget = cfg->hbm_budget_bytes;
   h->guard = (cfg->guard_bytes + 255) / 256 * 256;

@@ -192,6 +192,7 @@ struct mqnpm_handle {
   std::vector<int> fields_illum;
   // Krylov warm start: last forward field per illumination
   bool warm_start = false;
+  bool adjoint_from_b = true;                // adjoint solves start at z_0 = b (else at 0)
   float2* ufield = nullptr;      // [L][N]
   std::vector<int> have_field;   // [L]
   // outer-loop state (Algorithm 4.1)

@@ -661,14 +661,16 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool s
   return collect_states(h, nb, iters, stride, offset);
 }
 
-// Adjoint solve for nb slots: z = (I - G^H X)^{-1} b, b = G^H S^T r_det,
-// started at z_0 = b (the first term of z's Neumann series, as u_in starts a
-// cold forward solve): r_0 = b - (I - G^H X) b = G^H (x b), one more apply
-// that saves about one BiCGSTAB iteration (two applies) at the step's
-// contrasts.  The stopping rule keeps ||r|| <= tol ||b||.
+// Adjoint solve for nb slots: z = (I - G^H X)^{-1} b, b = G^H S^T r_det.
+// adjoint_from_b: started at z_0 = b (the first term of z's Neumann series,
+// as u_in starts a cold forward solve): r_0 = b - (I - G^H X) b = G^H (x b),
+// one more apply that saves about one BiCGSTAB iteration (two applies) at
+// contrasts up to about 0.04.  Otherwise started at z_0 = 0 (r_0 = b).  The
+// stopping rule is ||r|| <= tol ||b|| either way.
 static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int stride, int offset) {
   Workspace& w = h->w;
   cudaStream_t s = h->stream;
+  if (!h->adjoint_from_b) CK(cudaMemsetAsync(w.zs, 0, (size_t)nb * h->N * sizeof(float2), s));
   GreenCall c = base_call(h, nb, true);
   c.pro = PRO_LIFT;
   c.plane = true;                      // S^T r: nonzero on the detector plane only
@@ -676,6 +678,18 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   if (h->remote) {                     // S^T D^H r_det
     CK(detector_adjoint(h, w.rdet, w.rlift, nb));
     c.pa.rdet = w.rlift;
+  }
+  if (!h->adjoint_from_b) {            // r_0 = b = G^H S^T r_det (start z_0 = 0)
+    c.epi = EPI_INIT;
+    c.ea.out = w.r;
+    c.ea.out2 = w.rhat;
+    CK(glaunch(h, c, s));
+    k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, 0.0);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    const int rc = krylov_iterate(h, nb, x, w.zs, true);
+    if (rc != MQNPM_OK) return rc;
+    return collect_states(h, nb, iters, stride, offset);
   }
   c.epi = EPI_INIT;                    // z_0 = b = G^H S^T r_det, and ||b||^2
   c.ea.out = w.zs;

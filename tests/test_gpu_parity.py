@@ -179,6 +179,26 @@ def test_grad_batch_matches_oracle(model, n, nb, max_batch):
     h.close()
 
 
+@pytest.mark.parametrize("start", ["b", "zero"])
+@pytest.mark.parametrize("n", [24, 32])
+def test_both_adjoint_starts_match_oracle(start, n):
+    """The LS adjoint solve (I - G^H X) z = G^H S^T r started at b or at 0
+    (mqnpm_config.adjoint_start): the same gradient to the solver tolerance,
+    against the oracle (which starts at 0)."""
+    w, kd, xt, om, ys, subs, so = problem(n, "ls", L=6, batch=3)
+    h = make_handle(n, kd, so, [1.0] * w.S, krylov_tol=1e-6, max_batch=3, adjoint_start=start)
+    h.set_measurements(c64(ys).reshape(-1))
+    x = 0.7 * xt
+    illum = [0, 2, 4]
+    scale = w.S / w.L
+    g, loss, its = h.grad_batch(f32(x).reshape(-1), illum, scale)
+    lo, go = om.batch_loss_grad(x, illum, ys, scale)
+    assert rel(g.cpu().numpy().reshape(go.shape), go) < 1e-4, (start, its)
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    assert all(a > 0 and b > 0 for a, b in its)
+    h.close()
+
+
 def test_physical_units_strong_scattering_matches_oracle():
     """The paper's simulated set-up in physical units (50 nm voxels, 406 nm,
     medium index 1.333, contrast up to (1.43/1.333)^2 - 1 = 0.15) on a 32^3
