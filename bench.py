@@ -682,16 +682,17 @@ def weighted_vs_unweighted_prox(torch, h, x, infos, w):
 def prox_bytes(trace: dict, rank: int, N: int) -> int:
     """Algorithmic bytes of one weighted proximal mapping from the barrier
     counts of its phase trace (float32 vectors, N voxels, rank-S metric):
-    Gram set-up (4S + 4) N; per divergence pass (R in, d out, U in)
-    (16 + 4S) N; per Newton evaluation (U, v, d, status in, x out)
-    (13 + 4S) N; per fix-up after a rejected trial (12 + 4S) N; per dual
+    Gram set-up (4S + 4) N; per divergence pass with the first Newton
+    evaluation (R, U, v, status in; d, x out) (25 + 4S) N; per further Newton
+    evaluation (U, v, d, status in, x out) (13 + 4S) N; per fix-up after a
+    rejected trial (12 + 4S) N; per dual
     update (x, R, P in; P, R out) 52 N; unweighted x pass (R, v in, x out)
     20 N.  The last evaluation's fix-up passes no barrier and is not counted."""
     c = trace.get("counts", {})
     S = rank
     b = 0
     b += c.get("gram", 0) * (4 * S + 4)
-    b += c.get("div_UTd", 0) * (16 + 4 * S)
+    b += c.get("div_UTd", 0) * (25 + 4 * S)
     b += c.get("newton_eval", 0) * (13 + 4 * S)
     b += c.get("x_fixup", 0) * (12 + 4 * S)
     b += c.get("dual_update", 0) * 52

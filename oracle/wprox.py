@@ -20,6 +20,10 @@ Readings where the paper is silent (also listed in the design notes):
     reduce ||phi|| (at most 30 halvings).
   * FGP: t_1 = 1, t_{j+1} = (1 + sqrt(1 + 4 t_j^2))/2,
     R_{j+1} = P_j + (t_j - 1)/t_{j+1} (P_j - P_{j-1}); R_1 = P_0 (warm start).
+  * Newton start of each dual iteration: with w(P) = v - (c/tau) d(P) + U gamma(P),
+    gamma(P) = (c/tau^2) (I + U^T U/tau)^{-1} U^T d(P), the solve starts at
+    beta_0 = beta_prev + tau (gamma - gamma_prev), which keeps
+    theta = gamma - beta/tau of the previous solve (both 0 at the first one).
 """
 from __future__ import annotations
 
@@ -118,6 +122,15 @@ class WProx:
         """w(P) = v - c B^{-1} d(P) (flat)."""
         return v.reshape(-1) - self.c * self.Binv(tvops.d_of(P).reshape(-1))
 
+    def gamma_of(self, P: np.ndarray) -> np.ndarray:
+        """gamma(P) = (c/tau^2) (I + U^T U / tau)^{-1} U^T d(P) (the S-vector of
+        the Woodbury term: w(P) = v - (c/tau) d(P) + U gamma(P))."""
+        S = self.U.shape[1]
+        if S == 0:
+            return np.zeros(0)
+        small = np.eye(S) + (self.U.T @ self.U) / self.tau
+        return (self.c / self.tau ** 2) * np.linalg.solve(small, self.U.T @ tvops.d_of(P).reshape(-1))
+
     def prox_box(self, w: np.ndarray, beta0=None):
         return prox_box_metric(w, self.U, self.tau, self.lo, self.hi, beta0,
                                self.newton_tol, self.newton_maxit)
@@ -150,19 +163,28 @@ class WProx:
         P_prev = np.zeros((self.D,) + self.shape) if P0 is None else np.asarray(P0, np.float64).copy()
         R = P_prev.copy()
         t = 1.0
-        beta = None
+        S = self.U.shape[1]
+        beta, g_prev = np.zeros(S), np.zeros(S)
         step = self.tau / (4.0 * self.D * self.c)
         newton = []
-        for _ in range(J):
-            x, beta, it = self.prox_box(self.w_of(v, R), beta)
+
+        def solve_at(Q):
+            nonlocal beta, g_prev
+            g = self.gamma_of(Q)
+            beta0 = beta + self.tau * (g - g_prev)   # theta = gamma - beta/tau kept from the last solve
+            x, beta, it = self.prox_box(self.w_of(v, Q), beta0)
+            g_prev = g
             newton.append(it)
+            return x
+
+        for _ in range(J):
+            x = solve_at(R)
             P = tvops.project_dual(R + step * tvops.dT(x.reshape(self.shape)), self.kind)
             t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
             R = P + ((t - 1.0) / t_next) * (P - P_prev)
             P_prev = P
             t = t_next
-        x, beta, it = self.prox_box(self.w_of(v, P_prev), beta)
-        newton.append(it)
+        x = solve_at(P_prev)
         return x.reshape(self.shape), P_prev, {"newton": newton, "beta": beta}
 
 

@@ -5,7 +5,9 @@
 // fixed order; every wait is bounded):
 //   G  (U != 0, once)  G = U^T U, U^T v; every block forms M = (I + G/tau)^{-1}.
 //   per dual iteration j = 1..J, then once more on P_J:
-//   A  d = d(R) and U^T d              -> gamma = (c/tau^2) M U^T d   (Woodbury)
+//   A  d = d(R), U^T d and the first Newton evaluation, at the point that keeps
+//      theta = gamma - beta/tau of the previous solve (one pass, one barrier)
+//                                      -> gamma = (c/tau^2) M U^T d   (Woodbury)
 //   N  semi-smooth Newton on phi(beta) = U^T(w - clip(w - U beta/tau)) + beta
 //      (Theorem 3.1, Algorithm 4.3): each evaluation also writes
 //      x = clip(w - U beta/tau) speculatively, so the accepted evaluation leaves x.
@@ -29,7 +31,7 @@ namespace {
 constexpr int WP_THREADS = 256;
 constexpr int WP_BPS = 2;        // co-resident blocks per SM the kernel is compiled and launched for
 constexpr int NW = WP_THREADS / 32;
-constexpr int NVMAX = MQNPM_MAX_S + MQNPM_MAX_S * (MQNPM_MAX_S + 1) / 2;   // S + S(S+1)/2
+constexpr int NVMAX = 2 * MQNPM_MAX_S + MQNPM_MAX_S * (MQNPM_MAX_S + 1) / 2;   // 2S + S(S+1)/2
 // Trace layout (long long pairs): pair 0 = (barriers passed, start time),
 // pairs 1..TR_ACC-1 = (tag, time) per barrier, pairs from TR_ACC on hold block
 // 0's accumulated times: [2 TR_ACC] dual update, [+1] work before the dual
@@ -120,6 +122,36 @@ struct F4 {
     return F4{{q.x, q.y, q.z, q.w}};
   }
 };
+
+// Per-thread staging slots in dynamic shared memory: slot j of thread t is
+// wp_stage[j * WP_THREADS + t] (16 bytes; consecutive threads, consecutive
+// addresses, so the 16-byte reads back are conflict-free).  cp.async copies
+// land there without holding registers while in flight, so the number of
+// loads a thread keeps in flight does not depend on how many registers the
+// compiler leaves a pass; each thread reads back only the slots it filled,
+// after its own cp.async.wait_all, so no block barrier is needed.
+extern __shared__ float4 wp_stage[];
+constexpr int WP_SLOTS_DUAL = 10;   // the dual update's ten streams
+constexpr int WP_SU_MAX = 8;        // rows of U staged by the Newton passes (the rest are loaded directly)
+// slots per thread for rank S: the dual update's ten, or the merged pass's
+// staged U rows + v + six divergence loads + status
+constexpr int wp_slots(int S) {
+  return (S < WP_SU_MAX ? S : WP_SU_MAX) + 8 > WP_SLOTS_DUAL ? (S < WP_SU_MAX ? S : WP_SU_MAX) + 8 : WP_SLOTS_DUAL;
+}
+
+MQ_D void cp16(float4* dst, const float* src) {   // 16 bytes global -> shared, cached in L2 only
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+MQ_D void cp4(float4* dst, const float* src) {    // 4 bytes global -> the first word of a slot
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+MQ_D void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+MQ_D F4 slot4(const float4* p) {
+  const float4 q = *p;
+  return F4{{q.x, q.y, q.z, q.w}};
+}
 
 // Barrier counters of one launch: every block passes the same sequence of
 // barriers, so these agree across blocks.
@@ -236,16 +268,10 @@ MQ_D void coords4(int k4, int nx, int ny, int& x0, int& y, int& z) {
   y = r - z * ny;
 }
 
-// d(R) = sum_d q_d(i - e_d)[i_d >= 1] - q_d(i)[i_d <= n_d - 2] at four voxels.
-MQ_D F4 div4(const float* __restrict__ R, int N, int nx, int ny, int nz, int k4, int x0, int y, int z) {
-  const int n4 = nx / 4, nn4 = nx * ny / 4;
-  const float* qx = R;
-  const float* qy = R + N;
-  const float* qz = R + 2 * (size_t)N;
-  const F4 ax = F4::load(qx, k4), ay = F4::load(qy, k4), az = F4::load(qz, k4);
-  const float axm = x0 > 0 ? qx[4 * k4 - 1] : 0.f;
-  const F4 aym = y > 0 ? F4::load(qy, k4 - n4) : F4::zero();
-  const F4 azm = z > 0 ? F4::load(qz, k4 - nn4) : F4::zero();
+// d(R) = sum_d q_d(i - e_d)[i_d >= 1] - q_d(i)[i_d <= n_d - 2] at four voxels,
+// from the loaded values: a* = q_*(i), a*m = q_*(i - e_*) (zero where i_* = 0).
+MQ_D F4 div4_of(const F4& ax, float axm, const F4& ay, const F4& aym, const F4& az, const F4& azm, int nx,
+                int ny, int nz, int x0, int y, int z) {
   F4 d;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -258,6 +284,18 @@ MQ_D F4 div4(const float* __restrict__ R, int N, int nx, int ny, int nz, int k4,
     d.v[m] = s;
   }
   return d;
+}
+
+MQ_D F4 div4(const float* __restrict__ R, int N, int nx, int ny, int nz, int k4, int x0, int y, int z) {
+  const int n4 = nx / 4, nn4 = nx * ny / 4;
+  const float* qx = R;
+  const float* qy = R + N;
+  const float* qz = R + 2 * (size_t)N;
+  const F4 ax = F4::load(qx, k4), ay = F4::load(qy, k4), az = F4::load(qz, k4);
+  const float axm = x0 > 0 ? qx[4 * k4 - 1] : 0.f;
+  const F4 aym = y > 0 ? F4::load(qy, k4 - n4) : F4::zero();
+  const F4 azm = z > 0 ? F4::load(qz, k4 - nn4) : F4::zero();
+  return div4_of(ax, axm, ay, aym, az, azm, nx, ny, nz, x0, y, z);
 }
 
 template <int TV>
@@ -505,34 +543,6 @@ __device__ __noinline__ void pass_gram(Shared<S>* sh) {
     for (int k = 0; k < NG + S; ++k) sh->blk[k] = o[k];
 }
 
-// ---- phase A: d = d(src), block partials of U^T d into blk.
-template <int S>
-__device__ __noinline__ void pass_div(Shared<S>* sh, const float* src) {
-  const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
-  const int nx = a.nx, ny = a.ny, nz = a.nz, N = a.N, N4 = a.N / 4;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const float* __restrict__ rs = src;
-  float* __restrict__ dout = a.d;
-  float acc[S];
-#pragma unroll
-  for (int s = 0; s < S; ++s) acc[s] = 0.f;
-  for (int k4 = tid; k4 < N4; k4 += stride) {
-    int x0, y, z;
-    coords4(k4, nx, ny, x0, y, z);
-    F4 u[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) u[s] = F4::ldg(a.U.u[s], k4);   // U is read-only in the kernel
-    const F4 dv = div4(rs, N, nx, ny, nz, k4, x0, y, z);
-    dv.store(dout, k4);
-#pragma unroll
-    for (int s = 0; s < S; ++s) acc[s] += dot4(u[s], dv);
-  }
-  double o[S];
-  block_partial<S>(acc, o);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < S; ++k) sh->blk[k] = o[k];
-}
-
 // ---- phase X (U = 0): x = clip(v - (c/tau) d(src)).
 __device__ __noinline__ void pass_x(const WpArgs* pa, const float* src, float* xw) {
   const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
@@ -554,11 +564,16 @@ __device__ __noinline__ void pass_x(const WpArgs* pa, const float* src, float* x
 // ---- phase N: one evaluation at theta = gamma - beta_eval/tau.  Writes
 // x = clip(z) speculatively, block partials of U^T(w - clip(z)) into blk[0..S)
 // and of the status flips of sum_{inner} u u^T into blk[S..S+NG).
-template <int S>
-__device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
+// MERGED (the first evaluation of a dual iteration, in the divergence pass):
+// d = d(src) is formed here, stored, and its U^T d partials go to
+// blk[S+NG..2S+NG); gamma is not known yet, so the evaluation point is given
+// by theta alone (theta of the previous solve) and the partials are
+// U^T(v - (c/tau) d - clip(z)); the kernel adds G gamma once gamma is known.
+template <int S, bool MERGED>
+__device__ __noinline__ void pass_newton(Shared<S>* sh, const float* src, float* xw) {
   constexpr int NG = S * (S + 1) / 2;
   const WpArgs a = sh->a;   // private copy: loop loads cannot alias it, fields stay in registers
-  const int N4 = a.N / 4;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, N = a.N, N4 = a.N / 4;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   const int gw = tid >> 5, nwt = stride >> 5;
@@ -579,37 +594,81 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
   }
   float th[S], ga[S];
 #pragma unroll
-  for (int s = 0; s < S; ++s) { th[s] = sh->theta[s]; ga[s] = sh->gam[s]; }
-  float acc[S];
+  for (int s = 0; s < S; ++s) { th[s] = sh->theta[s]; ga[s] = MERGED ? 0.f : sh->gam[s]; }   // ga unused when MERGED
+  float acc[S], accd[MERGED ? S : 1];
 #pragma unroll
   for (int s = 0; s < S; ++s) acc[s] = 0.f;
+#pragma unroll
+  for (int s = 0; s < (MERGED ? S : 1); ++s) accd[s] = 0.f;
   float dH[NGL];
 #pragma unroll
   for (int j = 0; j < NGL; ++j) dH[j] = 0.f;
   const float* __restrict__ din = a.d;
+  float* __restrict__ dout = a.d;
+  const float* __restrict__ rs = src;
   float* __restrict__ xout = xw;
   uchar4* __restrict__ stat = reinterpret_cast<uchar4*>(a.status);
+  constexpr int SU = S < WP_SU_MAX ? S : WP_SU_MAX;   // staged rows of U
+  constexpr int SLOT_STAT = MERGED ? SU + 7 : SU + 2;
+  constexpr int T = WP_THREADS;
+  static_assert(SLOT_STAT < wp_slots(S), "staging slots");
+  const int n4 = nx / 4, nn4 = nx * ny / 4;
+  float4* st = wp_stage + threadIdx.x;
   for (int wbase = gw * 32; wbase < N4; wbase += nwt * 32) {
     const int k4 = wbase + lane;
     const bool valid = k4 < N4;
     F4 u[S];
     float sign[4] = {0.f, 0.f, 0.f, 0.f};
     if (valid) {
+      // stage SU rows of U, v, d (or the six divergence loads of src) and the
+      // status word; U rows beyond SU go to registers directly
+      int x0 = 0, y = 0, z = 0;
 #pragma unroll
-      for (int s = 0; s < S; ++s) u[s] = F4::ldg(a.U.u[s], k4);   // U, v are read-only in the kernel
-      const F4 v4 = F4::ldg(a.v, k4), d4 = F4::load(din, k4);
-      const uchar4 st4 = stat[k4];
+      for (int s = 0; s < SU; ++s) cp16(st + s * T, a.U.u[s] + 4 * (size_t)k4);
+      cp16(st + SU * T, a.v + 4 * (size_t)k4);
+      if constexpr (MERGED) {
+        coords4(k4, nx, ny, x0, y, z);
+        cp16(st + (SU + 1) * T, rs + 4 * (size_t)k4);
+        cp16(st + (SU + 2) * T, rs + N + 4 * (size_t)k4);
+        cp16(st + (SU + 3) * T, rs + 2 * (size_t)N + 4 * (size_t)k4);
+        if (y > 0) cp16(st + (SU + 4) * T, rs + N + 4 * (size_t)(k4 - n4));
+        if (z > 0) cp16(st + (SU + 5) * T, rs + 2 * (size_t)N + 4 * (size_t)(k4 - nn4));
+        if (x0 > 0) cp4(st + (SU + 6) * T, rs + 4 * (size_t)k4 - 1);
+      } else {
+        cp16(st + (SU + 1) * T, din + 4 * (size_t)k4);
+      }
+      cp4(st + SLOT_STAT * T, reinterpret_cast<const float*>(stat + k4));
+#pragma unroll
+      for (int s = SU; s < S; ++s) u[s] = F4::ldg(a.U.u[s], k4);   // U is read-only in the kernel
+      cp_wait_all();
+#pragma unroll
+      for (int s = 0; s < SU; ++s) u[s] = slot4(st + s * T);
+      const F4 v4 = slot4(st + SU * T);
+      F4 d4;
+      if constexpr (MERGED) {
+        const F4 ax = slot4(st + (SU + 1) * T), ay = slot4(st + (SU + 2) * T), az = slot4(st + (SU + 3) * T);
+        const F4 aym = y > 0 ? slot4(st + (SU + 4) * T) : F4::zero();
+        const F4 azm = z > 0 ? slot4(st + (SU + 5) * T) : F4::zero();
+        const float axm = x0 > 0 ? reinterpret_cast<const float*>(st + (SU + 6) * T)[0] : 0.f;
+        d4 = div4_of(ax, axm, ay, aym, az, azm, nx, ny, nz, x0, y, z);
+        d4.store(dout, k4);
+#pragma unroll
+        for (int s = 0; s < S; ++s) accd[s] += dot4(u[s], d4);
+      } else {
+        d4 = slot4(st + (SU + 1) * T);
+      }
+      const uchar4 st4 = *reinterpret_cast<const uchar4*>(st + SLOT_STAT * T);
       const unsigned char old[4] = {st4.x, st4.y, st4.z, st4.w};
       unsigned char nw[4];
       F4 xo;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const float base = v4.v[m] - cdt * d4.v[m];
-        float zz = base, ww = base;
+        float zz = base, ww = base;   // MERGED: w - U gamma (gamma added to the sums later)
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           zz = fmaf(u[s].v[m], th[s], zz);
-          ww = fmaf(u[s].v[m], ga[s], ww);
+          if constexpr (!MERGED) ww = fmaf(u[s].v[m], ga[s], ww);
         }
         const float xc = clampf(zz, a.lo, a.hi);
         xo.v[m] = xc;
@@ -650,6 +709,11 @@ __device__ __noinline__ void pass_newton(Shared<S>* sh, float* xw) {
   block_partial<S>(acc, o);
   if (threadIdx.x == 0)
     for (int k = 0; k < S; ++k) sh->blk[k] = o[k];
+  if constexpr (MERGED) {
+    block_partial<S>(accd, o);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < S; ++k) sh->blk[S + NG + k] = o[k];
+  }
 #pragma unroll
   for (int j = 0; j < NGL; ++j)
     if (lane + 32 * j < NG) sh->dH[wib][lane + 32 * j] = dH[j];
@@ -688,6 +752,8 @@ __device__ __noinline__ void pass_fixup(Shared<S>* sh, float* xw) {
 }
 
 // ---- phase D: P = Proj(R + step grad x), R = P + mom (P - P_prev), in place.
+// The ten input streams of four voxels (x, its +y and +z neighbours and the
+// next voxel in x, R and P_prev) are staged with cp.async before any is used.
 template <int TV>
 __device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
   const WpArgs a = *pa;     // private copy: loop loads cannot alias it, fields stay in registers
@@ -702,59 +768,51 @@ __device__ __noinline__ void pass_dual(const WpArgs* pa, float mom) {
   float* __restrict__ Py = a.Pd + N;
   float* __restrict__ Pz = a.Pd + 2 * (size_t)N;
   const float step = a.step;
-  // two groups of four voxels per iteration, every load issued before any store
-  constexpr int G = 2;
-  for (int kb = tid; kb < N4; kb += G * stride) {
-    int x0[G], y[G], z[G];
-    bool ok[G];
-    F4 x4[G], xy[G], xz[G], rx[G], ry[G], rz[G], ox[G], oy[G], oz[G];
-    float xnext[G];
+  float4* st = wp_stage + threadIdx.x;
+  constexpr int T = WP_THREADS;
+  static_assert(WP_SLOTS_DUAL <= wp_slots(0), "staging slots");
+  for (int k4 = tid; k4 < N4; k4 += stride) {
+    int x0, y, z;
+    coords4(k4, nx, ny, x0, y, z);
+    const bool hx = x0 + 4 < nx, hy = y < ny - 1, hz = z < nz - 1;
+    cp16(st, xs + 4 * (size_t)k4);
+    if (hy) cp16(st + T, xs + 4 * (size_t)(k4 + n4));
+    if (hz) cp16(st + 2 * T, xs + 4 * (size_t)(k4 + nn4));
+    cp16(st + 3 * T, Rx + 4 * (size_t)k4);
+    cp16(st + 4 * T, Ry + 4 * (size_t)k4);
+    cp16(st + 5 * T, Rz + 4 * (size_t)k4);
+    cp16(st + 6 * T, Px + 4 * (size_t)k4);
+    cp16(st + 7 * T, Py + 4 * (size_t)k4);
+    cp16(st + 8 * T, Pz + 4 * (size_t)k4);
+    if (hx) cp4(st + 9 * T, xs + 4 * (size_t)k4 + 4);
+    cp_wait_all();
+    const F4 x4 = slot4(st);
+    const F4 xy = hy ? slot4(st + T) : x4;
+    const F4 xz = hz ? slot4(st + 2 * T) : x4;
+    const float xnext = hx ? reinterpret_cast<const float*>(st + 9 * T)[0] : 0.f;
+    F4 rx = slot4(st + 3 * T), ry = slot4(st + 4 * T), rz = slot4(st + 5 * T);
+    F4 ox = slot4(st + 6 * T), oy = slot4(st + 7 * T), oz = slot4(st + 8 * T);
 #pragma unroll
-    for (int q = 0; q < G; ++q) {
-      const int k4 = kb + q * stride;
-      ok[q] = k4 < N4;
-      const int kk = ok[q] ? k4 : kb;
-      coords4(kk, nx, ny, x0[q], y[q], z[q]);
-      x4[q] = F4::load(xs, kk);
-      xnext[q] = (x0[q] + 4 < nx) ? xs[4 * kk + 4] : 0.f;
-      xy[q] = (y[q] < ny - 1) ? F4::load(xs, kk + n4) : x4[q];
-      xz[q] = (z[q] < nz - 1) ? F4::load(xs, kk + nn4) : x4[q];
-      rx[q] = F4::load(Rx, kk);
-      ry[q] = F4::load(Ry, kk);
-      rz[q] = F4::load(Rz, kk);
-      ox[q] = F4::load(Px, kk);
-      oy[q] = F4::load(Py, kk);
-      oz[q] = F4::load(Pz, kk);
+    for (int m = 0; m < 4; ++m) {
+      const float xn = (m < 3) ? x4.v[m + 1] : xnext;
+      const float gx = (x0 + m < nx - 1) ? xn - x4.v[m] : 0.f;
+      float px = rx.v[m] + step * gx;
+      float py = ry.v[m] + step * (xy.v[m] - x4.v[m]);
+      float pz = rz.v[m] + step * (xz.v[m] - x4.v[m]);
+      project<TV>(px, py, pz);
+      rx.v[m] = px + mom * (px - ox.v[m]);
+      ry.v[m] = py + mom * (py - oy.v[m]);
+      rz.v[m] = pz + mom * (pz - oz.v[m]);
+      ox.v[m] = px;
+      oy.v[m] = py;
+      oz.v[m] = pz;
     }
-#pragma unroll
-    for (int q = 0; q < G; ++q) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const float xn = (m < 3) ? x4[q].v[m + 1] : xnext[q];
-        const float gx = (x0[q] + m < nx - 1) ? xn - x4[q].v[m] : 0.f;
-        float px = rx[q].v[m] + step * gx;
-        float py = ry[q].v[m] + step * (xy[q].v[m] - x4[q].v[m]);
-        float pz = rz[q].v[m] + step * (xz[q].v[m] - x4[q].v[m]);
-        project<TV>(px, py, pz);
-        rx[q].v[m] = px + mom * (px - ox[q].v[m]);
-        ry[q].v[m] = py + mom * (py - oy[q].v[m]);
-        rz[q].v[m] = pz + mom * (pz - oz[q].v[m]);
-        ox[q].v[m] = px;
-        oy[q].v[m] = py;
-        oz[q].v[m] = pz;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < G; ++q) {
-      if (!ok[q]) continue;
-      const int k4 = kb + q * stride;
-      ox[q].store(Px, k4);
-      oy[q].store(Py, k4);
-      oz[q].store(Pz, k4);
-      rx[q].store(Rx, k4);
-      ry[q].store(Ry, k4);
-      rz[q].store(Rz, k4);
-    }
+    ox.store(Px, k4);
+    oy.store(Py, k4);
+    oz.store(Pz, k4);
+    rx.store(Rx, k4);
+    ry.store(Ry, k4);
+    rz.store(Rz, k4);
   }
 }
 
@@ -788,7 +846,10 @@ __global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
         }
       for (int s = 0; s < S; ++s) sh.Uv[s] = sh.tot[NG + s];
       form_woodbury<S>(sh.G, a.inv_tau, sh.M);
-      for (int s = 0; s < S; ++s) sh.beta[s] = 0.0;
+      for (int s = 0; s < S; ++s) {
+        sh.beta[s] = 0.0;
+        sh.theta[s] = 0.f;   // theta of the "previous solve" before the first one
+      }
     }
     __syncthreads();
   }
@@ -802,23 +863,38 @@ __global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
       pass_x(&sh.a, src, xw);
       if (!final_eval && !grid_reduce<0>(nullptr, nullptr, a, ep, 2)) return;
     } else {
+      // The divergence pass also takes the first Newton evaluation, at the
+      // point that keeps theta = gamma - beta/tau of the previous solve
+      // (beta_0 = beta_prev + tau (gamma - gamma_prev)): U^T d, the status
+      // flips and U^T(v - (c/tau) d - clip(z)) in one barrier.
       long long t0 = tracer(a) ? globaltimer() : 0;
-      pass_div<S>(&sh, src);
+      pass_newton<S, true>(&sh, src, xw);
       if (tracer(a)) tr_add(a, 4, globaltimer() - t0);
-      if (!grid_reduce<S>(sh.blk, sh.tot, a, ep, 3)) return;
-      // S threads in parallel: gamma = c/tau^2 M U^T d, then (U^T w)_s
+      if (!grid_reduce<NV + S>(sh.blk, sh.tot, a, ep, 3)) return;
+      const double* utd = sh.tot + NV;   // U^T d
+      // S threads in parallel: gamma = c/tau^2 M U^T d, then (U^T w)_s, the
+      // evaluation's U^T(w - clip(z)) = partials + (G gamma)_s, and its point
+      // beta' = tau (gamma - theta)
       if (threadIdx.x < S) {
         const int s = threadIdx.x;
         double g = 0.0;
-        for (int t = 0; t < S; ++t) g = fma(sh.M[s * S + t], sh.tot[t], g);
+        for (int t = 0; t < S; ++t) g = fma(sh.M[s * S + t], utd[t], g);
         sh.gamma[s] = a.c_tau2 * g;
       }
       __syncthreads();
       if (threadIdx.x < S) {
         const int s = threadIdx.x;
-        double g = sh.Uv[s] - a.c_tau * sh.tot[s];
-        for (int t = 0; t < S; ++t) g = fma(sh.G[s * S + t], sh.gamma[t], g);
-        sh.phi_cur[s] = g * g;   // scratch until the reset below
+        double gg = 0.0;
+        for (int t = 0; t < S; ++t) gg = fma(sh.G[s * S + t], sh.gamma[t], gg);
+        const double uw = sh.Uv[s] - a.c_tau * utd[s] + gg;
+        sh.phi_cur[s] = uw * uw;   // scratch until the reset below
+        sh.tot[s] += gg;
+        sh.beta_eval[s] = a.tau * (sh.gamma[s] - (double)sh.theta[s]);
+      }
+      if (threadIdx.x < NG) {   // H's off-identity terms after the evaluation's status flips
+        const double hv = sh.Htot[threadIdx.x] + sh.tot[S + threadIdx.x];
+        sh.Htot[threadIdx.x] = hv;
+        sh.Hf[threadIdx.x] = (float)(hv * a.inv_tau);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -826,7 +902,6 @@ __global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
         for (int s = 0; s < S; ++s) nrm += sh.phi_cur[s];
         sh.scale = fmax(1.0, nrm);   // the stopping test compares squared norms
         for (int s = 0; s < S; ++s) {
-          sh.beta_eval[s] = sh.beta[s];
           sh.dir[s] = 0.0;
           sh.phi_cur[s] = 0.0;
         }
@@ -839,15 +914,26 @@ __global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
       }
       __syncthreads();
       const int max_evals = a.maxit * 8;
-      int my_evals = 0;
-      while (true) {
+      int my_evals = 1;
+      if (threadIdx.x == 0) {
+        t0 = tracer(a) ? globaltimer() : 0;
+        NewtonState<S> ns{sh.beta, sh.beta_eval, sh.dir, sh.phi_cur, &sh.nphi_cur, &sh.tstep, &sh.halvings,
+                          &sh.accepted, &sh.first, &sh.accepted_last};
+        const int done = newton_decide<S>(ns, sh.tot, sh.Hf, a.tol * a.tol * sh.scale, a.maxit,
+                                          my_evals >= max_evals);
+        sh.done = done;
+        if (done) last_newton = sh.accepted;
+        if (tracer(a)) tr_add(a, 3, globaltimer() - t0);
+      }
+      __syncthreads();
+      while (!sh.done) {
         if (threadIdx.x < S) {
           sh.theta[threadIdx.x] = (float)(sh.gamma[threadIdx.x] - sh.beta_eval[threadIdx.x] * a.inv_tau);
           sh.gam[threadIdx.x] = (float)sh.gamma[threadIdx.x];
         }
         __syncthreads();
         t0 = tracer(a) ? globaltimer() : 0;
-        pass_newton<S>(&sh, xw);
+        pass_newton<S, false>(&sh, src, xw);
         if (tracer(a)) tr_add(a, 2, globaltimer() - t0);
         if (!grid_reduce<NV>(sh.blk, sh.tot, a, ep, 4)) return;
         ++my_evals;
@@ -868,7 +954,6 @@ __global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
           if (tracer(a)) tr_add(a, 3, globaltimer() - t0);
         }
         __syncthreads();
-        if (sh.done) break;
       }
       if (threadIdx.x == 0) {
         newton_max = max(newton_max, last_newton);
@@ -913,14 +998,17 @@ __global__ void __launch_bounds__(WP_THREADS, WP_BPS) k_wprox(WpArgs args) {
 
 template <int S, int TV>
 cudaError_t launch_wprox(mqnpm_handle* h, WpArgs& a) {
+  const size_t dyn = (size_t)wp_slots(S) * WP_THREADS * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(k_wprox<S, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wprox<S, TV>, WP_THREADS, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wprox<S, TV>, WP_THREADS, dyn);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   const int blocks = h->wp.nsm * std::min(per_sm, WP_BPS);
   if (blocks > WP_GS * WP_MAXG) return cudaErrorInvalidConfiguration;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((void*)k_wprox<S, TV>, dim3(blocks), dim3(WP_THREADS), args, 0, h->stream);
+  return cudaLaunchCooperativeKernel((void*)k_wprox<S, TV>, dim3(blocks), dim3(WP_THREADS), args, dyn, h->stream);
 }
 
 #ifdef MQ_WP_HIGH
