@@ -11,6 +11,24 @@
 #pragma once
 #include "common.cuh"
 
+// Complex sum and difference as one two-lane FP32 instruction each
+// (add/sub.rn.f32x2: the same round-to-nearest result per lane as two scalar
+// operations), for the butterflies whose operands are whole complex values.
+MQ_D float2 padd(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+MQ_D float2 psub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 // Multiply by W_R^J (forward, W = exp(-2 pi i / R)) or W_R^{-J} (inverse).
 template <long J, long R, bool INV>
 MQ_D float2 tw_mul(float2 a) {
@@ -50,8 +68,8 @@ MQ_D void dft(float2 (&a)[R]) {
     a[1] = a[0];
   } else if constexpr (R == 2) {
     float2 t = a[0];
-    a[0] = cadd(t, a[1]);
-    a[1] = csub(t, a[1]);
+    a[0] = padd(t, a[1]);
+    a[1] = psub(t, a[1]);
   } else if constexpr (R == 4 && NZ == 1) {
     a[1] = a[0];
     a[2] = a[0];
@@ -60,8 +78,8 @@ MQ_D void dft(float2 (&a)[R]) {
     // inputs (a0, a1, 0, 0): y_k = a0 + W^k a1
     const float2 a0 = a[0], a1 = a[1];
     const float2 r = INV ? make_float2(-a1.y, a1.x) : make_float2(a1.y, -a1.x);   // -i a1 (fwd)
-    a[0] = cadd(a0, a1);
-    a[2] = csub(a0, a1);
+    a[0] = padd(a0, a1);
+    a[2] = psub(a0, a1);
     a[1] = cadd(a0, r);
     a[3] = csub(a0, r);
   } else if constexpr (R == 3) {
@@ -75,12 +93,12 @@ MQ_D void dft(float2 (&a)[R]) {
     a[1] = cadd(m, rot);
     a[2] = csub(m, rot);
   } else if constexpr (R == 4) {
-    float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-    float2 s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
+    float2 s02 = padd(a[0], a[2]), d02 = psub(a[0], a[2]);
+    float2 s13 = padd(a[1], a[3]), d13 = psub(a[1], a[3]);
     // -i*d13 (fwd)
     float2 r = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-    a[0] = cadd(s02, s13);
-    a[2] = csub(s02, s13);
+    a[0] = padd(s02, s13);
+    a[2] = psub(s02, s13);
     a[1] = cadd(d02, r);
     a[3] = csub(d02, r);
   } else if constexpr (R == 5) {
