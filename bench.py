@@ -194,6 +194,13 @@ def adjoint_start(w, args=None):
     return forced or ADJOINT_START.get(w.name, "b")
 
 
+def forward_start(args=None):
+    """Start of the warm-started LS forward solves (mqnpm_config.forward_start):
+    the stored field refined by one fixed-point step unless forced."""
+    forced = getattr(args, "forward_start", None) if args is not None else None
+    return forced or "refine"
+
+
 def subset_of(w):
     so = np.zeros(w.L, dtype=np.int32)
     for s, idx in enumerate(synth.subsets(w)):
@@ -201,7 +208,7 @@ def subset_of(w):
     return so
 
 
-def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False, adj="b"):
+def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False, adj="b", fwd="refine"):
     """Synthetic measurements and alpha_s, produced with the library itself."""
     kd = synth.illumination_dirs(w)
     so = subset_of(w)
@@ -224,7 +231,7 @@ def make_problem(w, dev, torch, binding, seed_shift=0, tile=-1, direct=False, ad
     alpha = [setup.lipschitz(list(s), w.S / w.L, start, iters=10) for s in subs]
     setup.close()
     h = binding.MQNPM(w.n, kd, so, alpha, warm_start=True, tile=tile, direct_launches=direct, adjoint_start=adj,
-                      **common)
+                      forward_start=fwd, **common)
     h.set_measurements(y.reshape(-1))
     return h, y, alpha, kd, so, subs
 
@@ -815,7 +822,7 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
     repeat through host buffers and the per-kernel figures of one workload."""
     h, y, alpha, kd, so, subs = make_problem(w, dev, torch, binding, tile=args.tile,
                                              direct=getattr(args, "direct_launches", False),
-                                             adj=adjoint_start(w, args))
+                                             adj=adjoint_start(w, args), fwd=forward_start(args))
     x = torch.zeros(w.N, dtype=torch.float32, device=dev)
     shard = bool(getattr(args, "shard", False))
     if shard:
@@ -934,8 +941,10 @@ def run_workload(w, args, torch, binding, dev, local, world, rank, dist, full=Tr
                    "S": w.S, "model": "lippmann-schwinger" if w.model == "ls" else "first-born",
                    "krylov_tol": w.krylov_tol if w.model == "ls" else None, "dual_iters": w.dual_iters,
                    "tv": w.tv, "phase": "k > S (SR1-weighted)", "l2": "inputs larger than L2",
-                   "krylov_start": "forward solves warm-started from each illumination's last field; adjoint "
-                                   "solves from %s" % ("b = G^H S^T r" if adjoint_start(w, args) == "b" else "0")
+                   "krylov_start": "forward solves warm-started from each illumination's last field%s; "
+                                   "adjoint solves from %s" % (
+                                       ", refined by one fixed-point step" if forward_start(args) == "refine" else "",
+                                       "b = G^H S^T r" if adjoint_start(w, args) == "b" else "0")
                    if w.model == "ls" else None,
                    "parallelism": ("illumination-sharded x%d (one all-reduce per step)" % world) if shard
                    else ("replicas" if world > 1 else "single-gpu")},
@@ -1016,6 +1025,8 @@ def main():
                     help="write one JSON line per timed MQNPM iteration (step info) to this file")
     ap.add_argument("--adjoint-start", choices=["b", "zero"], default=None,
                     help="start of the LS adjoint solves (default: the workload's, b unless listed in ADJOINT_START)")
+    ap.add_argument("--forward-start", choices=["refine", "stored"], default=None,
+                    help="start of the warm-started LS forward solves (default: refine, one fixed-point step)")
     ap.add_argument("--tile", type=int, default=-1,
                     help="launch-shape tile of the Green's passes (-1: autotuned when a handle is created)")
     ap.add_argument("--serve-uneven", action="store_true",

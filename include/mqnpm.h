@@ -153,6 +153,12 @@ typedef struct mqnpm_config {
                               r_0 = G^H(x b); at contrasts up to about 0.04 it
                               saves one BiCGSTAB iteration, two applies);
                               1 starts at z_0 = 0 (r_0 = b)                    */
+  int forward_start;       /* LS forward solves started from a stored field u_s
+                              (warm_start): 0 refines it by one fixed-point
+                              step u_1 = u_s + r_0 before BiCGSTAB (one more
+                              Green's apply, r_1 = G(x r_0); a solve whose r_1
+                              meets the tolerance then takes no BiCGSTAB
+                              iteration); 1 starts BiCGSTAB at u_s          */
 } mqnpm_config;
 
 typedef struct mqnpm_handle mqnpm_handle;

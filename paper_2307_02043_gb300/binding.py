@@ -55,7 +55,7 @@ class Config(ctypes.Structure):
         ("green_hat", ctypes.POINTER(ctypes.c_float)), ("tile", ctypes.c_int),
         ("det_distance", ctypes.c_double), ("det_na", ctypes.c_double), ("guard_bytes", ctypes.c_size_t),
         ("barrier_wait_cycles", ctypes.c_longlong), ("green_kernel", ctypes.c_int),
-        ("adjoint_start", ctypes.c_int),
+        ("adjoint_start", ctypes.c_int), ("forward_start", ctypes.c_int),
     ]
 
 
@@ -193,7 +193,8 @@ class MQNPM:
                  hbm_budget_bytes: int = 0, device: int = 0, warm_start: bool = False,
                  direct_launches: bool = False, green_hat: Optional[np.ndarray] = None, tile: int = -1,
                  det_distance: float = 0.0, det_na: float = 0.0, guard_bytes: int = 0,
-                 barrier_wait_cycles: int = 0, green_kernel: str = "sampled", adjoint_start: str = "b"):
+                 barrier_wait_cycles: int = 0, green_kernel: str = "sampled", adjoint_start: str = "b",
+                 forward_start: str = "refine"):
         self.lib = load()
         if np.ndim(n) == 0:
             self.shape = (int(n),) * 3
@@ -251,6 +252,7 @@ class MQNPM:
         cfg.barrier_wait_cycles = int(barrier_wait_cycles)
         cfg.green_kernel = KERNEL[green_kernel]
         cfg.adjoint_start = {"b": 0, "zero": 1}[adjoint_start]
+        cfg.forward_start = {"refine": 0, "stored": 1}[forward_start]
         if green_hat is not None:
             gh = np.ascontiguousarray(np.asarray(green_hat, dtype=np.complex64))
             if gh.size != (nx + 1) * (ny + 1) * (nz + 1):

@@ -244,7 +244,7 @@ int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle*
       !(cfg->det_na >= 0.0 && std::isfinite(cfg->det_na)) || !std::isfinite(cfg->det_distance) ||
       cfg->barrier_wait_cycles < 0 ||
       (cfg->green_kernel != MQNPM_KERNEL_SAMPLED && cfg->green_kernel != MQNPM_KERNEL_TRUNCATED) ||
-      (cfg->adjoint_start != 0 && cfg->adjoint_start != 1)) {
+      (cfg->adjoint_start != 0 && cfg->adjoint_start != 1) || (cfg->forward_start != 0 && cfg->forward_start != 1)) {
     fprintf(stderr, "mqnpm_create: invalid configuration\n");
     delete h;
     return MQNPM_ERR_INVALID_ARG;
@@ -291,6 +291,7 @@ int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle*
   h->stream = static_cast<cudaStream_t>(cfg->stream);
   h->warm_start = cfg->warm_start != 0;
   h->adjoint_from_b = cfg->adjoint_start == 0;
+  h->forward_refine = cfg->forward_start == 0;
   h->direct_launches = cfg->direct_launches != 0;
   h->budget = cfg->hbm_budget_bytes;
   h->guard = (cfg->guard_bytes + 255) / 256 * 256;

@@ -56,9 +56,13 @@ __global__ void k_set_bnorm(KState* st, const double* part, int nctas) {
 
 // Slot state of a solve whose first residual r_0 has its partials in part.
 // bnorm2_fwd > 0: ||b||^2 for every slot; == 0: ||r_0||^2 (a start at 0);
-// < 0: the value k_set_bnorm left in the slot state.
-__global__ void k_fin_init(KState* st, const double* part, int nctas, double tol2, double bnorm2_fwd) {
+// < 0: the value k_set_bnorm (or an earlier k_fin_init) left in the slot
+// state.  keep_inactive: slots already stopped keep their state (their
+// partials were not recomputed).
+__global__ void k_fin_init(KState* st, const double* part, int nctas, double tol2, double bnorm2_fwd,
+                           int keep_inactive) {
   const int b = blockIdx.x;
+  if (keep_inactive && !st[b].active) return;
   double s[1];
   sum_partials<1>(part, b, nctas, s);
   if (threadIdx.x == 0) {
@@ -240,6 +244,14 @@ __global__ void k_init_u_warm(float2* u, float2* const* fwarm, const float2* tab
   const float2* src = fwarm[b];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     u[(size_t)b * N + i] = src ? src[i] : incident_at(tab, l, n, i);
+}
+
+// u += r on the slots still iterating (the fixed-point step u_1 = u_0 + r_0).
+__global__ void k_add_residual(float2* u, const float2* __restrict__ r, const KState* st, size_t N) {
+  const int b = blockIdx.y;
+  if (!st[b].active) return;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    u[(size_t)b * N + i] = cadd(u[(size_t)b * N + i], r[(size_t)b * N + i]);
 }
 
 // Keep each slot's converged field for its illumination's next solve
@@ -619,7 +631,12 @@ int collect_states(mqnpm_handle* h, int nb, int* iters_out, int stride, int offs
 // Forward LS solve for nb slots: u = (I - G X)^{-1} u_in.  The staged tables
 // of the chunk give each slot its start field (fwarm) and the place its
 // converged field is kept (fstore); warm selects the warm-start form of the
-// first residual.  x == NULL: each slot's own contrast (xslot).
+// first residual.  forward_refine: a warm start u_0 is refined by one
+// fixed-point step u_1 = u_0 + r_0 before BiCGSTAB (one more apply; r_1 =
+// G(x r_0) is smaller than r_0 by about the scattering strength, so a stored
+// field from a nearby contrast then often meets the tolerance without a
+// BiCGSTAB iteration).  The stopping rule is ||r|| <= tol ||u_in|| either
+// way.  x == NULL: each slot's own contrast (xslot).
 static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool store, int* iters, int stride,
                       int offset) {
   Workspace& w = h->w;
@@ -648,9 +665,27 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool s
   c.ea.out = w.r;
   c.ea.out2 = w.rhat;
   CK(glaunch(h, c, s));
-  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, (double)N);
+  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, (double)N, 0);
   CK(cudaGetLastError());
   h->launches += 2;   // init, fin_init
+  if (warm && h->forward_refine) {
+    // one fixed-point step on the slots still above the tolerance:
+    // u_1 = u_0 + r_0, r_1 = u_in - (I - G X) u_1 = G(x r_0), in place in r
+    k_add_residual<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, w.r, w.st, N);
+    GreenCall c1 = base_call(h, nb, false);
+    c1.st = w.st;                        // slots already converged are skipped
+    c1.pro = PRO_CONTRAST;
+    c1.pa.x = x;
+    c1.pa.xs = x ? nullptr : w.xslot;
+    c1.pa.q = w.r;
+    c1.epi = EPI_INIT;
+    c1.ea.out = w.r;
+    c1.ea.out2 = w.rhat;
+    CK(glaunch(h, c1, s));
+    k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, -1.0, 1);
+    CK(cudaGetLastError());
+    h->launches += 2;   // add_residual, fin_init
+  }
   int rc = krylov_iterate(h, nb, x, w.u, false);
   if (rc != MQNPM_OK) return rc;
   if (store) {
@@ -684,7 +719,7 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
     c.ea.out = w.r;
     c.ea.out2 = w.rhat;
     CK(glaunch(h, c, s));
-    k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, 0.0);
+    k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, 0.0, 0);
     CK(cudaGetLastError());
     h->launches += 1;
     const int rc = krylov_iterate(h, nb, x, w.zs, true);
@@ -705,7 +740,7 @@ static int adjoint_ls(mqnpm_handle* h, int nb, const float* x, int* iters, int s
   c0.ea.out = w.r;
   c0.ea.out2 = w.rhat;
   CK(glaunch(h, c0, s));
-  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, -1.0);
+  k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, -1.0, 0);
   CK(cudaGetLastError());
   h->launches += 2;
   int rc = krylov_iterate(h, nb, x, w.zs, true);

@@ -199,6 +199,28 @@ def test_both_adjoint_starts_match_oracle(start, n):
     h.close()
 
 
+@pytest.mark.parametrize("start", ["refine", "stored"])
+@pytest.mark.parametrize("n", [24, 32])
+def test_both_forward_starts_match_oracle(start, n):
+    """Warm-started LS forward solves from the stored field as is or refined
+    by one fixed-point step (mqnpm_config.forward_start): a first gradient at
+    x1 stores every illumination's field, a second one at a nearby x2 starts
+    from them; both gradients match the oracle (cold starts) to the solver
+    tolerance (1e-7 here: a refined start often stops just below it, where
+    BiCGSTAB's last iteration usually overshoots)."""
+    w, kd, xt, om, ys, subs, so = problem(n, "ls", L=6, batch=3)
+    h = make_handle(n, kd, so, [1.0] * w.S, krylov_tol=1e-7, max_batch=3, warm_start=True, forward_start=start)
+    h.set_measurements(c64(ys).reshape(-1))
+    illum = [0, 2, 4]
+    scale = w.S / w.L
+    for x in (0.7 * xt, 0.72 * xt):
+        g, loss, its = h.grad_batch(f32(x).reshape(-1), illum, scale)
+        lo, go = om.batch_loss_grad(x, illum, ys, scale)
+        assert rel(g.cpu().numpy().reshape(go.shape), go) < 1e-4, (start, its)
+        assert abs(loss - lo) <= 1e-5 * abs(lo)
+    h.close()
+
+
 def test_physical_units_strong_scattering_matches_oracle():
     """The paper's simulated set-up in physical units (50 nm voxels, 406 nm,
     medium index 1.333, contrast up to (1.43/1.333)^2 - 1 = 0.15) on a 32^3

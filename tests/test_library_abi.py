@@ -92,7 +92,8 @@ def _config(**kw):
     ("gamma", 1.5), ("h", 0.0), ("kb", -1.0), ("lam", -1.0), ("box_lo", 1.0), ("step", 0.0),
     ("krylov_tol", 0.0), ("krylov_maxit", 0), ("dual_iters", -1), ("model", 7), ("tv", 5),
     ("strategy", 3), ("tile", -2), ("tile", 32), ("det_na", -0.5), ("det_na", float("inf")),
-    ("det_distance", float("nan")), ("barrier_wait_cycles", -1), ("green_kernel", 2), ("green_kernel", -1), ("adjoint_start", 2), ("adjoint_start", -1)])
+    ("det_distance", float("nan")), ("barrier_wait_cycles", -1), ("green_kernel", 2), ("green_kernel", -1), ("adjoint_start", 2), ("adjoint_start", -1),
+    ("forward_start", 2), ("forward_start", -1)])
 def test_create_rejects_invalid_configurations(field, value):
     """Host-side validation of mqnpm_create runs before any CUDA call: every
     out-of-range option returns MQNPM_ERR_INVALID_ARG and no handle."""
