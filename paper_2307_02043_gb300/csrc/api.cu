@@ -291,7 +291,7 @@ int create_handle(const mqnpm_config* cfg, const float2* khat_src, mqnpm_handle*
   h->stream = static_cast<cudaStream_t>(cfg->stream);
   h->warm_start = cfg->warm_start != 0;
   h->adjoint_from_b = cfg->adjoint_start == 0;
-  h->forward_refine = cfg->forward_start == 0;
+  h->forward_refine_steps = cfg->forward_start == 0 ? 1 : 0;
   h->direct_launches = cfg->direct_launches != 0;
   h->budget = cfg->hbm_budget_bytes;
   h->guard = (cfg->guard_bytes + 255) / 256 * 256;

@@ -66,7 +66,7 @@ int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, s
     if (m->nx != m0->nx || m->ny != m0->ny || m->nz != m0->nz || m->h != m0->h || m->kb != m0->kb || m->device != m0->device || m->tile != m0->tile ||
         m->green_kernel != m0->green_kernel || m->krylov_tol != m0->krylov_tol ||
         m->krylov_maxit != m0->krylov_maxit || m->direct_launches != m0->direct_launches ||
-        m->adjoint_from_b != m0->adjoint_from_b || m->forward_refine != m0->forward_refine)
+        m->adjoint_from_b != m0->adjoint_from_b || m->forward_refine_steps != m0->forward_refine_steps)
       return MQNPM_ERR_INVALID_ARG;
     if (m->model != MQNPM_MODEL_LS || m->remote) return MQNPM_ERR_UNSUPPORTED;
   }
@@ -112,7 +112,7 @@ int mqnpm_group_create(mqnpm_handle* const* members, int count, int max_slots, s
   c.tile = m0->tile;
   c.green_kernel = m0->green_kernel;
   c.adjoint_start = m0->adjoint_from_b ? 0 : 1;
-  c.forward_start = m0->forward_refine ? 0 : 1;
+  c.forward_start = m0->forward_refine_steps > 0 ? 0 : 1;
   // the engine takes the members' spectrum (it may come from a caller's green_hat)
   int rc = create_handle(&c, m0->khat, &g->engine);
   if (rc != MQNPM_OK) {

@@ -193,7 +193,7 @@ struct mqnpm_handle {
   // Krylov warm start: last forward field per illumination
   bool warm_start = false;
   bool adjoint_from_b = true;                // adjoint solves start at z_0 = b (else at 0)
-  bool forward_refine = true;                // warm forward starts take one fixed-point step first
+  int forward_refine_steps = 1;              // fixed-point steps on a warm forward start before BiCGSTAB
   float2* ufield = nullptr;      // [L][N]
   std::vector<int> have_field;   // [L]
   // outer-loop state (Algorithm 4.1)

@@ -631,11 +631,11 @@ int collect_states(mqnpm_handle* h, int nb, int* iters_out, int stride, int offs
 // Forward LS solve for nb slots: u = (I - G X)^{-1} u_in.  The staged tables
 // of the chunk give each slot its start field (fwarm) and the place its
 // converged field is kept (fstore); warm selects the warm-start form of the
-// first residual.  forward_refine: a warm start u_0 is refined by one
-// fixed-point step u_1 = u_0 + r_0 before BiCGSTAB (one more apply; r_1 =
-// G(x r_0) is smaller than r_0 by about the scattering strength, so a stored
-// field from a nearby contrast then often meets the tolerance without a
-// BiCGSTAB iteration).  The stopping rule is ||r|| <= tol ||u_in|| either
+// first residual.  forward_refine_steps (1 by default): a warm start u_0 is
+// refined by fixed-point steps u_1 = u_0 + r_0 before BiCGSTAB (one more
+// apply each; r_1 = G(x r_0) is smaller than r_0 by about the scattering
+// strength, so a stored field from a nearby contrast then needs fewer
+// BiCGSTAB iterations).  The stopping rule is ||r|| <= tol ||u_in|| either
 // way.  x == NULL: each slot's own contrast (xslot).
 static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool store, int* iters, int stride,
                       int offset) {
@@ -668,8 +668,8 @@ static int forward_ls(mqnpm_handle* h, int nb, const float* x, bool warm, bool s
   k_fin_init<<<nb, 256, 0, s>>>(w.st, w.part5, w.ctas_row, h->krylov_tol * h->krylov_tol, (double)N, 0);
   CK(cudaGetLastError());
   h->launches += 2;   // init, fin_init
-  if (warm && h->forward_refine) {
-    // one fixed-point step on the slots still above the tolerance:
+  for (int step = 0; warm && step < h->forward_refine_steps; ++step) {
+    // a fixed-point step on the slots still above the tolerance:
     // u_1 = u_0 + r_0, r_1 = u_in - (I - G X) u_1 = G(x r_0), in place in r
     k_add_residual<<<dim3(w.ctas_vec, nb), 256, 0, s>>>(w.u, w.r, w.st, N);
     GreenCall c1 = base_call(h, nb, false);
