@@ -112,6 +112,36 @@ def test_ls_bicgstab_equals_dense_lu():
         assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) < 1e-10
 
 
+def test_fixed_point_step_residual_and_contraction():
+    """The refined warm start of the forward solve: for any u0 with residual
+    r0 = u_in - (I - G X) u0, the step u1 = u0 + r0 has residual exactly
+    G(x r0), checked against the dense operator (n = 5).  Repeated steps
+    multiply the error by G X (e_k = (G X)^k e_0), so at a weak contrast,
+    where the spectral radius of G X is below 1, the iterates approach the
+    dense LU solution at that rate."""
+    n = 5
+    x, m = small_problem(n, contrast=0.05)
+    Gd = direct_green_matrix(n, KB)
+    GX = Gd * x.reshape(-1)[None, :]
+    A = np.eye(n ** 3) - GX
+    rho = np.max(np.abs(np.linalg.eigvals(GX)))
+    assert rho < 1.0
+    rng = np.random.default_rng(3)
+    uin = m.u_in(0).reshape(-1)
+    ref = np.linalg.solve(A, uin)
+    u = ref + 1e-2 * (rng.standard_normal(uin.shape) + 1j * rng.standard_normal(uin.shape))
+    e0 = np.linalg.norm(u - ref)
+    kappa = np.linalg.cond(np.linalg.eig(GX)[1])   # ||(GX)^k|| <= kappa rho^k
+    r = uin - A @ u
+    for k in range(1, 7):
+        u1 = u + r
+        r1 = uin - A @ u1
+        assert np.linalg.norm(r1 - GX @ r) <= 1e-12 * np.linalg.norm(uin)
+        u, r = u1, r1
+        # the error e_k = ref - u_k = (G X)^k e_0
+        assert np.linalg.norm(u - ref) <= kappa * rho ** k * e0 * (1 + 1e-9) + 1e-13
+
+
 def test_born_limit_first_order():
     n = 6
     x, m = small_problem(n, contrast=1.0)
