@@ -177,12 +177,13 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
   // takes the unfused passes on that side.  Their time counts as the x pass's
   // (events 1 and 2, 3 and 4 coincide).
   const bool fuse = (c.tile & MQ_TILE_FUSED) && green_fused_supported(c.nx, c.ny);
-  const bool ffwd = fuse && !c.plane, finv = fuse && !c.outplane;
+  const bool ffwd = fuse && !c.plane && !c.after_pass1, finv = fuse && !c.outplane;
   if ((e = rec(0)) != cudaSuccess) return e;
   if (ffwd) {
     if ((e = fused_any(c, false, s)) != cudaSuccess || (e = rec(1)) != cudaSuccess || (e = rec(2)) != cudaSuccess)
       return e;
   } else if ((e = pass1_any(c, s)) != cudaSuccess || (e = rec(1)) != cudaSuccess ||
+             (c.after_pass1 && (e = c.after_pass1(c.after_pass1_ctx, s)) != cudaSuccess) ||
              (e = passy_any(c, false, s)) != cudaSuccess || (e = rec(2)) != cudaSuccess) {
     return e;
   }
@@ -194,7 +195,7 @@ cudaError_t green_launch(const GreenCall& c, cudaStream_t s) {
              (e = pass5_any(c, s)) != cudaSuccess || (e = rec(5)) != cudaSuccess) {
     return e;
   }
-  if (c.launches) *c.launches += 1 + (ffwd ? 1 : 2) + (finv ? 1 : 2);
+  if (c.launches) *c.launches += 1 + (ffwd ? 1 : 2) + (finv ? 1 : 2) + (c.after_pass1 ? 1 : 0);
   return e;
 }
 

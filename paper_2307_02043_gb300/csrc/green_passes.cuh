@@ -113,7 +113,9 @@ MQ_D void write_partials(const Parts<K>& p, double* partials, int b, int cta, in
   }
 }
 
-MQ_D bool slot_active(const KState* st, int b) { return st == nullptr || st[b].active != 0; }
+// active == 2: the slot met the tolerance at the half step of its iteration
+// and skips the rest of that iteration's second apply.
+MQ_D bool slot_active(const KState* st, int b) { return st == nullptr || st[b].active == 1; }
 
 // Twiddles W_P^(r q) as an R2 x R1 table in shared memory (r < R2, q < R1): a
 // thread whose first-stage index n2 is fixed reads row n2 at compile-time
@@ -391,7 +393,7 @@ k_pass3(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ T2, const
   const uint32_t tile_bytes = (uint32_t)SM::in_bytes(n);
   unsigned long long act = 0ull;   // active slots as a bit mask (nb <= 64)
   for (int q = 0; q < nb; ++q)
-    if (st == nullptr || st[q].active != 0) act |= 1ull << q;
+    if (slot_active(st, q)) act |= 1ull << q;
   if (act == 0ull) return;
   int b = __ffsll((long long)act) - 1;
   if (!PLANE && threadIdx.x == 0) {

@@ -33,6 +33,11 @@ struct GreenCall {
   int* err = nullptr;            // device flag raised when a bounded wait gives up
   bool plane = false;            // input nonzero on the last z-plane only (the lift S^T r; G^H only)
   bool outplane = false;         // only the last z-plane of the output is needed (first-Born data; G only)
+  // optional: launched right after pass 1 on the same stream; a slot it marks
+  // active = 2 skips the remaining passes (the fused x/y passes are not used
+  // on the forward side when it is set)
+  cudaError_t (*after_pass1)(void* ctx, cudaStream_t s) = nullptr;
+  void* after_pass1_ctx = nullptr;
   int tile = 0;                  // launch shapes: alternative shape of bit 0 the x passes, bit 1 the
                                  // y passes, bit 2 the z pass; bit 3 two z-pass exchange buffers;
                                  // bit 4 the fused x/y passes (square planes, P = 128 or 256)

@@ -111,9 +111,29 @@ __global__ void k_fin_alpha(KState* st, const double* part5, int nctas) {
   }
 }
 
+// The half step of a BiCGSTAB iteration, between pass 1 and pass 2 of its
+// second apply: a slot whose s = r - alpha v already meets the tolerance
+// takes x += alpha p, r = s (omega = 0, conv_pending) and is marked active = 2,
+// so the remaining passes of that apply skip it; k_fin_rho retires it.
+__global__ void k_fin_s(KState* st, const double* part1, int nctas) {
+  const int b = blockIdx.x;
+  if (st[b].active != 1) return;
+  double s1[1];
+  sum_partials<1>(part1, b, nctas, s1);
+  if (threadIdx.x == 0) {
+    KState& k = st[b];
+    if (s1[0] <= k.tol2 * k.bnorm2) {
+      k.conv_pending = 1;
+      k.omega_re = 0.0;
+      k.omega_im = 0.0;
+      k.active = 2;
+    }
+  }
+}
+
 __global__ void k_fin_omega(KState* st, const double* part1, const double* part5, int nctas) {
   const int b = blockIdx.x;
-  if (!st[b].active) return;
+  if (st[b].active != 1) return;   // 2: retired at the half step, omega = 0 already
   double s1[1], s5[3];
   sum_partials<1>(part1, b, nctas, s1);
   sum_partials<3>(part5, b, nctas, s5);
@@ -147,15 +167,16 @@ __global__ void k_update(const KState* __restrict__ st, float2* __restrict__ xs,
   const float2 omega = make_float2((float)st[b].omega_re, (float)st[b].omega_im);
   const float2 nomega = make_float2(-omega.x, -omega.y);
   const size_t off = (size_t)b * N;
+  const bool half = st[b].conv_pending != 0;   // converged at s: x += alpha p, r = s (t not read)
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     const size_t j = off + i;
     const float2 s = sv[j];
     float2 x = xs[j];
     x = caxpy(alpha, p[j], x);
-    x = caxpy(omega, s, x);
+    if (!half) x = caxpy(omega, s, x);
     xs[j] = x;
-    const float2 rn = caxpy(nomega, tv[j], s);
+    const float2 rn = half ? s : caxpy(nomega, tv[j], s);
     r[j] = rn;
     const float2 d = cmulc(rhat[j], rn);
     a0 += d.x;
@@ -413,6 +434,17 @@ GreenCall base_call(mqnpm_handle* h, int nb, bool adjoint) {
   return c;
 }
 
+struct FinSArgs {
+  KState* st;
+  const double* part1;
+  int nctas, nb;
+};
+cudaError_t fin_s_launch(void* ctx, cudaStream_t s) {
+  const FinSArgs* a = static_cast<const FinSArgs*>(ctx);
+  k_fin_s<<<a->nb, 256, 0, s>>>(a->st, a->part1, a->nctas);
+  return cudaGetLastError();
+}
+
 // One BiCGSTAB iteration of the nb slots on stream s; evA and evB receive the
 // pass boundaries of its two Green's applies (or are null).
 int iteration_body(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adjoint, cudaStream_t s,
@@ -438,6 +470,9 @@ int iteration_body(mqnpm_handle* h, int nb, const float* x, float2* xs, bool adj
   c.epi = EPI_T;
   c.ea.out = w.t;
   c.ea.a = w.s;
+  FinSArgs fs{w.st, w.part1, w.ctas_row, nb};
+  c.after_pass1 = fin_s_launch;        // ||s|| from pass 1: retire converged slots before pass 2
+  c.after_pass1_ctx = &fs;
   CK(glaunch_ev(h, c, s, evB));
   k_fin_omega<<<nb, 256, 0, s>>>(w.st, w.part1, w.part5, w.ctas_row);
   k_update<<<dim3(w.ctas_upd, nb), 256, 0, s>>>(w.st, xs, w.r, w.p, w.s, w.t, w.rhat, N, w.partu);

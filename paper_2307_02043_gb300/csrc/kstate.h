@@ -11,7 +11,8 @@ struct KState {
   double bnorm2;                // ||b||^2
   double rnorm2;                // ||r||^2 (recursive residual)
   double tol2;                  // tol^2
-  int active;                   // 1 while iterating
+  int active;                   // 1 while iterating; 2 from the half step that met the
+                                // tolerance to the end of that iteration
   int iters;
   int status;                   // KSTATUS_*
   int conv_pending;             // ||s|| met the tolerance in this iteration
